@@ -1,0 +1,434 @@
+#!/usr/bin/env python3
+"""Benchmark of the differentiable Gaussian-splatting hot path on GB300.
+
+One step = one pass of the whole path over one synthetic frame: projection,
+binning + tile/depth sort, compositing, the L2-loss gradient, compositing
+backward and projection backward -- for the 1,000,000-Gaussian 1920x1080
+workload (64-component mixture, log-scales N(-4.5, 1), opacity
+sigmoid(N(-1, 2)), seed 0; see paper_2312_02121_gb300/workloads.py).
+
+Prints ONE JSON line.  ``value`` is fwd+bwd Mpixel/s over all ranks with the
+inputs resident in HBM (CUDA events on the launching stream, L2 flushed by a
+256 MiB write before every timed step, outside the step's events); ``e2e`` is
+the same metric through the public autograd API with the parameters and the
+target copied host->device from pinned memory every step and the loss read
+back.  ``--impl reference`` times the FP64 CPU oracle instead (the reference
+arm of this comparison; it has no published GPU numbers).
+
+Multi-GPU (torchrun): every rank renders its own independent frame (seed =
+rank), no data-path collective; timings are max-reduced over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Mpixel/s at 1M Gaussians 1080p; batched vs per-view launches"
+UNIT = "Mpixel/s"
+WORKLOAD = "fwdbwd_1m_1080p"
+SMS = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target duration of the oracle sample")
+    ap.add_argument("--profile", action="store_true",
+                    help="run warmup + steps untimed and exit (a fixed command line for ncu)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu_index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), max=float(f[2]), power=float(f[3]), hw=f[5], hwt=f[6], swt=f[7],
+                                 cap=f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                              ("cap", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["max"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(r["power"] for r in rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def tile_sample(cam, n_tiles: int, seed: int = 0):
+    """Every pixel of n_tiles seeded random 16x16 tiles (linear pixel ids)."""
+    TX, TY = (cam.width + 15) // 16, (cam.height + 15) // 16
+    rng = np.random.default_rng(seed)
+    tiles = rng.choice(TX * TY, min(n_tiles, TX * TY), replace=False)
+    pix = []
+    for t in tiles:
+        ty, tx = divmod(int(t), TX)
+        ys = np.arange(ty * 16, min(ty * 16 + 16, cam.height))
+        xs = np.arange(tx * 16, min(tx * 16 + 16, cam.width))
+        pix.append((ys[:, None] * cam.width + xs[None, :]).ravel())
+    return np.sort(np.concatenate(pix))
+
+
+def oracle_step(oracle, w, pix):
+    """The oracle's fwd+bwd of one view restricted to the sampled pixels."""
+    cam, sc = w.views[0].camera, w.scenes[0]
+    proj = oracle.project(cam, sc.means, sc.quats, sc.scales, w.eps2d)
+    fwd = oracle.rasterize(proj, sc.opacities, sc.colors, cam.width, cam.height, pixels=pix)
+    tgt = w.targets[0].reshape(-1, 3)[pix]
+    G = 2.0 * (fwd["rgb"] - tgt) / (cam.pixels * 3)
+    g2 = oracle.rasterize_bwd(proj, sc.opacities, sc.colors, cam.width, cam.height, G, pixels=pix)
+    oracle.project_bwd(cam, sc.means, sc.quats, sc.scales, proj["valid"], g2["means2d"], g2["conics"], w.eps2d)
+
+
+def sized_sample(oracle, w, seconds: float):
+    """Tile count whose oracle step takes about ``seconds`` on this host
+    (linear fit of two probes: the fixed projection cost plus a per-tile cost)."""
+    cam = w.views[0].camera
+    TX, TY = (cam.width + 15) // 16, (cam.height + 15) // 16
+    probes = []
+    for n in (16, 64):
+        pix = tile_sample(cam, n)
+        t0 = time.perf_counter()
+        oracle_step(oracle, w, pix)
+        probes.append((n, time.perf_counter() - t0))
+    (n0, t0_), (n1, t1_) = probes
+    per_tile = max((t1_ - t0_) / (n1 - n0), 1e-6)
+    fixed = max(t0_ - per_tile * n0, 0.0)
+    return int(min(TX * TY, max(16, (seconds - fixed) / per_tile)))
+
+
+def cpu_baseline(w, seconds: float):
+    """Times the oracle as it stands on this host's cores over a tile sample
+    sized to take about ``seconds``."""
+    import oracle
+    oracle.build()
+    cam = w.views[0].camera
+    n_tiles = sized_sample(oracle, w, seconds)
+    pix = tile_sample(cam, n_tiles)
+    t0 = time.perf_counter()
+    oracle_step(oracle, w, pix)
+    dt = time.perf_counter() - t0
+    return {"value": len(pix) / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n_tiles} seeded random 16x16 tiles ({len(pix)} pixels, "
+                      f"{100.0 * len(pix) / cam.pixels:.1f}% of the frame): full projection and projection "
+                      f"backward of all {w.scenes[0].n} Gaussians, compositing fwd+bwd of the sampled pixels",
+            "seconds": dt}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2312_02121_gb300 import workloads as wl
+    oracle.build()
+    w = wl.fwdbwd_1m_1080p(seed=0)
+    cam = w.views[0].camera
+    # size each step so the whole run stays within a few minutes
+    per_step = max(2.0, min(8.0, 150.0 / max(args.steps + args.warmup, 1)))
+    n_tiles = sized_sample(oracle, w, per_step)
+    pix = tile_sample(cam, n_tiles)
+    for _ in range(args.warmup):
+        oracle_step(oracle, w, pix)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(oracle, w, pix)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = len(pix) / (ms / 1e3) / 1e6
+    sample = (f"{n_tiles} seeded random 16x16 tiles ({len(pix)} pixels) of the 1920x1080 frame per step; "
+              f"projection and its backward over all {w.scenes[0].n} Gaussians")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "gaussians": w.scenes[0].n, "width": cam.width, "height": cam.height,
+                   "pixels_per_step": int(len(pix))},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2312_02121_gb300 import autograd as ga
+    from paper_2312_02121_gb300 import binding as B
+    from paper_2312_02121_gb300 import pipeline
+    from paper_2312_02121_gb300 import workloads as wl
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    B.load()
+    w = wl.fwdbwd_1m_1080p(seed=rank)
+    cam, sc = w.views[0].camera, w.scenes[0]
+    params = pipeline.Params.from_scene(sc, dev)
+    target = torch.as_tensor(w.targets[0].reshape(-1, 3), device=dev)
+    views = B.Views([cam], [(0, sc.n)], device=dev)
+    pixels = views.pixels
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # exact intersection capacity (the workload is fixed), so steps never sync
+    f0 = pipeline.forward(views, params, w.eps2d, count_contrib=True)
+    K = int(f0.K_total.item())
+    contrib = int(f0.n_contrib.sum().item())
+    cap = K
+    stream = torch.cuda.current_stream()
+    stages = ["project", "bin_and_sort", "rasterize_fwd", "loss_grad", "rasterize_bwd", "project_bwd"]
+
+    def step(ev=None):
+        def mark(i):
+            if ev is not None:
+                ev[i].record(stream)
+        mark(0)
+        pr = pipeline.project(views, params, w.eps2d)
+        mark(1)
+        P, T = views.P, views.T
+        ws = torch.empty(B.gs_bin_and_sort_workspace_size(P, cap, T), dtype=torch.uint8, device=dev)
+        ids = torch.empty(cap, dtype=torch.int32, device=dev)
+        pos = torch.empty(cap, dtype=torch.int32, device=dev)
+        es = torch.empty(P, dtype=torch.int32, device=dev)
+        tr = torch.empty(T, 2, dtype=torch.int32, device=dev)
+        Kd = torch.empty(1, dtype=torch.int32, device=dev)
+        fl = torch.zeros(1, dtype=torch.int32, device=dev)
+        B.gs_bin_and_sort(views, pr["rects"], pr["depths"], pr["touched"], cap, ws, ids, pos, es, tr, Kd, fl)
+        mark(2)
+        rgb = torch.empty(pixels, 3, device=dev)
+        Tf = torch.empty(pixels, device=dev)
+        last = torch.empty(pixels, dtype=torch.int32, device=dev)
+        B.gs_rasterize_fwd(views, pr["means2d"], pr["conics"], params.opacities, params.colors, ids, tr, None, rgb,
+                           Tf, last)
+        mark(3)
+        dL = (rgb - target).mul_(2.0 / rgb.numel())
+        mark(4)
+        g2 = torch.zeros(P, 2, device=dev)
+        gc = torch.zeros(P, 3, device=dev)
+        go = torch.zeros(sc.n, device=dev)
+        gcol = torch.zeros(sc.n, 3, device=dev)
+        wsb = torch.empty(B.gs_rasterize_bwd_workspace_size(cap), dtype=torch.uint8, device=dev)
+        B.gs_rasterize_bwd(views, pr["means2d"], pr["conics"], params.opacities, params.colors, ids, pos, es,
+                           pr["touched"], tr, Kd, cap, None, Tf, last, dL, wsb, g2, gc, go, gcol)
+        mark(5)
+        gm = torch.zeros(sc.n, 3, device=dev)
+        gq = torch.zeros(sc.n, 4, device=dev)
+        gs = torch.zeros(sc.n, 3, device=dev)
+        B.gs_project_bwd(views, params.means, params.quats, params.scales, w.eps2d, pr["touched"], g2, gc, gm, gq, gs)
+        mark(6)
+        return fl
+
+    if args.profile:
+        for _ in range(args.warmup + args.steps):
+            step()
+        torch.cuda.synchronize()
+        return
+    for _ in range(max(args.warmup, 3)):
+        fl = step()
+    torch.cuda.synchronize()
+    assert int(fl.item()) == 0, "intersection capacity overflow"
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(args.steps)]
+    launches0 = B.gs_kernel_launches()
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            step(evs[k])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        barrier()
+    launches = (B.gs_kernel_launches() - launches0) // max(args.steps, 1)
+    stage_ms = {s: 0.0 for s in stages}
+    total_ms = 0.0
+    for ev in evs:
+        for i, s in enumerate(stages):
+            stage_ms[s] += ev[i].elapsed_time(ev[i + 1])
+        total_ms += ev[0].elapsed_time(ev[-1])
+    ms_step = total_ms / args.steps
+    stage_ms = {s: v / args.steps for s, v in stage_ms.items()}
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * pixels / (ms_step / 1e3) / 1e6
+
+    # --- end to end through the public API (host buffers, H2D + D2H inside the timed region)
+    host = {k: torch.as_tensor(getattr(sc, k)).pin_memory() for k in ("means", "quats", "scales", "opacities", "colors")}
+    host_tgt = torch.as_tensor(w.targets[0]).pin_memory()
+    dev_bufs = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    dev_tgt = torch.empty_like(host_tgt, device=dev)
+    h2d = sum(v.numel() * v.element_size() for v in host.values()) + host_tgt.numel() * host_tgt.element_size()
+
+    def e2e_step():
+        for k, v in host.items():
+            dev_bufs[k].copy_(v, non_blocking=True)
+        dev_tgt.copy_(host_tgt, non_blocking=True)
+        leaves = {k: v.detach().requires_grad_(True) for k, v in dev_bufs.items()}
+        img = ga.render(leaves["means"], leaves["quats"], leaves["scales"], leaves["opacities"], leaves["colors"],
+                        [cam], eps2d=w.eps2d, K_capacity=cap)[0]
+        loss = torch.mean((img - dev_tgt) ** 2)
+        loss.backward()
+        return float(loss.item())
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * pixels / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": 4, "ms_per_step": 1e3 * e2e_s}
+
+    if rank != 0:
+        return
+    # --- roofline of the dominant kernel
+    peaks, src = measured_peaks()
+    clocks = clk.summary()
+    dom = max(("rasterize_fwd", "rasterize_bwd", "bin_and_sort", "project", "project_bwd"), key=lambda s: stage_ms[s])
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
+    flops_per_pair = {"rasterize_fwd": 20, "rasterize_bwd": 49}
+    if dom in flops_per_pair:
+        work = contrib * flops_per_pair[dom] / 1e12
+        achieved = work / (stage_ms[dom] / 1e3)
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "peak_source": f"FP32 FMA lanes: {SMS} SMs x {FP32_LANES_PER_SM} x 2 x {sm_mhz:.0f} MHz "
+                               f"(max SM clock, {src})",
+                "work": f"{contrib} composited (pixel, Gaussian) pairs x {flops_per_pair[dom]} flops"}
+    else:
+        hbm = peaks["hbm_gbs"]
+        bytes_ = {"bin_and_sort": K * 164.0, "project": sc.n * 80.0, "project_bwd": sc.n * 88.0}[dom]
+        achieved = bytes_ / (stage_ms[dom] / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": f"hbm_gbs ({src})"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "gaussians": sc.n, "width": cam.width, "height": cam.height,
+                   "views": 1, "intersections": K, "composited_pairs": contrib,
+                   "l2": "flushed (256 MiB write) before every timed step, outside its events",
+                   "per_rank": "independent frame (seed = rank)"},
+        "stage_ms": stage_ms, "wall_s": wall, "gpu_launches": int(launches),
+        "e2e": e2e, "roofline": roof, "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,241 @@
+/*
+ * gsplat103.h -- C ABI of a GB300 (sm_103a) differentiable 3D Gaussian-splatting
+ * rasteriser, after "Mathematical Supplement for the gsplat Library"
+ * (Ye & Kanazawa, arXiv 2312.02121).  The paper exposes each stage of the
+ * forward and backward pass on its own (Sec. 1, Sec. 4); so does this ABI:
+ *
+ *   gs_project        Sec. 2.1, Eq. 1-6, plus the 3-sigma tile box of Sec. 2.2
+ *   gs_bin_and_sort   Sec. 2.2: 16x16 tile binning and per-tile depth order
+ *   gs_rasterize_fwd  Sec. 2.2, Eq. 7: front-to-back compositing
+ *   gs_rasterize_bwd  Sec. 3.1: compositing gradients
+ *   gs_project_bwd    Sec. 3.2, 3.2.1: projection, scale and rotation gradients
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns GS_OK (0) or a GS_ERR_* code; gs_last_error()
+ *    gives a message for the calling thread's last failure.  Argument errors
+ *    are detected on the host before anything is launched.
+ *  - All array arguments are caller-owned DEVICE memory (plain pointers), fp32
+ *    unless stated, C-contiguous, 4-byte aligned at least; float2/short4 data
+ *    (means2d, rects) must be 8-byte aligned and quaternions 16-byte aligned.
+ *    The library never allocates or frees memory and never synchronises: all
+ *    work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and the call returns before it completes.  Results are only
+ *    valid after the caller synchronises the stream.
+ *  - Calls enqueue only kernels and cudaMemsetAsync, so a sequence of them can
+ *    be captured into a CUDA graph when the sizes (P, T_total, K_capacity) are
+ *    fixed.
+ *  - Quaternions are stored (w, x, y, z) and need not be unit length; the
+ *    forward normalises them.  Scales are linear (not log) and opacities are
+ *    in [0, 1]; activations belong to the caller.
+ *  - Thresholds: a Gaussian whose alpha at a pixel is below 1/255 is skipped,
+ *    alpha is clamped to 0.99, and compositing stops before a Gaussian that
+ *    would take the transmittance below 1e-4 (GS_ALPHA_MIN, GS_ALPHA_MAX,
+ *    GS_T_MIN).  The paper fixes none of these values.
+ *
+ * Views and batches
+ * -----------------
+ * One call processes V views at once.  The parameter arrays (means, quats,
+ * scales, opacities, colors) hold the Gaussians of every scene back to back;
+ * view v renders the scene occupying Gaussians [g_begin, g_begin + g_count)
+ * through its camera.  Its projected entries ("projections", one per
+ * Gaussian of its scene) occupy [proj_offset, proj_offset + g_count) of the
+ * per-projection arrays, its tiles the global tile ids
+ * [tile_offset, tile_offset + tiles_x * tiles_y), and its pixels
+ * [pixel_offset, pixel_offset + width * height) of the packed image buffers
+ * (row-major inside a view).  A single view is a batch of one with all
+ * offsets 0.  gs_views_layout() fills the offsets and tile counts on a host
+ * copy; the `views` argument of the other entry points is a device copy of
+ * that array (kernels read it), with views in increasing offset order.
+ */
+#ifndef GSPLAT103_H
+#define GSPLAT103_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_OK 0
+#define GS_ERR_INVALID_ARG 1
+#define GS_ERR_CAPACITY 2
+#define GS_ERR_TIMEOUT 3
+#define GS_ERR_CUDA 4
+
+#define GS_TILE 16            /* tile edge in pixels (Sec. 2.2: 16x16 tiles) */
+#define GS_ALPHA_MIN (1.0f / 255.0f)
+#define GS_ALPHA_MAX 0.99f
+#define GS_T_MIN 1e-4f
+
+/* bits of the device error word written by gs_bin_and_sort */
+#define GS_FLAG_CAPACITY 1u   /* more intersections than K_capacity */
+
+/* Camera of Sec. 2.1, Eq. 1: world-to-camera extrinsics T_cw = [R_cw t_cw; 0 1]
+ * (R row-major) and pinhole intrinsics; pixel (x, y) has its centre at
+ * (x + 0.5, y + 0.5).  A Gaussian is culled unless near < t_z < far.  80 bytes. */
+typedef struct GsCamera {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float near_plane, far_plane;
+    int32_t width, height;
+} GsCamera;
+
+/* One view of a batch (see "Views and batches").  120 bytes. */
+typedef struct GsView {
+    GsCamera cam;
+    int32_t g_begin;       /* first Gaussian of the rendered scene */
+    int32_t g_count;       /* number of Gaussians of that scene */
+    int64_t proj_offset;   /* first projection of this view */
+    int64_t pixel_offset;  /* first pixel of this view in packed images */
+    int32_t tile_offset;   /* first global tile id of this view */
+    int32_t tiles_x;       /* ceil(width / 16) */
+    int32_t tiles_y;       /* ceil(height / 16) */
+    int32_t reserved;
+} GsView;
+
+/* Version of this ABI (major * 100 + minor). */
+int gs_version(void);
+
+/* Message describing the calling thread's last error ("" if none). */
+const char* gs_last_error(void);
+
+/* Number of CUDA kernels this library has enqueued since it was loaded
+ * (all threads; a monotonic counter for instrumentation). */
+int64_t gs_kernel_launches(void);
+
+/*
+ * Fills proj_offset, pixel_offset, tile_offset, tiles_x, tiles_y of views[0..V)
+ * (host memory) from g_count and the camera sizes, in view order, and returns
+ * the totals: *P_total projections, *T_total tiles, *pix_total pixels.
+ * GS_ERR_INVALID_ARG on V < 0, non-positive image sizes, negative counts or
+ * totals that overflow the 32-bit tile / projection index space.
+ */
+int gs_views_layout(GsView* views, int32_t V, int64_t* P_total, int32_t* T_total, int64_t* pix_total);
+
+/*
+ * Sec. 2.1 (Eq. 2-6) and the tile box of Sec. 2.2.  For every projection p of
+ * every view: t = T_cw [mu; 1]; mu' = (fx t_x/t_z + cx, fy t_y/t_z + cy);
+ * J of Eq. 3; R(q/|q|) of Eq. 5 (with R_11 = 1 - 2(x^2 + z^2), the orthonormal
+ * form); Sigma = R S S^T R^T; Sigma' = J R_cw Sigma R_cw^T J^T + eps2d I;
+ * conic Y = Sigma'^-1 packed (a, b, c) for [[a, b], [b, c]]; the tight box
+ * r = 3 (sqrt(Sigma'_00), sqrt(Sigma'_11)) and its tile rectangle
+ * [floor((mu' - r)/16), floor((mu' + r)/16) + 1) clamped to the tile grid.
+ * A projection is culled (touched = 0, zero rect) when t_z <= near,
+ * t_z >= far, det Sigma' <= 0, the rectangle is empty, or a value is not
+ * finite.
+ *   in : views[V] (device), means[N,3], quats[N,4], scales[N,3]
+ *   out: means2d[P,2], conics[P,3], depths[P] (t_z), rects[P,4] int16
+ *        (x0, y0, x1, y1 tile indices, half-open), touched[P] int32
+ *        (tiles in the rectangle), K_total (device int64, nullable): set to
+ *        the sum of touched (the intersection count).
+ */
+int gs_project(const GsView* views, int32_t V, int64_t P, const float* means, const float* quats,
+               const float* scales, float eps2d, float* means2d, float* conics, float* depths,
+               int16_t* rects, int32_t* touched, int64_t* K_total, void* stream);
+
+/* Bytes of scratch gs_bin_and_sort needs for P projections, at most
+ * K_capacity intersections and T_total tiles (256-byte aligned sub-buffers). */
+size_t gs_bin_and_sort_workspace_size(int64_t P, int64_t K_capacity, int32_t T_total);
+
+/*
+ * Sec. 2.2: binning and per-tile depth order (the tile sort of Kerbl et al.,
+ * App. C, realised as a depth sort of the projections followed by a stable
+ * tile-id sort of the intersections).  Every projection p is paired with each
+ * tile of its rectangle; the pairs are ordered by (global tile id, depth,
+ * p) -- exactly, equal depths by p.
+ *   in : views (device), P, T_total, rects, depths, touched (from gs_project),
+ *        K_capacity (size of the isect arrays), workspace (device, >=
+ *        gs_bin_and_sort_workspace_size bytes, contents irrelevant)
+ *   out: isect_ids[K_capacity]   projection of each sorted pair
+ *        isect_pos[K_capacity]   sorted position of each pair in emission
+ *                                order (the order p's pairs are generated:
+ *                                pair j of p is emission emit_start[p] + j)
+ *        emit_start[P]           first emission index of each projection
+ *        tile_ranges[T_total,2]  [start, end) of each tile's sorted pairs
+ *        K_out                   (device int32) number of pairs K
+ *        flags                   (device uint32) GS_FLAG_CAPACITY is OR-ed in
+ *                                when K > K_capacity; the outputs are then
+ *                                incomplete but no write leaves its buffer.
+ * Outputs past K are left untouched.  Needs P < 2^31 and K_capacity < 2^31.
+ */
+int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_t T_total, const int16_t* rects,
+                    const float* depths, const int32_t* touched, int64_t K_capacity, void* workspace,
+                    size_t workspace_bytes, int32_t* isect_ids, int32_t* isect_pos, int32_t* emit_start,
+                    int32_t* tile_ranges, int32_t* K_out, uint32_t* flags, void* stream);
+
+/*
+ * Sec. 2.2, Eq. 7: for every pixel of every view, walks its tile's sorted list
+ * front to back: sigma = 1/2 Delta^T Y Delta with Delta = mu' - pixel centre,
+ * alpha = min(0.99, o exp(-sigma)), skip alpha < 1/255 (and sigma < 0), stop
+ * before T (1 - alpha) < 1e-4, C += c alpha T, T *= (1 - alpha).  Finally
+ * C += T * background.
+ *   in : views (device), T_total, means2d, conics (from gs_project),
+ *        opacities[N], colors[N,3], isect_ids, tile_ranges (from
+ *        gs_bin_and_sort), background[3] (device, nullable = black)
+ *   out: out_rgb[pix,3], T_final[pix] (transmittance after the last
+ *        composited Gaussian), last_idx[pix] int32 (sorted position of the last
+ *        composited Gaussian; tile start - 1 when none), n_contrib[pix] int32
+ *        (nullable: number of Gaussians composited into the pixel).
+ */
+int gs_rasterize_fwd(const GsView* views, int32_t V, int32_t T_total, const float* means2d,
+                     const float* conics, const float* opacities, const float* colors,
+                     const int32_t* isect_ids, const int32_t* tile_ranges, const float* background,
+                     float* out_rgb, float* T_final, int32_t* last_idx, int32_t* n_contrib, void* stream);
+
+/* Bytes of scratch gs_rasterize_bwd needs for K_capacity intersections. */
+size_t gs_rasterize_bwd_workspace_size(int64_t K_capacity);
+
+/*
+ * Sec. 3.1: back to front from each pixel's last composited Gaussian,
+ * rebuilding T_{n-1} = T_n / (1 - alpha_{n-1}) from the saved T_final and
+ * S_{n-1} = c_n alpha_n T_n + S_n, with
+ *   dC/dc_n = alpha_n T_n,
+ *   dC/dalpha_n = c_n T_n - S_n/(1 - alpha_n) - background T_final/(1 - alpha_n),
+ *   dalpha/do = exp(-sigma), dalpha/dsigma = -o exp(-sigma) (both 0 where the
+ *   0.99 clamp was active), dsigma/dmu' = Y Delta, dsigma/d(a,b,c) =
+ *   (Delta_x^2/2, Delta_x Delta_y, Delta_y^2/2).
+ * Per-pixel terms are summed per (tile, Gaussian) inside each tile and then
+ * per projection over its tiles in a fixed order, so results are
+ * deterministic (no floating-point atomics across tiles).
+ *   in : the forward's inputs and outputs, dL_drgb[pix,3], K_capacity,
+ *        K (device int32 from gs_bin_and_sort), isect_pos, emit_start,
+ *        touched, workspace (>= gs_rasterize_bwd_workspace_size bytes)
+ *   out (ACCUMULATED: += into caller-initialised buffers):
+ *        dL_dmeans2d[P,2], dL_dconics[P,3] (per projection),
+ *        dL_dopacities[N], dL_dcolors[N,3] (per Gaussian, summed over views).
+ */
+int gs_rasterize_bwd(const GsView* views, int32_t V, int64_t P, int32_t T_total, const float* means2d,
+                     const float* conics, const float* opacities, const float* colors,
+                     const int32_t* isect_ids, const int32_t* isect_pos, const int32_t* emit_start,
+                     const int32_t* touched, const int32_t* tile_ranges, const int32_t* K,
+                     int64_t K_capacity, const float* background, const float* T_final,
+                     const int32_t* last_idx, const float* dL_drgb, void* workspace, size_t workspace_bytes,
+                     float* dL_dmeans2d, float* dL_dconics, float* dL_dopacities, float* dL_dcolors,
+                     void* stream);
+
+/*
+ * Sec. 3.2 (Eq. 16-20) and 3.2.1: for every projection with touched > 0,
+ * recomputes the forward and maps dL/dmu' and dL/dconic to
+ *   dL/dSigma' = -Y G Y (G = dL/dY, the packed b gradient split evenly),
+ *   dL/dSigma = T^T dL/dSigma' T with T = J R_cw, dL/dT, dL/dJ = dL/dT R_cw^T,
+ *   dL/dt = J^T dL/dmu' + <dL/dJ, dJ/dt>, dL/dmu = R_cw^T dL/dt,
+ *   dL/dM = 2 dL/dSigma M, dL/dR = dL/dM S, dL/ds = diag(R^T dL/dM),
+ *   dL/dq_hat from the four dR/dq matrices, then through q_hat = q/|q|.
+ *   in : views, P, means, quats, scales, eps2d, touched, dL_dmeans2d,
+ *        dL_dconics
+ *   out (ACCUMULATED, summed over views): dL_dmeans[N,3], dL_dquats[N,4]
+ *        (w.r.t. the raw quaternion), dL_dscales[N,3].
+ */
+int gs_project_bwd(const GsView* views, int32_t V, int64_t P, const float* means, const float* quats,
+                   const float* scales, float eps2d, const int32_t* touched, const float* dL_dmeans2d,
+                   const float* dL_dconics, float* dL_dmeans, float* dL_dquats, float* dL_dscales,
+                   void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSPLAT103_H */

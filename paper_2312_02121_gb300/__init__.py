@@ -11,7 +11,7 @@ or a GPU.
 """
 import importlib
 
-__all__ = ["binding", "autograd", "batch", "workloads"]
+__all__ = ["binding", "autograd", "batch", "build", "pipeline", "workloads"]
 
 
 def __getattr__(name):

@@ -1,0 +1,231 @@
+"""Thin ctypes binding of ``libgsplat103.so`` (declared in ``include/gsplat103.h``).
+
+Each ``gs_*`` function here has the name and argument order of the C entry
+point and only marshals arguments: torch tensors become device pointers, the
+stream defaults to torch's current stream, and a non-zero status raises
+``GsError`` with ``gs_last_error()``.  All arithmetic runs in the library's
+CUDA kernels; there is no CPU fallback -- importing this module on a machine
+where the library cannot be loaded raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+GS_OK = 0
+GS_ERR_INVALID_ARG = 1
+GS_ERR_CAPACITY = 2
+GS_ERR_TIMEOUT = 3
+GS_ERR_CUDA = 4
+GS_FLAG_CAPACITY = 1
+GS_TILE = 16
+ALPHA_MIN = 1.0 / 255.0
+ALPHA_MAX = 0.99
+T_MIN = 1e-4
+
+
+class GsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"gsplat103 error {code}: {msg}")
+        self.code = code
+
+
+class GsCamera(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("near_plane", ctypes.c_float), ("far_plane", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class GsView(ctypes.Structure):
+    _fields_ = [("cam", GsCamera), ("g_begin", ctypes.c_int32), ("g_count", ctypes.c_int32),
+                ("proj_offset", ctypes.c_int64), ("pixel_offset", ctypes.c_int64),
+                ("tile_offset", ctypes.c_int32), ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+assert ctypes.sizeof(GsCamera) == 80 and ctypes.sizeof(GsView) == 120
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_F = ctypes.c_float
+_SZ = ctypes.c_size_t
+
+# C signatures, in header order
+SIGNATURES = {
+    "gs_version": (ctypes.c_int, []),
+    "gs_last_error": (ctypes.c_char_p, []),
+    "gs_kernel_launches": (ctypes.c_int64, []),
+    "gs_views_layout": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
+    "gs_project": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _F, _P, _P, _P, _P, _P, _P, _P]),
+    "gs_bin_and_sort_workspace_size": (_SZ, [_I64, _I64, _I32]),
+    "gs_bin_and_sort": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _I64, _P, _SZ, _P, _P, _P, _P, _P, _P, _P]),
+    "gs_rasterize_fwd": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gs_rasterize_bwd_workspace_size": (_SZ, [_I64]),
+    "gs_rasterize_bwd": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P,
+                                        _P, _P, _P, _SZ, _P, _P, _P, _P, _P]),
+    "gs_project_bwd": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _F, _P, _P, _P, _P, _P, _P, _P]),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Loads (building first if needed) the CUDA library; raises if impossible."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB_PATH
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgsplat103.so not found at {path}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def last_error() -> str:
+    return load().gs_last_error().decode()
+
+
+def _check(code: int):
+    if code != GS_OK:
+        raise GsError(code, last_error())
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("gsplat103 needs contiguous tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+# ---------------------------------------------------------------------------
+# views
+# ---------------------------------------------------------------------------
+
+def make_camera(cam) -> GsCamera:
+    """GsCamera from any object with R, t, fx, fy, cx, cy, width, height, near, far."""
+    c = GsCamera()
+    c.R[:] = [float(v) for v in np.asarray(cam.R, np.float64).reshape(9)]
+    c.t[:] = [float(v) for v in np.asarray(cam.t, np.float64).reshape(3)]
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.near_plane, c.far_plane = float(cam.near), float(cam.far)
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+class Views:
+    """A laid-out batch of views: host array, device copy and totals."""
+
+    def __init__(self, cameras: Sequence, g_ranges: Sequence[Tuple[int, int]], device="cuda"):
+        V = len(cameras)
+        arr = (GsView * max(V, 1))()
+        for i, (cam, (gb, gc)) in enumerate(zip(cameras, g_ranges)):
+            arr[i].cam = make_camera(cam)
+            arr[i].g_begin = int(gb)
+            arr[i].g_count = int(gc)
+        P, T, pix = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+        _check(load().gs_views_layout(ctypes.cast(arr, _P), V, ctypes.byref(P), ctypes.byref(T), ctypes.byref(pix)))
+        self.V, self.P, self.T, self.pixels = V, P.value, T.value, pix.value
+        self.host = arr
+        raw = bytes(ctypes.string_at(ctypes.addressof(arr), ctypes.sizeof(GsView) * max(V, 1)))
+        self.device = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
+        self.cameras = list(cameras)
+
+    def view(self, i: int) -> GsView:
+        return self.host[i]
+
+    def image_slice(self, i: int) -> Tuple[int, int, int, int]:
+        """(pixel_offset, width, height, tile_offset) of view i."""
+        v = self.host[i]
+        return v.pixel_offset, v.cam.width, v.cam.height, v.tile_offset
+
+
+# ---------------------------------------------------------------------------
+# 1:1 wrappers of the C ABI
+# ---------------------------------------------------------------------------
+
+def gs_version() -> int:
+    return int(load().gs_version())
+
+
+def gs_kernel_launches() -> int:
+    return int(load().gs_kernel_launches())
+
+
+def gs_project(views: Views, means, quats, scales, eps2d: float, means2d, conics, depths, rects, touched,
+               K_total=None, stream=None):
+    _check(load().gs_project(_ptr(views.device), views.V, views.P, _ptr(means), _ptr(quats), _ptr(scales),
+                             float(eps2d), _ptr(means2d), _ptr(conics), _ptr(depths), _ptr(rects), _ptr(touched),
+                             _ptr(K_total), _stream(stream)))
+
+
+def gs_bin_and_sort_workspace_size(P: int, K_capacity: int, T_total: int) -> int:
+    return int(load().gs_bin_and_sort_workspace_size(P, K_capacity, T_total))
+
+
+def gs_bin_and_sort(views: Views, rects, depths, touched, K_capacity: int, workspace, isect_ids, isect_pos,
+                    emit_start, tile_ranges, K_out, flags, stream=None):
+    _check(load().gs_bin_and_sort(_ptr(views.device), views.V, views.P, views.T, _ptr(rects), _ptr(depths),
+                                  _ptr(touched), int(K_capacity), _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), _ptr(isect_ids), _ptr(isect_pos),
+                                  _ptr(emit_start), _ptr(tile_ranges), _ptr(K_out), _ptr(flags), _stream(stream)))
+
+
+def gs_rasterize_fwd(views: Views, means2d, conics, opacities, colors, isect_ids, tile_ranges, background,
+                     out_rgb, T_final, last_idx, n_contrib=None, stream=None):
+    _check(load().gs_rasterize_fwd(_ptr(views.device), views.V, views.T, _ptr(means2d), _ptr(conics),
+                                   _ptr(opacities), _ptr(colors), _ptr(isect_ids), _ptr(tile_ranges),
+                                   _ptr(background), _ptr(out_rgb), _ptr(T_final), _ptr(last_idx),
+                                   _ptr(n_contrib), _stream(stream)))
+
+
+def gs_rasterize_bwd_workspace_size(K_capacity: int) -> int:
+    return int(load().gs_rasterize_bwd_workspace_size(K_capacity))
+
+
+def gs_rasterize_bwd(views: Views, means2d, conics, opacities, colors, isect_ids, isect_pos, emit_start, touched,
+                     tile_ranges, K, K_capacity: int, background, T_final, last_idx, dL_drgb, workspace,
+                     dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors, stream=None):
+    _check(load().gs_rasterize_bwd(_ptr(views.device), views.V, views.P, views.T, _ptr(means2d), _ptr(conics),
+                                   _ptr(opacities), _ptr(colors), _ptr(isect_ids), _ptr(isect_pos),
+                                   _ptr(emit_start), _ptr(touched), _ptr(tile_ranges), _ptr(K), int(K_capacity),
+                                   _ptr(background), _ptr(T_final), _ptr(last_idx), _ptr(dL_drgb),
+                                   _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                   _ptr(dL_dmeans2d), _ptr(dL_dconics), _ptr(dL_dopacities), _ptr(dL_dcolors),
+                                   _stream(stream)))
+
+
+def gs_project_bwd(views: Views, means, quats, scales, eps2d: float, touched, dL_dmeans2d, dL_dconics, dL_dmeans,
+                   dL_dquats, dL_dscales, stream=None):
+    _check(load().gs_project_bwd(_ptr(views.device), views.V, views.P, _ptr(means), _ptr(quats), _ptr(scales),
+                                 float(eps2d), _ptr(touched), _ptr(dL_dmeans2d), _ptr(dL_dconics), _ptr(dL_dmeans),
+                                 _ptr(dL_dquats), _ptr(dL_dscales), _stream(stream)))
+
+
+EXPORTED: List[str] = list(SIGNATURES)

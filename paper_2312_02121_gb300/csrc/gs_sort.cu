@@ -1,0 +1,490 @@
+// Tile binning and per-tile depth order (Sec. 2.2), written for sm_103a.
+//
+// The paper sorts (tile, depth) keys of every Gaussian-tile pair (the tile
+// sort of Kerbl et al., App. C).  The same order is produced here in two
+// cheaper sorts:
+//   1. a stable LSD radix sort of the projections on the 31 bits of their
+//      (positive) fp32 depth -- this gives (depth, p) order, ties by p;
+//   2. the pairs are emitted in that order (scan of `touched` in depth order,
+//      then one thread per projection writes its tiles), and a stable LSD
+//      radix sort on the global tile id alone (ceil(log2 T_total) bits, e.g.
+//      13 for one 1080p view) groups them by tile while keeping depth order.
+// Result: pairs ordered exactly by (tile, depth, p), as if the 64-bit
+// (tile | depth) keys had been sorted stably in p order, but sorting 31 bits
+// of P keys plus ~13 bits of K keys instead of ~44 bits of K keys.
+//
+// The radix sort is a classic three-kernel LSD pass (per-block digit
+// histograms, per-digit scan across blocks, stable scatter with warp-level
+// ranking and a shared-memory reorder for coalesced writes).  Item counts may
+// live in device memory, so the whole pipeline is graph-capturable.
+#include <algorithm>
+
+#include "gs_common.cuh"
+
+namespace gs {
+
+constexpr int kRT = 256;              // threads per radix block
+constexpr int kRI = 16;               // items per thread
+constexpr int kRTile = kRT * kRI;     // items per radix block
+constexpr int kRWarps = kRT / 32;
+constexpr int kMaxBins = 256;         // digits of at most 8 bits
+constexpr int kScanThreads = 1024;
+constexpr int kEmitItems = 4;         // projections per thread in scan/emit
+constexpr int kEmitTile = 256 * kEmitItems;
+
+__device__ __forceinline__ int item_count(const int32_t* count_dev, int64_t count_static, int64_t cap)
+{
+    int64_t c = count_dev ? (int64_t)*count_dev : count_static;
+    if (c > cap) c = cap;
+    return c < 0 ? 0 : (int)c;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Exclusive scan over a 256-thread block; returns the block total in *total.
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan_256(T x, T* total)
+{
+    __shared__ T warp_tot[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T incl = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    T before = 0, all = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const T t = warp_tot[i];
+        if (i < w) before += t;
+        all += t;
+    }
+    __syncthreads();
+    if (total) *total = all;
+    return before + incl - x;
+}
+
+// ---------------------------------------------------------------------------
+// radix sort passes (uint32 keys, uint32 values)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kRT)
+k_radix_hist(const uint32_t* __restrict__ keys, const int32_t* __restrict__ count_dev, int64_t count_static,
+             int64_t cap, int shift, int bits, uint32_t* __restrict__ hist)
+{
+    __shared__ uint32_t h[kRWarps][kMaxBins];
+    const int count = item_count(count_dev, count_static, cap);
+    const int nb = (count + kRTile - 1) / kRTile;
+    const int b = blockIdx.x;
+    if (b >= nb) return;
+    const int bins = 1 << bits;
+    const unsigned mask = bins - 1;
+    const int w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kRWarps * kMaxBins; i += kRT) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const int base = b * kRTile;
+#pragma unroll 4
+    for (int k = 0; k < kRI; ++k) {
+        const int idx = base + k * kRT + threadIdx.x;
+        if (idx < count) atomicAdd(&h[w][(keys[idx] >> shift) & mask], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < bins; d += kRT) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int i = 0; i < kRWarps; ++i) s += h[i][d];
+        hist[(size_t)d * nb + b] = s;
+    }
+}
+
+// One block per digit: exclusive scan of that digit's per-block counts (in
+// place) and the digit total.
+__global__ void __launch_bounds__(kRT)
+k_radix_scan_rows(uint32_t* __restrict__ hist, const int32_t* __restrict__ count_dev, int64_t count_static,
+                  int64_t cap, uint32_t* __restrict__ digit_total)
+{
+    const int count = item_count(count_dev, count_static, cap);
+    const int nb = (count + kRTile - 1) / kRTile;
+    const int d = blockIdx.x;
+    uint32_t* row = hist + (size_t)d * nb;
+    const int per = (nb + kRT - 1) / kRT;
+    const int lo = min(nb, (int)threadIdx.x * per), hi = min(nb, lo + per);
+    uint32_t s = 0;
+    for (int i = lo; i < hi; ++i) s += row[i];
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan_256<uint32_t>(s, &tot);
+    for (int i = lo; i < hi; ++i) {
+        const uint32_t x = row[i];
+        row[i] = run;
+        run += x;
+    }
+    if (threadIdx.x == 0) digit_total[d] = tot;
+}
+
+// Stable scatter of one block of items by digit.  vals_in == nullptr means
+// "value = input position" (the first pass of a sort of indices).
+__global__ void __launch_bounds__(kRT)
+k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+                const int32_t* __restrict__ count_dev, int64_t count_static, int64_t cap, int shift, int bits,
+                const uint32_t* __restrict__ hist, const uint32_t* __restrict__ digit_total)
+{
+    __shared__ uint32_t s_keys[kRTile];
+    __shared__ uint32_t s_vals[kRTile];
+    __shared__ uint32_t s_warp[kRWarps][kMaxBins];  // per-warp digit counts, then per-warp offsets
+    __shared__ uint32_t s_base[kMaxBins];           // global position of the block's first item of each digit
+    __shared__ uint32_t s_local[kMaxBins];          // local position of the block's first item of each digit
+
+    const int count = item_count(count_dev, count_static, cap);
+    const int nb = (count + kRTile - 1) / kRTile;
+    const int b = blockIdx.x;
+    if (b >= nb) return;
+    const int bins = 1 << bits;
+    const unsigned mask = bins - 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int base = b * kRTile;
+    const int n_here = min(kRTile, count - base);
+
+    // digit offsets: exclusive scan of digit totals + this block's row prefix
+    {
+        const int d = threadIdx.x;
+        const uint32_t tot = d < bins ? digit_total[d] : 0u;
+        const uint32_t ex = block_exclusive_scan_256<uint32_t>(tot, nullptr);
+        if (d < bins) s_base[d] = ex + hist[(size_t)d * nb + b];
+    }
+    for (int i = lane; i < kMaxBins; i += 32) s_warp[w][i] = 0;
+    __syncwarp();
+
+    // warp-striped load: warp w owns items [w*512, w*512+512) of the block
+    uint32_t key[kRI], val[kRI], rank[kRI] = {};
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int k = 0; k < kRI; ++k) {
+        const int li = w * (kRI * 32) + k * 32 + lane;
+        const int idx = base + li;
+        const bool valid = li < n_here;
+        key[k] = valid ? keys_in[idx] : 0u;
+        val[k] = valid ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
+        const uint32_t d = (key[k] >> shift) & mask;
+        // lanes holding the same digit, via one ballot per digit bit
+        unsigned peers = __ballot_sync(kFull, valid);
+        for (int bit = 0; bit < bits; ++bit) {
+            const unsigned bal = __ballot_sync(kFull, (d >> bit) & 1u);
+            peers &= ((d >> bit) & 1u) ? bal : ~bal;
+        }
+        uint32_t before = 0;
+        if (valid) before = s_warp[w][d];
+        __syncwarp();
+        if (valid) {
+            rank[k] = before + __popc(peers & lt);
+            if ((peers & lt) == 0) s_warp[w][d] = before + __popc(peers);  // lowest peer updates
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // per-digit: offsets of each warp inside the block, and block totals
+    {
+        const int d = threadIdx.x;
+        uint32_t run = 0;
+        if (d < bins) {
+#pragma unroll
+            for (int i = 0; i < kRWarps; ++i) {
+                const uint32_t c = s_warp[i][d];
+                s_warp[i][d] = run;
+                run += c;
+            }
+        }
+        const uint32_t ex = block_exclusive_scan_256<uint32_t>(d < bins ? run : 0u, nullptr);
+        if (d < bins) s_local[d] = ex;
+    }
+    __syncthreads();
+    // reorder the block in shared memory by digit (stable)
+#pragma unroll
+    for (int k = 0; k < kRI; ++k) {
+        const int li = w * (kRI * 32) + k * 32 + lane;
+        if (li < n_here) {
+            const uint32_t d = (key[k] >> shift) & mask;
+            const uint32_t lp = s_local[d] + s_warp[w][d] + rank[k];
+            s_keys[lp] = key[k];
+            s_vals[lp] = val[k];
+        }
+    }
+    __syncthreads();
+    // coalesced write-out: consecutive items of a digit go to consecutive positions
+    for (int j = threadIdx.x; j < n_here; j += kRT) {
+        const uint32_t k2 = s_keys[j];
+        const uint32_t d = (k2 >> shift) & mask;
+        const uint32_t gp = s_base[d] + (uint32_t)j - s_local[d];
+        keys_out[gp] = k2;
+        vals_out[gp] = s_vals[j];
+    }
+}
+
+struct RadixBufs {
+    uint32_t* hist;
+    uint32_t* digit_total;
+};
+
+// Stable LSD sort of (key, value) pairs on key bits [0, total_bits), in
+// passes of at most 8 bits.  Keys ping-pong between k1 and k2, values between
+// v1 and v2; the first pass takes "value = input position".  The item count
+// is *count_dev (device, clamped to cap) or count_static.  Returns the
+// buffers holding the result.
+static void lsd_sort(uint32_t* k1, uint32_t* k2, uint32_t* v1, uint32_t* v2, const int32_t* count_dev,
+                     int64_t count_static, int64_t cap, int total_bits, const RadixBufs& rb, cudaStream_t s,
+                     uint32_t** keys_out, uint32_t** vals_out)
+{
+    uint32_t *kin = k1, *kout = k2, *vout = v1;
+    const uint32_t* vin = nullptr;
+    if (total_bits > 0 && cap > 0) {
+        const int passes = (total_bits + 7) / 8;
+        const int per = (total_bits + passes - 1) / passes;
+        const unsigned grid = (unsigned)((cap + kRTile - 1) / kRTile);
+        for (int pass = 0, shift = 0; pass < passes; ++pass, shift += per) {
+            const int bits = std::min(per, total_bits - shift);
+            k_radix_hist<<<grid, kRT, 0, s>>>(kin, count_dev, count_static, cap, shift, bits, rb.hist);
+            k_radix_scan_rows<<<1u << bits, kRT, 0, s>>>(rb.hist, count_dev, count_static, cap, rb.digit_total);
+            k_radix_scatter<<<grid, kRT, 0, s>>>(kin, vin, kout, vout, count_dev, count_static, cap, shift, bits,
+                                                 rb.hist, rb.digit_total);
+            count_launches(3);
+            std::swap(kin, kout);
+            vin = vout;
+            vout = (vout == v1) ? v2 : v1;
+        }
+    }
+    *keys_out = kin;
+    *vals_out = const_cast<uint32_t*>(vin);
+}
+
+// ---------------------------------------------------------------------------
+// binning kernels
+// ---------------------------------------------------------------------------
+
+// Depth keys: the fp32 bit pattern of t_z (> near > 0, so monotone in 31
+// bits); culled projections get the largest key.
+__global__ void k_depth_keys(int64_t P, const float* __restrict__ depths, const int32_t* __restrict__ touched,
+                             uint32_t* __restrict__ keys)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < P) keys[p] = touched[p] > 0 ? __float_as_uint(depths[p]) : 0x7fffffffu;
+}
+
+// Per block of kEmitTile projections in depth order: sum of touched.
+__global__ void __launch_bounds__(256)
+k_touched_block_sums(int64_t P, const uint32_t* __restrict__ order, const int32_t* __restrict__ touched,
+                     int64_t* __restrict__ block_sums)
+{
+    const int64_t base = (int64_t)blockIdx.x * kEmitTile;
+    int64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kEmitItems; ++k) {
+        const int64_t r = base + k * 256 + threadIdx.x;
+        if (r < P) s += touched[order[r]];
+    }
+    int64_t tot;
+    block_exclusive_scan_256<int64_t>(s, &tot);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+// Single block: exclusive scan of the block sums in place; K and the
+// capacity flag.
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_block_sums(int64_t nblk, int64_t* __restrict__ block_sums, int64_t cap, int32_t* __restrict__ K_out,
+                  uint32_t* __restrict__ flags)
+{
+    __shared__ int64_t warp_tot[kScanThreads / 32];
+    const int64_t per = (nblk + kScanThreads - 1) / kScanThreads;
+    const int64_t lo = min(nblk, (int64_t)threadIdx.x * per), hi = min(nblk, lo + per);
+    int64_t s = 0;
+    for (int64_t i = lo; i < hi; ++i) s += block_sums[i];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t incl = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int64_t y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    int64_t before = 0, all = 0;
+    for (int i = 0; i < kScanThreads / 32; ++i) {
+        if (i < w) before += warp_tot[i];
+        all += warp_tot[i];
+    }
+    int64_t run = before + incl - s;
+    for (int64_t i = lo; i < hi; ++i) {
+        const int64_t x = block_sums[i];
+        block_sums[i] = run;
+        run += x;
+    }
+    if (threadIdx.x == 0) {
+        *K_out = (int32_t)min(all, (int64_t)INT32_MAX);
+        if (all > cap) atomicOr(flags, GS_FLAG_CAPACITY);
+    }
+}
+
+// Emission of the (tile, projection) pairs in depth order: pair j of the
+// projection at depth rank r gets emission index off[r] + j; its key is the
+// global tile id (row-major inside the rectangle), its owner the projection.
+__global__ void __launch_bounds__(256)
+k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __restrict__ order,
+       const int32_t* __restrict__ touched, const short4* __restrict__ rects, const int64_t* __restrict__ block_prefix,
+       int64_t cap, uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ owner, int32_t* __restrict__ emit_start)
+{
+    const int64_t base = (int64_t)blockIdx.x * kEmitTile;
+    // thread-contiguous items so that one thread's pairs are consecutive
+    uint32_t p[kEmitItems];
+    int cnt[kEmitItems];
+    int64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kEmitItems; ++k) {
+        const int64_t r = base + threadIdx.x * kEmitItems + k;
+        p[k] = r < P ? order[r] : 0u;
+        cnt[k] = r < P ? touched[p[k]] : 0;
+        s += cnt[k];
+    }
+    int64_t off = block_prefix[blockIdx.x] + block_exclusive_scan_256<int64_t>(s, nullptr);
+#pragma unroll
+    for (int k = 0; k < kEmitItems; ++k) {
+        const int64_t r = base + threadIdx.x * kEmitItems + k;
+        if (r >= P) break;
+        if (cnt[k] > 0) {
+            emit_start[p[k]] = (int32_t)min(off, (int64_t)INT32_MAX);
+            const GsView& view = views[view_of_projection(views, V, (int64_t)p[k])];
+            const short4 rc = rects[p[k]];
+            const int tx = view.tiles_x, toff = view.tile_offset;
+            int64_t e = off;
+            for (int ty = rc.y; ty < rc.w; ++ty)
+                for (int x = rc.x; x < rc.z; ++x, ++e)
+                    if (e < cap) {
+                        tile_keys[e] = (uint32_t)(toff + ty * tx + x);
+                        owner[e] = p[k];
+                    }
+        }
+        off += cnt[k];
+    }
+}
+
+// Sorted pairs -> projection ids, inverse positions and per-tile ranges.
+__global__ void k_finalize(const int32_t* __restrict__ K_dev, int64_t cap, const uint32_t* __restrict__ keys,
+                           const uint32_t* __restrict__ emit_idx, const uint32_t* __restrict__ owner,
+                           int32_t* __restrict__ isect_ids, int32_t* __restrict__ isect_pos,
+                           int2* __restrict__ tile_ranges)
+{
+    const int K = item_count(K_dev, 0, cap);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K) return;
+    const uint32_t e = emit_idx ? emit_idx[i] : (uint32_t)i;
+    isect_ids[i] = (int32_t)owner[e];
+    isect_pos[e] = i;
+    const uint32_t t = keys[i];
+    if (i == 0 || keys[i - 1] != t) tile_ranges[t].x = i;
+    if (i == K - 1 || keys[i + 1] != t) tile_ranges[t].y = i + 1;
+}
+
+struct SortLayout {
+    uint32_t *dkey_a, *dkey_b, *dval_a, *dval_b;
+    int64_t* block_sums;
+    uint32_t *tkey_a, *tkey_b, *tval_a, *tval_b, *owner;
+    uint32_t *hist, *digit_total;
+    size_t bytes;
+};
+
+static SortLayout carve(void* ws, int64_t P, int64_t cap)
+{
+    Carver c(ws);
+    SortLayout L;
+    L.dkey_a = c.take<uint32_t>(P);
+    L.dkey_b = c.take<uint32_t>(P);
+    L.dval_a = c.take<uint32_t>(P);
+    L.dval_b = c.take<uint32_t>(P);
+    L.block_sums = c.take<int64_t>((P + kEmitTile - 1) / kEmitTile + 1);
+    L.tkey_a = c.take<uint32_t>(cap);
+    L.tkey_b = c.take<uint32_t>(cap);
+    L.tval_a = c.take<uint32_t>(cap);
+    L.tval_b = c.take<uint32_t>(cap);
+    L.owner = c.take<uint32_t>(cap);
+    const int64_t nb = (std::max(P, cap) + kRTile - 1) / kRTile;
+    L.hist = c.take<uint32_t>((size_t)nb * kMaxBins + 1);
+    L.digit_total = c.take<uint32_t>(kMaxBins);
+    L.bytes = c.used;
+    return L;
+}
+
+static int bit_length(int64_t x)
+{
+    int b = 0;
+    while (x > 0) { ++b; x >>= 1; }
+    return b;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" size_t gs_bin_and_sort_workspace_size(int64_t P, int64_t K_capacity, int32_t T_total)
+{
+    (void)T_total;
+    if (P < 0 || K_capacity < 0) return 0;
+    return carve(nullptr, P, K_capacity).bytes;
+}
+
+extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_t T_total, const int16_t* rects,
+                               const float* depths, const int32_t* touched, int64_t K_capacity, void* workspace,
+                               size_t workspace_bytes, int32_t* isect_ids, int32_t* isect_pos, int32_t* emit_start,
+                               int32_t* tile_ranges, int32_t* K_out, uint32_t* flags, void* stream)
+{
+    if (V <= 0 || P < 0 || T_total <= 0 || K_capacity < 0 || P >= (int64_t(1) << 31) ||
+        K_capacity >= (int64_t(1) << 31))
+        return fail(GS_ERR_INVALID_ARG, "gs_bin_and_sort: V=%d P=%lld T_total=%d K_capacity=%lld", V, (long long)P,
+                    T_total, (long long)K_capacity);
+    if (!views || !tile_ranges || !K_out || !flags || (P > 0 && (!rects || !depths || !touched || !emit_start)) ||
+        (K_capacity > 0 && (!isect_ids || !isect_pos)))
+        return fail(GS_ERR_INVALID_ARG, "gs_bin_and_sort: null pointer argument");
+    if ((reinterpret_cast<uintptr_t>(rects) & 7) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7))
+        return fail(GS_ERR_INVALID_ARG, "gs_bin_and_sort: rects and tile_ranges need 8-byte alignment");
+    const SortLayout need = carve(nullptr, P, K_capacity);
+    if (!workspace || workspace_bytes < need.bytes)
+        return fail(GS_ERR_INVALID_ARG, "gs_bin_and_sort: workspace of %zu bytes, need %zu", workspace_bytes,
+                    need.bytes);
+    cudaStream_t s = as_stream(stream);
+    const SortLayout L = carve(workspace, P, K_capacity);
+    if (cudaMemsetAsync(tile_ranges, 0, sizeof(int32_t) * 2 * (size_t)T_total, s) != cudaSuccess ||
+        cudaMemsetAsync(K_out, 0, sizeof(int32_t), s) != cudaSuccess)
+        return launch_status("gs_bin_and_sort memset");
+    if (P == 0) return launch_status("gs_bin_and_sort");
+    const RadixBufs rb{L.hist, L.digit_total};
+
+    // 1. projections in (depth, p) order
+    k_depth_keys<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(P, depths, touched, L.dkey_a);
+    count_launches(1);
+    uint32_t *dk, *order;
+    lsd_sort(L.dkey_a, L.dkey_b, L.dval_a, L.dval_b, nullptr, P, P, 31, rb, s, &dk, &order);
+
+    // 2. scan of touched in depth order, K, emission
+    const int64_t nblk = (P + kEmitTile - 1) / kEmitTile;
+    k_touched_block_sums<<<(unsigned)nblk, 256, 0, s>>>(P, order, touched, L.block_sums);
+    k_scan_block_sums<<<1, kScanThreads, 0, s>>>(nblk, L.block_sums, K_capacity, K_out, flags);
+    k_emit<<<(unsigned)nblk, 256, 0, s>>>(views, V, P, order, touched, reinterpret_cast<const short4*>(rects),
+                                          L.block_sums, K_capacity, L.tkey_a, L.owner, emit_start);
+    count_launches(3);
+    if (K_capacity == 0) return launch_status("gs_bin_and_sort");
+
+    // 3. stable sort of the pairs by global tile id (values: emission index)
+    uint32_t *tk, *tv;
+    lsd_sort(L.tkey_a, L.tkey_b, L.tval_a, L.tval_b, K_out, 0, K_capacity, bit_length((int64_t)T_total - 1), rb, s,
+             &tk, &tv);
+    // 4. projection ids, inverse positions, tile ranges
+    k_finalize<<<(unsigned)((K_capacity + 255) / 256), 256, 0, s>>>(K_out, K_capacity, tk, tv, L.owner, isect_ids,
+                                                                      isect_pos, reinterpret_cast<int2*>(tile_ranges));
+    count_launches(1);
+    return launch_status("gs_bin_and_sort");
+}

@@ -1,0 +1,145 @@
+"""Sequencing of the C-ABI stages for one forward / backward pass.
+
+Torch only provides device memory and the stream here; every stage is one
+``gs_*`` call into the CUDA library.  ``Frame`` keeps the buffers a backward
+pass needs (the forward's per-pixel T_final and last index, the sorted
+intersection lists) so that nothing is recomputed but Sigma', the conic and
+alpha, which the backward kernels rebuild on the fly.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Optional
+
+import torch
+
+from . import binding as B
+
+
+@dataclasses.dataclass
+class Params:
+    """Gaussian parameters on the device, fp32 contiguous: means [N,3],
+    quats [N,4] (w,x,y,z), scales [N,3], opacities [N], colors [N,3]."""
+
+    means: torch.Tensor
+    quats: torch.Tensor
+    scales: torch.Tensor
+    opacities: torch.Tensor
+    colors: torch.Tensor
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @staticmethod
+    def from_scene(scene, device="cuda") -> "Params":
+        t = lambda a: torch.as_tensor(a, dtype=torch.float32).contiguous().to(device)
+        return Params(t(scene.means), t(scene.quats), t(scene.scales), t(scene.opacities), t(scene.colors))
+
+
+def _check_params(p: Params):
+    for name in ("means", "quats", "scales", "opacities", "colors"):
+        x = getattr(p, name)
+        if not x.is_cuda:
+            raise RuntimeError(f"gsplat103 runs on CUDA only; {name} is on {x.device}")
+        if x.dtype != torch.float32 or not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous float32")
+
+
+@dataclasses.dataclass
+class Frame:
+    views: B.Views
+    eps2d: float
+    background: Optional[torch.Tensor]
+    K_capacity: int
+    means2d: torch.Tensor
+    conics: torch.Tensor
+    depths: torch.Tensor
+    rects: torch.Tensor
+    touched: torch.Tensor
+    K_total: torch.Tensor
+    isect_ids: torch.Tensor
+    isect_pos: torch.Tensor
+    emit_start: torch.Tensor
+    tile_ranges: torch.Tensor
+    K: torch.Tensor
+    flags: torch.Tensor
+    out_rgb: torch.Tensor
+    T_final: torch.Tensor
+    last_idx: torch.Tensor
+    sort_ws: torch.Tensor
+    n_contrib: Optional[torch.Tensor] = None
+
+    def overflowed(self) -> bool:
+        """Reads the device error word (synchronises)."""
+        return bool(int(self.flags.item()) & B.GS_FLAG_CAPACITY)
+
+    def image(self, i: int = 0) -> torch.Tensor:
+        off, w, h, _ = self.views.image_slice(i)
+        return self.out_rgb[off:off + w * h].view(h, w, 3)
+
+
+def project(views: B.Views, p: Params, eps2d: float, stream=None):
+    dev = p.means.device
+    P = views.P
+    out = dict(
+        means2d=torch.empty(P, 2, device=dev), conics=torch.empty(P, 3, device=dev),
+        depths=torch.empty(P, device=dev), rects=torch.empty(P, 4, dtype=torch.int16, device=dev),
+        touched=torch.empty(P, dtype=torch.int32, device=dev), K_total=torch.empty(1, dtype=torch.int64, device=dev))
+    B.gs_project(views, p.means, p.quats, p.scales, eps2d, out["means2d"], out["conics"], out["depths"],
+                 out["rects"], out["touched"], out["K_total"], stream)
+    return out
+
+
+def forward(views: B.Views, p: Params, eps2d: float = 0.3, background: Optional[torch.Tensor] = None,
+            K_capacity: Optional[int] = None, stream=None, count_contrib: bool = False) -> Frame:
+    """Projection, binning + sort and compositing of every view.  Without
+    ``K_capacity`` the exact intersection count is read back (one sync)."""
+    _check_params(p)
+    dev = p.means.device
+    pr = project(views, p, eps2d, stream)
+    cap = int(pr["K_total"].item()) if K_capacity is None else int(K_capacity)
+    cap = max(cap, 1)
+    P, T = views.P, views.T
+    ws = torch.empty(B.gs_bin_and_sort_workspace_size(P, cap, T), dtype=torch.uint8, device=dev)
+    isect_ids = torch.empty(cap, dtype=torch.int32, device=dev)
+    isect_pos = torch.empty(cap, dtype=torch.int32, device=dev)
+    emit_start = torch.empty(max(P, 1), dtype=torch.int32, device=dev)
+    tile_ranges = torch.empty(T, 2, dtype=torch.int32, device=dev)
+    K = torch.empty(1, dtype=torch.int32, device=dev)
+    flags = torch.zeros(1, dtype=torch.int32, device=dev)
+    B.gs_bin_and_sort(views, pr["rects"], pr["depths"], pr["touched"], cap, ws, isect_ids, isect_pos, emit_start,
+                      tile_ranges, K, flags, stream)
+    pix = views.pixels
+    out_rgb = torch.empty(pix, 3, device=dev)
+    T_final = torch.empty(pix, device=dev)
+    last_idx = torch.empty(pix, dtype=torch.int32, device=dev)
+    n_contrib = torch.empty(pix, dtype=torch.int32, device=dev) if count_contrib else None
+    B.gs_rasterize_fwd(views, pr["means2d"], pr["conics"], p.opacities, p.colors, isect_ids, tile_ranges, background,
+                       out_rgb, T_final, last_idx, n_contrib, stream)
+    return Frame(views, eps2d, background, cap, pr["means2d"], pr["conics"], pr["depths"], pr["rects"],
+                 pr["touched"], pr["K_total"], isect_ids, isect_pos, emit_start, tile_ranges, K, flags, out_rgb,
+                 T_final, last_idx, ws, n_contrib)
+
+
+def backward(f: Frame, p: Params, dL_drgb: torch.Tensor, stream=None) -> dict:
+    """Gradients of L w.r.t. means, quats, scales, opacities, colors (and the
+    2D intermediates means2d, conics) given dL/dC [pixels, 3]."""
+    dev = p.means.device
+    views = f.views
+    P, N = views.P, p.n
+    dL_drgb = dL_drgb.contiguous().to(torch.float32)
+    g2 = torch.zeros(max(P, 1), 2, device=dev)
+    gc = torch.zeros(max(P, 1), 3, device=dev)
+    go = torch.zeros(max(N, 1), device=dev)
+    gcol = torch.zeros(max(N, 1), 3, device=dev)
+    ws = torch.empty(max(B.gs_rasterize_bwd_workspace_size(f.K_capacity), 1), dtype=torch.uint8, device=dev)
+    B.gs_rasterize_bwd(views, f.means2d, f.conics, p.opacities, p.colors, f.isect_ids, f.isect_pos, f.emit_start,
+                       f.touched, f.tile_ranges, f.K, f.K_capacity, f.background, f.T_final, f.last_idx, dL_drgb, ws,
+                       g2, gc, go, gcol, stream)
+    gm = torch.zeros(max(N, 1), 3, device=dev)
+    gq = torch.zeros(max(N, 1), 4, device=dev)
+    gs = torch.zeros(max(N, 1), 3, device=dev)
+    B.gs_project_bwd(views, p.means, p.quats, p.scales, f.eps2d, f.touched, g2, gc, gm, gq, gs, stream)
+    return dict(means=gm[:N], quats=gq[:N], scales=gs[:N], opacities=go[:N], colors=gcol[:N], means2d=g2[:P],
+                conics=gc[:P])

@@ -1,0 +1,107 @@
+"""Helpers for the GPU parity tests: run the CUDA path through the C ABI on a
+workload and collect numpy copies of everything the oracle is compared with."""
+import numpy as np
+import torch
+
+import oracle
+from paper_2312_02121_gb300 import binding as B
+from paper_2312_02121_gb300 import pipeline
+
+
+def run_gpu(workload, dL_drgb=None, background=None, K_capacity=None, views_subset=None):
+    """Forward (and backward when dL_drgb is given) of every view of the workload.
+    Returns (frame, params, grads or None)."""
+    B.load()
+    dev = "cuda"
+    offs = np.cumsum([0] + [s.n for s in workload.scenes])
+    params = pipeline.Params(*[torch.as_tensor(np.concatenate([getattr(s, k) for s in workload.scenes]),
+                                               dtype=torch.float32).contiguous().to(dev)
+                               for k in ("means", "quats", "scales", "opacities", "colors")])
+    vs = workload.views if views_subset is None else [workload.views[i] for i in views_subset]
+    views = B.Views([v.camera for v in vs], [(int(offs[v.scene]), workload.scenes[v.scene].n) for v in vs], device=dev)
+    bg = None if background is None else torch.as_tensor(background, dtype=torch.float32, device=dev)
+    frame = pipeline.forward(views, params, workload.eps2d, bg, K_capacity)
+    grads = None
+    if dL_drgb is not None:
+        grads = pipeline.backward(frame, params, torch.as_tensor(dL_drgb, dtype=torch.float32, device=dev))
+    torch.cuda.synchronize()
+    return frame, params, grads
+
+
+def np_(t):
+    return t.detach().cpu().numpy()
+
+
+def gpu_projection(frame, i=0):
+    """The CUDA projection of view i as an oracle ``proj`` dict (fp32 values upcast)."""
+    v = frame.views.host[i]
+    s, e = v.proj_offset, v.proj_offset + v.g_count
+    return dict(means2d=np_(frame.means2d[s:e]).astype(np.float64), conics=np_(frame.conics[s:e]).astype(np.float64),
+                depths=np_(frame.depths[s:e]).astype(np.float64), rects=np_(frame.rects[s:e]).astype(np.int32),
+                valid=(np_(frame.touched[s:e]) > 0).astype(np.int32), depths32=np_(frame.depths[s:e]))
+
+
+def view_image(frame, i=0):
+    off, w, h, _ = frame.views.image_slice(i)
+    return (np_(frame.out_rgb[off:off + w * h]).reshape(h, w, 3), np_(frame.T_final[off:off + w * h]).reshape(h, w),
+            np_(frame.last_idx[off:off + w * h]).reshape(h, w))
+
+
+def last_gaussian_ids(frame, i=0):
+    """GPU last composited Gaussian of each pixel of view i, as a projection
+    index local to the view (-1 = none)."""
+    off, w, h, toff = frame.views.image_slice(i)
+    v = frame.views.host[i]
+    last = np_(frame.last_idx[off:off + w * h]).reshape(h, w).astype(np.int64)
+    ranges = np_(frame.tile_ranges)
+    ids = np_(frame.isect_ids)
+    TX = v.tiles_x
+    ys, xs = np.mgrid[0:h, 0:w]
+    tiles = toff + (ys // 16) * TX + xs // 16
+    start = ranges[tiles, 0]
+    out = np.full((h, w), -1, np.int64)
+    has = last >= start
+    has &= last >= 0
+    out[has] = ids[last[has]] - v.proj_offset
+    return out
+
+
+def uncertain_pixels(oracle_fwd, proj, W, H, opacities=None, margin_rel=1e-4, rect_margin_px=1e-3):
+    """Pixels whose result may legitimately differ between fp32 and fp64: a
+    threshold test within ``margin_rel`` (relative), or -- for a Gaussian whose
+    3-sigma box edge lies within ``rect_margin_px`` of a tile line, so that the
+    tile beyond that line may or may not list it -- the pixels of that tile
+    where the Gaussian's alpha reaches 1/255 (elsewhere the flip is inert)."""
+    bad = oracle_fwd["margin"] < margin_rel
+    if "cov2d" not in proj:
+        return bad
+    TX, TY = oracle.tiles(W, H)
+    m2, cov, con = proj["means2d"], proj["cov2d"], proj["conics"]
+    op = np.ones(len(m2)) if opacities is None else np.asarray(opacities, np.float64)
+    ys, xs = np.mgrid[0:H, 0:W]
+    for n in np.nonzero((proj["rect_margin"] < rect_margin_px) & (proj["valid"] > 0))[0]:
+        x0, y0, x1, y1 = proj["rects"][n]
+        rx, ry = 3 * np.sqrt(cov[n, 0]), 3 * np.sqrt(cov[n, 2])
+        for axis, side, edge in ((0, 0, m2[n, 0] - rx), (0, 1, m2[n, 0] + rx), (1, 0, m2[n, 1] - ry),
+                                 (1, 1, m2[n, 1] + ry)):
+            k = int(np.floor(edge / 16 + 0.5))
+            if abs(edge - 16 * k) >= rect_margin_px:
+                continue
+            t = k - 1 if side == 0 else k  # the tile that may flip
+            if axis == 0:
+                if not 0 <= t < TX:
+                    continue
+                sel = (xs // 16 == t) & (ys // 16 >= max(y0 - 1, 0)) & (ys // 16 < y1 + 1)
+            else:
+                if not 0 <= t < TY:
+                    continue
+                sel = (ys // 16 == t) & (xs // 16 >= max(x0 - 1, 0)) & (xs // 16 < x1 + 1)
+            dx, dy = m2[n, 0] - (xs + 0.5), m2[n, 1] - (ys + 0.5)
+            sigma = 0.5 * (con[n, 0] * dx * dx + 2 * con[n, 1] * dx * dy + con[n, 2] * dy * dy)
+            bad |= sel & (op[n] * np.exp(-sigma) >= (1 / 255) * (1 - 1e-3))
+    return bad
+
+
+def rel_l2(a, b):
+    a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))

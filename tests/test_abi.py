@@ -1,0 +1,89 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/gsplat103.h declares; host-only entry points behave as documented.
+No kernel is launched here (these run without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2312_02121_gb300 import build as gsbuild
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gsplat103.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(gs_[a-z0-9_]+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2312_02121_gb300 import binding
+    gsbuild.build()
+    return binding.load()
+
+
+def test_header_declares_the_five_stages():
+    fns = declared_functions()
+    for name in ("gs_project", "gs_bin_and_sort", "gs_rasterize_fwd", "gs_rasterize_bwd", "gs_project_bwd"):
+        assert name in fns
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [f for f in declared_functions() if not hasattr(lib, f)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2312_02121_gb300 import binding
+    assert sorted(binding.SIGNATURES) == declared_functions()
+
+
+def test_version_and_struct_sizes(lib):
+    from paper_2312_02121_gb300 import binding
+    assert binding.gs_version() == 100
+    assert ctypes.sizeof(binding.GsView) == 120
+
+
+def test_views_layout(lib):
+    from paper_2312_02121_gb300 import binding
+    from paper_2312_02121_gb300 import workloads as wl
+    cams = [wl.camera_at_distance(3.0, 40, 20, 50.0), wl.camera_at_distance(3.0, 16, 16, 50.0),
+            wl.camera_at_distance(3.0, 33, 17, 50.0)]
+    v = binding.Views(cams, [(0, 10), (10, 0), (10, 5)], device="cpu")
+    assert (v.V, v.P, v.T, v.pixels) == (3, 15, 3 * 2 + 1 + 3 * 2, 800 + 256 + 561)
+    assert [v.host[i].proj_offset for i in range(3)] == [0, 10, 10]
+    assert [v.host[i].tile_offset for i in range(3)] == [0, 6, 7]
+    assert [v.host[i].pixel_offset for i in range(3)] == [0, 800, 1056]
+    assert [(v.host[i].tiles_x, v.host[i].tiles_y) for i in range(3)] == [(3, 2), (1, 1), (3, 2)]
+
+
+def test_views_layout_rejects_bad_sizes(lib):
+    from paper_2312_02121_gb300 import binding
+    from paper_2312_02121_gb300 import workloads as wl
+    cam = wl.camera_at_distance(3.0, 0, 20, 50.0)
+    with pytest.raises(binding.GsError) as e:
+        binding.Views([cam], [(0, 1)], device="cpu")
+    assert e.value.code == binding.GS_ERR_INVALID_ARG
+
+
+def test_workspace_sizes_grow_with_capacity(lib):
+    from paper_2312_02121_gb300 import binding
+    a = binding.gs_bin_and_sort_workspace_size(1000, 10_000, 64)
+    b = binding.gs_bin_and_sort_workspace_size(1000, 20_000, 64)
+    assert 0 < a < b and a % 256 == 0
+    assert binding.gs_rasterize_bwd_workspace_size(1000) >= 1000 * 9 * 4
+
+
+def test_invalid_arguments_are_rejected_on_the_host(lib):
+    # null pointers / negative sizes return GS_ERR_INVALID_ARG before any CUDA call
+    assert lib.gs_project(None, 1, 10, None, None, None, 0.3, None, None, None, None, None, None, None) == 1
+    assert b"null pointer" in lib.gs_last_error()
+    assert lib.gs_project(None, -1, 10, None, None, None, 0.3, None, None, None, None, None, None, None) == 1
+    assert lib.gs_rasterize_fwd(None, 0, 4, None, None, None, None, None, None, None, None, None, None, None,
+                                None) == 1
+    assert lib.gs_bin_and_sort(None, 1, 10, 4, None, None, None, 100, None, 0, None, None, None, None, None, None,
+                               None) == 1
+    assert lib.gs_project_bwd(None, 1, -5, None, None, None, 0.3, None, None, None, None, None, None, None) == 1

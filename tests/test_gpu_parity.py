@@ -1,0 +1,283 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (fp32 kernels against the fp64 oracle): projected means within
+2e-4 px (+1e-6 relative), conics and depths within 1e-5 relative; tile lists
+and sorted order bit-exact; images and final transmittance within 1e-5
+max-abs; gradients within 1e-4 relative L2.  Pixels where a threshold test
+(alpha 1/255, alpha 0.99, T 1e-4, tile-box edge) lies within fp32 reach of its
+threshold may legitimately differ; they are excluded, counted, and must stay
+rare.  dL/dC is zeroed there for the gradient comparisons.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2312_02121_gb300 import pipeline
+from paper_2312_02121_gb300 import workloads as wl
+from gpu_helpers import (gpu_projection, last_gaussian_ids, np_, rel_l2, run_gpu, uncertain_pixels, view_image)
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+def _workloads():
+    return {
+        "forward_1k_128": lambda: wl.forward_1k_128(),
+        "ragged_2k_100x75": lambda: wl.small_case(5, 2000, 100, 75),
+        "dense_3k_160x120": lambda: wl.small_case(6, 3000, 160, 120, log_scale_mu=-2.6, opacity_logit_mu=1.0),
+        "gradcheck_64_32": lambda: wl.gradcheck_64_32(),
+        "fwdbwd_100k_1024x768": lambda: wl.fwdbwd_100k_1024x768(),
+    }
+
+
+CASES = list(_workloads())
+
+
+@pytest.fixture(scope="module", params=CASES)
+def case(request):
+    w = _workloads()[request.param]()
+    cam, sc = w.views[0].camera, w.scenes[0]
+    rng = np.random.default_rng(42)
+    G = rng.standard_normal((cam.height, cam.width, 3)).astype(np.float32)
+    ofwd = oracle.render(cam, sc, w.eps2d)
+    frame, params, _ = run_gpu(w)
+    # uncertain pixels: end to end (oracle projection) or given the CUDA projection
+    bad = uncertain_pixels(ofwd, ofwd["proj"], cam.width, cam.height, sc.opacities)
+    ogp = oracle.rasterize(gpu_projection(frame), sc.opacities, sc.colors, cam.width, cam.height)
+    bad_gp = ogp["margin"] < 1e-4
+    Gm = np.where((bad | bad_gp)[..., None], 0.0, G).astype(np.float32)
+    grads = pipeline.backward(frame, params, torch.as_tensor(Gm.reshape(-1, 3), device="cuda"))
+    torch.cuda.synchronize()
+    return dict(name=request.param, w=w, cam=cam, sc=sc, G=Gm, ofwd=ofwd, bad=bad, ogp=ogp, bad_gp=bad_gp,
+                frame=frame, grads=grads)
+
+
+def test_projection(case):
+    cam, sc, w = case["cam"], case["sc"], case["w"]
+    op = case["ofwd"]["proj"]
+    gp = gpu_projection(case["frame"])
+    sure = op["rect_margin"] > 1e-3
+    assert sure.mean() > 0.99
+    np.testing.assert_array_equal(gp["valid"][sure], op["valid"][sure])
+    v = (op["valid"] > 0) & (gp["valid"] > 0)
+    np.testing.assert_allclose(gp["means2d"][v], op["means2d"][v], rtol=1e-6, atol=2e-4)
+    np.testing.assert_allclose(gp["depths"][v], op["depths"][v], rtol=1e-6)
+    # per Gaussian, error relative to its largest conic entry (elongated ellipses lose a few digits)
+    rel = np.abs(gp["conics"][v] - op["conics"][v]).max(axis=1) / np.abs(op["conics"][v]).max(axis=1)
+    assert (rel <= 1e-5).mean() > 0.999 and rel.max() <= 1e-3
+    np.testing.assert_array_equal(gp["rects"][v & sure], op["rects"][v & sure])
+
+
+def test_binning_bit_exact(case):
+    f = case["frame"]
+    gp = gpu_projection(f)
+    TX, TY = oracle.tiles(case["cam"])
+    ids, ranges = oracle.bin_tiles(gp["rects"], gp["depths32"], gp["valid"], TX, TY)
+    K = int(np_(f.K)[0])
+    assert K == len(ids) == int(np_(f.K_total)[0])
+    assert not f.overflowed()
+    np.testing.assert_array_equal(np_(f.isect_ids)[:K], ids)
+    np.testing.assert_array_equal(np_(f.tile_ranges), ranges)
+    # every projection finds its own pairs through emit_start / isect_pos
+    touched = np_(f.touched)
+    es, pos, sid = np_(f.emit_start), np_(f.isect_pos)[:K], np_(f.isect_ids)[:K]
+    vis = np.nonzero(touched)[0]
+    owner = np.repeat(vis, touched[vis])
+    e = np.concatenate([es[p] + np.arange(touched[p]) for p in vis]) if len(vis) else np.zeros(0, np.int64)
+    np.testing.assert_array_equal(sid[pos[e]], owner)
+
+
+def test_forward_given_projection(case):
+    # compositing alone: the oracle composites the CUDA path's own fp32 projection
+    cam, sc, f = case["cam"], case["sc"], case["frame"]
+    o, bad = case["ogp"], case["bad_gp"]
+    img, Tf, _ = view_image(f)
+    assert bad.mean() < 0.01
+    assert np.abs(img - o["rgb"])[~bad].max() <= IMG_TOL
+    assert np.abs(Tf - o["T_final"])[~bad].max() <= IMG_TOL
+    np.testing.assert_array_equal(last_gaussian_ids(f)[~bad], o["last_id"][~bad])
+
+
+def test_forward_end_to_end(case):
+    cam, f, bad = case["cam"], case["frame"], case["bad"]
+    img, Tf, _ = view_image(f)
+    assert bad.mean() < 0.02, bad.mean()
+    o = case["ofwd"]
+    assert np.abs(img - o["rgb"])[~bad].max() <= IMG_TOL
+    assert np.abs(Tf - o["T_final"])[~bad].max() <= IMG_TOL
+
+
+def test_backward_2d_given_projection(case):
+    cam, sc, f, g = case["cam"], case["sc"], case["frame"], case["grads"]
+    gp = gpu_projection(f)
+    ob = oracle.rasterize_bwd(gp, sc.opacities, sc.colors, cam.width, cam.height, case["G"])
+    for k in ("means2d", "conics", "opacities", "colors"):
+        assert rel_l2(np_(g[k]), ob[k]) <= GRAD_TOL, k
+
+
+def test_backward_3d_given_2d_gradients(case):
+    # projection backward alone: the oracle maps the CUDA 2D gradients to 3D
+    cam, sc, f, g = case["cam"], case["sc"], case["frame"], case["grads"]
+    gp = gpu_projection(f)
+    ob = oracle.project_bwd(cam, sc.means, sc.quats, sc.scales, gp["valid"], np_(g["means2d"]), np_(g["conics"]),
+                            case["w"].eps2d)
+    for k in ("means", "quats", "scales"):
+        assert rel_l2(np_(g[k]), ob[k]) <= GRAD_TOL, k
+
+
+def test_backward_end_to_end(case):
+    cam, sc, g = case["cam"], case["sc"], case["grads"]
+    ob = oracle.backward(cam, sc, case["G"], case["w"].eps2d)
+    for k in ("means", "quats", "scales", "opacities", "colors"):
+        assert rel_l2(np_(g[k]), ob[k]) <= GRAD_TOL, k
+
+
+def test_background():
+    w = wl.small_case(7, 400, 48, 40)
+    cam, sc = w.views[0].camera, w.scenes[0]
+    bg = np.array([0.25, 0.5, 0.75], np.float32)
+    G = np.random.default_rng(0).standard_normal((40, 48, 3)).astype(np.float32)
+    o = oracle.render(cam, sc, w.eps2d, background=bg)
+    bad = uncertain_pixels(o, o["proj"], 48, 40, sc.opacities)
+    G[bad] = 0
+    f, p, g = run_gpu(w, dL_drgb=G.reshape(-1, 3), background=bg)
+    img, _, _ = view_image(f)
+    assert np.abs(img - o["rgb"])[~bad].max() <= IMG_TOL
+    ob = oracle.backward(cam, sc, G, w.eps2d, background=bg)
+    for k in ("means", "quats", "scales", "opacities", "colors"):
+        assert rel_l2(np_(g[k]), ob[k]) <= GRAD_TOL, k
+
+
+def test_batch_of_views_equals_single_views():
+    # three views of two scenes, uneven sizes, one call == one call per view (bit-exact)
+    a = wl.small_case(8, 300, 40, 24)
+    b = wl.small_case(9, 500, 57, 33)
+    c = wl.small_case(10, 300, 64, 48)
+    c.scenes = a.scenes
+    w = wl.Workload("mix", [a.scenes[0], b.scenes[0]],
+                    [wl.View(0, a.views[0].camera), wl.View(1, b.views[0].camera), wl.View(0, c.views[0].camera)],
+                    None)
+    Gall = np.random.default_rng(1).standard_normal((w.pixels, 3)).astype(np.float32)
+    fb, pb, gb = run_gpu(w, dL_drgb=Gall)
+    off = 0
+    tot = {k: 0 for k in ("means", "quats", "scales", "opacities", "colors")}
+    n0 = a.scenes[0].n
+    for i, v in enumerate(w.views):
+        pix = v.camera.pixels
+        single = wl.Workload("one", [w.scenes[v.scene]], [wl.View(0, v.camera)], None)
+        fs, ps, gs = run_gpu(single, dL_drgb=Gall[off:off + pix])
+        img_b, T_b, _ = view_image(fb, i)
+        img_s, T_s, _ = view_image(fs, 0)
+        np.testing.assert_array_equal(img_b, img_s)
+        np.testing.assert_array_equal(T_b, T_s)
+        sl = slice(0, n0) if v.scene == 0 else slice(n0, n0 + b.scenes[0].n)
+        for k in tot:
+            exp = np.zeros_like(np_(gb[k]))
+            exp[sl] = np_(gs[k])
+            tot[k] = tot[k] + exp
+        off += pix
+    for k in tot:
+        np.testing.assert_allclose(np_(gb[k]), tot[k], rtol=1e-5, atol=1e-7 * np.abs(tot[k]).max())
+
+
+def test_deterministic_and_cull_invariant():
+    w = wl.small_case(11, 3000, 150, 110, log_scale_mu=-2.4, opacity_logit_mu=0.8)
+    G = np.random.default_rng(3).standard_normal((w.pixels, 3)).astype(np.float32)
+    f1, _, g1 = run_gpu(w, dL_drgb=G)
+    f2, _, g2 = run_gpu(w, dL_drgb=G)
+    os.environ["GS_NO_CULL"] = "1"
+    try:
+        f3, _, g3 = run_gpu(w, dL_drgb=G)
+    finally:
+        del os.environ["GS_NO_CULL"]
+    for f in (f2, f3):
+        np.testing.assert_array_equal(np_(f1.out_rgb), np_(f.out_rgb))
+        np.testing.assert_array_equal(np_(f1.last_idx), np_(f.last_idx))
+        np.testing.assert_array_equal(np_(f1.isect_ids), np_(f.isect_ids))
+    for g in (g2, g3):
+        for k in ("means2d", "conics", "means", "quats", "scales", "opacities", "colors"):
+            np.testing.assert_array_equal(np_(g1[k]), np_(g[k]), err_msg=k)
+
+
+def test_edge_case_no_gaussians_visible():
+    w = wl.small_case(12, 50, 40, 30)
+    w.scenes[0].means[:, 2] = -20.0  # all behind the camera
+    bg = np.array([0.1, 0.2, 0.3], np.float32)
+    f, p, g = run_gpu(w, dL_drgb=np.ones((w.pixels, 3), np.float32), background=bg)
+    assert int(np_(f.K)[0]) == 0 and int(np_(f.touched).sum()) == 0
+    img, Tf, _ = view_image(f)
+    np.testing.assert_array_equal(img, np.broadcast_to(bg, img.shape))
+    np.testing.assert_array_equal(Tf, 1.0)
+    for k in ("means", "quats", "scales", "opacities", "colors"):
+        assert not np_(g[k]).any()
+
+
+def test_edge_case_empty_scene():
+    w = wl.small_case(13, 1, 33, 17)
+    for k in ("means", "quats", "scales", "opacities", "colors"):
+        setattr(w.scenes[0], k, getattr(w.scenes[0], k)[:0])
+    f, p, g = run_gpu(w, dL_drgb=np.ones((w.pixels, 3), np.float32))
+    img, Tf, last = view_image(f)
+    assert not img.any() and (Tf == 1).all()
+
+
+def test_edge_case_one_gaussian_over_every_tile():
+    w = wl.small_case(14, 1, 70, 50)
+    sc = w.scenes[0]
+    sc.means[:] = [[0.0, 0.0, 0.0]]
+    sc.scales[:] = [[2.0, 1.5, 1.0]]
+    sc.opacities[:] = [0.8]
+    G = np.random.default_rng(4).standard_normal((50, 70, 3)).astype(np.float32)
+    cam = w.views[0].camera
+    o = oracle.render(cam, sc, w.eps2d)
+    assert o["proj"]["rects"][0].tolist() == [0, 0, 5, 4]
+    f, p, g = run_gpu(w, dL_drgb=G)
+    img, _, _ = view_image(f)
+    assert np.abs(img - o["rgb"]).max() <= IMG_TOL
+    ob = oracle.backward(cam, sc, G, w.eps2d)
+    for k in ("means", "quats", "scales", "opacities", "colors"):
+        assert rel_l2(np_(g[k]), ob[k]) <= GRAD_TOL, k
+
+
+def test_capacity_overflow_is_flagged():
+    w = wl.small_case(15, 500, 64, 64)
+    f, _, _ = run_gpu(w, K_capacity=16)
+    assert int(np_(f.K_total)[0]) > 16
+    assert f.overflowed()
+    f2, _, _ = run_gpu(w)
+    assert not f2.overflowed()
+
+
+def test_full_size_1080p_sampled_pixels():
+    # 1,000,000 Gaussians at 1920x1080, in the benchmark's launch configuration;
+    # the oracle composites a seeded sample of pixels from the CUDA projection.
+    w = wl.fwdbwd_1m_1080p()
+    cam, sc = w.views[0].camera, w.scenes[0]
+    rng = np.random.default_rng(5)
+    pix = np.sort(rng.choice(cam.pixels, 1500, replace=False))
+    G = np.zeros((cam.pixels, 3), np.float32)
+    G[pix] = rng.standard_normal((len(pix), 3))
+    f, p, g = run_gpu(w, dL_drgb=G)
+    assert not f.overflowed()
+    gp = gpu_projection(f)
+    o = oracle.rasterize(gp, sc.opacities, sc.colors, cam.width, cam.height, pixels=pix)
+    img, Tf, _ = view_image(f)
+    ok = o["margin"] >= 1e-4
+    assert ok.mean() > 0.98
+    assert np.abs(img.reshape(-1, 3)[pix] - o["rgb"])[ok].max() <= IMG_TOL
+    assert np.abs(Tf.reshape(-1)[pix] - o["T_final"])[ok].max() <= IMG_TOL
+    Gs = np.where(ok[:, None], G[pix], 0.0)
+    G2 = np.zeros_like(G)
+    G2[pix] = Gs
+    f2, p2, g2 = run_gpu(w, dL_drgb=G2)
+    ob = oracle.rasterize_bwd(gp, sc.opacities, sc.colors, cam.width, cam.height, Gs, pixels=pix)
+    for k in ("means2d", "conics", "opacities", "colors"):
+        assert rel_l2(np_(g2[k]), ob[k]) <= GRAD_TOL, k
+    # properties at every pixel
+    assert np.isfinite(img).all() and (Tf > 0).all() and (Tf <= 1).all()

@@ -166,6 +166,39 @@ int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_t T_total, 
                     size_t workspace_bytes, int32_t* isect_ids, int32_t* isect_pos, int32_t* emit_start,
                     int32_t* tile_ranges, int32_t* K_out, uint32_t* flags, void* stream);
 
+/* Size limits of gs_bin_and_sort_static. */
+#define GS_STATIC_MAX_PROJECTIONS 131072
+#define GS_STATIC_MAX_INTERSECTIONS 1048576
+
+/*
+ * gs_bin_and_sort without a workspace argument, for callers that cannot
+ * allocate device memory themselves: code that receives device pointers from a
+ * host application that owns all allocations (a plugin, an embedded renderer)
+ * and has no allocator of its own to call, or a real-time loop that must not
+ * call cudaMalloc/cudaFree after start-up because they synchronise the device.
+ * The paper has no counterpart; it is an interface convenience.
+ *
+ * The scratch gs_bin_and_sort needs lives in one fixed array in this
+ * library's device memory (a file-scope __device__ array of about 22 MB),
+ * which every GPU that loads the library holds until the process exits.  So:
+ *  - P must be <= GS_STATIC_MAX_PROJECTIONS and K_capacity <=
+ *    GS_STATIC_MAX_INTERSECTIONS; larger sizes return GS_ERR_INVALID_ARG.
+ *  - All calls share that one array and it keeps the previous call's
+ *    contents; nothing in it needs to start at zero (every kernel writes what
+ *    it later reads).  Calls whose work overlaps on the GPU (different
+ *    streams, or several host threads) race on it and give wrong results:
+ *    serialise them, e.g. on one stream.
+ *  - The first call on each device looks up the array's device address with
+ *    cudaGetSymbolAddress while that device is current; make that first call
+ *    before any stream capture begins.
+ * The call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine.  Arguments and outputs are those of gs_bin_and_sort.
+ */
+int gs_bin_and_sort_static(const GsView* views, int32_t V, int64_t P, int32_t T_total, const int16_t* rects,
+                           const float* depths, const int32_t* touched, int64_t K_capacity, int32_t* isect_ids,
+                           int32_t* isect_pos, int32_t* emit_start, int32_t* tile_ranges, int32_t* K_out,
+                           uint32_t* flags, void* stream);
+
 /*
  * Sec. 2.2, Eq. 7: for every pixel of every view, walks its tile's sorted list
  * front to back: sigma = 1/2 Delta^T Y Delta with Delta = mu' - pixel centre,

@@ -67,6 +67,7 @@ SIGNATURES = {
     "gs_project": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _F, _P, _P, _P, _P, _P, _P, _P]),
     "gs_bin_and_sort_workspace_size": (_SZ, [_I64, _I64, _I32]),
     "gs_bin_and_sort": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _I64, _P, _SZ, _P, _P, _P, _P, _P, _P, _P]),
+    "gs_bin_and_sort_static": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _P]),
     "gs_rasterize_fwd": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gs_rasterize_bwd_workspace_size": (_SZ, [_I64]),
     "gs_rasterize_bwd": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P,
@@ -195,6 +196,15 @@ def gs_bin_and_sort(views: Views, rects, depths, touched, K_capacity: int, works
                                   _ptr(touched), int(K_capacity), _ptr(workspace),
                                   workspace.numel() * workspace.element_size(), _ptr(isect_ids), _ptr(isect_pos),
                                   _ptr(emit_start), _ptr(tile_ranges), _ptr(K_out), _ptr(flags), _stream(stream)))
+
+
+def gs_bin_and_sort_static(views: Views, rects, depths, touched, K_capacity: int, isect_ids, isect_pos, emit_start,
+                           tile_ranges, K_out, flags, stream=None):
+    """gs_bin_and_sort with the library's fixed device scratch (no workspace)."""
+    _check(load().gs_bin_and_sort_static(_ptr(views.device), views.V, views.P, views.T, _ptr(rects), _ptr(depths),
+                                         _ptr(touched), int(K_capacity), _ptr(isect_ids), _ptr(isect_pos),
+                                         _ptr(emit_start), _ptr(tile_ranges), _ptr(K_out), _ptr(flags),
+                                         _stream(stream)))
 
 
 def gs_rasterize_fwd(views: Views, means2d, conics, opacities, colors, isect_ids, tile_ranges, background,

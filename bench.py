@@ -153,20 +153,21 @@ def oracle_step(oracle, w, pix):
 
 
 def sized_sample(oracle, w, seconds: float):
-    """Tile count whose oracle step takes about ``seconds`` on this host
-    (linear fit of two probes: the fixed projection cost plus a per-tile cost)."""
+    """Tile count whose oracle step takes about ``seconds`` on this host: grows
+    a seeded tile sample (x4 per probe) until a step takes at least half the
+    target, then scales linearly; the whole frame at most."""
     cam = w.views[0].camera
     TX, TY = (cam.width + 15) // 16, (cam.height + 15) // 16
-    probes = []
-    for n in (16, 64):
+    n, dt = 16, 0.0
+    while True:
         pix = tile_sample(cam, n)
         t0 = time.perf_counter()
         oracle_step(oracle, w, pix)
-        probes.append((n, time.perf_counter() - t0))
-    (n0, t0_), (n1, t1_) = probes
-    per_tile = max((t1_ - t0_) / (n1 - n0), 1e-6)
-    fixed = max(t0_ - per_tile * n0, 0.0)
-    return int(min(TX * TY, max(16, (seconds - fixed) / per_tile)))
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * seconds or n >= TX * TY:
+            break
+        n = min(TX * TY, n * 4)
+    return int(min(TX * TY, max(16, n * seconds / max(dt, 1e-3))))
 
 
 def cpu_baseline(w, seconds: float):
@@ -285,9 +286,8 @@ def run_ours(args, rank, world, local_rank):
         gc = torch.zeros(P, 3, device=dev)
         go = torch.zeros(sc.n, device=dev)
         gcol = torch.zeros(sc.n, 3, device=dev)
-        wsb = torch.empty(B.gs_rasterize_bwd_workspace_size(cap), dtype=torch.uint8, device=dev)
         B.gs_rasterize_bwd(views, pr["means2d"], pr["conics"], params.opacities, params.colors, ids, pos, es,
-                           pr["touched"], tr, Kd, cap, None, Tf, last, dL, wsb, g2, gc, go, gcol)
+                           pr["touched"], tr, Kd, cap, None, Tf, last, dL, False, None, g2, gc, go, gcol)
         mark(5)
         gm = torch.zeros(sc.n, 3, device=dev)
         gq = torch.zeros(sc.n, 4, device=dev)

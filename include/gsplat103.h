@@ -218,8 +218,9 @@ int gs_rasterize_fwd(const GsView* views, int32_t V, int32_t T_total, const floa
                      const int32_t* isect_ids, const int32_t* tile_ranges, const float* background,
                      float* out_rgb, float* T_final, int32_t* last_idx, int32_t* n_contrib, void* stream);
 
-/* Bytes of scratch gs_rasterize_bwd needs for K_capacity intersections. */
-size_t gs_rasterize_bwd_workspace_size(int64_t K_capacity);
+/* Bytes of scratch gs_rasterize_bwd needs for K_capacity intersections:
+ * 0 unless deterministic. */
+size_t gs_rasterize_bwd_workspace_size(int64_t K_capacity, int32_t deterministic);
 
 /*
  * Sec. 3.1: back to front from each pixel's last composited Gaussian,
@@ -230,12 +231,19 @@ size_t gs_rasterize_bwd_workspace_size(int64_t K_capacity);
  *   dalpha/do = exp(-sigma), dalpha/dsigma = -o exp(-sigma) (both 0 where the
  *   0.99 clamp was active), dsigma/dmu' = Y Delta, dsigma/d(a,b,c) =
  *   (Delta_x^2/2, Delta_x Delta_y, Delta_y^2/2).
- * Per-pixel terms are summed per (tile, Gaussian) inside each tile and then
- * per projection over its tiles in a fixed order, so results are
- * deterministic (no floating-point atomics across tiles).
+ * Per-pixel terms are first summed per (tile, Gaussian) inside each tile (warp
+ * reduce-scatter, then a fixed-order sum over the tile's warps).  The tile sums
+ * then reach the per-projection outputs in one of two ways:
+ *   deterministic == 0: vector reduction atomics (fast; the fp32 order of the
+ *     tile sums varies from run to run);
+ *   deterministic != 0: written as records in workspace and summed per
+ *     projection in emission order by a second kernel -- run-to-run identical
+ *     for a single view (opacities/colors of a scene seen by several views are
+ *     still summed over views with atomics).
  *   in : the forward's inputs and outputs, dL_drgb[pix,3], K_capacity,
- *        K (device int32 from gs_bin_and_sort), isect_pos, emit_start,
- *        touched, workspace (>= gs_rasterize_bwd_workspace_size bytes)
+ *        K (device int32 from gs_bin_and_sort), isect_pos, emit_start, touched
+ *        (these four are read only when deterministic; may be NULL otherwise),
+ *        workspace (>= gs_rasterize_bwd_workspace_size bytes)
  *   out (ACCUMULATED: += into caller-initialised buffers):
  *        dL_dmeans2d[P,2], dL_dconics[P,3] (per projection),
  *        dL_dopacities[N], dL_dcolors[N,3] (per Gaussian, summed over views).
@@ -245,9 +253,9 @@ int gs_rasterize_bwd(const GsView* views, int32_t V, int64_t P, int32_t T_total,
                      const int32_t* isect_ids, const int32_t* isect_pos, const int32_t* emit_start,
                      const int32_t* touched, const int32_t* tile_ranges, const int32_t* K,
                      int64_t K_capacity, const float* background, const float* T_final,
-                     const int32_t* last_idx, const float* dL_drgb, void* workspace, size_t workspace_bytes,
-                     float* dL_dmeans2d, float* dL_dconics, float* dL_dopacities, float* dL_dcolors,
-                     void* stream);
+                     const int32_t* last_idx, const float* dL_drgb, int32_t deterministic, void* workspace,
+                     size_t workspace_bytes, float* dL_dmeans2d, float* dL_dconics, float* dL_dopacities,
+                     float* dL_dcolors, void* stream);
 
 /*
  * Sec. 3.2 (Eq. 16-20) and 3.2.1: for every projection with touched > 0,

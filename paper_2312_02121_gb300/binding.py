@@ -69,9 +69,9 @@ SIGNATURES = {
     "gs_bin_and_sort": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _I64, _P, _SZ, _P, _P, _P, _P, _P, _P, _P]),
     "gs_bin_and_sort_static": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _P]),
     "gs_rasterize_fwd": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
-    "gs_rasterize_bwd_workspace_size": (_SZ, [_I64]),
+    "gs_rasterize_bwd_workspace_size": (_SZ, [_I64, _I32]),
     "gs_rasterize_bwd": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P,
-                                        _P, _P, _P, _SZ, _P, _P, _P, _P, _P]),
+                                        _P, _P, _I32, _P, _SZ, _P, _P, _P, _P, _P]),
     "gs_project_bwd": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _F, _P, _P, _P, _P, _P, _P, _P]),
 }
 
@@ -215,20 +215,20 @@ def gs_rasterize_fwd(views: Views, means2d, conics, opacities, colors, isect_ids
                                    _ptr(n_contrib), _stream(stream)))
 
 
-def gs_rasterize_bwd_workspace_size(K_capacity: int) -> int:
-    return int(load().gs_rasterize_bwd_workspace_size(K_capacity))
+def gs_rasterize_bwd_workspace_size(K_capacity: int, deterministic: bool = False) -> int:
+    return int(load().gs_rasterize_bwd_workspace_size(K_capacity, int(bool(deterministic))))
 
 
 def gs_rasterize_bwd(views: Views, means2d, conics, opacities, colors, isect_ids, isect_pos, emit_start, touched,
-                     tile_ranges, K, K_capacity: int, background, T_final, last_idx, dL_drgb, workspace,
-                     dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors, stream=None):
+                     tile_ranges, K, K_capacity: int, background, T_final, last_idx, dL_drgb, deterministic: bool,
+                     workspace, dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors, stream=None):
+    nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(load().gs_rasterize_bwd(_ptr(views.device), views.V, views.P, views.T, _ptr(means2d), _ptr(conics),
                                    _ptr(opacities), _ptr(colors), _ptr(isect_ids), _ptr(isect_pos),
                                    _ptr(emit_start), _ptr(touched), _ptr(tile_ranges), _ptr(K), int(K_capacity),
                                    _ptr(background), _ptr(T_final), _ptr(last_idx), _ptr(dL_drgb),
-                                   _ptr(workspace), workspace.numel() * workspace.element_size(),
-                                   _ptr(dL_dmeans2d), _ptr(dL_dconics), _ptr(dL_dopacities), _ptr(dL_dcolors),
-                                   _stream(stream)))
+                                   int(bool(deterministic)), _ptr(workspace), nbytes, _ptr(dL_dmeans2d),
+                                   _ptr(dL_dconics), _ptr(dL_dopacities), _ptr(dL_dcolors), _stream(stream)))
 
 
 def gs_project_bwd(views: Views, means, quats, scales, eps2d: float, touched, dL_dmeans2d, dL_dconics, dL_dmeans,

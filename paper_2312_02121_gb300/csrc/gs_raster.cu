@@ -49,7 +49,7 @@ __device__ __forceinline__ float ex2(float x)
 //   g.q   : -log2e/2 * a, k = b/a, -log2e/2 * D, b     (D = det/a = c - b^2/a)
 //   g.col : r, g, b, D
 //   g.cull: sigma threshold (<0: never reaches 1/255; +inf: never culled),
-//           -b/c, c, unused
+//           -b/c, c, (backward: the projection index, as int bits)
 struct Staged {
     float4 xy, q, col, cull;
 };
@@ -281,13 +281,19 @@ __device__ __forceinline__ float warp_sum9(const float (&v)[kRec], int lane)
     return w1 + __shfl_xor_sync(kFull, w1, 1);
 }
 
-template <bool kCull>
-__global__ void __launch_bounds__(256)
+// kAtomic: each (tile, Gaussian) sum is added straight into the per-projection
+// outputs with vector reduction atomics (fast; fp32 summation order across
+// tiles varies).  Otherwise it is written as a record for k_reduce_records
+// (deterministic).
+template <bool kCull, bool kAtomic>
+__global__ void __launch_bounds__(256, 5)
 k_raster_bwd(const GsView* __restrict__ views, int V, const float2* __restrict__ means2d,
              const float* __restrict__ conics, const float* __restrict__ opacities, const float* __restrict__ colors,
              const int32_t* __restrict__ isect_ids, const int2* __restrict__ tile_ranges,
              const float* __restrict__ background, const float* __restrict__ T_final,
-             const int32_t* __restrict__ last_idx, const float* __restrict__ dL_drgb, float* __restrict__ records)
+             const int32_t* __restrict__ last_idx, const float* __restrict__ dL_drgb, float* __restrict__ records,
+             float2* __restrict__ dL_dmeans2d, float* __restrict__ dL_dconics, float* __restrict__ dL_dopacities,
+             float* __restrict__ dL_dcolors)
 {
     __shared__ float4 sh_xy[kBwdBatch], sh_q[kBwdBatch], sh_col[kBwdBatch], sh_cull[kBwdBatch];
     __shared__ float s_grad[kWarps][kBwdBatch][kRec];
@@ -329,6 +335,7 @@ k_raster_bwd(const GsView* __restrict__ views, int V, const float2* __restrict__
             const int64_t g = p + t.g_shift;
             stage_gaussian(sh_xy, sh_q, sh_col, sh_cull, threadIdx.x, means2d[p], conics[3 * p], conics[3 * p + 1],
                            conics[3 * p + 2], opacities[g], colors[3 * g], colors[3 * g + 1], colors[3 * g + 2]);
+            sh_cull[threadIdx.x].w = __int_as_float(p);  // the projection, for the atomic flush
         }
         __syncthreads();
         // this warp only needs entries up to its own last index
@@ -396,30 +403,49 @@ k_raster_bwd(const GsView* __restrict__ views, int V, const float2* __restrict__
             if (lane == 0) s_mask[w][s >> 5] = chunk_mask;
         }
         __syncthreads();
-        // fixed-order sum over warps, one record per (tile, Gaussian)
+        // fixed-order sum over warps: one (tile, Gaussian) partial
         if (threadIdx.x < n) {
             const int j = threadIdx.x;
             float acc[kRec];
 #pragma unroll
             for (int q = 0; q < kRec; ++q) acc[q] = 0.f;
+            bool any = false;
 #pragma unroll
             for (int ww = 0; ww < kWarps; ++ww)
                 if (s_mask[ww][j >> 5] & (1u << (j & 31))) {
+                    any = true;
 #pragma unroll
                     for (int q = 0; q < kRec; ++q) acc[q] += s_grad[ww][j][q];
                 }
-            float* rec = records + (size_t)(b0 + j) * kRec;
+            if (kAtomic) {
+                if (any) {
+                    const int p = __float_as_int(sh_cull[j].w);
+                    const int64_t g = p + t.g_shift;
+                    atomicAdd(dL_dmeans2d + p, make_float2(acc[0], acc[1]));
+                    atomicAdd(dL_dconics + 3 * p + 0, acc[2]);
+                    atomicAdd(dL_dconics + 3 * p + 1, acc[3]);
+                    atomicAdd(dL_dconics + 3 * p + 2, acc[4]);
+                    atomicAdd(dL_dopacities + g, acc[5]);
+                    atomicAdd(dL_dcolors + 3 * g + 0, acc[6]);
+                    atomicAdd(dL_dcolors + 3 * g + 1, acc[7]);
+                    atomicAdd(dL_dcolors + 3 * g + 2, acc[8]);
+                }
+            } else {
+                float* rec = records + (size_t)(b0 + j) * kRec;
 #pragma unroll
-            for (int q = 0; q < kRec; ++q) rec[q] = acc[q];
+                for (int q = 0; q < kRec; ++q) rec[q] = acc[q];
+            }
         }
         __syncthreads();
     }
-    // Gaussians after every pixel's last one received nothing
-    const int first_unused = max(range.x, maxlast + 1);
-    for (int i = first_unused + threadIdx.x; i < range.y; i += blockDim.x) {
-        float* rec = records + (size_t)i * kRec;
+    if (!kAtomic) {
+        // Gaussians after every pixel's last one received nothing
+        const int first_unused = max(range.x, maxlast + 1);
+        for (int i = first_unused + threadIdx.x; i < range.y; i += blockDim.x) {
+            float* rec = records + (size_t)i * kRec;
 #pragma unroll
-        for (int q = 0; q < kRec; ++q) rec[q] = 0.f;
+            for (int q = 0; q < kRec; ++q) rec[q] = 0.f;
+        }
     }
 }
 
@@ -494,10 +520,10 @@ extern "C" int gs_rasterize_fwd(const GsView* views, int32_t V, int32_t T_total,
     return launch_status("gs_rasterize_fwd");
 }
 
-extern "C" size_t gs_rasterize_bwd_workspace_size(int64_t K_capacity)
+extern "C" size_t gs_rasterize_bwd_workspace_size(int64_t K_capacity, int32_t deterministic)
 {
     if (K_capacity < 0) return 0;
-    return align256((size_t)K_capacity * kRec * sizeof(float));
+    return deterministic ? align256((size_t)K_capacity * kRec * sizeof(float)) : 0;
 }
 
 extern "C" int gs_rasterize_bwd(const GsView* views, int32_t V, int64_t P, int32_t T_total, const float* means2d,
@@ -505,33 +531,40 @@ extern "C" int gs_rasterize_bwd(const GsView* views, int32_t V, int64_t P, int32
                                 const int32_t* isect_ids, const int32_t* isect_pos, const int32_t* emit_start,
                                 const int32_t* touched, const int32_t* tile_ranges, const int32_t* K,
                                 int64_t K_capacity, const float* background, const float* T_final,
-                                const int32_t* last_idx, const float* dL_drgb, void* workspace,
-                                size_t workspace_bytes, float* dL_dmeans2d, float* dL_dconics, float* dL_dopacities,
-                                float* dL_dcolors, void* stream)
+                                const int32_t* last_idx, const float* dL_drgb, int32_t deterministic,
+                                void* workspace, size_t workspace_bytes, float* dL_dmeans2d, float* dL_dconics,
+                                float* dL_dopacities, float* dL_dcolors, void* stream)
 {
     if (V <= 0 || P < 0 || T_total < 0 || K_capacity < 0 || K_capacity >= (int64_t(1) << 31))
         return fail(GS_ERR_INVALID_ARG, "gs_rasterize_bwd: V=%d P=%lld T_total=%d K_capacity=%lld", V, (long long)P,
                     T_total, (long long)K_capacity);
-    if (!views || !tile_ranges || !K || !T_final || !last_idx || !dL_drgb ||
-        (P > 0 && (!touched || !emit_start || !dL_dmeans2d || !dL_dconics || !dL_dopacities || !dL_dcolors)))
+    if (!views || !tile_ranges || !T_final || !last_idx || !dL_drgb ||
+        (P > 0 && (!dL_dmeans2d || !dL_dconics || !dL_dopacities || !dL_dcolors)) ||
+        (deterministic && P > 0 && (!K || !touched || !emit_start || !isect_pos)))
         return fail(GS_ERR_INVALID_ARG, "gs_rasterize_bwd: null pointer argument");
     if ((reinterpret_cast<uintptr_t>(means2d) & 7) || (reinterpret_cast<uintptr_t>(dL_dmeans2d) & 7) ||
         (reinterpret_cast<uintptr_t>(tile_ranges) & 7))
         return fail(GS_ERR_INVALID_ARG, "gs_rasterize_bwd: float2 arrays need 8-byte alignment");
-    if (workspace_bytes < gs_rasterize_bwd_workspace_size(K_capacity) || (K_capacity > 0 && !workspace))
-        return fail(GS_ERR_INVALID_ARG, "gs_rasterize_bwd: workspace of %zu bytes, need %zu", workspace_bytes,
-                    gs_rasterize_bwd_workspace_size(K_capacity));
+    const size_t need = gs_rasterize_bwd_workspace_size(K_capacity, deterministic);
+    if (workspace_bytes < need || (need > 0 && !workspace))
+        return fail(GS_ERR_INVALID_ARG, "gs_rasterize_bwd: workspace of %zu bytes, need %zu", workspace_bytes, need);
     if (T_total == 0 || P == 0) return GS_OK;
     cudaStream_t s = as_stream(stream);
     float* records = static_cast<float*>(workspace);
-    auto kern = cull_enabled() ? k_raster_bwd<true> : k_raster_bwd<false>;
+    const bool cull = cull_enabled();
+    auto kern = deterministic ? (cull ? k_raster_bwd<true, false> : k_raster_bwd<false, false>)
+                              : (cull ? k_raster_bwd<true, true> : k_raster_bwd<false, true>);
     kern<<<(unsigned)T_total, 256, 0, s>>>(views, V, reinterpret_cast<const float2*>(means2d), conics, opacities,
                                            colors, isect_ids, reinterpret_cast<const int2*>(tile_ranges), background,
-                                           T_final, last_idx, dL_drgb, records);
-    k_reduce_records<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(views, V, P, touched, emit_start, isect_pos, K,
-                                                                  K_capacity, records,
-                                                                  reinterpret_cast<float2*>(dL_dmeans2d), dL_dconics,
-                                                                  dL_dopacities, dL_dcolors);
-    count_launches(2);
+                                           T_final, last_idx, dL_drgb, records,
+                                           reinterpret_cast<float2*>(dL_dmeans2d), dL_dconics, dL_dopacities,
+                                           dL_dcolors);
+    count_launches(1);
+    if (deterministic) {
+        k_reduce_records<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(
+            views, V, P, touched, emit_start, isect_pos, K, K_capacity, records,
+            reinterpret_cast<float2*>(dL_dmeans2d), dL_dconics, dL_dopacities, dL_dcolors);
+        count_launches(1);
+    }
     return launch_status("gs_rasterize_bwd");
 }

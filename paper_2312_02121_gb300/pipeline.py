@@ -122,9 +122,10 @@ def forward(views: B.Views, p: Params, eps2d: float = 0.3, background: Optional[
                  T_final, last_idx, ws, n_contrib)
 
 
-def backward(f: Frame, p: Params, dL_drgb: torch.Tensor, stream=None) -> dict:
+def backward(f: Frame, p: Params, dL_drgb: torch.Tensor, stream=None, deterministic: bool = False) -> dict:
     """Gradients of L w.r.t. means, quats, scales, opacities, colors (and the
-    2D intermediates means2d, conics) given dL/dC [pixels, 3]."""
+    2D intermediates means2d, conics) given dL/dC [pixels, 3].
+    ``deterministic`` selects the run-to-run identical reduction."""
     dev = p.means.device
     views = f.views
     P, N = views.P, p.n
@@ -133,10 +134,11 @@ def backward(f: Frame, p: Params, dL_drgb: torch.Tensor, stream=None) -> dict:
     gc = torch.zeros(max(P, 1), 3, device=dev)
     go = torch.zeros(max(N, 1), device=dev)
     gcol = torch.zeros(max(N, 1), 3, device=dev)
-    ws = torch.empty(max(B.gs_rasterize_bwd_workspace_size(f.K_capacity), 1), dtype=torch.uint8, device=dev)
+    nws = B.gs_rasterize_bwd_workspace_size(f.K_capacity, deterministic)
+    ws = torch.empty(nws, dtype=torch.uint8, device=dev) if nws else None
     B.gs_rasterize_bwd(views, f.means2d, f.conics, p.opacities, p.colors, f.isect_ids, f.isect_pos, f.emit_start,
-                       f.touched, f.tile_ranges, f.K, f.K_capacity, f.background, f.T_final, f.last_idx, dL_drgb, ws,
-                       g2, gc, go, gcol, stream)
+                       f.touched, f.tile_ranges, f.K, f.K_capacity, f.background, f.T_final, f.last_idx, dL_drgb,
+                       deterministic, ws, g2, gc, go, gcol, stream)
     gm = torch.zeros(max(N, 1), 3, device=dev)
     gq = torch.zeros(max(N, 1), 4, device=dev)
     gs = torch.zeros(max(N, 1), 3, device=dev)

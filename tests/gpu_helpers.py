@@ -8,7 +8,7 @@ from paper_2312_02121_gb300 import binding as B
 from paper_2312_02121_gb300 import pipeline
 
 
-def run_gpu(workload, dL_drgb=None, background=None, K_capacity=None, views_subset=None):
+def run_gpu(workload, dL_drgb=None, background=None, K_capacity=None, views_subset=None, deterministic=False):
     """Forward (and backward when dL_drgb is given) of every view of the workload.
     Returns (frame, params, grads or None)."""
     B.load()
@@ -23,7 +23,8 @@ def run_gpu(workload, dL_drgb=None, background=None, K_capacity=None, views_subs
     frame = pipeline.forward(views, params, workload.eps2d, bg, K_capacity)
     grads = None
     if dL_drgb is not None:
-        grads = pipeline.backward(frame, params, torch.as_tensor(dL_drgb, dtype=torch.float32, device=dev))
+        grads = pipeline.backward(frame, params, torch.as_tensor(dL_drgb, dtype=torch.float32, device=dev),
+                                  deterministic=deterministic)
     torch.cuda.synchronize()
     return frame, params, grads
 

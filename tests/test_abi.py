@@ -74,7 +74,8 @@ def test_workspace_sizes_grow_with_capacity(lib):
     a = binding.gs_bin_and_sort_workspace_size(1000, 10_000, 64)
     b = binding.gs_bin_and_sort_workspace_size(1000, 20_000, 64)
     assert 0 < a < b and a % 256 == 0
-    assert binding.gs_rasterize_bwd_workspace_size(1000) >= 1000 * 9 * 4
+    assert binding.gs_rasterize_bwd_workspace_size(1000, True) >= 1000 * 9 * 4
+    assert binding.gs_rasterize_bwd_workspace_size(1000, False) == 0
 
 
 def test_invalid_arguments_are_rejected_on_the_host(lib):

@@ -187,22 +187,30 @@ def test_batch_of_views_equals_single_views():
 
 
 def test_deterministic_and_cull_invariant():
+    # deterministic mode: bit-identical across runs and with the pair cull disabled;
+    # atomic mode: equal to it up to fp32 summation order (1e-5 relative L2: the
+    # quaternion gradient sums terms of both signs, so reordering shows most there)
     w = wl.small_case(11, 3000, 150, 110, log_scale_mu=-2.4, opacity_logit_mu=0.8)
     G = np.random.default_rng(3).standard_normal((w.pixels, 3)).astype(np.float32)
-    f1, _, g1 = run_gpu(w, dL_drgb=G)
-    f2, _, g2 = run_gpu(w, dL_drgb=G)
+    f1, _, g1 = run_gpu(w, dL_drgb=G, deterministic=True)
+    f2, _, g2 = run_gpu(w, dL_drgb=G, deterministic=True)
     os.environ["GS_NO_CULL"] = "1"
     try:
-        f3, _, g3 = run_gpu(w, dL_drgb=G)
+        f3, _, g3 = run_gpu(w, dL_drgb=G, deterministic=True)
+        f5, _, g5 = run_gpu(w, dL_drgb=G)
     finally:
         del os.environ["GS_NO_CULL"]
-    for f in (f2, f3):
+    f4, _, g4 = run_gpu(w, dL_drgb=G)
+    for f in (f2, f3, f4, f5):
         np.testing.assert_array_equal(np_(f1.out_rgb), np_(f.out_rgb))
         np.testing.assert_array_equal(np_(f1.last_idx), np_(f.last_idx))
         np.testing.assert_array_equal(np_(f1.isect_ids), np_(f.isect_ids))
     for g in (g2, g3):
         for k in ("means2d", "conics", "means", "quats", "scales", "opacities", "colors"):
             np.testing.assert_array_equal(np_(g1[k]), np_(g[k]), err_msg=k)
+    for g in (g4, g5):
+        for k in ("means2d", "conics", "means", "quats", "scales", "opacities", "colors"):
+            assert rel_l2(np_(g[k]), np_(g1[k])) <= 1e-5, k
 
 
 def test_edge_case_no_gaussians_visible():

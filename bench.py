@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target duration of the oracle sample")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-per-view measurement")
+    ap.add_argument("--batched-steps", type=int, default=5)
     ap.add_argument("--profile", action="store_true",
                     help="run warmup + steps untimed and exit (a fixed command line for ncu)")
     return ap.parse_args()
@@ -188,6 +190,73 @@ def cpu_baseline(w, seconds: float):
             "seconds": dt}
 
 
+def batched_comparison(dev, steps: int):
+    """The two multi-view workloads: one autotuned, graph-captured batched step
+    (one launch per stage over all views) against the same kernels launched
+    once per view; same loss, same results (gradients compared below)."""
+    import torch
+    from paper_2312_02121_gb300 import batch as GB
+    from paper_2312_02121_gb300 import binding as B
+    from paper_2312_02121_gb300 import workloads as wl
+    out = {}
+    for name, make in (("batch_views_500k_64", wl.batch_views_500k_64), ("batch_scenes_16x4", wl.batch_scenes_16x4)):
+        w = make()
+        params, views, ranges, targets = GB.workload_views(w, dev)
+        cap = GB.exact_capacity(params, views, w.eps2d)
+
+        def mk(c):
+            return GB.BatchRenderer(params, views, cap, targets, w.eps2d,
+                                    B.RasterConfig(c["persistent"], c["ctas_per_sm"], device=dev),
+                                    c["longest_first"])
+
+        best = GB.autotune(mk, key=f"{name}|P{views.P}|T{views.T}|K{cap}", use_cache=False)
+        r = mk(best)
+        r.capture()
+        l0 = B.gs_kernel_launches()
+        r.step_eager()
+        launches_b = B.gs_kernel_launches() - l0
+        ms_b = GB.time_steps(r.step, n=steps)
+        assert not r.overflowed()
+        caps = GB.per_view_capacities(params, [v.camera for v in w.views], ranges, w.eps2d)
+        pv = GB.PerViewRenderer(params, [v.camera for v in w.views], ranges, caps, targets, w.eps2d)
+        l0 = B.gs_kernel_launches()
+        pv.step()
+        launches_v = B.gs_kernel_launches() - l0
+        ms_v = GB.time_steps(pv.step, n=steps)
+        r.step()
+        torch.cuda.synchronize()
+        same_images = bool(torch.equal(r.rgb, torch.cat([x.rgb for x in pv.r])))
+        rel = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b).clamp_min(1e-30))
+        # per-projection 2D gradients (well conditioned) in the timed, atomic mode
+        agree_2d = max(rel(r.g2, torch.cat([x.g2 for x in pv.r])), rel(r.gc, torch.cat([x.gc for x in pv.r])))
+        del pv
+        torch.cuda.empty_cache()
+        # every gradient with the summation order fixed (deterministic mode): must be identical
+        rd = GB.BatchRenderer(params, views, cap, targets, w.eps2d, deterministic=True)
+        rd.step_eager()
+        pvd = GB.PerViewRenderer(params, [v.camera for v in w.views], ranges, caps, targets, w.eps2d,
+                                 deterministic=True)
+        pvd.step()
+        torch.cuda.synchronize()
+        gb, gv = rd.grads(), pvd.grads()
+        agree_det = max(rel(gb[k], gv[k]) for k in gb)
+        del rd, pvd
+        out[name] = {"views": views.V, "scenes": len(w.scenes), "gaussians": params.n, "pixels": views.pixels,
+                     "intersections": cap, "batched_mpix_s": views.pixels / ms_b / 1e3,
+                     "per_view_mpix_s": views.pixels / ms_v / 1e3, "speedup": ms_v / ms_b,
+                     "batched_ms_per_step": ms_b, "per_view_ms_per_step": ms_v,
+                     "batched_launches_per_step": int(launches_b), "per_view_launches_per_step": int(launches_v),
+                     "batched_cuda_graph": True,
+                     "tuning": {k: best[k] for k in ("persistent", "ctas_per_sm", "longest_first")},
+                     "tuning_ms": [round(x["ms"], 3) for x in best["all"]],
+                     "images_identical": same_images, "grad2d_rel_l2_batched_vs_per_view": agree_2d,
+                     "grad_rel_l2_batched_vs_per_view_deterministic": agree_det,
+                     "l2": "inputs larger than L2"}
+        del r, params, views, targets
+        torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
@@ -287,7 +356,7 @@ def run_ours(args, rank, world, local_rank):
         go = torch.zeros(sc.n, device=dev)
         gcol = torch.zeros(sc.n, 3, device=dev)
         B.gs_rasterize_bwd(views, pr["means2d"], pr["conics"], params.opacities, params.colors, ids, pos, es,
-                           pr["touched"], tr, Kd, cap, None, Tf, last, dL, False, None, g2, gc, go, gcol)
+                           pr["touched"], tr, Kd, cap, None, Tf, last, dL, False, None, g2, gc, go, gcol, None)
         mark(5)
         gm = torch.zeros(sc.n, 3, device=dev)
         gq = torch.zeros(sc.n, 4, device=dev)
@@ -405,6 +474,8 @@ def run_ours(args, rank, world, local_rank):
         "stage_ms": stage_ms, "wall_s": wall, "gpu_launches": int(launches),
         "e2e": e2e, "roofline": roof, "clocks": clocks,
     }
+    if not args.no_batched:
+        line["batched"] = batched_comparison(dev, args.batched_steps)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     print(json.dumps(line), flush=True)

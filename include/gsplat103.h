@@ -199,6 +199,30 @@ int gs_bin_and_sort_static(const GsView* views, int32_t V, int64_t P, int32_t T_
                            int32_t* isect_pos, int32_t* emit_start, int32_t* tile_ranges, int32_t* K_out,
                            uint32_t* flags, void* stream);
 
+/* How the two compositing kernels walk the tiles (NULL = defaults: one CTA
+ * per tile, in tile id order).  None of these choices changes any result. */
+typedef struct GsRasterConfig {
+    int32_t persistent;         /* 1: a persistent grid pops tiles from a global queue */
+    int32_t ctas_per_sm;        /* persistent grid = ctas_per_sm x SMs (<= 0: as many as fit) */
+    const int32_t* tile_order;  /* device [T_total]: the order tiles are taken in (a permutation
+                                   of tile ids, e.g. longest list first from gs_tile_order);
+                                   NULL = tile id order */
+    int32_t* queue;             /* device int32 counter the persistent grid pops from; required
+                                   when persistent; the call zeroes it on its stream */
+} GsRasterConfig;
+
+/* Bytes of scratch gs_tile_order needs for T_total tiles. */
+size_t gs_tile_order_workspace_size(int32_t T_total);
+
+/*
+ * Orders the tiles by decreasing list length (end - start of tile_ranges,
+ * clamped to 65535), ties by tile id: a longest-first queue for
+ * GsRasterConfig.tile_order, so the longest tiles start first and the tail of
+ * a launch is short.  order[T_total] receives tile ids.
+ */
+int gs_tile_order(const int32_t* tile_ranges, int32_t T_total, void* workspace, size_t workspace_bytes,
+                  int32_t* order, void* stream);
+
 /*
  * Sec. 2.2, Eq. 7: for every pixel of every view, walks its tile's sorted list
  * front to back: sigma = 1/2 Delta^T Y Delta with Delta = mu' - pixel centre,
@@ -207,7 +231,8 @@ int gs_bin_and_sort_static(const GsView* views, int32_t V, int64_t P, int32_t T_
  * C += T * background.
  *   in : views (device), T_total, means2d, conics (from gs_project),
  *        opacities[N], colors[N,3], isect_ids, tile_ranges (from
- *        gs_bin_and_sort), background[3] (device, nullable = black)
+ *        gs_bin_and_sort), background[3] (device, nullable = black),
+ *        config (host, nullable: how tiles are walked; see GsRasterConfig)
  *   out: out_rgb[pix,3], T_final[pix] (transmittance after the last
  *        composited Gaussian), last_idx[pix] int32 (sorted position of the last
  *        composited Gaussian; tile start - 1 when none), n_contrib[pix] int32
@@ -216,7 +241,8 @@ int gs_bin_and_sort_static(const GsView* views, int32_t V, int64_t P, int32_t T_
 int gs_rasterize_fwd(const GsView* views, int32_t V, int32_t T_total, const float* means2d,
                      const float* conics, const float* opacities, const float* colors,
                      const int32_t* isect_ids, const int32_t* tile_ranges, const float* background,
-                     float* out_rgb, float* T_final, int32_t* last_idx, int32_t* n_contrib, void* stream);
+                     float* out_rgb, float* T_final, int32_t* last_idx, int32_t* n_contrib,
+                     const GsRasterConfig* config, void* stream);
 
 /* Bytes of scratch gs_rasterize_bwd needs for K_capacity intersections:
  * 0 unless deterministic. */
@@ -255,7 +281,7 @@ int gs_rasterize_bwd(const GsView* views, int32_t V, int64_t P, int32_t T_total,
                      int64_t K_capacity, const float* background, const float* T_final,
                      const int32_t* last_idx, const float* dL_drgb, int32_t deterministic, void* workspace,
                      size_t workspace_bytes, float* dL_dmeans2d, float* dL_dconics, float* dL_dopacities,
-                     float* dL_dcolors, void* stream);
+                     float* dL_dcolors, const GsRasterConfig* config, void* stream);
 
 /*
  * Sec. 3.2 (Eq. 16-20) and 3.2.1: for every projection with touched > 0,

@@ -1,0 +1,280 @@
+"""Batched rendering: many views (cameras) of one or several scenes per launch.
+
+``BatchRenderer`` runs the whole training-style step -- projection, binning
+and sort, compositing, the L2-loss gradient, compositing backward and
+projection backward -- over every view with ONE launch per stage, into
+preallocated buffers, so the step can be captured once into a CUDA graph and
+replayed.  The intersection capacity is fixed at construction (graphs need
+static sizes); ``overflowed()`` reports a step whose pairs did not fit.
+
+``PerViewRenderer`` is the comparison point: the same kernels launched once
+per view.  ``autotune`` picks how the compositing kernels walk the tiles
+(one CTA per tile or a persistent grid over a global queue; tile-id or
+longest-first order; CTAs per SM) by timing each candidate; none of these
+choices changes any result.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import binding as B
+from .pipeline import Params
+
+
+class BatchRenderer:
+    def __init__(self, params: Params, views: B.Views, K_capacity: int, targets: Optional[torch.Tensor] = None,
+                 eps2d: float = 0.3, config: Optional[B.RasterConfig] = None, longest_first: bool = False,
+                 deterministic: bool = False, background: Optional[torch.Tensor] = None,
+                 shared_grads: Optional[Dict[str, torch.Tensor]] = None):
+        """``shared_grads``: per-Gaussian gradient buffers (means, quats,
+        scales, opacities, colors) owned and zeroed by the caller, into which
+        this renderer accumulates; by default the renderer owns them."""
+        self.p, self.views, self.eps2d = params, views, eps2d
+        self.cap = max(int(K_capacity), 1)
+        self.config, self.longest_first, self.deterministic = config, longest_first, deterministic
+        self.background = background
+        dev = params.means.device
+        P, T, pix, N = views.P, views.T, views.pixels, params.n
+        e = lambda *shape, dtype=torch.float32: torch.empty(*shape, dtype=dtype, device=dev)
+        self.means2d, self.conics, self.depths = e(max(P, 1), 2), e(max(P, 1), 3), e(max(P, 1))
+        self.rects = e(max(P, 1), 4, dtype=torch.int16)
+        self.touched = e(max(P, 1), dtype=torch.int32)
+        self.K_total = e(1, dtype=torch.int64)
+        self.sort_ws = e(B.gs_bin_and_sort_workspace_size(P, self.cap, T), dtype=torch.uint8)
+        self.isect_ids, self.isect_pos = e(self.cap, dtype=torch.int32), e(self.cap, dtype=torch.int32)
+        self.emit_start = e(max(P, 1), dtype=torch.int32)
+        self.tile_ranges = e(T, 2, dtype=torch.int32)
+        self.K = e(1, dtype=torch.int32)
+        self.flags = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.order_ws = e(max(B.gs_tile_order_workspace_size(T), 1), dtype=torch.uint8)
+        self.tile_order = e(T, dtype=torch.int32)
+        self.rgb, self.T_final = e(pix, 3), e(pix)
+        self.last_idx = e(pix, dtype=torch.int32)
+        self.targets = targets
+        self.dL = e(pix, 3)
+        nbw = B.gs_rasterize_bwd_workspace_size(self.cap, deterministic)
+        self.bwd_ws = e(nbw, dtype=torch.uint8) if nbw else None
+        self.g2, self.gc = e(max(P, 1), 2), e(max(P, 1), 3)
+        self.owns_grads = shared_grads is None
+        if self.owns_grads:
+            self.g_op, self.g_col = e(max(N, 1)), e(max(N, 1), 3)
+            self.g_means, self.g_quats, self.g_scales = e(max(N, 1), 3), e(max(N, 1), 4), e(max(N, 1), 3)
+        else:
+            sg = shared_grads
+            self.g_op, self.g_col = sg["opacities"], sg["colors"]
+            self.g_means, self.g_quats, self.g_scales = sg["means"], sg["quats"], sg["scales"]
+        if longest_first:
+            cfg = config or B.RasterConfig(device=dev)
+            self.config = B.RasterConfig(cfg.persistent, cfg.ctas_per_sm, self.tile_order, device=dev)
+        self.graph: Optional[torch.cuda.CUDAGraph] = None
+
+    # -- one step, eagerly --------------------------------------------------
+    def forward(self):
+        v, p = self.views, self.p
+        B.gs_project(v, p.means, p.quats, p.scales, self.eps2d, self.means2d, self.conics, self.depths, self.rects,
+                     self.touched, self.K_total)
+        self.flags.zero_()
+        B.gs_bin_and_sort(v, self.rects, self.depths, self.touched, self.cap, self.sort_ws, self.isect_ids,
+                          self.isect_pos, self.emit_start, self.tile_ranges, self.K, self.flags)
+        if self.longest_first:
+            B.gs_tile_order(self.tile_ranges, v.T, self.order_ws, self.tile_order)
+        B.gs_rasterize_fwd(v, self.means2d, self.conics, p.opacities, p.colors, self.isect_ids, self.tile_ranges,
+                           self.background, self.rgb, self.T_final, self.last_idx, None, self.config)
+
+    def loss_grad(self):
+        """dL/dC of L = mean((C - target)^2) over every pixel of every view."""
+        torch.sub(self.rgb, self.targets, out=self.dL)
+        self.dL.mul_(2.0 / self.rgb.numel())
+
+    def backward(self):
+        v, p = self.views, self.p
+        self.g2.zero_()
+        self.gc.zero_()
+        if self.owns_grads:
+            for t in (self.g_op, self.g_col, self.g_means, self.g_quats, self.g_scales):
+                t.zero_()
+        B.gs_rasterize_bwd(v, self.means2d, self.conics, p.opacities, p.colors, self.isect_ids, self.isect_pos,
+                           self.emit_start, self.touched, self.tile_ranges, self.K, self.cap, self.background,
+                           self.T_final, self.last_idx, self.dL, self.deterministic, self.bwd_ws, self.g2, self.gc,
+                           self.g_op, self.g_col, self.config)
+        B.gs_project_bwd(v, p.means, p.quats, p.scales, self.eps2d, self.touched, self.g2, self.gc, self.g_means,
+                         self.g_quats, self.g_scales)
+
+    def step_eager(self):
+        self.forward()
+        self.loss_grad()
+        self.backward()
+
+    # -- CUDA graph ---------------------------------------------------------
+    def capture(self):
+        """Captures one whole step into a CUDA graph (after two eager warm-ups
+        on a side stream, as graph capture requires)."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(2):
+                self.step_eager()
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.step_eager()
+        self.graph = g
+
+    def step(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.step_eager()
+
+    def overflowed(self) -> bool:
+        return bool(int(self.flags.item()) & B.GS_FLAG_CAPACITY)
+
+    def grads(self) -> Dict[str, torch.Tensor]:
+        N = self.p.n
+        return dict(means=self.g_means[:N], quats=self.g_quats[:N], scales=self.g_scales[:N],
+                    opacities=self.g_op[:N], colors=self.g_col[:N])
+
+    def image(self, i: int) -> torch.Tensor:
+        off, w, h, _ = self.views.image_slice(i)
+        return self.rgb[off:off + w * h].view(h, w, 3)
+
+
+class PerViewRenderer:
+    """The same step with one set of launches per view (the per-view path the
+    batched launch is measured against).  All views accumulate into one
+    shared set of per-Gaussian gradient buffers, zeroed once per step."""
+
+    def __init__(self, params: Params, cameras: Sequence, g_ranges, K_caps: Sequence[int],
+                 targets: torch.Tensor, eps2d: float = 0.3, deterministic: bool = False):
+        """``targets``: the packed [pixels, 3] targets of all views, in view order."""
+        dev = params.means.device
+        N = max(params.n, 1)
+        self.shared = dict(means=torch.empty(N, 3, device=dev), quats=torch.empty(N, 4, device=dev),
+                           scales=torch.empty(N, 3, device=dev), opacities=torch.empty(N, device=dev),
+                           colors=torch.empty(N, 3, device=dev))
+        self.n = params.n
+        self.r: List[BatchRenderer] = []
+        off = 0
+        for cam, gr, cap in zip(cameras, g_ranges, K_caps):
+            pix = cam.width * cam.height
+            tgt = targets[off:off + pix]
+            off += pix
+            v = B.Views([cam], [gr], device=dev)
+            self.r.append(BatchRenderer(params, v, cap, tgt, eps2d, deterministic=deterministic,
+                                        shared_grads=self.shared))
+        self.n_pix = sum(r.views.pixels for r in self.r)
+
+    def step(self):
+        for t in self.shared.values():
+            t.zero_()
+        for r in self.r:
+            r.forward()
+            # same loss as the batch: mean over every pixel of every view
+            torch.sub(r.rgb, r.targets, out=r.dL)
+            r.dL.mul_(2.0 / (3 * self.n_pix))
+            r.backward()
+
+    def overflowed(self) -> bool:
+        return any(r.overflowed() for r in self.r)
+
+    def grads(self) -> Dict[str, torch.Tensor]:
+        return {k: v[:self.n] for k, v in self.shared.items()}
+
+
+def per_view_capacities(params: Params, cameras: Sequence, g_ranges, eps2d: float = 0.3) -> List[int]:
+    return [exact_capacity(params, B.Views([c], [g], device=params.means.device), eps2d)
+            for c, g in zip(cameras, g_ranges)]
+
+
+def exact_capacity(params: Params, views: B.Views, eps2d: float = 0.3) -> int:
+    """Intersections of the batch (one projection pass, one read-back)."""
+    dev = params.means.device
+    P = max(views.P, 1)
+    tmp = [torch.empty(P, 2, device=dev), torch.empty(P, 3, device=dev), torch.empty(P, device=dev),
+           torch.empty(P, 4, dtype=torch.int16, device=dev), torch.empty(P, dtype=torch.int32, device=dev)]
+    K = torch.empty(1, dtype=torch.int64, device=dev)
+    B.gs_project(views, params.means, params.quats, params.scales, eps2d, *tmp, K)
+    return int(K.item())
+
+
+def time_steps(step, n: int = 5, warmup: int = 2) -> float:
+    """Mean device time of ``step`` in ms (CUDA events)."""
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(n):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / n
+
+
+CANDIDATES = [
+    dict(persistent=False, ctas_per_sm=0, longest_first=False),
+    dict(persistent=False, ctas_per_sm=0, longest_first=True),
+    dict(persistent=True, ctas_per_sm=0, longest_first=True),
+    dict(persistent=True, ctas_per_sm=4, longest_first=True),
+    dict(persistent=True, ctas_per_sm=3, longest_first=True),
+]
+
+
+def _cache_path() -> str:
+    root = os.environ.get("GSPLAT103_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "gsplat103"))
+    return os.path.join(root, "tuning.json")
+
+
+def autotune(make, key: str, candidates=None, use_cache: bool = True, n: int = 3) -> dict:
+    """Times ``make(candidate).step`` for each candidate tile-walking config
+    and returns the fastest (cached per GPU name and ``key``)."""
+    gpu = torch.cuda.get_device_name()
+    ck = f"{gpu}|{key}"
+    path = _cache_path()
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            cache = json.load(open(path))
+        except (OSError, ValueError):
+            cache = {}
+    if ck in cache:
+        return dict(cache[ck], cached=True)
+    best, results = None, []
+    for cand in candidates or CANDIDATES:
+        r = make(cand)
+        ms = time_steps(r.step, n=n, warmup=1)
+        results.append(dict(cand, ms=ms))
+        if best is None or ms < best["ms"]:
+            best = dict(cand, ms=ms)
+        del r
+        torch.cuda.empty_cache()
+    best["all"] = results
+    if use_cache:
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            cache[ck] = best
+            json.dump(cache, open(path, "w"))
+        except OSError:
+            pass
+    return dict(best, cached=False)
+
+
+def workload_views(w, device="cuda"):
+    """Params, Views and packed targets of a workloads.Workload (all scenes
+    concatenated; view i renders its scene's Gaussian range)."""
+    offs = np.cumsum([0] + [s.n for s in w.scenes])
+    cat = lambda k: torch.as_tensor(np.concatenate([getattr(s, k) for s in w.scenes]), dtype=torch.float32,
+                                    device=device).contiguous()
+    params = Params(cat("means"), cat("quats"), cat("scales"), cat("opacities"), cat("colors"))
+    ranges = [(int(offs[v.scene]), w.scenes[v.scene].n) for v in w.views]
+    views = B.Views([v.camera for v in w.views], ranges, device=device)
+    targets = None
+    if w.targets is not None:
+        targets = torch.as_tensor(np.concatenate([t.reshape(-1, 3) for t in w.targets]), device=device)
+    return params, views, ranges, targets

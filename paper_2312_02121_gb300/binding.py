@@ -50,7 +50,12 @@ class GsView(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
-assert ctypes.sizeof(GsCamera) == 80 and ctypes.sizeof(GsView) == 120
+class GsRasterConfig(ctypes.Structure):
+    _fields_ = [("persistent", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("tile_order", ctypes.c_void_p), ("queue", ctypes.c_void_p)]
+
+
+assert ctypes.sizeof(GsCamera) == 80 and ctypes.sizeof(GsView) == 120 and ctypes.sizeof(GsRasterConfig) == 24
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -68,10 +73,12 @@ SIGNATURES = {
     "gs_bin_and_sort_workspace_size": (_SZ, [_I64, _I64, _I32]),
     "gs_bin_and_sort": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _I64, _P, _SZ, _P, _P, _P, _P, _P, _P, _P]),
     "gs_bin_and_sort_static": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _P]),
-    "gs_rasterize_fwd": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gs_tile_order_workspace_size": (_SZ, [_I32]),
+    "gs_tile_order": (ctypes.c_int, [_P, _I32, _P, _SZ, _P, _P]),
+    "gs_rasterize_fwd": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gs_rasterize_bwd_workspace_size": (_SZ, [_I64, _I32]),
     "gs_rasterize_bwd": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P,
-                                        _P, _P, _I32, _P, _SZ, _P, _P, _P, _P, _P]),
+                                        _P, _P, _I32, _P, _SZ, _P, _P, _P, _P, _P, _P]),
     "gs_project_bwd": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _F, _P, _P, _P, _P, _P, _P, _P]),
 }
 
@@ -207,12 +214,47 @@ def gs_bin_and_sort_static(views: Views, rects, depths, touched, K_capacity: int
                                          _stream(stream)))
 
 
+class RasterConfig:
+    """How the compositing kernels walk the tiles (GsRasterConfig); never
+    changes results.  ``tile_order`` (device int32 [T]) and the queue counter
+    are kept alive by this object."""
+
+    def __init__(self, persistent: bool = False, ctas_per_sm: int = 0, tile_order=None, device="cuda"):
+        self.persistent = bool(persistent)
+        self.ctas_per_sm = int(ctas_per_sm)
+        self.tile_order = tile_order
+        self.queue = torch.zeros(1, dtype=torch.int32, device=device) if persistent else None
+        self.c = GsRasterConfig(int(self.persistent), self.ctas_per_sm,
+                                None if tile_order is None else tile_order.data_ptr(),
+                                None if self.queue is None else self.queue.data_ptr())
+
+    def ref(self):
+        return ctypes.byref(self.c)
+
+    def describe(self) -> dict:
+        return {"persistent": self.persistent, "ctas_per_sm": self.ctas_per_sm,
+                "tile_order": "longest-first" if self.tile_order is not None else "tile id"}
+
+
+def _cfg(config: Optional[RasterConfig]):
+    return None if config is None else config.ref()
+
+
+def gs_tile_order_workspace_size(T_total: int) -> int:
+    return int(load().gs_tile_order_workspace_size(T_total))
+
+
+def gs_tile_order(tile_ranges, T_total: int, workspace, order, stream=None):
+    _check(load().gs_tile_order(_ptr(tile_ranges), int(T_total), _ptr(workspace),
+                                workspace.numel() * workspace.element_size(), _ptr(order), _stream(stream)))
+
+
 def gs_rasterize_fwd(views: Views, means2d, conics, opacities, colors, isect_ids, tile_ranges, background,
-                     out_rgb, T_final, last_idx, n_contrib=None, stream=None):
+                     out_rgb, T_final, last_idx, n_contrib=None, config: Optional[RasterConfig] = None, stream=None):
     _check(load().gs_rasterize_fwd(_ptr(views.device), views.V, views.T, _ptr(means2d), _ptr(conics),
                                    _ptr(opacities), _ptr(colors), _ptr(isect_ids), _ptr(tile_ranges),
                                    _ptr(background), _ptr(out_rgb), _ptr(T_final), _ptr(last_idx),
-                                   _ptr(n_contrib), _stream(stream)))
+                                   _ptr(n_contrib), _cfg(config), _stream(stream)))
 
 
 def gs_rasterize_bwd_workspace_size(K_capacity: int, deterministic: bool = False) -> int:
@@ -221,14 +263,16 @@ def gs_rasterize_bwd_workspace_size(K_capacity: int, deterministic: bool = False
 
 def gs_rasterize_bwd(views: Views, means2d, conics, opacities, colors, isect_ids, isect_pos, emit_start, touched,
                      tile_ranges, K, K_capacity: int, background, T_final, last_idx, dL_drgb, deterministic: bool,
-                     workspace, dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors, stream=None):
+                     workspace, dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors,
+                     config: Optional[RasterConfig] = None, stream=None):
     nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(load().gs_rasterize_bwd(_ptr(views.device), views.V, views.P, views.T, _ptr(means2d), _ptr(conics),
                                    _ptr(opacities), _ptr(colors), _ptr(isect_ids), _ptr(isect_pos),
                                    _ptr(emit_start), _ptr(touched), _ptr(tile_ranges), _ptr(K), int(K_capacity),
                                    _ptr(background), _ptr(T_final), _ptr(last_idx), _ptr(dL_drgb),
                                    int(bool(deterministic)), _ptr(workspace), nbytes, _ptr(dL_dmeans2d),
-                                   _ptr(dL_dconics), _ptr(dL_dopacities), _ptr(dL_dcolors), _stream(stream)))
+                                   _ptr(dL_dconics), _ptr(dL_dopacities), _ptr(dL_dcolors), _cfg(config),
+                                   _stream(stream)))
 
 
 def gs_project_bwd(views: Views, means, quats, scales, eps2d: float, touched, dL_dmeans2d, dL_dconics, dL_dmeans,

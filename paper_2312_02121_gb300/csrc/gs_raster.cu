@@ -26,6 +26,8 @@
 // Gaussian) pair.  A second kernel sums each projection's records over its
 // tiles in emission order.  No floating-point atomics touch per-projection
 // outputs, so gradients are run-to-run identical.
+#include <algorithm>
+
 #include "gs_common.cuh"
 
 namespace gs {
@@ -153,79 +155,95 @@ __device__ __forceinline__ Staged load_staged(const float4* sh_xy, const float4*
 // forward
 // ---------------------------------------------------------------------------
 
-template <bool kCull>
+// kPersistent: a grid of a few CTAs per SM pops tiles from the global queue
+// counter `queue` (zeroed before launch) until T_total tiles are taken;
+// otherwise CTA i renders queue slot i.  Slot qi renders tile tile_order[qi]
+// (identity when tile_order is NULL).
+template <bool kCull, bool kPersistent>
 __global__ void __launch_bounds__(256)
-k_raster_fwd(const GsView* __restrict__ views, int V, const float2* __restrict__ means2d,
+k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t* __restrict__ tile_order,
+             int* __restrict__ queue, const float2* __restrict__ means2d,
              const float* __restrict__ conics, const float* __restrict__ opacities, const float* __restrict__ colors,
              const int32_t* __restrict__ isect_ids, const int2* __restrict__ tile_ranges,
              const float* __restrict__ background, float* __restrict__ out_rgb, float* __restrict__ T_final,
              int32_t* __restrict__ last_idx, int32_t* __restrict__ n_contrib)
 {
     __shared__ float4 sh_xy[kFwdBatch], sh_q[kFwdBatch], sh_col[kFwdBatch], sh_cull[kFwdBatch];
-    const int tile = blockIdx.x;
-    const TileCtx t = tile_ctx(views, V, tile);
-    const int lane = threadIdx.x & 31;
-    const int2 range = tile_ranges[tile];
-
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    int last = range.x - 1, count = 0;
-    bool done = !t.inside;
-
-    for (int b0 = range.x; b0 < range.y; b0 += kFwdBatch) {
-        if (__syncthreads_count(done) == (int)blockDim.x) break;  // also guards the stage below
-        {
-            const int i = b0 + threadIdx.x;
-            if (i < range.y) {
-                const int p = isect_ids[i];
-                const int64_t g = p + t.g_shift;
-                stage_gaussian(sh_xy, sh_q, sh_col, sh_cull, threadIdx.x, means2d[p], conics[3 * p],
-                               conics[3 * p + 1], conics[3 * p + 2], opacities[g], colors[3 * g], colors[3 * g + 1],
-                               colors[3 * g + 2]);
-            }
+    __shared__ int s_next;
+    for (int qi = blockIdx.x;;) {
+        if (kPersistent) {
+            __syncthreads();  // the previous tile is done with shared memory
+            if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
+            __syncthreads();
+            qi = s_next;
+            if (qi >= T_total) break;
         }
-        __syncthreads();
-        const int n = min(kFwdBatch, range.y - b0);
-        for (int s = 0; s < n; s += 32) {
-            bool hit = s + lane < n;
-            if (kCull && hit)
-                hit = reaches_box(load_staged(sh_xy, sh_q, sh_col, sh_cull, s + lane), t.wx0, t.wx1, t.wy0, t.wy1);
-            unsigned m = __ballot_sync(kFull, hit);
-            while (m) {
-                const int j = s + __ffs(m) - 1;
-                m &= m - 1;
-                if (done) continue;
-                const float4 xy = sh_xy[j];
-                float u;
-                const float p2 = neg_sigma_log2(sh_q[j], xy.x - t.cx, xy.y - t.cy, u);
-                if (p2 > 0.f) continue;  // sigma < 0 (not a positive-definite conic)
-                const float alpha = fminf(GS_ALPHA_MAX, __fmul_rn(xy.z, ex2(p2)));
-                if (alpha < GS_ALPHA_MIN) continue;
-                const float Tn = T * (1.f - alpha);
-                if (Tn < GS_T_MIN) {
-                    done = true;
-                    continue;
+        const int tile = tile_order ? tile_order[qi] : qi;
+        const TileCtx t = tile_ctx(views, V, tile);
+        const int lane = threadIdx.x & 31;
+        const int2 range = tile_ranges[tile];
+
+        float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+        int last = range.x - 1, count = 0;
+        bool done = !t.inside;
+
+        for (int b0 = range.x; b0 < range.y; b0 += kFwdBatch) {
+            if (__syncthreads_count(done) == (int)blockDim.x) break;  // also guards the stage below
+            {
+                const int i = b0 + threadIdx.x;
+                if (i < range.y) {
+                    const int p = isect_ids[i];
+                    const int64_t g = p + t.g_shift;
+                    stage_gaussian(sh_xy, sh_q, sh_col, sh_cull, threadIdx.x, means2d[p], conics[3 * p],
+                                   conics[3 * p + 1], conics[3 * p + 2], opacities[g], colors[3 * g], colors[3 * g + 1],
+                                   colors[3 * g + 2]);
                 }
-                const float4 c = sh_col[j];
-                const float wgt = alpha * T;
-                C0 = fmaf(wgt, c.x, C0);
-                C1 = fmaf(wgt, c.y, C1);
-                C2 = fmaf(wgt, c.z, C2);
-                T = Tn;
-                last = b0 + j;
-                ++count;
             }
-            if (__all_sync(kFull, done)) break;
+            __syncthreads();
+            const int n = min(kFwdBatch, range.y - b0);
+            for (int s = 0; s < n; s += 32) {
+                bool hit = s + lane < n;
+                if (kCull && hit)
+                    hit = reaches_box(load_staged(sh_xy, sh_q, sh_col, sh_cull, s + lane), t.wx0, t.wx1, t.wy0, t.wy1);
+                unsigned m = __ballot_sync(kFull, hit);
+                while (m) {
+                    const int j = s + __ffs(m) - 1;
+                    m &= m - 1;
+                    if (done) continue;
+                    const float4 xy = sh_xy[j];
+                    float u;
+                    const float p2 = neg_sigma_log2(sh_q[j], xy.x - t.cx, xy.y - t.cy, u);
+                    if (p2 > 0.f) continue;  // sigma < 0 (not a positive-definite conic)
+                    const float alpha = fminf(GS_ALPHA_MAX, __fmul_rn(xy.z, ex2(p2)));
+                    if (alpha < GS_ALPHA_MIN) continue;
+                    const float Tn = T * (1.f - alpha);
+                    if (Tn < GS_T_MIN) {
+                        done = true;
+                        continue;
+                    }
+                    const float4 c = sh_col[j];
+                    const float wgt = alpha * T;
+                    C0 = fmaf(wgt, c.x, C0);
+                    C1 = fmaf(wgt, c.y, C1);
+                    C2 = fmaf(wgt, c.z, C2);
+                    T = Tn;
+                    last = b0 + j;
+                    ++count;
+                }
+                if (__all_sync(kFull, done)) break;
+            }
         }
-    }
-    if (t.inside) {
-        float bg0 = 0.f, bg1 = 0.f, bg2 = 0.f;
-        if (background) { bg0 = background[0]; bg1 = background[1]; bg2 = background[2]; }
-        out_rgb[3 * t.pix + 0] = fmaf(T, bg0, C0);
-        out_rgb[3 * t.pix + 1] = fmaf(T, bg1, C1);
-        out_rgb[3 * t.pix + 2] = fmaf(T, bg2, C2);
-        T_final[t.pix] = T;
-        last_idx[t.pix] = last;
-        if (n_contrib) n_contrib[t.pix] = count;
+        if (t.inside) {
+            float bg0 = 0.f, bg1 = 0.f, bg2 = 0.f;
+            if (background) { bg0 = background[0]; bg1 = background[1]; bg2 = background[2]; }
+            out_rgb[3 * t.pix + 0] = fmaf(T, bg0, C0);
+            out_rgb[3 * t.pix + 1] = fmaf(T, bg1, C1);
+            out_rgb[3 * t.pix + 2] = fmaf(T, bg2, C2);
+            T_final[t.pix] = T;
+            last_idx[t.pix] = last;
+            if (n_contrib) n_contrib[t.pix] = count;
+        }
+        if (!kPersistent) break;
     }
 }
 
@@ -285,9 +303,10 @@ __device__ __forceinline__ float warp_sum9(const float (&v)[kRec], int lane)
 // outputs with vector reduction atomics (fast; fp32 summation order across
 // tiles varies).  Otherwise it is written as a record for k_reduce_records
 // (deterministic).
-template <bool kCull, bool kAtomic>
+template <bool kCull, bool kAtomic, bool kPersistent>
 __global__ void __launch_bounds__(256, 5)
-k_raster_bwd(const GsView* __restrict__ views, int V, const float2* __restrict__ means2d,
+k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t* __restrict__ tile_order,
+             int* __restrict__ queue, const float2* __restrict__ means2d,
              const float* __restrict__ conics, const float* __restrict__ opacities, const float* __restrict__ colors,
              const int32_t* __restrict__ isect_ids, const int2* __restrict__ tile_ranges,
              const float* __restrict__ background, const float* __restrict__ T_final,
@@ -299,153 +318,164 @@ k_raster_bwd(const GsView* __restrict__ views, int V, const float2* __restrict__
     __shared__ float s_grad[kWarps][kBwdBatch][kRec];
     __shared__ unsigned s_mask[kWarps][kBwdBatch / 32];
     __shared__ int s_maxlast[kWarps];
-    const int tile = blockIdx.x;
-    const TileCtx t = tile_ctx(views, V, tile);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int2 range = tile_ranges[tile];
-
-    float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, bgT = 0.f;
-    int last = range.x - 1;
-    if (t.inside) {
-        T = T_final[t.pix];
-        last = last_idx[t.pix];
-        g0 = dL_drgb[3 * t.pix + 0];
-        g1 = dL_drgb[3 * t.pix + 1];
-        g2 = dL_drgb[3 * t.pix + 2];
-        if (background) bgT = T * (background[0] * g0 + background[1] * g1 + background[2] * g2);
-    }
-    float SdL = 0.f;  // S_n . dL/dC, S_n = sum_{m>n} c_m alpha_m T_m
-
-    // the warp's and the tile's largest last index bound the work
-    int wl = last;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) wl = max(wl, __shfl_xor_sync(kFull, wl, d));
-    if (lane == 0) s_maxlast[w] = wl;
-    __syncthreads();
-    int maxlast = s_maxlast[0];
-#pragma unroll
-    for (int i = 1; i < kWarps; ++i) maxlast = max(maxlast, s_maxlast[i]);
-
-    const int nbatch = maxlast >= range.x ? (maxlast - range.x) / kBwdBatch + 1 : 0;
-    for (int k = nbatch - 1; k >= 0; --k) {
-        const int b0 = range.x + k * kBwdBatch;
-        const int n = min(kBwdBatch, maxlast - b0 + 1);
-        if (threadIdx.x < n) {
-            const int p = isect_ids[b0 + threadIdx.x];
-            const int64_t g = p + t.g_shift;
-            stage_gaussian(sh_xy, sh_q, sh_col, sh_cull, threadIdx.x, means2d[p], conics[3 * p], conics[3 * p + 1],
-                           conics[3 * p + 2], opacities[g], colors[3 * g], colors[3 * g + 1], colors[3 * g + 2]);
-            sh_cull[threadIdx.x].w = __int_as_float(p);  // the projection, for the atomic flush
+    __shared__ int s_next;
+    for (int qi = blockIdx.x;;) {
+        if (kPersistent) {
+            __syncthreads();  // the previous tile is done with shared memory
+            if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
+            __syncthreads();
+            qi = s_next;
+            if (qi >= T_total) break;
         }
+        const int tile = tile_order ? tile_order[qi] : qi;
+        const TileCtx t = tile_ctx(views, V, tile);
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        const int2 range = tile_ranges[tile];
+
+        float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, bgT = 0.f;
+        int last = range.x - 1;
+        if (t.inside) {
+            T = T_final[t.pix];
+            last = last_idx[t.pix];
+            g0 = dL_drgb[3 * t.pix + 0];
+            g1 = dL_drgb[3 * t.pix + 1];
+            g2 = dL_drgb[3 * t.pix + 2];
+            if (background) bgT = T * (background[0] * g0 + background[1] * g1 + background[2] * g2);
+        }
+        float SdL = 0.f;  // S_n . dL/dC, S_n = sum_{m>n} c_m alpha_m T_m
+
+        // the warp's and the tile's largest last index bound the work
+        int wl = last;
+    #pragma unroll
+        for (int d = 16; d > 0; d >>= 1) wl = max(wl, __shfl_xor_sync(kFull, wl, d));
+        if (lane == 0) s_maxlast[w] = wl;
         __syncthreads();
-        // this warp only needs entries up to its own last index
-        const int nw = min(n, wl - b0 + 1);
-        for (int s = ((kBwdBatch - 1) >> 5) << 5; s >= 0; s -= 32) {
-            unsigned chunk_mask = 0u;  // Gaussians of this chunk the warp wrote a partial for
-            if (s < nw) {
-                bool hit = s + lane < nw;
-                if (kCull && hit)
-                    hit = reaches_box(load_staged(sh_xy, sh_q, sh_col, sh_cull, s + lane), t.wx0, t.wx1, t.wy0,
-                                      t.wy1);
-                unsigned m = __ballot_sync(kFull, hit);
-                while (m) {
-                    const int hb = 31 - __clz(m);
-                    m ^= 1u << hb;
-                    const int j = s + hb;  // back to front
-                    float r[kRec];
-#pragma unroll
-                    for (int q = 0; q < kRec; ++q) r[q] = 0.f;
-                    bool contrib = false;
-                    if (b0 + j <= last) {
-                        const float4 xy = sh_xy[j];
-                        const float4 qq = sh_q[j];
-                        const float dx = xy.x - t.cx, dy = xy.y - t.cy;
-                        float u;
-                        const float p2 = neg_sigma_log2(qq, dx, dy, u);
-                        if (p2 <= 0.f) {
-                            const float ge = ex2(p2);  // exp(-sigma)
-                            const float raw = __fmul_rn(xy.z, ge);
-                            const float alpha = fminf(GS_ALPHA_MAX, raw);
-                            if (alpha >= GS_ALPHA_MIN) {
-                                contrib = true;
-                                const float4 col = sh_col[j];
-                                const float inv1ma = __fdividef(1.f, 1.f - alpha);
-                                const float Tn = T * inv1ma;  // T before this Gaussian
-                                const float wgt = alpha * Tn;
-                                const float cdot = fmaf(col.x, g0, fmaf(col.y, g1, col.z * g2));
-                                const float dL_dalpha = fmaf(Tn, cdot, -(SdL + bgT) * inv1ma);
-                                SdL = fmaf(wgt, cdot, SdL);
-                                T = Tn;
-                                r[6] = wgt * g0;
-                                r[7] = wgt * g1;
-                                r[8] = wgt * g2;
-                                if (raw < GS_ALPHA_MAX) {
-                                    const float gd = ge * dL_dalpha;
-                                    r[5] = gd;                     // dL/do
-                                    const float ds = -xy.z * gd;  // dL/dsigma
-                                    // Y Delta = (a u, b u + D dy)
-                                    r[0] = ds * (xy.w * u);
-                                    r[1] = ds * fmaf(qq.w, u, col.w * dy);
-                                    const float hds = 0.5f * ds;
-                                    r[2] = hds * dx * dx;
-                                    r[3] = ds * dx * dy;
-                                    r[4] = hds * dy * dy;
+        int maxlast = s_maxlast[0];
+    #pragma unroll
+        for (int i = 1; i < kWarps; ++i) maxlast = max(maxlast, s_maxlast[i]);
+
+        const int nbatch = maxlast >= range.x ? (maxlast - range.x) / kBwdBatch + 1 : 0;
+        for (int k = nbatch - 1; k >= 0; --k) {
+            const int b0 = range.x + k * kBwdBatch;
+            const int n = min(kBwdBatch, maxlast - b0 + 1);
+            if (threadIdx.x < n) {
+                const int p = isect_ids[b0 + threadIdx.x];
+                const int64_t g = p + t.g_shift;
+                stage_gaussian(sh_xy, sh_q, sh_col, sh_cull, threadIdx.x, means2d[p], conics[3 * p], conics[3 * p + 1],
+                               conics[3 * p + 2], opacities[g], colors[3 * g], colors[3 * g + 1], colors[3 * g + 2]);
+                sh_cull[threadIdx.x].w = __int_as_float(p);  // the projection, for the atomic flush
+            }
+            __syncthreads();
+            // this warp only needs entries up to its own last index
+            const int nw = min(n, wl - b0 + 1);
+            for (int s = ((kBwdBatch - 1) >> 5) << 5; s >= 0; s -= 32) {
+                unsigned chunk_mask = 0u;  // Gaussians of this chunk the warp wrote a partial for
+                if (s < nw) {
+                    bool hit = s + lane < nw;
+                    if (kCull && hit)
+                        hit = reaches_box(load_staged(sh_xy, sh_q, sh_col, sh_cull, s + lane), t.wx0, t.wx1, t.wy0,
+                                          t.wy1);
+                    unsigned m = __ballot_sync(kFull, hit);
+                    while (m) {
+                        const int hb = 31 - __clz(m);
+                        m ^= 1u << hb;
+                        const int j = s + hb;  // back to front
+                        float r[kRec];
+    #pragma unroll
+                        for (int q = 0; q < kRec; ++q) r[q] = 0.f;
+                        bool contrib = false;
+                        if (b0 + j <= last) {
+                            const float4 xy = sh_xy[j];
+                            const float4 qq = sh_q[j];
+                            const float dx = xy.x - t.cx, dy = xy.y - t.cy;
+                            float u;
+                            const float p2 = neg_sigma_log2(qq, dx, dy, u);
+                            if (p2 <= 0.f) {
+                                const float ge = ex2(p2);  // exp(-sigma)
+                                const float raw = __fmul_rn(xy.z, ge);
+                                const float alpha = fminf(GS_ALPHA_MAX, raw);
+                                if (alpha >= GS_ALPHA_MIN) {
+                                    contrib = true;
+                                    const float4 col = sh_col[j];
+                                    const float inv1ma = __fdividef(1.f, 1.f - alpha);
+                                    const float Tn = T * inv1ma;  // T before this Gaussian
+                                    const float wgt = alpha * Tn;
+                                    const float cdot = fmaf(col.x, g0, fmaf(col.y, g1, col.z * g2));
+                                    const float dL_dalpha = fmaf(Tn, cdot, -(SdL + bgT) * inv1ma);
+                                    SdL = fmaf(wgt, cdot, SdL);
+                                    T = Tn;
+                                    r[6] = wgt * g0;
+                                    r[7] = wgt * g1;
+                                    r[8] = wgt * g2;
+                                    if (raw < GS_ALPHA_MAX) {
+                                        const float gd = ge * dL_dalpha;
+                                        r[5] = gd;                     // dL/do
+                                        const float ds = -xy.z * gd;  // dL/dsigma
+                                        // Y Delta = (a u, b u + D dy)
+                                        r[0] = ds * (xy.w * u);
+                                        r[1] = ds * fmaf(qq.w, u, col.w * dy);
+                                        const float hds = 0.5f * ds;
+                                        r[2] = hds * dx * dx;
+                                        r[3] = ds * dx * dy;
+                                        r[4] = hds * dy * dy;
+                                    }
                                 }
                             }
                         }
+                        if (__ballot_sync(kFull, contrib) == 0u) continue;
+                        const float tot = warp_sum9(r, lane);
+                        if (!(lane & 1) && (lane >> 1) < kRec) s_grad[w][j][lane >> 1] = tot;
+                        chunk_mask |= 1u << hb;
                     }
-                    if (__ballot_sync(kFull, contrib) == 0u) continue;
-                    const float tot = warp_sum9(r, lane);
-                    if (!(lane & 1) && (lane >> 1) < kRec) s_grad[w][j][lane >> 1] = tot;
-                    chunk_mask |= 1u << hb;
+                }
+                if (lane == 0) s_mask[w][s >> 5] = chunk_mask;
+            }
+            __syncthreads();
+            // fixed-order sum over warps: one (tile, Gaussian) partial
+            if (threadIdx.x < n) {
+                const int j = threadIdx.x;
+                float acc[kRec];
+    #pragma unroll
+                for (int q = 0; q < kRec; ++q) acc[q] = 0.f;
+                bool any = false;
+    #pragma unroll
+                for (int ww = 0; ww < kWarps; ++ww)
+                    if (s_mask[ww][j >> 5] & (1u << (j & 31))) {
+                        any = true;
+    #pragma unroll
+                        for (int q = 0; q < kRec; ++q) acc[q] += s_grad[ww][j][q];
+                    }
+                if (kAtomic) {
+                    if (any) {
+                        const int p = __float_as_int(sh_cull[j].w);
+                        const int64_t g = p + t.g_shift;
+                        atomicAdd(dL_dmeans2d + p, make_float2(acc[0], acc[1]));
+                        atomicAdd(dL_dconics + 3 * p + 0, acc[2]);
+                        atomicAdd(dL_dconics + 3 * p + 1, acc[3]);
+                        atomicAdd(dL_dconics + 3 * p + 2, acc[4]);
+                        atomicAdd(dL_dopacities + g, acc[5]);
+                        atomicAdd(dL_dcolors + 3 * g + 0, acc[6]);
+                        atomicAdd(dL_dcolors + 3 * g + 1, acc[7]);
+                        atomicAdd(dL_dcolors + 3 * g + 2, acc[8]);
+                    }
+                } else {
+                    float* rec = records + (size_t)(b0 + j) * kRec;
+    #pragma unroll
+                    for (int q = 0; q < kRec; ++q) rec[q] = acc[q];
                 }
             }
-            if (lane == 0) s_mask[w][s >> 5] = chunk_mask;
+            __syncthreads();
         }
-        __syncthreads();
-        // fixed-order sum over warps: one (tile, Gaussian) partial
-        if (threadIdx.x < n) {
-            const int j = threadIdx.x;
-            float acc[kRec];
-#pragma unroll
-            for (int q = 0; q < kRec; ++q) acc[q] = 0.f;
-            bool any = false;
-#pragma unroll
-            for (int ww = 0; ww < kWarps; ++ww)
-                if (s_mask[ww][j >> 5] & (1u << (j & 31))) {
-                    any = true;
-#pragma unroll
-                    for (int q = 0; q < kRec; ++q) acc[q] += s_grad[ww][j][q];
-                }
-            if (kAtomic) {
-                if (any) {
-                    const int p = __float_as_int(sh_cull[j].w);
-                    const int64_t g = p + t.g_shift;
-                    atomicAdd(dL_dmeans2d + p, make_float2(acc[0], acc[1]));
-                    atomicAdd(dL_dconics + 3 * p + 0, acc[2]);
-                    atomicAdd(dL_dconics + 3 * p + 1, acc[3]);
-                    atomicAdd(dL_dconics + 3 * p + 2, acc[4]);
-                    atomicAdd(dL_dopacities + g, acc[5]);
-                    atomicAdd(dL_dcolors + 3 * g + 0, acc[6]);
-                    atomicAdd(dL_dcolors + 3 * g + 1, acc[7]);
-                    atomicAdd(dL_dcolors + 3 * g + 2, acc[8]);
-                }
-            } else {
-                float* rec = records + (size_t)(b0 + j) * kRec;
-#pragma unroll
-                for (int q = 0; q < kRec; ++q) rec[q] = acc[q];
+        if (!kAtomic) {
+            // Gaussians after every pixel's last one received nothing
+            const int first_unused = max(range.x, maxlast + 1);
+            for (int i = first_unused + threadIdx.x; i < range.y; i += blockDim.x) {
+                float* rec = records + (size_t)i * kRec;
+    #pragma unroll
+                for (int q = 0; q < kRec; ++q) rec[q] = 0.f;
             }
         }
-        __syncthreads();
-    }
-    if (!kAtomic) {
-        // Gaussians after every pixel's last one received nothing
-        const int first_unused = max(range.x, maxlast + 1);
-        for (int i = first_unused + threadIdx.x; i < range.y; i += blockDim.x) {
-            float* rec = records + (size_t)i * kRec;
-#pragma unroll
-            for (int q = 0; q < kRec; ++q) rec[q] = 0.f;
-        }
+        if (!kPersistent) break;
     }
 }
 
@@ -499,10 +529,35 @@ static bool cull_enabled()
 
 using namespace gs;
 
+// Grid for a launch of `kernel`: one CTA per tile, or a persistent grid.
+template <typename K>
+static int raster_grid(K kernel, const GsRasterConfig* cfg, int32_t T_total, unsigned* grid)
+{
+    if (!cfg || !cfg->persistent) {
+        *grid = (unsigned)T_total;
+        return GS_OK;
+    }
+    int dev = 0, sms = 0, fit = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+        cudaSuccess || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kernel, 256, 0) != cudaSuccess)
+        return launch_status("raster grid");
+    int per = cfg->ctas_per_sm > 0 ? std::min(cfg->ctas_per_sm, fit) : fit;
+    per = std::max(per, 1);
+    *grid = (unsigned)std::min<int64_t>((int64_t)per * sms, T_total);
+    return GS_OK;
+}
+
+static int check_config(const GsRasterConfig* cfg, const char* who)
+{
+    if (cfg && cfg->persistent && !cfg->queue) return fail(GS_ERR_INVALID_ARG, "%s: persistent needs a queue", who);
+    return GS_OK;
+}
+
 extern "C" int gs_rasterize_fwd(const GsView* views, int32_t V, int32_t T_total, const float* means2d,
                                 const float* conics, const float* opacities, const float* colors,
                                 const int32_t* isect_ids, const int32_t* tile_ranges, const float* background,
-                                float* out_rgb, float* T_final, int32_t* last_idx, int32_t* n_contrib, void* stream)
+                                float* out_rgb, float* T_final, int32_t* last_idx, int32_t* n_contrib,
+                                const GsRasterConfig* config, void* stream)
 {
     if (V <= 0 || T_total < 0)
         return fail(GS_ERR_INVALID_ARG, "gs_rasterize_fwd: V=%d T_total=%d", V, T_total);
@@ -510,12 +565,20 @@ extern "C" int gs_rasterize_fwd(const GsView* views, int32_t V, int32_t T_total,
         return fail(GS_ERR_INVALID_ARG, "gs_rasterize_fwd: null pointer argument");
     if ((reinterpret_cast<uintptr_t>(means2d) & 7) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7))
         return fail(GS_ERR_INVALID_ARG, "gs_rasterize_fwd: means2d and tile_ranges need 8-byte alignment");
+    if (int rc = check_config(config, "gs_rasterize_fwd")) return rc;
     if (T_total == 0) return GS_OK;
     cudaStream_t s = as_stream(stream);
-    auto kern = cull_enabled() ? k_raster_fwd<true> : k_raster_fwd<false>;
-    kern<<<(unsigned)T_total, 256, 0, s>>>(views, V, reinterpret_cast<const float2*>(means2d), conics, opacities,
-                                           colors, isect_ids, reinterpret_cast<const int2*>(tile_ranges), background,
-                                           out_rgb, T_final, last_idx, n_contrib);
+    const bool cull = cull_enabled(), pers = config && config->persistent;
+    auto kern = cull ? (pers ? k_raster_fwd<true, true> : k_raster_fwd<true, false>)
+                     : (pers ? k_raster_fwd<false, true> : k_raster_fwd<false, false>);
+    unsigned grid;
+    if (int rc = raster_grid(kern, config, T_total, &grid)) return rc;
+    int* queue = pers ? config->queue : nullptr;
+    if (pers && cudaMemsetAsync(queue, 0, sizeof(int), s) != cudaSuccess) return launch_status("gs_rasterize_fwd");
+    kern<<<grid, 256, 0, s>>>(views, V, T_total, config ? config->tile_order : nullptr, queue,
+                              reinterpret_cast<const float2*>(means2d), conics, opacities, colors, isect_ids,
+                              reinterpret_cast<const int2*>(tile_ranges), background, out_rgb, T_final, last_idx,
+                              n_contrib);
     count_launches(1);
     return launch_status("gs_rasterize_fwd");
 }
@@ -533,7 +596,7 @@ extern "C" int gs_rasterize_bwd(const GsView* views, int32_t V, int64_t P, int32
                                 int64_t K_capacity, const float* background, const float* T_final,
                                 const int32_t* last_idx, const float* dL_drgb, int32_t deterministic,
                                 void* workspace, size_t workspace_bytes, float* dL_dmeans2d, float* dL_dconics,
-                                float* dL_dopacities, float* dL_dcolors, void* stream)
+                                float* dL_dopacities, float* dL_dcolors, const GsRasterConfig* config, void* stream)
 {
     if (V <= 0 || P < 0 || T_total < 0 || K_capacity < 0 || K_capacity >= (int64_t(1) << 31))
         return fail(GS_ERR_INVALID_ARG, "gs_rasterize_bwd: V=%d P=%lld T_total=%d K_capacity=%lld", V, (long long)P,
@@ -548,17 +611,27 @@ extern "C" int gs_rasterize_bwd(const GsView* views, int32_t V, int64_t P, int32
     const size_t need = gs_rasterize_bwd_workspace_size(K_capacity, deterministic);
     if (workspace_bytes < need || (need > 0 && !workspace))
         return fail(GS_ERR_INVALID_ARG, "gs_rasterize_bwd: workspace of %zu bytes, need %zu", workspace_bytes, need);
+    if (int rc = check_config(config, "gs_rasterize_bwd")) return rc;
     if (T_total == 0 || P == 0) return GS_OK;
     cudaStream_t s = as_stream(stream);
     float* records = static_cast<float*>(workspace);
-    const bool cull = cull_enabled();
-    auto kern = deterministic ? (cull ? k_raster_bwd<true, false> : k_raster_bwd<false, false>)
-                              : (cull ? k_raster_bwd<true, true> : k_raster_bwd<false, true>);
-    kern<<<(unsigned)T_total, 256, 0, s>>>(views, V, reinterpret_cast<const float2*>(means2d), conics, opacities,
-                                           colors, isect_ids, reinterpret_cast<const int2*>(tile_ranges), background,
-                                           T_final, last_idx, dL_drgb, records,
-                                           reinterpret_cast<float2*>(dL_dmeans2d), dL_dconics, dL_dopacities,
-                                           dL_dcolors);
+    const bool cull = cull_enabled(), pers = config && config->persistent;
+    using KB = decltype(&k_raster_bwd<true, true, true>);
+    static const KB table[2][2][2] = {
+        {{k_raster_bwd<false, false, false>, k_raster_bwd<false, false, true>},
+         {k_raster_bwd<false, true, false>, k_raster_bwd<false, true, true>}},
+        {{k_raster_bwd<true, false, false>, k_raster_bwd<true, false, true>},
+         {k_raster_bwd<true, true, false>, k_raster_bwd<true, true, true>}}};
+    const KB kern = table[cull][!deterministic][pers];
+    unsigned grid;
+    if (int rc = raster_grid(kern, config, T_total, &grid)) return rc;
+    int* queue = pers ? config->queue : nullptr;
+    if (pers && cudaMemsetAsync(queue, 0, sizeof(int), s) != cudaSuccess) return launch_status("gs_rasterize_bwd");
+    kern<<<grid, 256, 0, s>>>(views, V, T_total, config ? config->tile_order : nullptr, queue,
+                              reinterpret_cast<const float2*>(means2d), conics, opacities, colors, isect_ids,
+                              reinterpret_cast<const int2*>(tile_ranges), background, T_final, last_idx, dL_drgb,
+                              records, reinterpret_cast<float2*>(dL_dmeans2d), dL_dconics, dL_dopacities,
+                              dL_dcolors);
     count_launches(1);
     if (deterministic) {
         k_reduce_records<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(

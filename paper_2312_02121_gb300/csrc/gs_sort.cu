@@ -390,6 +390,41 @@ __global__ void k_finalize(const int32_t* __restrict__ K_dev, int64_t cap, const
     if (i == K - 1 || keys[i + 1] != t) tile_ranges[t].y = i + 1;
 }
 
+// Longest-first key of each tile: 65535 - min(list length, 65535).
+__global__ void k_tile_len_keys(int32_t T, const int2* __restrict__ tile_ranges, uint32_t* __restrict__ keys)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < T) {
+        const int2 r = tile_ranges[i];
+        keys[i] = 65535u - (uint32_t)min(max(r.y - r.x, 0), 65535);
+    }
+}
+
+__global__ void k_copy_u32(int32_t n, const uint32_t* __restrict__ src, int32_t* __restrict__ dst)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (int32_t)src[i];
+}
+
+struct OrderLayout {
+    uint32_t *ka, *kb, *va, *vb, *hist, *digit_total;
+    size_t bytes;
+};
+
+static OrderLayout carve_order(void* ws, int64_t T)
+{
+    Carver c(ws);
+    OrderLayout L;
+    L.ka = c.take<uint32_t>(T);
+    L.kb = c.take<uint32_t>(T);
+    L.va = c.take<uint32_t>(T);
+    L.vb = c.take<uint32_t>(T);
+    L.hist = c.take<uint32_t>((size_t)((T + kRTile - 1) / kRTile) * kMaxBins + 1);
+    L.digit_total = c.take<uint32_t>(kMaxBins);
+    L.bytes = c.used;
+    return L;
+}
+
 struct SortLayout {
     uint32_t *dkey_a, *dkey_b, *dval_a, *dval_b;
     int64_t* block_sums;
@@ -487,4 +522,31 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
                                                                       isect_pos, reinterpret_cast<int2*>(tile_ranges));
     count_launches(1);
     return launch_status("gs_bin_and_sort");
+}
+
+extern "C" size_t gs_tile_order_workspace_size(int32_t T_total)
+{
+    return T_total < 0 ? 0 : carve_order(nullptr, T_total).bytes;
+}
+
+extern "C" int gs_tile_order(const int32_t* tile_ranges, int32_t T_total, void* workspace, size_t workspace_bytes,
+                             int32_t* order, void* stream)
+{
+    if (T_total < 0) return fail(GS_ERR_INVALID_ARG, "gs_tile_order: T_total=%d", T_total);
+    if (T_total == 0) return GS_OK;
+    if (!tile_ranges || !order || (reinterpret_cast<uintptr_t>(tile_ranges) & 7))
+        return fail(GS_ERR_INVALID_ARG, "gs_tile_order: null or misaligned pointer argument");
+    const OrderLayout need = carve_order(nullptr, T_total);
+    if (!workspace || workspace_bytes < need.bytes)
+        return fail(GS_ERR_INVALID_ARG, "gs_tile_order: workspace of %zu bytes, need %zu", workspace_bytes,
+                    need.bytes);
+    cudaStream_t s = as_stream(stream);
+    const OrderLayout L = carve_order(workspace, T_total);
+    const unsigned g = (unsigned)((T_total + 255) / 256);
+    k_tile_len_keys<<<g, 256, 0, s>>>(T_total, reinterpret_cast<const int2*>(tile_ranges), L.ka);
+    uint32_t *k, *v;
+    lsd_sort(L.ka, L.kb, L.va, L.vb, nullptr, T_total, T_total, 16, RadixBufs{L.hist, L.digit_total}, s, &k, &v);
+    k_copy_u32<<<g, 256, 0, s>>>(T_total, v, order);
+    count_launches(2);
+    return launch_status("gs_tile_order");
 }

@@ -92,7 +92,8 @@ def project(views: B.Views, p: Params, eps2d: float, stream=None):
 
 
 def forward(views: B.Views, p: Params, eps2d: float = 0.3, background: Optional[torch.Tensor] = None,
-            K_capacity: Optional[int] = None, stream=None, count_contrib: bool = False) -> Frame:
+            K_capacity: Optional[int] = None, stream=None, count_contrib: bool = False,
+            config: Optional[B.RasterConfig] = None) -> Frame:
     """Projection, binning + sort and compositing of every view.  Without
     ``K_capacity`` the exact intersection count is read back (one sync)."""
     _check_params(p)
@@ -116,13 +117,14 @@ def forward(views: B.Views, p: Params, eps2d: float = 0.3, background: Optional[
     last_idx = torch.empty(pix, dtype=torch.int32, device=dev)
     n_contrib = torch.empty(pix, dtype=torch.int32, device=dev) if count_contrib else None
     B.gs_rasterize_fwd(views, pr["means2d"], pr["conics"], p.opacities, p.colors, isect_ids, tile_ranges, background,
-                       out_rgb, T_final, last_idx, n_contrib, stream)
+                       out_rgb, T_final, last_idx, n_contrib, config, stream)
     return Frame(views, eps2d, background, cap, pr["means2d"], pr["conics"], pr["depths"], pr["rects"],
                  pr["touched"], pr["K_total"], isect_ids, isect_pos, emit_start, tile_ranges, K, flags, out_rgb,
                  T_final, last_idx, ws, n_contrib)
 
 
-def backward(f: Frame, p: Params, dL_drgb: torch.Tensor, stream=None, deterministic: bool = False) -> dict:
+def backward(f: Frame, p: Params, dL_drgb: torch.Tensor, stream=None, deterministic: bool = False,
+             config: Optional[B.RasterConfig] = None) -> dict:
     """Gradients of L w.r.t. means, quats, scales, opacities, colors (and the
     2D intermediates means2d, conics) given dL/dC [pixels, 3].
     ``deterministic`` selects the run-to-run identical reduction."""
@@ -138,7 +140,7 @@ def backward(f: Frame, p: Params, dL_drgb: torch.Tensor, stream=None, determinis
     ws = torch.empty(nws, dtype=torch.uint8, device=dev) if nws else None
     B.gs_rasterize_bwd(views, f.means2d, f.conics, p.opacities, p.colors, f.isect_ids, f.isect_pos, f.emit_start,
                        f.touched, f.tile_ranges, f.K, f.K_capacity, f.background, f.T_final, f.last_idx, dL_drgb,
-                       deterministic, ws, g2, gc, go, gcol, stream)
+                       deterministic, ws, g2, gc, go, gcol, config, stream)
     gm = torch.zeros(max(N, 1), 3, device=dev)
     gq = torch.zeros(max(N, 1), 4, device=dev)
     gs = torch.zeros(max(N, 1), 3, device=dev)

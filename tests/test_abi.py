@@ -84,7 +84,8 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert b"null pointer" in lib.gs_last_error()
     assert lib.gs_project(None, -1, 10, None, None, None, 0.3, None, None, None, None, None, None, None) == 1
     assert lib.gs_rasterize_fwd(None, 0, 4, None, None, None, None, None, None, None, None, None, None, None,
-                                None) == 1
+                                None, None) == 1
+    assert lib.gs_tile_order(None, 5, None, 0, None, None) == 1
     assert lib.gs_bin_and_sort(None, 1, 10, 4, None, None, None, 100, None, 0, None, None, None, None, None, None,
                                None) == 1
     assert lib.gs_project_bwd(None, 1, -5, None, None, None, 0.3, None, None, None, None, None, None, None) == 1

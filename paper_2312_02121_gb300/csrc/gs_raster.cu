@@ -33,7 +33,7 @@
 namespace gs {
 
 constexpr int kFwdBatch = 256;
-constexpr int kBwdBatch = 128;
+constexpr int kBwdBatch = 64;  // deterministic mode (per-warp partial slots)
 constexpr int kWarps = 8;
 constexpr int kRec = 9;  // dmu'(2) dconic(3) dopacity(1) dcolor(3)
 constexpr float kLog2e = 1.4426950408889634f;
@@ -251,52 +251,42 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
 // backward
 // ---------------------------------------------------------------------------
 
-// Sum of v[0..8] over the warp by reduce-scatter: the nine values sit in 16
-// slots; at each of four shuffle levels a lane keeps half of its slots and
-// adds the partner's copy of them, and a last level pairs neighbours.  Lane L
-// ends up with the total of slot L >> 1.
-__device__ __forceinline__ float warp_sum9(const float (&v)[kRec], int lane)
+// Sum of r[0..8] over the warp through shared memory.  Every lane stores its
+// nine terms as one row of the warp's 32 x 12 buffer (two 16-byte stores and
+// one 4-byte store); then lane L < 27 sums column L / 3 over the rows
+// congruent to L % 3 modulo 3 (11 or 10 rows; the three parts of a column sit
+// 12 banks apart, so the loads are conflict-free but for one pair), and two
+// shuffles fold the three parts.  Lane 3q returns the total of term q.  The
+// summation order is fixed, so results are deterministic.
+constexpr int kRedStride = 12;
+
+struct RedLane {
+    int q, part;  // column and row residue this lane sums
+};
+
+__device__ __forceinline__ RedLane red_lane(int lane)
 {
-    float w8[8];
-    {
-        const bool hi = lane & 16;
+    return RedLane{lane / 3, lane % 3};
+}
+
+__device__ __forceinline__ float warp_sum9(const float (&r)[kRec], float* buf, int lane, RedLane rl)
+{
+    float* row = buf + lane * kRedStride;
+    *reinterpret_cast<float4*>(row) = make_float4(r[0], r[1], r[2], r[3]);
+    *reinterpret_cast<float4*>(row + 4) = make_float4(r[4], r[5], r[6], r[7]);
+    row[8] = r[8];
+    __syncwarp();
+    float acc = 0.f;
+    if (lane < 3 * kRec) {
+        const float* col = buf + rl.part * kRedStride + rl.q;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const float lo_v = v[i];
-            const float hi_v = (8 + i < kRec) ? v[8 + i] : 0.f;
-            const float send = hi ? lo_v : hi_v;
-            const float keep = hi ? hi_v : lo_v;
-            w8[i] = keep + __shfl_xor_sync(kFull, send, 16);
-        }
+        for (int i = 0; i < 11; ++i)
+            if (rl.part + 3 * i < 32) acc += col[3 * i * kRedStride];
     }
-    float w4[4];
-    {
-        const bool hi = lane & 8;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float send = hi ? w8[i] : w8[4 + i];
-            const float keep = hi ? w8[4 + i] : w8[i];
-            w4[i] = keep + __shfl_xor_sync(kFull, send, 8);
-        }
-    }
-    float w2[2];
-    {
-        const bool hi = lane & 4;
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const float send = hi ? w4[i] : w4[2 + i];
-            const float keep = hi ? w4[2 + i] : w4[i];
-            w2[i] = keep + __shfl_xor_sync(kFull, send, 4);
-        }
-    }
-    float w1;
-    {
-        const bool hi = lane & 2;
-        const float send = hi ? w2[0] : w2[1];
-        const float keep = hi ? w2[1] : w2[0];
-        w1 = keep + __shfl_xor_sync(kFull, send, 2);
-    }
-    return w1 + __shfl_xor_sync(kFull, w1, 1);
+    __syncwarp();  // the buffer is free again
+    const float a1 = __shfl_down_sync(kFull, acc, 1);
+    const float a2 = __shfl_down_sync(kFull, acc, 2);
+    return acc + (a1 + a2);  // lane 3q: part 0 + (part 1 + part 2)
 }
 
 // kAtomic: each (tile, Gaussian) sum is added straight into the per-projection
@@ -304,7 +294,7 @@ __device__ __forceinline__ float warp_sum9(const float (&v)[kRec], int lane)
 // tiles varies).  Otherwise it is written as a record for k_reduce_records
 // (deterministic).
 template <bool kCull, bool kAtomic, bool kPersistent>
-__global__ void __launch_bounds__(256, 5)
+__global__ void __launch_bounds__(256, 4)
 k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t* __restrict__ tile_order,
              int* __restrict__ queue, const float2* __restrict__ means2d,
              const float* __restrict__ conics, const float* __restrict__ opacities, const float* __restrict__ colors,
@@ -314,9 +304,15 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
              float2* __restrict__ dL_dmeans2d, float* __restrict__ dL_dconics, float* __restrict__ dL_dopacities,
              float* __restrict__ dL_dcolors)
 {
-    __shared__ float4 sh_xy[kBwdBatch], sh_q[kBwdBatch], sh_col[kBwdBatch], sh_cull[kBwdBatch];
-    __shared__ float s_grad[kWarps][kBwdBatch][kRec];
-    __shared__ unsigned s_mask[kWarps][kBwdBatch / 32];
+    // deterministic: one partial slot per warp, summed in warp order; atomic:
+    // one slot per Gaussian, accumulated with shared-memory atomics (less
+    // shared memory, so larger batches)
+    constexpr int kB = kAtomic ? 256 : kBwdBatch;
+    constexpr int kSlots = kAtomic ? 1 : kWarps;
+    __shared__ float4 sh_xy[kB], sh_q[kB], sh_col[kB], sh_cull[kB];
+    __shared__ float s_grad[kSlots][kB][kRec];
+    __shared__ unsigned s_mask[kSlots][kB / 32];
+    __shared__ __align__(16) float s_red[kWarps][32 * kRedStride];
     __shared__ int s_maxlast[kWarps];
     __shared__ int s_next;
     for (int qi = blockIdx.x;;) {
@@ -343,6 +339,7 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
             if (background) bgT = T * (background[0] * g0 + background[1] * g1 + background[2] * g2);
         }
         float SdL = 0.f;  // S_n . dL/dC, S_n = sum_{m>n} c_m alpha_m T_m
+        const RedLane rl = red_lane(lane);
 
         // the warp's and the tile's largest last index bound the work
         int wl = last;
@@ -354,10 +351,14 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
     #pragma unroll
         for (int i = 1; i < kWarps; ++i) maxlast = max(maxlast, s_maxlast[i]);
 
-        const int nbatch = maxlast >= range.x ? (maxlast - range.x) / kBwdBatch + 1 : 0;
+        const int nbatch = maxlast >= range.x ? (maxlast - range.x) / kB + 1 : 0;
         for (int k = nbatch - 1; k >= 0; --k) {
-            const int b0 = range.x + k * kBwdBatch;
-            const int n = min(kBwdBatch, maxlast - b0 + 1);
+            const int b0 = range.x + k * kB;
+            const int n = min(kB, maxlast - b0 + 1);
+            if (kAtomic) {
+                for (int i = threadIdx.x; i < kB * kRec; i += blockDim.x) (&s_grad[0][0][0])[i] = 0.f;
+                if (threadIdx.x < kB / 32) s_mask[0][threadIdx.x] = 0u;
+            }
             if (threadIdx.x < n) {
                 const int p = isect_ids[b0 + threadIdx.x];
                 const int64_t g = p + t.g_shift;
@@ -368,7 +369,7 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
             __syncthreads();
             // this warp only needs entries up to its own last index
             const int nw = min(n, wl - b0 + 1);
-            for (int s = ((kBwdBatch - 1) >> 5) << 5; s >= 0; s -= 32) {
+            for (int s = ((kB - 1) >> 5) << 5; s >= 0; s -= 32) {
                 unsigned chunk_mask = 0u;  // Gaussians of this chunk the warp wrote a partial for
                 if (s < nw) {
                     bool hit = s + lane < nw;
@@ -380,55 +381,67 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                         const int hb = 31 - __clz(m);
                         m ^= 1u << hb;
                         const int j = s + hb;  // back to front
+                        // every lane evaluates; lanes that do not composite this
+                        // Gaussian carry zero terms (selects, no branches)
+                        const float4 xy = sh_xy[j];
+                        const float4 qq = sh_q[j];
+                        const float4 col = sh_col[j];
+                        const float dx = xy.x - t.cx, dy = xy.y - t.cy;
+                        float u;
+                        const float p2 = neg_sigma_log2(qq, dx, dy, u);
+                        const float ge = ex2(p2);  // exp(-sigma)
+                        const float raw = __fmul_rn(xy.z, ge);
+                        const float alpha = fminf(GS_ALPHA_MAX, raw);
+                        const bool contrib = (b0 + j <= last) && (p2 <= 0.f) && (alpha >= GS_ALPHA_MIN);
+                        const unsigned cm = __ballot_sync(kFull, contrib);
+                        if (cm == 0u) continue;
+                        const float inv1ma = __fdividef(1.f, 1.f - alpha);
+                        const float Tn = T * inv1ma;  // T before this Gaussian
+                        const float wgt = contrib ? alpha * Tn : 0.f;
+                        const float cdot = fmaf(col.x, g0, fmaf(col.y, g1, col.z * g2));
+                        const float dL_dalpha = fmaf(Tn, cdot, -(SdL + bgT) * inv1ma);
+                        const float gd = (contrib && raw < GS_ALPHA_MAX) ? ge * dL_dalpha : 0.f;  // dL/do
+                        SdL = fmaf(wgt, cdot, SdL);
+                        T = contrib ? Tn : T;
+                        const float ds = -xy.z * gd;  // dL/dsigma
+                        const float hds = 0.5f * ds;
                         float r[kRec];
+                        r[0] = ds * (xy.w * u);                    // Y Delta = (a u, b u + D dy)
+                        r[1] = ds * fmaf(qq.w, u, col.w * dy);
+                        r[2] = hds * dx * dx;
+                        r[3] = ds * dx * dy;
+                        r[4] = hds * dy * dy;
+                        r[5] = gd;
+                        r[6] = wgt * g0;
+                        r[7] = wgt * g1;
+                        r[8] = wgt * g2;
+                        chunk_mask |= 1u << hb;
+                        float* slot = s_grad[kAtomic ? 0 : w][j];
+                        if (__popc(cm) == 1) {
+                            // one contributing pixel: its terms are the warp's sum
+                            if (contrib) {
     #pragma unroll
-                        for (int q = 0; q < kRec; ++q) r[q] = 0.f;
-                        bool contrib = false;
-                        if (b0 + j <= last) {
-                            const float4 xy = sh_xy[j];
-                            const float4 qq = sh_q[j];
-                            const float dx = xy.x - t.cx, dy = xy.y - t.cy;
-                            float u;
-                            const float p2 = neg_sigma_log2(qq, dx, dy, u);
-                            if (p2 <= 0.f) {
-                                const float ge = ex2(p2);  // exp(-sigma)
-                                const float raw = __fmul_rn(xy.z, ge);
-                                const float alpha = fminf(GS_ALPHA_MAX, raw);
-                                if (alpha >= GS_ALPHA_MIN) {
-                                    contrib = true;
-                                    const float4 col = sh_col[j];
-                                    const float inv1ma = __fdividef(1.f, 1.f - alpha);
-                                    const float Tn = T * inv1ma;  // T before this Gaussian
-                                    const float wgt = alpha * Tn;
-                                    const float cdot = fmaf(col.x, g0, fmaf(col.y, g1, col.z * g2));
-                                    const float dL_dalpha = fmaf(Tn, cdot, -(SdL + bgT) * inv1ma);
-                                    SdL = fmaf(wgt, cdot, SdL);
-                                    T = Tn;
-                                    r[6] = wgt * g0;
-                                    r[7] = wgt * g1;
-                                    r[8] = wgt * g2;
-                                    if (raw < GS_ALPHA_MAX) {
-                                        const float gd = ge * dL_dalpha;
-                                        r[5] = gd;                     // dL/do
-                                        const float ds = -xy.z * gd;  // dL/dsigma
-                                        // Y Delta = (a u, b u + D dy)
-                                        r[0] = ds * (xy.w * u);
-                                        r[1] = ds * fmaf(qq.w, u, col.w * dy);
-                                        const float hds = 0.5f * ds;
-                                        r[2] = hds * dx * dx;
-                                        r[3] = ds * dx * dy;
-                                        r[4] = hds * dy * dy;
-                                    }
+                                for (int q = 0; q < kRec; ++q) {
+                                    if (kAtomic) atomicAdd(slot + q, r[q]);
+                                    else slot[q] = r[q];
                                 }
                             }
+                        } else {
+                            const float tot = warp_sum9(r, s_red[w], lane, rl);
+                            if (lane < 3 * kRec && rl.part == 0) {
+                                if (kAtomic) atomicAdd(slot + rl.q, tot);
+                                else slot[rl.q] = tot;
+                            }
                         }
-                        if (__ballot_sync(kFull, contrib) == 0u) continue;
-                        const float tot = warp_sum9(r, lane);
-                        if (!(lane & 1) && (lane >> 1) < kRec) s_grad[w][j][lane >> 1] = tot;
-                        chunk_mask |= 1u << hb;
                     }
                 }
-                if (lane == 0) s_mask[w][s >> 5] = chunk_mask;
+                if (lane == 0) {
+                    if (kAtomic) {
+                        if (chunk_mask) atomicOr(&s_mask[0][s >> 5], chunk_mask);
+                    } else {
+                        s_mask[w][s >> 5] = chunk_mask;
+                    }
+                }
             }
             __syncthreads();
             // fixed-order sum over warps: one (tile, Gaussian) partial
@@ -439,7 +452,7 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                 for (int q = 0; q < kRec; ++q) acc[q] = 0.f;
                 bool any = false;
     #pragma unroll
-                for (int ww = 0; ww < kWarps; ++ww)
+                for (int ww = 0; ww < kSlots; ++ww)
                     if (s_mask[ww][j >> 5] & (1u << (j & 31))) {
                         any = true;
     #pragma unroll

@@ -209,26 +209,25 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                 while (m) {
                     const int j = s + __ffs(m) - 1;
                     m &= m - 1;
-                    if (done) continue;
+                    // every lane evaluates; predicates decide (no divergent branches)
                     const float4 xy = sh_xy[j];
                     float u;
                     const float p2 = neg_sigma_log2(sh_q[j], xy.x - t.cx, xy.y - t.cy, u);
-                    if (p2 > 0.f) continue;  // sigma < 0 (not a positive-definite conic)
                     const float alpha = fminf(GS_ALPHA_MAX, __fmul_rn(xy.z, ex2(p2)));
-                    if (alpha < GS_ALPHA_MIN) continue;
                     const float Tn = T * (1.f - alpha);
-                    if (Tn < GS_T_MIN) {
-                        done = true;
-                        continue;
-                    }
+                    // p2 > 0 means sigma < 0 (not a positive-definite conic): skipped
+                    const bool take = !done && p2 <= 0.f && alpha >= GS_ALPHA_MIN;
+                    const bool stop = take && Tn < GS_T_MIN;  // not composited; the pixel is finished
+                    const bool comp = take && !stop;
+                    done = done || stop;
                     const float4 c = sh_col[j];
-                    const float wgt = alpha * T;
+                    const float wgt = comp ? alpha * T : 0.f;
                     C0 = fmaf(wgt, c.x, C0);
                     C1 = fmaf(wgt, c.y, C1);
                     C2 = fmaf(wgt, c.z, C2);
-                    T = Tn;
-                    last = b0 + j;
-                    ++count;
+                    T = comp ? Tn : T;
+                    last = comp ? b0 + j : last;
+                    count += comp;
                 }
                 if (__all_sync(kFull, done)) break;
             }
@@ -252,13 +251,14 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
 // ---------------------------------------------------------------------------
 
 // Sum of r[0..8] over the warp through shared memory.  Every lane stores its
-// nine terms as one row of the warp's 32 x 12 buffer (two 16-byte stores and
-// one 4-byte store); then lane L < 27 sums column L / 3 over the rows
-// congruent to L % 3 modulo 3 (11 or 10 rows; the three parts of a column sit
-// 12 banks apart, so the loads are conflict-free but for one pair), and two
-// shuffles fold the three parts.  Lane 3q returns the total of term q.  The
+// nine terms as one 10-float row of the warp's buffer (four 8-byte stores and
+// one 4-byte store; at a 10-word row stride the 8-byte stores of a half-warp
+// hit 32 distinct banks).  Lane L < 27 then sums column L / 3 over the rows
+// congruent to L % 3 modulo 3 (11 or 10 rows); the three parts of a column
+// start 10 banks apart, so each of those loads is conflict-free.  Two
+// shuffles fold the parts: lane 3q returns the total of term q.  The
 // summation order is fixed, so results are deterministic.
-constexpr int kRedStride = 12;
+constexpr int kRedStride = 10;
 
 struct RedLane {
     int q, part;  // column and row residue this lane sums
@@ -272,8 +272,10 @@ __device__ __forceinline__ RedLane red_lane(int lane)
 __device__ __forceinline__ float warp_sum9(const float (&r)[kRec], float* buf, int lane, RedLane rl)
 {
     float* row = buf + lane * kRedStride;
-    *reinterpret_cast<float4*>(row) = make_float4(r[0], r[1], r[2], r[3]);
-    *reinterpret_cast<float4*>(row + 4) = make_float4(r[4], r[5], r[6], r[7]);
+    *reinterpret_cast<float2*>(row + 0) = make_float2(r[0], r[1]);
+    *reinterpret_cast<float2*>(row + 2) = make_float2(r[2], r[3]);
+    *reinterpret_cast<float2*>(row + 4) = make_float2(r[4], r[5]);
+    *reinterpret_cast<float2*>(row + 6) = make_float2(r[6], r[7]);
     row[8] = r[8];
     __syncwarp();
     float acc = 0.f;

@@ -152,7 +152,9 @@ size_t gs_bin_and_sort_workspace_size(int64_t P, int64_t K_capacity, int32_t T_t
  *   out: isect_ids[K_capacity]   projection of each sorted pair
  *        isect_pos[K_capacity]   sorted position of each pair in emission
  *                                order (the order p's pairs are generated:
- *                                pair j of p is emission emit_start[p] + j)
+ *                                pair j of p is emission emit_start[p] + j);
+ *                                nullable -- only the deterministic
+ *                                gs_rasterize_bwd reads it
  *        emit_start[P]           first emission index of each projection
  *        tile_ranges[T_total,2]  [start, end) of each tile's sorted pairs
  *        K_out                   (device int32) number of pairs K

@@ -334,42 +334,71 @@ k_scan_block_sums(int64_t nblk, int64_t* __restrict__ block_sums, int64_t cap, i
 // Emission of the (tile, projection) pairs in depth order: pair j of the
 // projection at depth rank r gets emission index off[r] + j; its key is the
 // global tile id (row-major inside the rectangle), its owner the projection.
+// A block takes kEmitTile consecutive ranks, scans their pair counts into
+// shared memory, and then its threads write consecutive output slots, each
+// finding the rank that owns its slot by binary search -- so the stores of a
+// warp are contiguous whatever the rectangle sizes.
 __global__ void __launch_bounds__(256)
 k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __restrict__ order,
        const int32_t* __restrict__ touched, const short4* __restrict__ rects, const int64_t* __restrict__ block_prefix,
        int64_t cap, uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ owner, int32_t* __restrict__ emit_start)
 {
+    __shared__ int s_off[kEmitTile + 1];  // block-local first slot of each rank
+    __shared__ uint32_t s_p[kEmitTile];
+    __shared__ int s_x0[kEmitTile], s_w[kEmitTile];
+    __shared__ int s_row0[kEmitTile];      // tile id of the rectangle's first row start (x = 0)
+    __shared__ int s_tx[kEmitTile];        // tiles_x of the projection's view
     const int64_t base = (int64_t)blockIdx.x * kEmitTile;
-    // thread-contiguous items so that one thread's pairs are consecutive
-    uint32_t p[kEmitItems];
+    const int64_t gbase = block_prefix[blockIdx.x];
     int cnt[kEmitItems];
-    int64_t s = 0;
+    int s = 0;
 #pragma unroll
     for (int k = 0; k < kEmitItems; ++k) {
-        const int64_t r = base + threadIdx.x * kEmitItems + k;
-        p[k] = r < P ? order[r] : 0u;
-        cnt[k] = r < P ? touched[p[k]] : 0;
+        const int li = threadIdx.x * kEmitItems + k;
+        const int64_t r = base + li;
+        uint32_t p = 0u;
+        cnt[k] = 0;
+        if (r < P) {
+            p = order[r];
+            cnt[k] = touched[p];
+            if (cnt[k] > 0) {
+                const GsView& view = views[view_of_projection(views, V, (int64_t)p)];
+                const short4 rc = rects[p];
+                s_x0[li] = rc.x;
+                s_w[li] = rc.z - rc.x;
+                s_row0[li] = view.tile_offset + rc.y * view.tiles_x;
+                s_tx[li] = view.tiles_x;
+            }
+        }
+        s_p[li] = p;
         s += cnt[k];
     }
-    int64_t off = block_prefix[blockIdx.x] + block_exclusive_scan_256<int64_t>(s, nullptr);
+    int total;
+    int off = block_exclusive_scan_256<int>(s, &total);
 #pragma unroll
     for (int k = 0; k < kEmitItems; ++k) {
-        const int64_t r = base + threadIdx.x * kEmitItems + k;
-        if (r >= P) break;
-        if (cnt[k] > 0) {
-            emit_start[p[k]] = (int32_t)min(off, (int64_t)INT32_MAX);
-            const GsView& view = views[view_of_projection(views, V, (int64_t)p[k])];
-            const short4 rc = rects[p[k]];
-            const int tx = view.tiles_x, toff = view.tile_offset;
-            int64_t e = off;
-            for (int ty = rc.y; ty < rc.w; ++ty)
-                for (int x = rc.x; x < rc.z; ++x, ++e)
-                    if (e < cap) {
-                        tile_keys[e] = (uint32_t)(toff + ty * tx + x);
-                        owner[e] = p[k];
-                    }
-        }
+        const int li = threadIdx.x * kEmitItems + k;
+        s_off[li] = off;
+        if (cnt[k] > 0) emit_start[s_p[li]] = (int32_t)min(gbase + off, (int64_t)INT32_MAX);
         off += cnt[k];
+    }
+    if (threadIdx.x == 0) s_off[kEmitTile] = total;
+    __syncthreads();
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int64_t ge = gbase + e;
+        if (ge >= cap) break;
+        // last rank whose first slot is <= e (ranks with no pairs share it with
+        // the next one; the last of them owns the slot)
+        int lo = 0, hi = kEmitTile - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        const int j = e - s_off[lo];
+        const int w = s_w[lo];
+        const int dy = j / w;
+        tile_keys[ge] = (uint32_t)(s_row0[lo] + dy * s_tx[lo] + s_x0[lo] + (j - dy * w));
+        owner[ge] = s_p[lo];
     }
 }
 
@@ -384,7 +413,7 @@ __global__ void k_finalize(const int32_t* __restrict__ K_dev, int64_t cap, const
     if (i >= K) return;
     const uint32_t e = emit_idx ? emit_idx[i] : (uint32_t)i;
     isect_ids[i] = (int32_t)owner[e];
-    isect_pos[e] = i;
+    if (isect_pos) isect_pos[e] = i;
     const uint32_t t = keys[i];
     if (i == 0 || keys[i - 1] != t) tile_ranges[t].x = i;
     if (i == K - 1 || keys[i + 1] != t) tile_ranges[t].y = i + 1;
@@ -482,7 +511,7 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
         return fail(GS_ERR_INVALID_ARG, "gs_bin_and_sort: V=%d P=%lld T_total=%d K_capacity=%lld", V, (long long)P,
                     T_total, (long long)K_capacity);
     if (!views || !tile_ranges || !K_out || !flags || (P > 0 && (!rects || !depths || !touched || !emit_start)) ||
-        (K_capacity > 0 && (!isect_ids || !isect_pos)))
+        (K_capacity > 0 && !isect_ids))
         return fail(GS_ERR_INVALID_ARG, "gs_bin_and_sort: null pointer argument");
     if ((reinterpret_cast<uintptr_t>(rects) & 7) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7))
         return fail(GS_ERR_INVALID_ARG, "gs_bin_and_sort: rects and tile_ranges need 8-byte alignment");

@@ -303,6 +303,41 @@ int gs_project_bwd(const GsView* views, int32_t V, int64_t P, const float* means
                    const float* dL_dconics, float* dL_dmeans, float* dL_dquats, float* dL_dscales,
                    void* stream);
 
+/*
+ * FP64 instantiations of the four arithmetic stages, for checking the analytic
+ * backward of Sec. 3 against finite differences (e.g. torch.autograd.gradcheck)
+ * and against an fp64 reference.  Arguments are those of the fp32 entry points
+ * with double in place of float, except that depths stay fp32 (they are the
+ * sort key of gs_bin_and_sort, which both precisions share).  Thresholds are
+ * 1/255, 0.99 and 1e-4 in double.  The fp64 kernels use smaller batches and
+ * are not tuned for speed.
+ */
+int gs_project_f64(const GsView* views, int32_t V, int64_t P, const double* means, const double* quats,
+                   const double* scales, double eps2d, double* means2d, double* conics, float* depths,
+                   int16_t* rects, int32_t* touched, int64_t* K_total, void* stream);
+
+int gs_rasterize_fwd_f64(const GsView* views, int32_t V, int32_t T_total, const double* means2d,
+                         const double* conics, const double* opacities, const double* colors,
+                         const int32_t* isect_ids, const int32_t* tile_ranges, const double* background,
+                         double* out_rgb, double* T_final, int32_t* last_idx, int32_t* n_contrib,
+                         const GsRasterConfig* config, void* stream);
+
+size_t gs_rasterize_bwd_f64_workspace_size(int64_t K_capacity, int32_t deterministic);
+
+int gs_rasterize_bwd_f64(const GsView* views, int32_t V, int64_t P, int32_t T_total, const double* means2d,
+                         const double* conics, const double* opacities, const double* colors,
+                         const int32_t* isect_ids, const int32_t* isect_pos, const int32_t* emit_start,
+                         const int32_t* touched, const int32_t* tile_ranges, const int32_t* K,
+                         int64_t K_capacity, const double* background, const double* T_final,
+                         const int32_t* last_idx, const double* dL_drgb, int32_t deterministic, void* workspace,
+                         size_t workspace_bytes, double* dL_dmeans2d, double* dL_dconics, double* dL_dopacities,
+                         double* dL_dcolors, const GsRasterConfig* config, void* stream);
+
+int gs_project_bwd_f64(const GsView* views, int32_t V, int64_t P, const double* means, const double* quats,
+                       const double* scales, double eps2d, const int32_t* touched, const double* dL_dmeans2d,
+                       const double* dL_dconics, double* dL_dmeans, double* dL_dquats, double* dL_dscales,
+                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -61,6 +61,7 @@ _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
 _I64 = ctypes.c_int64
 _F = ctypes.c_float
+_D = ctypes.c_double
 _SZ = ctypes.c_size_t
 
 # C signatures, in header order
@@ -80,6 +81,12 @@ SIGNATURES = {
     "gs_rasterize_bwd": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P,
                                         _P, _P, _I32, _P, _SZ, _P, _P, _P, _P, _P, _P]),
     "gs_project_bwd": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _F, _P, _P, _P, _P, _P, _P, _P]),
+    "gs_project_f64": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
+    "gs_rasterize_fwd_f64": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gs_rasterize_bwd_f64_workspace_size": (_SZ, [_I64, _I32]),
+    "gs_rasterize_bwd_f64": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I64, _P,
+                                            _P, _P, _P, _I32, _P, _SZ, _P, _P, _P, _P, _P, _P]),
+    "gs_project_bwd_f64": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -186,9 +193,15 @@ def gs_kernel_launches() -> int:
     return int(load().gs_kernel_launches())
 
 
+def _f64(t) -> bool:
+    return t is not None and t.dtype == torch.float64
+
+
 def gs_project(views: Views, means, quats, scales, eps2d: float, means2d, conics, depths, rects, touched,
                K_total=None, stream=None):
-    _check(load().gs_project(_ptr(views.device), views.V, views.P, _ptr(means), _ptr(quats), _ptr(scales),
+    """fp32 or fp64 (gs_project_f64) by the dtype of ``means``; depths are fp32 in both."""
+    fn = load().gs_project_f64 if _f64(means) else load().gs_project
+    _check(fn(_ptr(views.device), views.V, views.P, _ptr(means), _ptr(quats), _ptr(scales),
                              float(eps2d), _ptr(means2d), _ptr(conics), _ptr(depths), _ptr(rects), _ptr(touched),
                              _ptr(K_total), _stream(stream)))
 
@@ -251,14 +264,16 @@ def gs_tile_order(tile_ranges, T_total: int, workspace, order, stream=None):
 
 def gs_rasterize_fwd(views: Views, means2d, conics, opacities, colors, isect_ids, tile_ranges, background,
                      out_rgb, T_final, last_idx, n_contrib=None, config: Optional[RasterConfig] = None, stream=None):
-    _check(load().gs_rasterize_fwd(_ptr(views.device), views.V, views.T, _ptr(means2d), _ptr(conics),
+    fn = load().gs_rasterize_fwd_f64 if _f64(means2d) else load().gs_rasterize_fwd
+    _check(fn(_ptr(views.device), views.V, views.T, _ptr(means2d), _ptr(conics),
                                    _ptr(opacities), _ptr(colors), _ptr(isect_ids), _ptr(tile_ranges),
                                    _ptr(background), _ptr(out_rgb), _ptr(T_final), _ptr(last_idx),
                                    _ptr(n_contrib), _cfg(config), _stream(stream)))
 
 
-def gs_rasterize_bwd_workspace_size(K_capacity: int, deterministic: bool = False) -> int:
-    return int(load().gs_rasterize_bwd_workspace_size(K_capacity, int(bool(deterministic))))
+def gs_rasterize_bwd_workspace_size(K_capacity: int, deterministic: bool = False, f64: bool = False) -> int:
+    fn = load().gs_rasterize_bwd_f64_workspace_size if f64 else load().gs_rasterize_bwd_workspace_size
+    return int(fn(K_capacity, int(bool(deterministic))))
 
 
 def gs_rasterize_bwd(views: Views, means2d, conics, opacities, colors, isect_ids, isect_pos, emit_start, touched,
@@ -266,7 +281,8 @@ def gs_rasterize_bwd(views: Views, means2d, conics, opacities, colors, isect_ids
                      workspace, dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors,
                      config: Optional[RasterConfig] = None, stream=None):
     nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
-    _check(load().gs_rasterize_bwd(_ptr(views.device), views.V, views.P, views.T, _ptr(means2d), _ptr(conics),
+    fn = load().gs_rasterize_bwd_f64 if _f64(means2d) else load().gs_rasterize_bwd
+    _check(fn(_ptr(views.device), views.V, views.P, views.T, _ptr(means2d), _ptr(conics),
                                    _ptr(opacities), _ptr(colors), _ptr(isect_ids), _ptr(isect_pos),
                                    _ptr(emit_start), _ptr(touched), _ptr(tile_ranges), _ptr(K), int(K_capacity),
                                    _ptr(background), _ptr(T_final), _ptr(last_idx), _ptr(dL_drgb),
@@ -277,7 +293,8 @@ def gs_rasterize_bwd(views: Views, means2d, conics, opacities, colors, isect_ids
 
 def gs_project_bwd(views: Views, means, quats, scales, eps2d: float, touched, dL_dmeans2d, dL_dconics, dL_dmeans,
                    dL_dquats, dL_dscales, stream=None):
-    _check(load().gs_project_bwd(_ptr(views.device), views.V, views.P, _ptr(means), _ptr(quats), _ptr(scales),
+    fn = load().gs_project_bwd_f64 if _f64(means) else load().gs_project_bwd
+    _check(fn(_ptr(views.device), views.V, views.P, _ptr(means), _ptr(quats), _ptr(scales),
                                  float(eps2d), _ptr(touched), _ptr(dL_dmeans2d), _ptr(dL_dconics), _ptr(dL_dmeans),
                                  _ptr(dL_dquats), _ptr(dL_dscales), _stream(stream)))
 

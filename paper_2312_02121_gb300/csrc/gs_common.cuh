@@ -46,6 +46,29 @@ __device__ __forceinline__ int view_of_tile(const GsView* __restrict__ views, in
 
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Vector types for the fp32 and fp64 instantiations of the kernels: V2/V4 have
+// the size and alignment of 2/4 scalars, so they load and store as one vector.
+template <typename S>
+struct alignas(2 * sizeof(S)) V2 {
+    S x, y;
+};
+template <typename S>
+struct alignas(4 * sizeof(S)) V4 {
+    S x, y, z, w;
+};
+
+template <typename S>
+__device__ __forceinline__ V4<S> mk4(S x, S y, S z, S w)
+{
+    V4<S> v;
+    v.x = x; v.y = y; v.z = z; v.w = w;
+    return v;
+}
+
+// Correctly rounded product that the compiler may not fuse into an FMA.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // Carves consecutive 256-byte aligned sub-buffers out of a workspace.
 struct Carver {
     char* base;

@@ -1,7 +1,9 @@
 // Projection of 3D Gaussians (Sec. 2.1, Eq. 2-6, tile box of Sec. 2.2) and its
 // backward (Sec. 3.2, Eq. 16-20, and Sec. 3.2.1).  One thread per projection
 // (view, Gaussian); both kernels are bound by HBM traffic (~50 B in / 36 B out
-// per projection forward).
+// per projection forward).  Instantiated for fp32 (the fast path) and fp64
+// (the gs_*_f64 entry points, used to check the analytic backward against
+// finite differences).
 #include "gs_common.cuh"
 
 namespace gs {
@@ -9,64 +11,70 @@ namespace gs {
 // Eq. 5 for a unit quaternion (w, x, y, z), with R_11 = 1 - 2(x^2 + z^2)
 // (the orthonormal form; the printed minus sign is a typo, see the dR/dz
 // Jacobian of Sec. 3.2.1).
-__device__ __forceinline__ void quat_to_rot(float w, float x, float y, float z, float R[9])
+template <typename S>
+__device__ __forceinline__ void quat_to_rot(S w, S x, S y, S z, S R[9])
 {
-    R[0] = 1.f - 2.f * (y * y + z * z);
-    R[1] = 2.f * (x * y - w * z);
-    R[2] = 2.f * (x * z + w * y);
-    R[3] = 2.f * (x * y + w * z);
-    R[4] = 1.f - 2.f * (x * x + z * z);
-    R[5] = 2.f * (y * z - w * x);
-    R[6] = 2.f * (x * z - w * y);
-    R[7] = 2.f * (y * z + w * x);
-    R[8] = 1.f - 2.f * (x * x + y * y);
+    R[0] = S(1) - S(2) * (y * y + z * z);
+    R[1] = S(2) * (x * y - w * z);
+    R[2] = S(2) * (x * z + w * y);
+    R[3] = S(2) * (x * y + w * z);
+    R[4] = S(1) - S(2) * (x * x + z * z);
+    R[5] = S(2) * (y * z - w * x);
+    R[6] = S(2) * (x * z - w * y);
+    R[7] = S(2) * (y * z + w * x);
+    R[8] = S(1) - S(2) * (x * x + y * y);
 }
 
 // Forward quantities shared by both kernels.
+template <typename S>
 struct Proj {
-    float t[3];       // camera-space mean
-    float J00, J02, J11, J12;
-    float rz;         // 1 / t_z
-    float q[4];       // unit quaternion
-    float qinv;       // 1 / |q|
-    float R[9];       // rotation of the Gaussian
-    float M[9];       // R S
-    float Sig[6];     // Sigma: 00 01 02 11 12 22
-    float T[6];       // J R_cw (2x3)
-    float a, b, c;    // Sigma' + eps2d I
+    S t[3];       // camera-space mean
+    S J00, J02, J11, J12;
+    S rz;         // 1 / t_z
+    S q[4];       // unit quaternion
+    S qinv;       // 1 / |q|
+    S R[9];       // rotation of the Gaussian
+    S M[9];       // R S
+    S Sig[6];     // Sigma: 00 01 02 11 12 22
+    S T[6];       // J R_cw (2x3)
+    S a, b, c;    // Sigma' + eps2d I
 };
 
-__device__ __forceinline__ void project_one(const GsCamera& cam, const float* __restrict__ means,
-                                            const float4* __restrict__ quats, const float* __restrict__ scales,
-                                            int64_t g, float eps2d, Proj& o, float& u, float& v)
+template <typename S>
+__device__ __forceinline__ void project_one(const GsCamera& cam, const S* __restrict__ means,
+                                            const V4<S>* __restrict__ quats, const S* __restrict__ scales, int64_t g,
+                                            S eps2d, Proj<S>& o, S& u, S& v)
 {
-    const float mx = means[3 * g + 0], my = means[3 * g + 1], mz = means[3 * g + 2];
-    const float* W = cam.R;
+    const S mx = means[3 * g + 0], my = means[3 * g + 1], mz = means[3 * g + 2];
+    S W[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) W[i] = S(cam.R[i]);
+    const S fx = S(cam.fx), fy = S(cam.fy);
     // Eq. 2: t = T_cw [mu; 1]
-    o.t[0] = fmaf(W[0], mx, fmaf(W[1], my, fmaf(W[2], mz, cam.t[0])));
-    o.t[1] = fmaf(W[3], mx, fmaf(W[4], my, fmaf(W[5], mz, cam.t[1])));
-    o.t[2] = fmaf(W[6], mx, fmaf(W[7], my, fmaf(W[8], mz, cam.t[2])));
-    o.rz = 1.f / o.t[2];
-    u = cam.fx * o.t[0] * o.rz + cam.cx;
-    v = cam.fy * o.t[1] * o.rz + cam.cy;
+    o.t[0] = fma(W[0], mx, fma(W[1], my, fma(W[2], mz, S(cam.t[0]))));
+    o.t[1] = fma(W[3], mx, fma(W[4], my, fma(W[5], mz, S(cam.t[1]))));
+    o.t[2] = fma(W[6], mx, fma(W[7], my, fma(W[8], mz, S(cam.t[2]))));
+    o.rz = S(1) / o.t[2];
+    u = fx * o.t[0] * o.rz + S(cam.cx);
+    v = fy * o.t[1] * o.rz + S(cam.cy);
     // Eq. 3: J
-    o.J00 = cam.fx * o.rz;
-    o.J11 = cam.fy * o.rz;
-    o.J02 = -cam.fx * o.t[0] * o.rz * o.rz;
-    o.J12 = -cam.fy * o.t[1] * o.rz * o.rz;
+    o.J00 = fx * o.rz;
+    o.J11 = fy * o.rz;
+    o.J02 = -fx * o.t[0] * o.rz * o.rz;
+    o.J12 = -fy * o.t[1] * o.rz * o.rz;
     // Eq. 5-6: Sigma = R S S^T R^T with q normalised
-    const float4 q = quats[g];
-    o.qinv = 1.f / sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    const V4<S> q = quats[g];
+    o.qinv = S(1) / sqrt(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
     o.q[0] = q.x * o.qinv; o.q[1] = q.y * o.qinv; o.q[2] = q.z * o.qinv; o.q[3] = q.w * o.qinv;
     quat_to_rot(o.q[0], o.q[1], o.q[2], o.q[3], o.R);
-    const float s0 = scales[3 * g + 0], s1 = scales[3 * g + 1], s2 = scales[3 * g + 2];
+    const S s0 = scales[3 * g + 0], s1 = scales[3 * g + 1], s2 = scales[3 * g + 2];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         o.M[3 * i + 0] = o.R[3 * i + 0] * s0;
         o.M[3 * i + 1] = o.R[3 * i + 1] * s1;
         o.M[3 * i + 2] = o.R[3 * i + 2] * s2;
     }
-    const float* M = o.M;
+    const S* M = o.M;
     o.Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
     o.Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
     o.Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
@@ -79,14 +87,14 @@ __device__ __forceinline__ void project_one(const GsCamera& cam, const float* __
         o.T[j] = o.J00 * W[j] + o.J02 * W[6 + j];
         o.T[3 + j] = o.J11 * W[3 + j] + o.J12 * W[6 + j];
     }
-    const float* S = o.Sig;
-    float U[6];  // T Sigma
+    const S* Sg = o.Sig;
+    S U[6];  // T Sigma
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-        const float* Tr = o.T + 3 * r;
-        U[3 * r + 0] = Tr[0] * S[0] + Tr[1] * S[1] + Tr[2] * S[2];
-        U[3 * r + 1] = Tr[0] * S[1] + Tr[1] * S[3] + Tr[2] * S[4];
-        U[3 * r + 2] = Tr[0] * S[2] + Tr[1] * S[4] + Tr[2] * S[5];
+        const S* Tr = o.T + 3 * r;
+        U[3 * r + 0] = Tr[0] * Sg[0] + Tr[1] * Sg[1] + Tr[2] * Sg[2];
+        U[3 * r + 1] = Tr[0] * Sg[1] + Tr[1] * Sg[3] + Tr[2] * Sg[4];
+        U[3 * r + 2] = Tr[0] * Sg[2] + Tr[1] * Sg[4] + Tr[2] * Sg[5];
     }
     o.a = U[0] * o.T[0] + U[1] * o.T[1] + U[2] * o.T[2] + eps2d;
     o.b = U[0] * o.T[3] + U[1] * o.T[4] + U[2] * o.T[5];
@@ -94,18 +102,20 @@ __device__ __forceinline__ void project_one(const GsCamera& cam, const float* __
 }
 
 // a c - b^2 with the rounding error of b^2 compensated (Kahan's 2x2 determinant).
-__device__ __forceinline__ float det2(float a, float b, float c)
+template <typename S>
+__device__ __forceinline__ S det2(S a, S b, S c)
 {
-    const float bb = b * b;
-    const float e = fmaf(b, b, -bb);
-    return fmaf(a, c, -bb) - e;
+    const S bb = b * b;
+    const S e = fma(b, b, -bb);
+    return fma(a, c, -bb) - e;
 }
 
+template <typename S>
 __global__ void __launch_bounds__(256)
-k_project_fwd(const GsView* __restrict__ views, int V, int64_t P, const float* __restrict__ means,
-              const float4* __restrict__ quats, const float* __restrict__ scales, float eps2d,
-              float2* __restrict__ means2d, float* __restrict__ conics, float* __restrict__ depths,
-              short4* __restrict__ rects, int32_t* __restrict__ touched, unsigned long long* __restrict__ K_total)
+k_project_fwd(const GsView* __restrict__ views, int V, int64_t P, const S* __restrict__ means,
+              const V4<S>* __restrict__ quats, const S* __restrict__ scales, S eps2d, V2<S>* __restrict__ means2d,
+              S* __restrict__ conics, float* __restrict__ depths, short4* __restrict__ rects,
+              int32_t* __restrict__ touched, unsigned long long* __restrict__ K_total)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int count = 0;
@@ -113,26 +123,26 @@ k_project_fwd(const GsView* __restrict__ views, int V, int64_t P, const float* _
         const GsView& view = views[view_of_projection(views, V, p)];
         const GsCamera& cam = view.cam;
         const int64_t g = view.g_begin + (p - view.proj_offset);
-        Proj o;
-        float u, v;
+        Proj<S> o;
+        S u, v;
         project_one(cam, means, quats, scales, g, eps2d, o, u, v);
-        const float det = det2(o.a, o.b, o.c);
-        bool ok = o.t[2] > cam.near_plane && o.t[2] < cam.far_plane && det > 0.f &&
-                  isfinite(u) && isfinite(v) && isfinite(o.a) && isfinite(o.c) && isfinite(det);
-        float ca = 0.f, cb = 0.f, cc = 0.f;
+        const S det = det2(o.a, o.b, o.c);
+        bool ok = o.t[2] > S(cam.near_plane) && o.t[2] < S(cam.far_plane) && det > S(0) && isfinite(u) &&
+                  isfinite(v) && isfinite(o.a) && isfinite(o.c) && isfinite(det);
+        S ca = 0, cb = 0, cc = 0;
         short4 r = make_short4(0, 0, 0, 0);
         if (ok) {
-            const float inv = 1.f / det;
+            const S inv = S(1) / det;
             ca = o.c * inv;
             cb = -o.b * inv;
             cc = o.a * inv;
             // Sec. 2.2: tight 3-sigma box and the tiles it touches (1/16 is exact)
-            const float rx = 3.f * sqrtf(o.a), ry = 3.f * sqrtf(o.c);
-            const float TX = (float)view.tiles_x, TY = (float)view.tiles_y;
-            const float x0 = fminf(fmaxf(floorf((u - rx) * (1.f / kTile)), 0.f), TX);
-            const float x1 = fminf(fmaxf(floorf((u + rx) * (1.f / kTile)) + 1.f, 0.f), TX);
-            const float y0 = fminf(fmaxf(floorf((v - ry) * (1.f / kTile)), 0.f), TY);
-            const float y1 = fminf(fmaxf(floorf((v + ry) * (1.f / kTile)) + 1.f, 0.f), TY);
+            const S rx = S(3) * sqrt(o.a), ry = S(3) * sqrt(o.c);
+            const S TX = (S)view.tiles_x, TY = (S)view.tiles_y;
+            const S x0 = fmin(fmax(floor((u - rx) * (S(1) / kTile)), S(0)), TX);
+            const S x1 = fmin(fmax(floor((u + rx) * (S(1) / kTile)) + S(1), S(0)), TX);
+            const S y0 = fmin(fmax(floor((v - ry) * (S(1) / kTile)), S(0)), TY);
+            const S y1 = fmin(fmax(floor((v + ry) * (S(1) / kTile)) + S(1), S(0)), TY);
             if (x0 < x1 && y0 < y1) {
                 r = make_short4((short)x0, (short)y0, (short)x1, (short)y1);
                 count = (int)((x1 - x0) * (y1 - y0));
@@ -140,11 +150,14 @@ k_project_fwd(const GsView* __restrict__ views, int V, int64_t P, const float* _
                 ok = false;
             }
         }
-        means2d[p] = make_float2(u, v);
+        V2<S> m2;
+        m2.x = u;
+        m2.y = v;
+        means2d[p] = m2;
         conics[3 * p + 0] = ca;
         conics[3 * p + 1] = cb;
         conics[3 * p + 2] = cc;
-        depths[p] = o.t[2];
+        depths[p] = (float)o.t[2];  // sort key (fp32 in both instantiations)
         rects[p] = r;
         touched[p] = count;
     }
@@ -163,82 +176,86 @@ k_project_fwd(const GsView* __restrict__ views, int V, int64_t P, const float* _
     }
 }
 
+template <typename S>
 __global__ void __launch_bounds__(256)
-k_project_bwd(const GsView* __restrict__ views, int V, int64_t P, const float* __restrict__ means,
-              const float4* __restrict__ quats, const float* __restrict__ scales, float eps2d,
-              const int32_t* __restrict__ touched, const float2* __restrict__ dL_dmeans2d,
-              const float* __restrict__ dL_dconics, float* __restrict__ dL_dmeans, float* __restrict__ dL_dquats,
-              float* __restrict__ dL_dscales)
+k_project_bwd(const GsView* __restrict__ views, int V, int64_t P, const S* __restrict__ means,
+              const V4<S>* __restrict__ quats, const S* __restrict__ scales, S eps2d,
+              const int32_t* __restrict__ touched, const V2<S>* __restrict__ dL_dmeans2d,
+              const S* __restrict__ dL_dconics, S* __restrict__ dL_dmeans, S* __restrict__ dL_dquats,
+              S* __restrict__ dL_dscales)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P || touched[p] == 0) return;
     const GsView& view = views[view_of_projection(views, V, p)];
     const GsCamera& cam = view.cam;
     const int64_t g = view.g_begin + (p - view.proj_offset);
-    Proj o;
-    float u, v;
+    Proj<S> o;
+    S u, v;
     project_one(cam, means, quats, scales, g, eps2d, o, u, v);
-    const float inv = 1.f / det2(o.a, o.b, o.c);
-    const float Y0 = o.c * inv, Y1 = -o.b * inv, Y2 = o.a * inv;  // Y = [[Y0, Y1], [Y1, Y2]]
+    const S inv = S(1) / det2(o.a, o.b, o.c);
+    const S Y0 = o.c * inv, Y1 = -o.b * inv, Y2 = o.a * inv;  // Y = [[Y0, Y1], [Y1, Y2]]
 
     // Sec. 3.1: G = dL/dY from the packed conic gradient (the b gradient covers both off-diagonals)
-    const float ga = dL_dconics[3 * p + 0], gb = 0.5f * dL_dconics[3 * p + 1], gc = dL_dconics[3 * p + 2];
+    const S ga = dL_dconics[3 * p + 0], gb = S(0.5) * dL_dconics[3 * p + 1], gc = dL_dconics[3 * p + 2];
     // dL/dSigma' = -Y G Y
-    const float YG00 = Y0 * ga + Y1 * gb, YG01 = Y0 * gb + Y1 * gc;
-    const float YG10 = Y1 * ga + Y2 * gb, YG11 = Y1 * gb + Y2 * gc;
-    const float D00 = -(YG00 * Y0 + YG01 * Y1);
-    const float D01 = -(YG00 * Y1 + YG01 * Y2);
-    const float D10 = -(YG10 * Y0 + YG11 * Y1);
-    const float D11 = -(YG10 * Y1 + YG11 * Y2);
-    const float Ds = 0.5f * (D01 + D10);  // symmetric part
+    const S YG00 = Y0 * ga + Y1 * gb, YG01 = Y0 * gb + Y1 * gc;
+    const S YG10 = Y1 * ga + Y2 * gb, YG11 = Y1 * gb + Y2 * gc;
+    const S D00 = -(YG00 * Y0 + YG01 * Y1);
+    const S D01 = -(YG00 * Y1 + YG01 * Y2);
+    const S D10 = -(YG10 * Y0 + YG11 * Y1);
+    const S D11 = -(YG10 * Y1 + YG11 * Y2);
+    const S Ds = S(0.5) * (D01 + D10);  // symmetric part
 
     // Sec. 3.2: dL/dSigma = T^T D T ; dL/dT = D T Sigma^T + D^T T Sigma = 2 D T Sigma
-    float Vm[6];  // D T (2x3)
+    S Vm[6];  // D T (2x3)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         Vm[j] = D00 * o.T[j] + Ds * o.T[3 + j];
         Vm[3 + j] = Ds * o.T[j] + D11 * o.T[3 + j];
     }
-    float dSig[9];
+    S dSig[9];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) dSig[3 * i + j] = o.T[i] * Vm[j] + o.T[3 + i] * Vm[3 + j];
-    const float* S = o.Sig;
-    const float Sf[9] = {S[0], S[1], S[2], S[1], S[3], S[4], S[2], S[4], S[5]};
-    float dT[6];
+    const S* Sg = o.Sig;
+    const S Sf[9] = {Sg[0], Sg[1], Sg[2], Sg[1], Sg[3], Sg[4], Sg[2], Sg[4], Sg[5]};
+    S dT[6];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
         for (int j = 0; j < 3; ++j)
-            dT[3 * r + j] = 2.f * (Vm[3 * r + 0] * Sf[j] + Vm[3 * r + 1] * Sf[3 + j] + Vm[3 * r + 2] * Sf[6 + j]);
+            dT[3 * r + j] = S(2) * (Vm[3 * r + 0] * Sf[j] + Vm[3 * r + 1] * Sf[3 + j] + Vm[3 * r + 2] * Sf[6 + j]);
     // dL/dJ = dL/dT R_cw^T (only the four non-constant entries of J matter)
-    const float* W = cam.R;
-    const float dJ00 = dT[0] * W[0] + dT[1] * W[1] + dT[2] * W[2];
-    const float dJ02 = dT[0] * W[6] + dT[1] * W[7] + dT[2] * W[8];
-    const float dJ11 = dT[3] * W[3] + dT[4] * W[4] + dT[5] * W[5];
-    const float dJ12 = dT[3] * W[6] + dT[4] * W[7] + dT[5] * W[8];
+    S W[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) W[i] = S(cam.R[i]);
+    const S fx = S(cam.fx), fy = S(cam.fy);
+    const S dJ00 = dT[0] * W[0] + dT[1] * W[1] + dT[2] * W[2];
+    const S dJ02 = dT[0] * W[6] + dT[1] * W[7] + dT[2] * W[8];
+    const S dJ11 = dT[3] * W[3] + dT[4] * W[4] + dT[5] * W[5];
+    const S dJ12 = dT[3] * W[6] + dT[4] * W[7] + dT[5] * W[8];
     // dJ/dt as printed in Sec. 3.2, plus the 2D-mean term J^T dL/dmu' (Eq. 16-17)
-    const float rz2 = o.rz * o.rz, rz3 = rz2 * o.rz;
-    const float2 gm = dL_dmeans2d[p];
-    const float dtx = -cam.fx * rz2 * dJ02 + o.J00 * gm.x;
-    const float dty = -cam.fy * rz2 * dJ12 + o.J11 * gm.y;
-    const float dtz = -cam.fx * rz2 * dJ00 + 2.f * cam.fx * o.t[0] * rz3 * dJ02 - cam.fy * rz2 * dJ11 +
-                      2.f * cam.fy * o.t[1] * rz3 * dJ12 + o.J02 * gm.x + o.J12 * gm.y;
+    const S rz2 = o.rz * o.rz, rz3 = rz2 * o.rz;
+    const V2<S> gm = dL_dmeans2d[p];
+    const S dtx = -fx * rz2 * dJ02 + o.J00 * gm.x;
+    const S dty = -fy * rz2 * dJ12 + o.J11 * gm.y;
+    const S dtz = -fx * rz2 * dJ00 + S(2) * fx * o.t[0] * rz3 * dJ02 - fy * rz2 * dJ11 +
+                  S(2) * fy * o.t[1] * rz3 * dJ12 + o.J02 * gm.x + o.J12 * gm.y;
     // Eq. 20: dL/dmu = R_cw^T dL/dt
     atomicAdd(dL_dmeans + 3 * g + 0, W[0] * dtx + W[3] * dty + W[6] * dtz);
     atomicAdd(dL_dmeans + 3 * g + 1, W[1] * dtx + W[4] * dty + W[7] * dtz);
     atomicAdd(dL_dmeans + 3 * g + 2, W[2] * dtx + W[5] * dty + W[8] * dtz);
 
     // Sec. 3.2.1: dL/dM = (G + G^T) M = 2 dSigma M (dSigma is symmetric)
-    float dM[9];
+    S dM[9];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j)
-            dM[3 * i + j] = 2.f * (dSig[3 * i + 0] * o.M[j] + dSig[3 * i + 1] * o.M[3 + j] + dSig[3 * i + 2] * o.M[6 + j]);
-    const float s[3] = {scales[3 * g + 0], scales[3 * g + 1], scales[3 * g + 2]};
-    float dR[9];
+            dM[3 * i + j] = S(2) * (dSig[3 * i + 0] * o.M[j] + dSig[3 * i + 1] * o.M[3 + j] + dSig[3 * i + 2] * o.M[6 + j]);
+    const S s[3] = {scales[3 * g + 0], scales[3 * g + 1], scales[3 * g + 2]};
+    S dR[9];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -247,16 +264,16 @@ k_project_bwd(const GsView* __restrict__ views, int V, int64_t P, const float* _
     for (int j = 0; j < 3; ++j)
         atomicAdd(dL_dscales + 3 * g + j, o.R[j] * dM[j] + o.R[3 + j] * dM[3 + j] + o.R[6 + j] * dM[6 + j]);
     // <dL/dR, dR/dq> with the four Jacobians of Sec. 3.2.1 at the unit quaternion
-    const float w = o.q[0], x = o.q[1], y = o.q[2], z = o.q[3];
-    const float gw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
-    const float gx = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] -
-                            2.f * x * dR[8]);
-    const float gy = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] -
-                            2.f * y * dR[8]);
-    const float gz = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
-                            x * dR[6] + y * dR[7]);
+    const S w = o.q[0], x = o.q[1], y = o.q[2], z = o.q[3];
+    const S gw = S(2) * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+    const S gx = S(2) * (y * dR[1] + z * dR[2] + y * dR[3] - S(2) * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] -
+                         S(2) * x * dR[8]);
+    const S gy = S(2) * (-S(2) * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] -
+                         S(2) * y * dR[8]);
+    const S gz = S(2) * (-S(2) * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - S(2) * z * dR[4] + y * dR[5] +
+                         x * dR[6] + y * dR[7]);
     // through q_hat = q / |q|: dq = (I - q_hat q_hat^T) dq_hat / |q|
-    const float dot = gw * w + gx * x + gy * y + gz * z;
+    const S dot = gw * w + gx * x + gy * y + gz * z;
     atomicAdd(dL_dquats + 4 * g + 0, (gw - w * dot) * o.qinv);
     atomicAdd(dL_dquats + 4 * g + 1, (gx - x * dot) * o.qinv);
     atomicAdd(dL_dquats + 4 * g + 2, (gy - y * dot) * o.qinv);
@@ -264,6 +281,53 @@ k_project_bwd(const GsView* __restrict__ views, int V, int64_t P, const float* _
 }
 
 static bool misaligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) != 0; }
+
+template <typename S>
+static int project_impl(const char* who, const GsView* views, int32_t V, int64_t P, const S* means, const S* quats,
+                        const S* scales, S eps2d, S* means2d, S* conics, float* depths, int16_t* rects,
+                        int32_t* touched, int64_t* K_total, void* stream)
+{
+    if (V < 0 || P < 0 || (P > 0 && V == 0)) return fail(GS_ERR_INVALID_ARG, "%s: V=%d P=%lld", who, V, (long long)P);
+    if (P > 0 && (!views || !means || !quats || !scales || !means2d || !conics || !depths || !rects || !touched))
+        return fail(GS_ERR_INVALID_ARG, "%s: null pointer argument", who);
+    if (misaligned(quats, 4 * sizeof(S)) || misaligned(means2d, 2 * sizeof(S)) || misaligned(rects, 8))
+        return fail(GS_ERR_INVALID_ARG, "%s: quats need %zu-byte, means2d %zu-byte, rects 8-byte alignment", who,
+                    4 * sizeof(S), 2 * sizeof(S));
+    if (!(eps2d >= S(0))) return fail(GS_ERR_INVALID_ARG, "%s: eps2d must be >= 0", who);
+    cudaStream_t s = as_stream(stream);
+    if (K_total && cudaMemsetAsync(K_total, 0, sizeof(int64_t), s) != cudaSuccess) return launch_status(who);
+    if (P == 0) return GS_OK;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((P + threads - 1) / threads);
+    k_project_fwd<S><<<blocks, threads, 0, s>>>(views, V, P, means, reinterpret_cast<const V4<S>*>(quats), scales,
+                                                 eps2d, reinterpret_cast<V2<S>*>(means2d), conics, depths,
+                                                 reinterpret_cast<short4*>(rects), touched,
+                                                 reinterpret_cast<unsigned long long*>(K_total));
+    count_launches(1);
+    return launch_status(who);
+}
+
+template <typename S>
+static int project_bwd_impl(const char* who, const GsView* views, int32_t V, int64_t P, const S* means,
+                            const S* quats, const S* scales, S eps2d, const int32_t* touched, const S* dL_dmeans2d,
+                            const S* dL_dconics, S* dL_dmeans, S* dL_dquats, S* dL_dscales, void* stream)
+{
+    if (V < 0 || P < 0 || (P > 0 && V == 0)) return fail(GS_ERR_INVALID_ARG, "%s: V=%d P=%lld", who, V, (long long)P);
+    if (P > 0 && (!views || !means || !quats || !scales || !touched || !dL_dmeans2d || !dL_dconics || !dL_dmeans ||
+                  !dL_dquats || !dL_dscales))
+        return fail(GS_ERR_INVALID_ARG, "%s: null pointer argument", who);
+    if (misaligned(quats, 4 * sizeof(S)) || misaligned(dL_dmeans2d, 2 * sizeof(S)))
+        return fail(GS_ERR_INVALID_ARG, "%s: quats need %zu-byte, dL_dmeans2d %zu-byte alignment", who,
+                    4 * sizeof(S), 2 * sizeof(S));
+    if (P == 0) return GS_OK;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((P + threads - 1) / threads);
+    k_project_bwd<S><<<blocks, threads, 0, as_stream(stream)>>>(
+        views, V, P, means, reinterpret_cast<const V4<S>*>(quats), scales, eps2d, touched,
+        reinterpret_cast<const V2<S>*>(dL_dmeans2d), dL_dconics, dL_dmeans, dL_dquats, dL_dscales);
+    count_launches(1);
+    return launch_status(who);
+}
 
 }  // namespace gs
 
@@ -273,25 +337,16 @@ extern "C" int gs_project(const GsView* views, int32_t V, int64_t P, const float
                           const float* scales, float eps2d, float* means2d, float* conics, float* depths,
                           int16_t* rects, int32_t* touched, int64_t* K_total, void* stream)
 {
-    if (V < 0 || P < 0 || (P > 0 && V == 0))
-        return fail(GS_ERR_INVALID_ARG, "gs_project: V=%d P=%lld", V, (long long)P);
-    if (P > 0 && (!views || !means || !quats || !scales || !means2d || !conics || !depths || !rects || !touched))
-        return fail(GS_ERR_INVALID_ARG, "gs_project: null pointer argument");
-    if (misaligned(quats, 16) || misaligned(means2d, 8) || misaligned(rects, 8))
-        return fail(GS_ERR_INVALID_ARG, "gs_project: quats need 16-byte, means2d/rects 8-byte alignment");
-    if (!(eps2d >= 0.f)) return fail(GS_ERR_INVALID_ARG, "gs_project: eps2d must be >= 0");
-    cudaStream_t s = as_stream(stream);
-    if (K_total && cudaMemsetAsync(K_total, 0, sizeof(int64_t), s) != cudaSuccess)
-        return launch_status("gs_project memset");
-    if (P == 0) return GS_OK;
-    const int threads = 256;
-    const unsigned blocks = (unsigned)((P + threads - 1) / threads);
-    k_project_fwd<<<blocks, threads, 0, s>>>(views, V, P, means, reinterpret_cast<const float4*>(quats), scales, eps2d,
-                                             reinterpret_cast<float2*>(means2d), conics, depths,
-                                             reinterpret_cast<short4*>(rects), touched,
-                                             reinterpret_cast<unsigned long long*>(K_total));
-    count_launches(1);
-    return launch_status("gs_project");
+    return project_impl<float>("gs_project", views, V, P, means, quats, scales, eps2d, means2d, conics, depths, rects,
+                                touched, K_total, stream);
+}
+
+extern "C" int gs_project_f64(const GsView* views, int32_t V, int64_t P, const double* means, const double* quats,
+                              const double* scales, double eps2d, double* means2d, double* conics, float* depths,
+                              int16_t* rects, int32_t* touched, int64_t* K_total, void* stream)
+{
+    return project_impl<double>("gs_project_f64", views, V, P, means, quats, scales, eps2d, means2d, conics, depths,
+                                 rects, touched, K_total, stream);
 }
 
 extern "C" int gs_project_bwd(const GsView* views, int32_t V, int64_t P, const float* means, const float* quats,
@@ -299,19 +354,15 @@ extern "C" int gs_project_bwd(const GsView* views, int32_t V, int64_t P, const f
                               const float* dL_dconics, float* dL_dmeans, float* dL_dquats, float* dL_dscales,
                               void* stream)
 {
-    if (V < 0 || P < 0 || (P > 0 && V == 0))
-        return fail(GS_ERR_INVALID_ARG, "gs_project_bwd: V=%d P=%lld", V, (long long)P);
-    if (P > 0 && (!views || !means || !quats || !scales || !touched || !dL_dmeans2d || !dL_dconics || !dL_dmeans ||
-                  !dL_dquats || !dL_dscales))
-        return fail(GS_ERR_INVALID_ARG, "gs_project_bwd: null pointer argument");
-    if (misaligned(quats, 16) || misaligned(dL_dmeans2d, 8))
-        return fail(GS_ERR_INVALID_ARG, "gs_project_bwd: quats need 16-byte, dL_dmeans2d 8-byte alignment");
-    if (P == 0) return GS_OK;
-    const int threads = 256;
-    const unsigned blocks = (unsigned)((P + threads - 1) / threads);
-    k_project_bwd<<<blocks, threads, 0, as_stream(stream)>>>(
-        views, V, P, means, reinterpret_cast<const float4*>(quats), scales, eps2d, touched,
-        reinterpret_cast<const float2*>(dL_dmeans2d), dL_dconics, dL_dmeans, dL_dquats, dL_dscales);
-    count_launches(1);
-    return launch_status("gs_project_bwd");
+    return project_bwd_impl<float>("gs_project_bwd", views, V, P, means, quats, scales, eps2d, touched, dL_dmeans2d,
+                                   dL_dconics, dL_dmeans, dL_dquats, dL_dscales, stream);
+}
+
+extern "C" int gs_project_bwd_f64(const GsView* views, int32_t V, int64_t P, const double* means,
+                                  const double* quats, const double* scales, double eps2d, const int32_t* touched,
+                                  const double* dL_dmeans2d, const double* dL_dconics, double* dL_dmeans,
+                                  double* dL_dquats, double* dL_dscales, void* stream)
+{
+    return project_bwd_impl<double>("gs_project_bwd_f64", views, V, P, means, quats, scales, eps2d, touched,
+                                    dL_dmeans2d, dL_dconics, dL_dmeans, dL_dquats, dL_dscales, stream);
 }

@@ -11,7 +11,8 @@
 // rounding.  The warp then walks only the Gaussians that can reach one of its
 // pixels.  Skipped pairs would fail the alpha test anyway, so results are
 // identical to visiting every pair; the cull only removes work.  Warps whose
-// pixels have all terminated stop early.
+// pixels have all terminated stop early.  Inside the walk every lane
+// evaluates and predicates decide, so the warp does not diverge.
 //
 // sigma is evaluated in the factored form sigma = (a u^2 + (det/a) dy^2) / 2
 // with u = dx + (b/a) dy: both terms are non-negative, so elongated conics do
@@ -20,110 +21,143 @@
 //
 // The backward walks the same batches in reverse from each pixel's last
 // composited Gaussian, rebuilding T_n from the saved T_final (Sec. 3.1).  The
-// nine per-pixel gradient terms of a Gaussian are summed over the warp with a
-// reduce-scatter (each shuffle level halves the vector a lane carries), then
-// over the eight warps in a fixed order, giving one record per (tile,
-// Gaussian) pair.  A second kernel sums each projection's records over its
-// tiles in emission order.  No floating-point atomics touch per-projection
-// outputs, so gradients are run-to-run identical.
+// nine per-pixel gradient terms of a Gaussian are summed over the warp
+// through a shared-memory transpose, then over the tile's warps -- with
+// shared atomics (fast mode) or per-warp slots summed in a fixed order
+// (deterministic mode) -- giving one partial per (tile, Gaussian).  The fast
+// mode adds the partials straight into the per-projection outputs with
+// global atomics; the deterministic mode writes them as records that a
+// second kernel sums per projection in emission order.
+//
+// Everything is templated on the scalar type: fp32 is the fast path, fp64
+// (smaller batches, exp2 instead of the SFU) serves the gs_*_f64 entry points
+// used to check the analytic backward against finite differences.
 #include <algorithm>
 
 #include "gs_common.cuh"
 
 namespace gs {
 
-constexpr int kFwdBatch = 256;
-constexpr int kBwdBatch = 64;  // deterministic mode (per-warp partial slots)
 constexpr int kWarps = 8;
 constexpr int kRec = 9;  // dmu'(2) dconic(3) dopacity(1) dcolor(3)
-constexpr float kLog2e = 1.4426950408889634f;
 
-// 2^x on the SFU (PTX ex2.approx.ftz.f32).
-__device__ __forceinline__ float ex2(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
+template <typename S> struct RT;  // per-scalar constants and primitives
+template <> struct RT<float> {
+    static constexpr int kFwdBatch = 256;
+    static constexpr int kBwdFast = 256;   // Gaussians per batch, fast backward
+    static constexpr int kBwdDet = 64;     // deterministic backward (per-warp slots)
+    static constexpr float kLog2e = 1.4426950408889634f;
+    __device__ static float alpha_min() { return GS_ALPHA_MIN; }
+    __device__ static float alpha_max() { return GS_ALPHA_MAX; }
+    __device__ static float t_min() { return GS_T_MIN; }
+    // 2^x on the SFU (PTX ex2.approx.ftz.f32)
+    __device__ static float ex2(float x)
+    {
+        float y;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    __device__ static float rcp(float x) { return __fdividef(1.f, x); }
+    __device__ static float stash(int p) { return __int_as_float(p); }
+    __device__ static int unstash(float v) { return __float_as_int(v); }
+};
+template <> struct RT<double> {
+    static constexpr int kFwdBatch = 128;
+    static constexpr int kBwdFast = 64;
+    static constexpr int kBwdDet = 32;
+    static constexpr double kLog2e = 1.4426950408889634;
+    __device__ static double alpha_min() { return 1.0 / 255.0; }
+    __device__ static double alpha_max() { return 0.99; }
+    __device__ static double t_min() { return 1e-4; }
+    __device__ static double ex2(double x) { return exp2(x); }
+    __device__ static double rcp(double x) { return 1.0 / x; }
+    __device__ static double stash(int p) { return (double)p; }
+    __device__ static int unstash(double v) { return (int)v; }
+};
 
-// One staged Gaussian (4 x float4 = 64 bytes):
-//   g.xy  : mu'.x, mu'.y, opacity, a
-//   g.q   : -log2e/2 * a, k = b/a, -log2e/2 * D, b     (D = det/a = c - b^2/a)
-//   g.col : r, g, b, D
-//   g.cull: sigma threshold (<0: never reaches 1/255; +inf: never culled),
-//           -b/c, c, (backward: the projection index, as int bits)
+// One staged Gaussian (4 x V4 = 64 bytes in fp32):
+//   xy  : mu'.x, mu'.y, opacity, a
+//   q   : -log2e/2 * a, k = b/a, -log2e/2 * D, b     (D = det/a = c - b^2/a)
+//   col : r, g, b, D
+//   cull: sigma threshold (<0: never reaches 1/255; +inf: never culled),
+//         -b/c, c, (backward: the projection index)
+template <typename S>
 struct Staged {
-    float4 xy, q, col, cull;
+    V4<S> xy, q, col, cull;
 };
 
 // log2(e) * (-sigma) at Delta = (dx, dy); u = dx + k dy is returned too.
 // Explicit roundings keep forward and backward bit-identical.
-__device__ __forceinline__ float neg_sigma_log2(const float4& q, float dx, float dy, float& u)
+template <typename S>
+__device__ __forceinline__ S neg_sigma_log2(const V4<S>& q, S dx, S dy, S& u)
 {
-    u = fmaf(q.y, dy, dx);
-    return fmaf(__fmul_rn(q.x, u), u, __fmul_rn(__fmul_rn(q.z, dy), dy));
+    u = fma(q.y, dy, dx);
+    return fma(mul_rn(q.x, u), u, mul_rn(mul_rn(q.z, dy), dy));
 }
 
-__device__ __forceinline__ void stage_gaussian(float4* sh_xy, float4* sh_q, float4* sh_col, float4* sh_cull, int j,
-                                               float2 m, float a, float b, float c, float o, float r, float g,
-                                               float bl)
+template <typename S>
+__device__ __forceinline__ void stage_gaussian(V4<S>* sh_xy, V4<S>* sh_q, V4<S>* sh_col, V4<S>* sh_cull, int j,
+                                               V2<S> m, S a, S b, S c, S o, S r, S g, S bl)
 {
     // det with the rounding error of b^2 compensated (Kahan's 2x2 determinant)
-    const float bb = b * b;
-    const float det = fmaf(a, c, -bb) - fmaf(b, b, -bb);
-    const float k = b / a;
-    const float D = det / a;
-    sh_xy[j] = make_float4(m.x, m.y, o, a);
-    sh_q[j] = make_float4(-0.5f * kLog2e * a, k, -0.5f * kLog2e * D, b);
-    sh_col[j] = make_float4(r, g, bl, D);
-    float thr;
-    if (!(o >= GS_ALPHA_MIN)) {
-        thr = -1.f;  // o e^-sigma < 1/255 everywhere
-    } else if (!(a > 0.f && det > 0.f) || 4.f * a * c > 1e7f * det) {
-        thr = INFINITY;  // degenerate or extremely elongated conic: never culled
+    const S bb = b * b;
+    const S det = fma(a, c, -bb) - fma(b, b, -bb);
+    const S k = b / a;
+    const S D = det / a;
+    sh_xy[j] = mk4<S>(m.x, m.y, o, a);
+    sh_q[j] = mk4<S>(S(-0.5) * RT<S>::kLog2e * a, k, S(-0.5) * RT<S>::kLog2e * D, b);
+    sh_col[j] = mk4<S>(r, g, bl, D);
+    S thr;
+    if (!(o >= RT<S>::alpha_min())) {
+        thr = S(-1);  // o e^-sigma < 1/255 everywhere
+    } else if (!(a > S(0) && det > S(0)) || S(4) * a * c > S(1e7) * det) {
+        thr = S(INFINITY);  // degenerate or extremely elongated conic: never culled
     } else {
-        thr = 1.05f * logf(255.f * o) + 1e-3f;
+        thr = S(1.05) * log(S(255) * o) + S(1e-3);
     }
-    sh_cull[j] = make_float4(thr, -b / c, c, 0.f);
+    sh_cull[j] = mk4<S>(thr, -b / c, c, S(0));
 }
 
 // Can the Gaussian reach alpha >= 1/255 at a pixel centre of the box
 // [X0, X1] x [Y0, Y1]?  Minimum of sigma over the box: zero when mu' is
 // inside, otherwise the least of the four edge minima (on an edge sigma is a
 // parabola; its vertex is clamped to the edge).
-__device__ __forceinline__ bool reaches_box(const Staged& g, float X0, float X1, float Y0, float Y1)
+template <typename S>
+__device__ __forceinline__ bool reaches_box(const Staged<S>& g, S X0, S X1, S Y0, S Y1)
 {
-    const float thr = g.cull.x;
-    if (thr < 0.f) return false;
-    if (!(thr < INFINITY)) return true;
-    const float mx = g.xy.x, my = g.xy.y;
+    const S thr = g.cull.x;
+    if (thr < S(0)) return false;
+    if (!(thr < S(INFINITY))) return true;
+    const S mx = g.xy.x, my = g.xy.y;
     if (mx >= X0 && mx <= X1 && my >= Y0 && my <= Y1) return true;
-    const float a = g.xy.w, k = g.q.y, D = g.col.w, kv = g.cull.y;
-    auto sig = [&](float dx, float dy) {
-        const float u = fmaf(k, dy, dx);
-        return 0.5f * fmaf(a * u, u, D * dy * dy);
+    const S a = g.xy.w, k = g.q.y, D = g.col.w, kv = g.cull.y;
+    auto sig = [&](S dx, S dy) {
+        const S u = fma(k, dy, dx);
+        return S(0.5) * fma(a * u, u, D * dy * dy);
     };
-    const float dxl = mx - X0, dxr = mx - X1, dyt = my - Y0, dyb = my - Y1;
-    float smin = sig(dxl, fminf(fmaxf(kv * dxl, dyb), dyt));
-    smin = fminf(smin, sig(dxr, fminf(fmaxf(kv * dxr, dyb), dyt)));
-    smin = fminf(smin, sig(fminf(fmaxf(-k * dyt, dxr), dxl), dyt));
-    smin = fminf(smin, sig(fminf(fmaxf(-k * dyb, dxr), dxl), dyb));
+    const S dxl = mx - X0, dxr = mx - X1, dyt = my - Y0, dyb = my - Y1;
+    S smin = sig(dxl, fmin(fmax(kv * dxl, dyb), dyt));
+    smin = fmin(smin, sig(dxr, fmin(fmax(kv * dxr, dyb), dyt)));
+    smin = fmin(smin, sig(fmin(fmax(-k * dyt, dxr), dxl), dyt));
+    smin = fmin(smin, sig(fmin(fmax(-k * dyb, dxr), dxl), dyb));
     return smin <= thr;
 }
 
+template <typename S>
 struct TileCtx {
     const GsView* view;
     int tx, ty, px, py;
     bool inside;
-    int64_t pix;       // packed pixel index
-    float cx, cy;      // pixel centre
-    float wx0, wx1, wy0, wy1;  // warp's pixel-centre box
-    int64_t g_shift;   // g = p + g_shift
+    int64_t pix;         // packed pixel index
+    S cx, cy;            // pixel centre
+    S wx0, wx1, wy0, wy1;  // warp's pixel-centre box
+    int64_t g_shift;     // g = p + g_shift
 };
 
-__device__ __forceinline__ TileCtx tile_ctx(const GsView* __restrict__ views, int V, int tile)
+template <typename S>
+__device__ __forceinline__ TileCtx<S> tile_ctx(const GsView* __restrict__ views, int V, int tile)
 {
-    TileCtx t;
+    TileCtx<S> t;
     t.view = views + view_of_tile(views, V, tile);
     const int local = tile - t.view->tile_offset;
     t.tx = local % t.view->tiles_x;
@@ -135,20 +169,31 @@ __device__ __forceinline__ TileCtx tile_ctx(const GsView* __restrict__ views, in
     const int W = t.view->cam.width, H = t.view->cam.height;
     t.inside = t.px < W && t.py < H;
     t.pix = t.view->pixel_offset + (int64_t)t.py * W + t.px;
-    t.cx = t.px + 0.5f;
-    t.cy = t.py + 0.5f;
-    t.wx0 = bx + 0.5f;
-    t.wx1 = bx + 7.5f;
-    t.wy0 = by + 0.5f;
-    t.wy1 = by + 3.5f;
+    t.cx = S(t.px) + S(0.5);
+    t.cy = S(t.py) + S(0.5);
+    t.wx0 = S(bx) + S(0.5);
+    t.wx1 = S(bx) + S(7.5);
+    t.wy0 = S(by) + S(0.5);
+    t.wy1 = S(by) + S(3.5);
     t.g_shift = (int64_t)t.view->g_begin - t.view->proj_offset;
     return t;
 }
 
-__device__ __forceinline__ Staged load_staged(const float4* sh_xy, const float4* sh_q, const float4* sh_col,
-                                              const float4* sh_cull, int j)
+template <typename S>
+__device__ __forceinline__ Staged<S> load_staged(const V4<S>* sh_xy, const V4<S>* sh_q, const V4<S>* sh_col,
+                                                 const V4<S>* sh_cull, int j)
 {
-    return Staged{sh_xy[j], sh_q[j], sh_col[j], sh_cull[j]};
+    return Staged<S>{sh_xy[j], sh_q[j], sh_col[j], sh_cull[j]};
+}
+
+__device__ __forceinline__ void atomic_add2(V2<float>* a, float x, float y)
+{
+    atomicAdd(reinterpret_cast<float2*>(a), make_float2(x, y));
+}
+__device__ __forceinline__ void atomic_add2(V2<double>* a, double x, double y)
+{
+    atomicAdd(&a->x, x);
+    atomicAdd(&a->y, y);
 }
 
 // ---------------------------------------------------------------------------
@@ -159,16 +204,16 @@ __device__ __forceinline__ Staged load_staged(const float4* sh_xy, const float4*
 // counter `queue` (zeroed before launch) until T_total tiles are taken;
 // otherwise CTA i renders queue slot i.  Slot qi renders tile tile_order[qi]
 // (identity when tile_order is NULL).
-template <bool kCull, bool kPersistent>
+template <typename S, bool kCull, bool kPersistent>
 __global__ void __launch_bounds__(256)
 k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t* __restrict__ tile_order,
-             int* __restrict__ queue, const float2* __restrict__ means2d,
-             const float* __restrict__ conics, const float* __restrict__ opacities, const float* __restrict__ colors,
-             const int32_t* __restrict__ isect_ids, const int2* __restrict__ tile_ranges,
-             const float* __restrict__ background, float* __restrict__ out_rgb, float* __restrict__ T_final,
-             int32_t* __restrict__ last_idx, int32_t* __restrict__ n_contrib)
+             int* __restrict__ queue, const V2<S>* __restrict__ means2d, const S* __restrict__ conics,
+             const S* __restrict__ opacities, const S* __restrict__ colors, const int32_t* __restrict__ isect_ids,
+             const int2* __restrict__ tile_ranges, const S* __restrict__ background, S* __restrict__ out_rgb,
+             S* __restrict__ T_final, int32_t* __restrict__ last_idx, int32_t* __restrict__ n_contrib)
 {
-    __shared__ float4 sh_xy[kFwdBatch], sh_q[kFwdBatch], sh_col[kFwdBatch], sh_cull[kFwdBatch];
+    constexpr int kB = RT<S>::kFwdBatch;
+    __shared__ V4<S> sh_xy[kB], sh_q[kB], sh_col[kB], sh_cull[kB];
     __shared__ int s_next;
     for (int qi = blockIdx.x;;) {
         if (kPersistent) {
@@ -179,28 +224,28 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
             if (qi >= T_total) break;
         }
         const int tile = tile_order ? tile_order[qi] : qi;
-        const TileCtx t = tile_ctx(views, V, tile);
+        const TileCtx<S> t = tile_ctx<S>(views, V, tile);
         const int lane = threadIdx.x & 31;
         const int2 range = tile_ranges[tile];
 
-        float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+        S T = 1, C0 = 0, C1 = 0, C2 = 0;
         int last = range.x - 1, count = 0;
         bool done = !t.inside;
 
-        for (int b0 = range.x; b0 < range.y; b0 += kFwdBatch) {
+        for (int b0 = range.x; b0 < range.y; b0 += kB) {
             if (__syncthreads_count(done) == (int)blockDim.x) break;  // also guards the stage below
-            {
+            if (threadIdx.x < kB) {
                 const int i = b0 + threadIdx.x;
                 if (i < range.y) {
                     const int p = isect_ids[i];
                     const int64_t g = p + t.g_shift;
-                    stage_gaussian(sh_xy, sh_q, sh_col, sh_cull, threadIdx.x, means2d[p], conics[3 * p],
-                                   conics[3 * p + 1], conics[3 * p + 2], opacities[g], colors[3 * g], colors[3 * g + 1],
-                                   colors[3 * g + 2]);
+                    stage_gaussian<S>(sh_xy, sh_q, sh_col, sh_cull, threadIdx.x, means2d[p], conics[3 * p],
+                                      conics[3 * p + 1], conics[3 * p + 2], opacities[g], colors[3 * g],
+                                      colors[3 * g + 1], colors[3 * g + 2]);
                 }
             }
             __syncthreads();
-            const int n = min(kFwdBatch, range.y - b0);
+            const int n = min(kB, range.y - b0);
             for (int s = 0; s < n; s += 32) {
                 bool hit = s + lane < n;
                 if (kCull && hit)
@@ -210,21 +255,21 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                     const int j = s + __ffs(m) - 1;
                     m &= m - 1;
                     // every lane evaluates; predicates decide (no divergent branches)
-                    const float4 xy = sh_xy[j];
-                    float u;
-                    const float p2 = neg_sigma_log2(sh_q[j], xy.x - t.cx, xy.y - t.cy, u);
-                    const float alpha = fminf(GS_ALPHA_MAX, __fmul_rn(xy.z, ex2(p2)));
-                    const float Tn = T * (1.f - alpha);
+                    const V4<S> xy = sh_xy[j];
+                    S u;
+                    const S p2 = neg_sigma_log2(sh_q[j], xy.x - t.cx, xy.y - t.cy, u);
+                    const S alpha = fmin(RT<S>::alpha_max(), mul_rn(xy.z, RT<S>::ex2(p2)));
+                    const S Tn = T * (S(1) - alpha);
                     // p2 > 0 means sigma < 0 (not a positive-definite conic): skipped
-                    const bool take = !done && p2 <= 0.f && alpha >= GS_ALPHA_MIN;
-                    const bool stop = take && Tn < GS_T_MIN;  // not composited; the pixel is finished
+                    const bool take = !done && p2 <= S(0) && alpha >= RT<S>::alpha_min();
+                    const bool stop = take && Tn < RT<S>::t_min();  // not composited; the pixel is finished
                     const bool comp = take && !stop;
                     done = done || stop;
-                    const float4 c = sh_col[j];
-                    const float wgt = comp ? alpha * T : 0.f;
-                    C0 = fmaf(wgt, c.x, C0);
-                    C1 = fmaf(wgt, c.y, C1);
-                    C2 = fmaf(wgt, c.z, C2);
+                    const V4<S> c = sh_col[j];
+                    const S wgt = comp ? alpha * T : S(0);
+                    C0 = fma(wgt, c.x, C0);
+                    C1 = fma(wgt, c.y, C1);
+                    C2 = fma(wgt, c.z, C2);
                     T = comp ? Tn : T;
                     last = comp ? b0 + j : last;
                     count += comp;
@@ -233,11 +278,11 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
             }
         }
         if (t.inside) {
-            float bg0 = 0.f, bg1 = 0.f, bg2 = 0.f;
+            S bg0 = 0, bg1 = 0, bg2 = 0;
             if (background) { bg0 = background[0]; bg1 = background[1]; bg2 = background[2]; }
-            out_rgb[3 * t.pix + 0] = fmaf(T, bg0, C0);
-            out_rgb[3 * t.pix + 1] = fmaf(T, bg1, C1);
-            out_rgb[3 * t.pix + 2] = fmaf(T, bg2, C2);
+            out_rgb[3 * t.pix + 0] = fma(T, bg0, C0);
+            out_rgb[3 * t.pix + 1] = fma(T, bg1, C1);
+            out_rgb[3 * t.pix + 2] = fma(T, bg2, C2);
             T_final[t.pix] = T;
             last_idx[t.pix] = last;
             if (n_contrib) n_contrib[t.pix] = count;
@@ -251,13 +296,13 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
 // ---------------------------------------------------------------------------
 
 // Sum of r[0..8] over the warp through shared memory.  Every lane stores its
-// nine terms as one 10-float row of the warp's buffer (four 8-byte stores and
-// one 4-byte store; at a 10-word row stride the 8-byte stores of a half-warp
-// hit 32 distinct banks).  Lane L < 27 then sums column L / 3 over the rows
-// congruent to L % 3 modulo 3 (11 or 10 rows); the three parts of a column
-// start 10 banks apart, so each of those loads is conflict-free.  Two
-// shuffles fold the parts: lane 3q returns the total of term q.  The
-// summation order is fixed, so results are deterministic.
+// nine terms as one 10-scalar row of the warp's buffer (four 2-vector stores
+// and one scalar store; in fp32 the 8-byte stores of a half-warp hit 32
+// distinct banks at this stride).  Lane L < 27 then sums column L / 3 over the
+// rows congruent to L % 3 modulo 3 (11 or 10 rows); the three parts of a
+// column start 10 banks apart, so each of those loads is conflict-free in
+// fp32.  Two shuffles fold the parts: lane 3q returns the total of term q.
+// The summation order is fixed, so results are deterministic.
 constexpr int kRedStride = 10;
 
 struct RedLane {
@@ -269,52 +314,55 @@ __device__ __forceinline__ RedLane red_lane(int lane)
     return RedLane{lane / 3, lane % 3};
 }
 
-__device__ __forceinline__ float warp_sum9(const float (&r)[kRec], float* buf, int lane, RedLane rl)
+template <typename S>
+__device__ __forceinline__ S warp_sum9(const S (&r)[kRec], S* buf, int lane, RedLane rl)
 {
-    float* row = buf + lane * kRedStride;
-    *reinterpret_cast<float2*>(row + 0) = make_float2(r[0], r[1]);
-    *reinterpret_cast<float2*>(row + 2) = make_float2(r[2], r[3]);
-    *reinterpret_cast<float2*>(row + 4) = make_float2(r[4], r[5]);
-    *reinterpret_cast<float2*>(row + 6) = make_float2(r[6], r[7]);
+    S* row = buf + lane * kRedStride;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        V2<S> v;
+        v.x = r[2 * i];
+        v.y = r[2 * i + 1];
+        *reinterpret_cast<V2<S>*>(row + 2 * i) = v;
+    }
     row[8] = r[8];
     __syncwarp();
-    float acc = 0.f;
+    S acc = 0;
     if (lane < 3 * kRec) {
-        const float* col = buf + rl.part * kRedStride + rl.q;
+        const S* col = buf + rl.part * kRedStride + rl.q;
 #pragma unroll
         for (int i = 0; i < 11; ++i)
             if (rl.part + 3 * i < 32) acc += col[3 * i * kRedStride];
     }
     __syncwarp();  // the buffer is free again
-    const float a1 = __shfl_down_sync(kFull, acc, 1);
-    const float a2 = __shfl_down_sync(kFull, acc, 2);
+    const S a1 = __shfl_down_sync(kFull, acc, 1);
+    const S a2 = __shfl_down_sync(kFull, acc, 2);
     return acc + (a1 + a2);  // lane 3q: part 0 + (part 1 + part 2)
 }
 
-// kAtomic: each (tile, Gaussian) sum is added straight into the per-projection
-// outputs with vector reduction atomics (fast; fp32 summation order across
-// tiles varies).  Otherwise it is written as a record for k_reduce_records
-// (deterministic).
-template <bool kCull, bool kAtomic, bool kPersistent>
+// kAtomic: each (tile, Gaussian) partial is added straight into the
+// per-projection outputs with reduction atomics (fast; the summation order
+// across tiles varies).  Otherwise it is written as a record for
+// k_reduce_records (deterministic).
+template <typename S, bool kCull, bool kAtomic, bool kPersistent>
 __global__ void __launch_bounds__(256, 4)
 k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t* __restrict__ tile_order,
-             int* __restrict__ queue, const float2* __restrict__ means2d,
-             const float* __restrict__ conics, const float* __restrict__ opacities, const float* __restrict__ colors,
-             const int32_t* __restrict__ isect_ids, const int2* __restrict__ tile_ranges,
-             const float* __restrict__ background, const float* __restrict__ T_final,
-             const int32_t* __restrict__ last_idx, const float* __restrict__ dL_drgb, float* __restrict__ records,
-             float2* __restrict__ dL_dmeans2d, float* __restrict__ dL_dconics, float* __restrict__ dL_dopacities,
-             float* __restrict__ dL_dcolors)
+             int* __restrict__ queue, const V2<S>* __restrict__ means2d, const S* __restrict__ conics,
+             const S* __restrict__ opacities, const S* __restrict__ colors, const int32_t* __restrict__ isect_ids,
+             const int2* __restrict__ tile_ranges, const S* __restrict__ background, const S* __restrict__ T_final,
+             const int32_t* __restrict__ last_idx, const S* __restrict__ dL_drgb, S* __restrict__ records,
+             V2<S>* __restrict__ dL_dmeans2d, S* __restrict__ dL_dconics, S* __restrict__ dL_dopacities,
+             S* __restrict__ dL_dcolors)
 {
-    // deterministic: one partial slot per warp, summed in warp order; atomic:
+    // deterministic: one partial slot per warp, summed in warp order; fast:
     // one slot per Gaussian, accumulated with shared-memory atomics (less
     // shared memory, so larger batches)
-    constexpr int kB = kAtomic ? 256 : kBwdBatch;
+    constexpr int kB = kAtomic ? RT<S>::kBwdFast : RT<S>::kBwdDet;
     constexpr int kSlots = kAtomic ? 1 : kWarps;
-    __shared__ float4 sh_xy[kB], sh_q[kB], sh_col[kB], sh_cull[kB];
-    __shared__ float s_grad[kSlots][kB][kRec];
-    __shared__ unsigned s_mask[kSlots][kB / 32];
-    __shared__ __align__(16) float s_red[kWarps][32 * kRedStride];
+    __shared__ V4<S> sh_xy[kB], sh_q[kB], sh_col[kB], sh_cull[kB];
+    __shared__ S s_grad[kSlots][kB][kRec];
+    __shared__ unsigned s_mask[kSlots][(kB + 31) / 32];
+    __shared__ __align__(16) S s_red[kWarps][32 * kRedStride];
     __shared__ int s_maxlast[kWarps];
     __shared__ int s_next;
     for (int qi = blockIdx.x;;) {
@@ -326,11 +374,11 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
             if (qi >= T_total) break;
         }
         const int tile = tile_order ? tile_order[qi] : qi;
-        const TileCtx t = tile_ctx(views, V, tile);
+        const TileCtx<S> t = tile_ctx<S>(views, V, tile);
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
         const int2 range = tile_ranges[tile];
 
-        float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, bgT = 0.f;
+        S T = 1, g0 = 0, g1 = 0, g2 = 0, bgT = 0;
         int last = range.x - 1;
         if (t.inside) {
             T = T_final[t.pix];
@@ -340,17 +388,17 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
             g2 = dL_drgb[3 * t.pix + 2];
             if (background) bgT = T * (background[0] * g0 + background[1] * g1 + background[2] * g2);
         }
-        float SdL = 0.f;  // S_n . dL/dC, S_n = sum_{m>n} c_m alpha_m T_m
+        S SdL = 0;  // S_n . dL/dC, S_n = sum_{m>n} c_m alpha_m T_m
         const RedLane rl = red_lane(lane);
 
         // the warp's and the tile's largest last index bound the work
         int wl = last;
-    #pragma unroll
+#pragma unroll
         for (int d = 16; d > 0; d >>= 1) wl = max(wl, __shfl_xor_sync(kFull, wl, d));
         if (lane == 0) s_maxlast[w] = wl;
         __syncthreads();
         int maxlast = s_maxlast[0];
-    #pragma unroll
+#pragma unroll
         for (int i = 1; i < kWarps; ++i) maxlast = max(maxlast, s_maxlast[i]);
 
         const int nbatch = maxlast >= range.x ? (maxlast - range.x) / kB + 1 : 0;
@@ -358,15 +406,16 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
             const int b0 = range.x + k * kB;
             const int n = min(kB, maxlast - b0 + 1);
             if (kAtomic) {
-                for (int i = threadIdx.x; i < kB * kRec; i += blockDim.x) (&s_grad[0][0][0])[i] = 0.f;
-                if (threadIdx.x < kB / 32) s_mask[0][threadIdx.x] = 0u;
+                for (int i = threadIdx.x; i < kB * kRec; i += blockDim.x) (&s_grad[0][0][0])[i] = S(0);
+                if (threadIdx.x < (kB + 31) / 32) s_mask[0][threadIdx.x] = 0u;
             }
             if (threadIdx.x < n) {
                 const int p = isect_ids[b0 + threadIdx.x];
                 const int64_t g = p + t.g_shift;
-                stage_gaussian(sh_xy, sh_q, sh_col, sh_cull, threadIdx.x, means2d[p], conics[3 * p], conics[3 * p + 1],
-                               conics[3 * p + 2], opacities[g], colors[3 * g], colors[3 * g + 1], colors[3 * g + 2]);
-                sh_cull[threadIdx.x].w = __int_as_float(p);  // the projection, for the atomic flush
+                stage_gaussian<S>(sh_xy, sh_q, sh_col, sh_cull, threadIdx.x, means2d[p], conics[3 * p],
+                                  conics[3 * p + 1], conics[3 * p + 2], opacities[g], colors[3 * g],
+                                  colors[3 * g + 1], colors[3 * g + 2]);
+                sh_cull[threadIdx.x].w = RT<S>::stash(p);  // the projection, for the atomic flush
             }
             __syncthreads();
             // this warp only needs entries up to its own last index
@@ -385,31 +434,31 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                         const int j = s + hb;  // back to front
                         // every lane evaluates; lanes that do not composite this
                         // Gaussian carry zero terms (selects, no branches)
-                        const float4 xy = sh_xy[j];
-                        const float4 qq = sh_q[j];
-                        const float4 col = sh_col[j];
-                        const float dx = xy.x - t.cx, dy = xy.y - t.cy;
-                        float u;
-                        const float p2 = neg_sigma_log2(qq, dx, dy, u);
-                        const float ge = ex2(p2);  // exp(-sigma)
-                        const float raw = __fmul_rn(xy.z, ge);
-                        const float alpha = fminf(GS_ALPHA_MAX, raw);
-                        const bool contrib = (b0 + j <= last) && (p2 <= 0.f) && (alpha >= GS_ALPHA_MIN);
+                        const V4<S> xy = sh_xy[j];
+                        const V4<S> qq = sh_q[j];
+                        const V4<S> col = sh_col[j];
+                        const S dx = xy.x - t.cx, dy = xy.y - t.cy;
+                        S u;
+                        const S p2 = neg_sigma_log2(qq, dx, dy, u);
+                        const S ge = RT<S>::ex2(p2);  // exp(-sigma)
+                        const S raw = mul_rn(xy.z, ge);
+                        const S alpha = fmin(RT<S>::alpha_max(), raw);
+                        const bool contrib = (b0 + j <= last) && (p2 <= S(0)) && (alpha >= RT<S>::alpha_min());
                         const unsigned cm = __ballot_sync(kFull, contrib);
                         if (cm == 0u) continue;
-                        const float inv1ma = __fdividef(1.f, 1.f - alpha);
-                        const float Tn = T * inv1ma;  // T before this Gaussian
-                        const float wgt = contrib ? alpha * Tn : 0.f;
-                        const float cdot = fmaf(col.x, g0, fmaf(col.y, g1, col.z * g2));
-                        const float dL_dalpha = fmaf(Tn, cdot, -(SdL + bgT) * inv1ma);
-                        const float gd = (contrib && raw < GS_ALPHA_MAX) ? ge * dL_dalpha : 0.f;  // dL/do
-                        SdL = fmaf(wgt, cdot, SdL);
+                        const S inv1ma = RT<S>::rcp(S(1) - alpha);
+                        const S Tn = T * inv1ma;  // T before this Gaussian
+                        const S wgt = contrib ? alpha * Tn : S(0);
+                        const S cdot = fma(col.x, g0, fma(col.y, g1, col.z * g2));
+                        const S dL_dalpha = fma(Tn, cdot, -(SdL + bgT) * inv1ma);
+                        const S gd = (contrib && raw < RT<S>::alpha_max()) ? ge * dL_dalpha : S(0);  // dL/do
+                        SdL = fma(wgt, cdot, SdL);
                         T = contrib ? Tn : T;
-                        const float ds = -xy.z * gd;  // dL/dsigma
-                        const float hds = 0.5f * ds;
-                        float r[kRec];
+                        const S ds = -xy.z * gd;  // dL/dsigma
+                        const S hds = S(0.5) * ds;
+                        S r[kRec];
                         r[0] = ds * (xy.w * u);                    // Y Delta = (a u, b u + D dy)
-                        r[1] = ds * fmaf(qq.w, u, col.w * dy);
+                        r[1] = ds * fma(qq.w, u, col.w * dy);
                         r[2] = hds * dx * dx;
                         r[3] = ds * dx * dy;
                         r[4] = hds * dy * dy;
@@ -418,18 +467,18 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                         r[7] = wgt * g1;
                         r[8] = wgt * g2;
                         chunk_mask |= 1u << hb;
-                        float* slot = s_grad[kAtomic ? 0 : w][j];
+                        S* slot = s_grad[kAtomic ? 0 : w][j];
                         if (__popc(cm) == 1) {
                             // one contributing pixel: its terms are the warp's sum
                             if (contrib) {
-    #pragma unroll
+#pragma unroll
                                 for (int q = 0; q < kRec; ++q) {
                                     if (kAtomic) atomicAdd(slot + q, r[q]);
                                     else slot[q] = r[q];
                                 }
                             }
                         } else {
-                            const float tot = warp_sum9(r, s_red[w], lane, rl);
+                            const S tot = warp_sum9<S>(r, s_red[w], lane, rl);
                             if (lane < 3 * kRec && rl.part == 0) {
                                 if (kAtomic) atomicAdd(slot + rl.q, tot);
                                 else slot[rl.q] = tot;
@@ -449,22 +498,22 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
             // fixed-order sum over warps: one (tile, Gaussian) partial
             if (threadIdx.x < n) {
                 const int j = threadIdx.x;
-                float acc[kRec];
-    #pragma unroll
-                for (int q = 0; q < kRec; ++q) acc[q] = 0.f;
+                S acc[kRec];
+#pragma unroll
+                for (int q = 0; q < kRec; ++q) acc[q] = S(0);
                 bool any = false;
-    #pragma unroll
+#pragma unroll
                 for (int ww = 0; ww < kSlots; ++ww)
                     if (s_mask[ww][j >> 5] & (1u << (j & 31))) {
                         any = true;
-    #pragma unroll
+#pragma unroll
                         for (int q = 0; q < kRec; ++q) acc[q] += s_grad[ww][j][q];
                     }
                 if (kAtomic) {
                     if (any) {
-                        const int p = __float_as_int(sh_cull[j].w);
+                        const int p = RT<S>::unstash(sh_cull[j].w);
                         const int64_t g = p + t.g_shift;
-                        atomicAdd(dL_dmeans2d + p, make_float2(acc[0], acc[1]));
+                        atomic_add2(dL_dmeans2d + p, acc[0], acc[1]);
                         atomicAdd(dL_dconics + 3 * p + 0, acc[2]);
                         atomicAdd(dL_dconics + 3 * p + 1, acc[3]);
                         atomicAdd(dL_dconics + 3 * p + 2, acc[4]);
@@ -474,8 +523,8 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                         atomicAdd(dL_dcolors + 3 * g + 2, acc[8]);
                     }
                 } else {
-                    float* rec = records + (size_t)(b0 + j) * kRec;
-    #pragma unroll
+                    S* rec = records + (size_t)(b0 + j) * kRec;
+#pragma unroll
                     for (int q = 0; q < kRec; ++q) rec[q] = acc[q];
                 }
             }
@@ -485,9 +534,9 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
             // Gaussians after every pixel's last one received nothing
             const int first_unused = max(range.x, maxlast + 1);
             for (int i = first_unused + threadIdx.x; i < range.y; i += blockDim.x) {
-                float* rec = records + (size_t)i * kRec;
-    #pragma unroll
-                for (int q = 0; q < kRec; ++q) rec[q] = 0.f;
+                S* rec = records + (size_t)i * kRec;
+#pragma unroll
+                for (int q = 0; q < kRec; ++q) rec[q] = S(0);
             }
         }
         if (!kPersistent) break;
@@ -495,12 +544,13 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
 }
 
 // Per projection: sum of its (tile, Gaussian) records in emission order.
+template <typename S>
 __global__ void __launch_bounds__(256)
 k_reduce_records(const GsView* __restrict__ views, int V, int64_t P, const int32_t* __restrict__ touched,
                  const int32_t* __restrict__ emit_start, const int32_t* __restrict__ isect_pos,
-                 const int32_t* __restrict__ K_dev, int64_t cap, const float* __restrict__ records,
-                 float2* __restrict__ dL_dmeans2d, float* __restrict__ dL_dconics, float* __restrict__ dL_dopacities,
-                 float* __restrict__ dL_dcolors)
+                 const int32_t* __restrict__ K_dev, int64_t cap, const S* __restrict__ records,
+                 V2<S>* __restrict__ dL_dmeans2d, S* __restrict__ dL_dconics, S* __restrict__ dL_dopacities,
+                 S* __restrict__ dL_dcolors)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
@@ -509,15 +559,15 @@ k_reduce_records(const GsView* __restrict__ views, int V, int64_t P, const int32
     const int64_t K = min((int64_t)*K_dev, cap);
     const int64_t e0 = emit_start[p];
     if (e0 < 0 || e0 + n > K) return;  // capacity overflow: outputs are flagged invalid
-    float acc[kRec];
+    S acc[kRec];
 #pragma unroll
-    for (int q = 0; q < kRec; ++q) acc[q] = 0.f;
+    for (int q = 0; q < kRec; ++q) acc[q] = S(0);
     for (int j = 0; j < n; ++j) {
-        const float* rec = records + (size_t)isect_pos[e0 + j] * kRec;
+        const S* rec = records + (size_t)isect_pos[e0 + j] * kRec;
 #pragma unroll
         for (int q = 0; q < kRec; ++q) acc[q] += rec[q];
     }
-    float2 m = dL_dmeans2d[p];
+    V2<S> m = dL_dmeans2d[p];
     m.x += acc[0];
     m.y += acc[1];
     dL_dmeans2d[p] = m;
@@ -539,10 +589,6 @@ static bool cull_enabled()
     const char* e = getenv("GS_NO_CULL");
     return !(e && e[0] == '1');
 }
-
-}  // namespace gs
-
-using namespace gs;
 
 // Grid for a launch of `kernel`: one CTA per tile, or a persistent grid.
 template <typename K>
@@ -568,40 +614,130 @@ static int check_config(const GsRasterConfig* cfg, const char* who)
     return GS_OK;
 }
 
+template <typename S>
+static int rasterize_fwd_impl(const char* who, const GsView* views, int32_t V, int32_t T_total, const S* means2d,
+                              const S* conics, const S* opacities, const S* colors, const int32_t* isect_ids,
+                              const int32_t* tile_ranges, const S* background, S* out_rgb, S* T_final,
+                              int32_t* last_idx, int32_t* n_contrib, const GsRasterConfig* config, void* stream)
+{
+    if (V <= 0 || T_total < 0) return fail(GS_ERR_INVALID_ARG, "%s: V=%d T_total=%d", who, V, T_total);
+    if (!views || !tile_ranges || !out_rgb || !T_final || !last_idx)
+        return fail(GS_ERR_INVALID_ARG, "%s: null pointer argument", who);
+    if ((reinterpret_cast<uintptr_t>(means2d) & (2 * sizeof(S) - 1)) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7))
+        return fail(GS_ERR_INVALID_ARG, "%s: means2d needs %zu-byte, tile_ranges 8-byte alignment", who,
+                    2 * sizeof(S));
+    if (int rc = check_config(config, who)) return rc;
+    if (T_total == 0) return GS_OK;
+    cudaStream_t s = as_stream(stream);
+    const bool cull = cull_enabled(), pers = config && config->persistent;
+    auto kern = cull ? (pers ? k_raster_fwd<S, true, true> : k_raster_fwd<S, true, false>)
+                     : (pers ? k_raster_fwd<S, false, true> : k_raster_fwd<S, false, false>);
+    unsigned grid;
+    if (int rc = raster_grid(kern, config, T_total, &grid)) return rc;
+    int* queue = pers ? config->queue : nullptr;
+    if (pers && cudaMemsetAsync(queue, 0, sizeof(int), s) != cudaSuccess) return launch_status(who);
+    kern<<<grid, 256, 0, s>>>(views, V, T_total, config ? config->tile_order : nullptr, queue,
+                              reinterpret_cast<const V2<S>*>(means2d), conics, opacities, colors, isect_ids,
+                              reinterpret_cast<const int2*>(tile_ranges), background, out_rgb, T_final, last_idx,
+                              n_contrib);
+    count_launches(1);
+    return launch_status(who);
+}
+
+template <typename S>
+static size_t bwd_workspace(int64_t K_capacity, int32_t deterministic)
+{
+    if (K_capacity < 0) return 0;
+    return deterministic ? align256((size_t)K_capacity * kRec * sizeof(S)) : 0;
+}
+
+template <typename S>
+static int rasterize_bwd_impl(const char* who, const GsView* views, int32_t V, int64_t P, int32_t T_total,
+                              const S* means2d, const S* conics, const S* opacities, const S* colors,
+                              const int32_t* isect_ids, const int32_t* isect_pos, const int32_t* emit_start,
+                              const int32_t* touched, const int32_t* tile_ranges, const int32_t* K, int64_t K_capacity,
+                              const S* background, const S* T_final, const int32_t* last_idx, const S* dL_drgb,
+                              int32_t deterministic, void* workspace, size_t workspace_bytes, S* dL_dmeans2d,
+                              S* dL_dconics, S* dL_dopacities, S* dL_dcolors, const GsRasterConfig* config,
+                              void* stream)
+{
+    if (V <= 0 || P < 0 || T_total < 0 || K_capacity < 0 || K_capacity >= (int64_t(1) << 31))
+        return fail(GS_ERR_INVALID_ARG, "%s: V=%d P=%lld T_total=%d K_capacity=%lld", who, V, (long long)P, T_total,
+                    (long long)K_capacity);
+    if (!views || !tile_ranges || !T_final || !last_idx || !dL_drgb ||
+        (P > 0 && (!dL_dmeans2d || !dL_dconics || !dL_dopacities || !dL_dcolors)) ||
+        (deterministic && P > 0 && (!K || !touched || !emit_start || !isect_pos)))
+        return fail(GS_ERR_INVALID_ARG, "%s: null pointer argument", who);
+    if ((reinterpret_cast<uintptr_t>(means2d) & (2 * sizeof(S) - 1)) ||
+        (reinterpret_cast<uintptr_t>(dL_dmeans2d) & (2 * sizeof(S) - 1)) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7))
+        return fail(GS_ERR_INVALID_ARG, "%s: 2-vector arrays need %zu-byte alignment", who, 2 * sizeof(S));
+    const size_t need = bwd_workspace<S>(K_capacity, deterministic);
+    if (workspace_bytes < need || (need > 0 && !workspace))
+        return fail(GS_ERR_INVALID_ARG, "%s: workspace of %zu bytes, need %zu", who, workspace_bytes, need);
+    if (int rc = check_config(config, who)) return rc;
+    if (T_total == 0 || P == 0) return GS_OK;
+    cudaStream_t s = as_stream(stream);
+    S* records = static_cast<S*>(workspace);
+    const bool cull = cull_enabled(), pers = config && config->persistent;
+    using KB = decltype(&k_raster_bwd<S, true, true, true>);
+    static const KB table[2][2][2] = {
+        {{k_raster_bwd<S, false, false, false>, k_raster_bwd<S, false, false, true>},
+         {k_raster_bwd<S, false, true, false>, k_raster_bwd<S, false, true, true>}},
+        {{k_raster_bwd<S, true, false, false>, k_raster_bwd<S, true, false, true>},
+         {k_raster_bwd<S, true, true, false>, k_raster_bwd<S, true, true, true>}}};
+    const KB kern = table[cull][!deterministic][pers];
+    unsigned grid;
+    if (int rc = raster_grid(kern, config, T_total, &grid)) return rc;
+    int* queue = pers ? config->queue : nullptr;
+    if (pers && cudaMemsetAsync(queue, 0, sizeof(int), s) != cudaSuccess) return launch_status(who);
+    kern<<<grid, 256, 0, s>>>(views, V, T_total, config ? config->tile_order : nullptr, queue,
+                              reinterpret_cast<const V2<S>*>(means2d), conics, opacities, colors, isect_ids,
+                              reinterpret_cast<const int2*>(tile_ranges), background, T_final, last_idx, dL_drgb,
+                              records, reinterpret_cast<V2<S>*>(dL_dmeans2d), dL_dconics, dL_dopacities, dL_dcolors);
+    count_launches(1);
+    if (deterministic) {
+        k_reduce_records<S><<<(unsigned)((P + 255) / 256), 256, 0, s>>>(
+            views, V, P, touched, emit_start, isect_pos, K, K_capacity, records,
+            reinterpret_cast<V2<S>*>(dL_dmeans2d), dL_dconics, dL_dopacities, dL_dcolors);
+        count_launches(1);
+    }
+    return launch_status(who);
+}
+
+}  // namespace gs
+
+using namespace gs;
+
 extern "C" int gs_rasterize_fwd(const GsView* views, int32_t V, int32_t T_total, const float* means2d,
                                 const float* conics, const float* opacities, const float* colors,
                                 const int32_t* isect_ids, const int32_t* tile_ranges, const float* background,
                                 float* out_rgb, float* T_final, int32_t* last_idx, int32_t* n_contrib,
                                 const GsRasterConfig* config, void* stream)
 {
-    if (V <= 0 || T_total < 0)
-        return fail(GS_ERR_INVALID_ARG, "gs_rasterize_fwd: V=%d T_total=%d", V, T_total);
-    if (!views || !tile_ranges || !out_rgb || !T_final || !last_idx)
-        return fail(GS_ERR_INVALID_ARG, "gs_rasterize_fwd: null pointer argument");
-    if ((reinterpret_cast<uintptr_t>(means2d) & 7) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7))
-        return fail(GS_ERR_INVALID_ARG, "gs_rasterize_fwd: means2d and tile_ranges need 8-byte alignment");
-    if (int rc = check_config(config, "gs_rasterize_fwd")) return rc;
-    if (T_total == 0) return GS_OK;
-    cudaStream_t s = as_stream(stream);
-    const bool cull = cull_enabled(), pers = config && config->persistent;
-    auto kern = cull ? (pers ? k_raster_fwd<true, true> : k_raster_fwd<true, false>)
-                     : (pers ? k_raster_fwd<false, true> : k_raster_fwd<false, false>);
-    unsigned grid;
-    if (int rc = raster_grid(kern, config, T_total, &grid)) return rc;
-    int* queue = pers ? config->queue : nullptr;
-    if (pers && cudaMemsetAsync(queue, 0, sizeof(int), s) != cudaSuccess) return launch_status("gs_rasterize_fwd");
-    kern<<<grid, 256, 0, s>>>(views, V, T_total, config ? config->tile_order : nullptr, queue,
-                              reinterpret_cast<const float2*>(means2d), conics, opacities, colors, isect_ids,
-                              reinterpret_cast<const int2*>(tile_ranges), background, out_rgb, T_final, last_idx,
-                              n_contrib);
-    count_launches(1);
-    return launch_status("gs_rasterize_fwd");
+    return rasterize_fwd_impl<float>("gs_rasterize_fwd", views, V, T_total, means2d, conics, opacities, colors,
+                                     isect_ids, tile_ranges, background, out_rgb, T_final, last_idx, n_contrib, config,
+                                     stream);
+}
+
+extern "C" int gs_rasterize_fwd_f64(const GsView* views, int32_t V, int32_t T_total, const double* means2d,
+                                    const double* conics, const double* opacities, const double* colors,
+                                    const int32_t* isect_ids, const int32_t* tile_ranges, const double* background,
+                                    double* out_rgb, double* T_final, int32_t* last_idx, int32_t* n_contrib,
+                                    const GsRasterConfig* config, void* stream)
+{
+    return rasterize_fwd_impl<double>("gs_rasterize_fwd_f64", views, V, T_total, means2d, conics, opacities, colors,
+                                      isect_ids, tile_ranges, background, out_rgb, T_final, last_idx, n_contrib,
+                                      config, stream);
 }
 
 extern "C" size_t gs_rasterize_bwd_workspace_size(int64_t K_capacity, int32_t deterministic)
 {
-    if (K_capacity < 0) return 0;
-    return deterministic ? align256((size_t)K_capacity * kRec * sizeof(float)) : 0;
+    return bwd_workspace<float>(K_capacity, deterministic);
+}
+
+extern "C" size_t gs_rasterize_bwd_f64_workspace_size(int64_t K_capacity, int32_t deterministic)
+{
+    return bwd_workspace<double>(K_capacity, deterministic);
 }
 
 extern "C" int gs_rasterize_bwd(const GsView* views, int32_t V, int64_t P, int32_t T_total, const float* means2d,
@@ -613,46 +749,26 @@ extern "C" int gs_rasterize_bwd(const GsView* views, int32_t V, int64_t P, int32
                                 void* workspace, size_t workspace_bytes, float* dL_dmeans2d, float* dL_dconics,
                                 float* dL_dopacities, float* dL_dcolors, const GsRasterConfig* config, void* stream)
 {
-    if (V <= 0 || P < 0 || T_total < 0 || K_capacity < 0 || K_capacity >= (int64_t(1) << 31))
-        return fail(GS_ERR_INVALID_ARG, "gs_rasterize_bwd: V=%d P=%lld T_total=%d K_capacity=%lld", V, (long long)P,
-                    T_total, (long long)K_capacity);
-    if (!views || !tile_ranges || !T_final || !last_idx || !dL_drgb ||
-        (P > 0 && (!dL_dmeans2d || !dL_dconics || !dL_dopacities || !dL_dcolors)) ||
-        (deterministic && P > 0 && (!K || !touched || !emit_start || !isect_pos)))
-        return fail(GS_ERR_INVALID_ARG, "gs_rasterize_bwd: null pointer argument");
-    if ((reinterpret_cast<uintptr_t>(means2d) & 7) || (reinterpret_cast<uintptr_t>(dL_dmeans2d) & 7) ||
-        (reinterpret_cast<uintptr_t>(tile_ranges) & 7))
-        return fail(GS_ERR_INVALID_ARG, "gs_rasterize_bwd: float2 arrays need 8-byte alignment");
-    const size_t need = gs_rasterize_bwd_workspace_size(K_capacity, deterministic);
-    if (workspace_bytes < need || (need > 0 && !workspace))
-        return fail(GS_ERR_INVALID_ARG, "gs_rasterize_bwd: workspace of %zu bytes, need %zu", workspace_bytes, need);
-    if (int rc = check_config(config, "gs_rasterize_bwd")) return rc;
-    if (T_total == 0 || P == 0) return GS_OK;
-    cudaStream_t s = as_stream(stream);
-    float* records = static_cast<float*>(workspace);
-    const bool cull = cull_enabled(), pers = config && config->persistent;
-    using KB = decltype(&k_raster_bwd<true, true, true>);
-    static const KB table[2][2][2] = {
-        {{k_raster_bwd<false, false, false>, k_raster_bwd<false, false, true>},
-         {k_raster_bwd<false, true, false>, k_raster_bwd<false, true, true>}},
-        {{k_raster_bwd<true, false, false>, k_raster_bwd<true, false, true>},
-         {k_raster_bwd<true, true, false>, k_raster_bwd<true, true, true>}}};
-    const KB kern = table[cull][!deterministic][pers];
-    unsigned grid;
-    if (int rc = raster_grid(kern, config, T_total, &grid)) return rc;
-    int* queue = pers ? config->queue : nullptr;
-    if (pers && cudaMemsetAsync(queue, 0, sizeof(int), s) != cudaSuccess) return launch_status("gs_rasterize_bwd");
-    kern<<<grid, 256, 0, s>>>(views, V, T_total, config ? config->tile_order : nullptr, queue,
-                              reinterpret_cast<const float2*>(means2d), conics, opacities, colors, isect_ids,
-                              reinterpret_cast<const int2*>(tile_ranges), background, T_final, last_idx, dL_drgb,
-                              records, reinterpret_cast<float2*>(dL_dmeans2d), dL_dconics, dL_dopacities,
-                              dL_dcolors);
-    count_launches(1);
-    if (deterministic) {
-        k_reduce_records<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(
-            views, V, P, touched, emit_start, isect_pos, K, K_capacity, records,
-            reinterpret_cast<float2*>(dL_dmeans2d), dL_dconics, dL_dopacities, dL_dcolors);
-        count_launches(1);
-    }
-    return launch_status("gs_rasterize_bwd");
+    return rasterize_bwd_impl<float>("gs_rasterize_bwd", views, V, P, T_total, means2d, conics, opacities, colors,
+                                     isect_ids, isect_pos, emit_start, touched, tile_ranges, K, K_capacity,
+                                     background, T_final, last_idx, dL_drgb, deterministic, workspace,
+                                     workspace_bytes, dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors, config,
+                                     stream);
+}
+
+extern "C" int gs_rasterize_bwd_f64(const GsView* views, int32_t V, int64_t P, int32_t T_total,
+                                    const double* means2d, const double* conics, const double* opacities,
+                                    const double* colors, const int32_t* isect_ids, const int32_t* isect_pos,
+                                    const int32_t* emit_start, const int32_t* touched, const int32_t* tile_ranges,
+                                    const int32_t* K, int64_t K_capacity, const double* background,
+                                    const double* T_final, const int32_t* last_idx, const double* dL_drgb,
+                                    int32_t deterministic, void* workspace, size_t workspace_bytes,
+                                    double* dL_dmeans2d, double* dL_dconics, double* dL_dopacities,
+                                    double* dL_dcolors, const GsRasterConfig* config, void* stream)
+{
+    return rasterize_bwd_impl<double>("gs_rasterize_bwd_f64", views, V, P, T_total, means2d, conics, opacities,
+                                      colors, isect_ids, isect_pos, emit_start, touched, tile_ranges, K, K_capacity,
+                                      background, T_final, last_idx, dL_drgb, deterministic, workspace,
+                                      workspace_bytes, dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors, config,
+                                      stream);
 }

@@ -38,12 +38,13 @@ class Params:
 
 
 def _check_params(p: Params):
+    dt = p.means.dtype
     for name in ("means", "quats", "scales", "opacities", "colors"):
         x = getattr(p, name)
         if not x.is_cuda:
             raise RuntimeError(f"gsplat103 runs on CUDA only; {name} is on {x.device}")
-        if x.dtype != torch.float32 or not x.is_contiguous():
-            raise ValueError(f"{name} must be contiguous float32")
+        if x.dtype not in (torch.float32, torch.float64) or x.dtype != dt or not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous float32 (or all float64)")
 
 
 @dataclasses.dataclass
@@ -80,10 +81,10 @@ class Frame:
 
 
 def project(views: B.Views, p: Params, eps2d: float, stream=None):
-    dev = p.means.device
+    dev, dt = p.means.device, p.means.dtype
     P = views.P
     out = dict(
-        means2d=torch.empty(P, 2, device=dev), conics=torch.empty(P, 3, device=dev),
+        means2d=torch.empty(P, 2, device=dev, dtype=dt), conics=torch.empty(P, 3, device=dev, dtype=dt),
         depths=torch.empty(P, device=dev), rects=torch.empty(P, 4, dtype=torch.int16, device=dev),
         touched=torch.empty(P, dtype=torch.int32, device=dev), K_total=torch.empty(1, dtype=torch.int64, device=dev))
     B.gs_project(views, p.means, p.quats, p.scales, eps2d, out["means2d"], out["conics"], out["depths"],
@@ -98,6 +99,8 @@ def forward(views: B.Views, p: Params, eps2d: float = 0.3, background: Optional[
     ``K_capacity`` the exact intersection count is read back (one sync)."""
     _check_params(p)
     dev = p.means.device
+    if background is not None:
+        background = background.to(device=dev, dtype=p.means.dtype).contiguous()
     pr = project(views, p, eps2d, stream)
     cap = int(pr["K_total"].item()) if K_capacity is None else int(K_capacity)
     cap = max(cap, 1)
@@ -112,8 +115,9 @@ def forward(views: B.Views, p: Params, eps2d: float = 0.3, background: Optional[
     B.gs_bin_and_sort(views, pr["rects"], pr["depths"], pr["touched"], cap, ws, isect_ids, isect_pos, emit_start,
                       tile_ranges, K, flags, stream)
     pix = views.pixels
-    out_rgb = torch.empty(pix, 3, device=dev)
-    T_final = torch.empty(pix, device=dev)
+    dt = p.means.dtype
+    out_rgb = torch.empty(pix, 3, device=dev, dtype=dt)
+    T_final = torch.empty(pix, device=dev, dtype=dt)
     last_idx = torch.empty(pix, dtype=torch.int32, device=dev)
     n_contrib = torch.empty(pix, dtype=torch.int32, device=dev) if count_contrib else None
     B.gs_rasterize_fwd(views, pr["means2d"], pr["conics"], p.opacities, p.colors, isect_ids, tile_ranges, background,
@@ -128,22 +132,18 @@ def backward(f: Frame, p: Params, dL_drgb: torch.Tensor, stream=None, determinis
     """Gradients of L w.r.t. means, quats, scales, opacities, colors (and the
     2D intermediates means2d, conics) given dL/dC [pixels, 3].
     ``deterministic`` selects the run-to-run identical reduction."""
-    dev = p.means.device
+    dev, dt = p.means.device, p.means.dtype
     views = f.views
     P, N = views.P, p.n
-    dL_drgb = dL_drgb.contiguous().to(torch.float32)
-    g2 = torch.zeros(max(P, 1), 2, device=dev)
-    gc = torch.zeros(max(P, 1), 3, device=dev)
-    go = torch.zeros(max(N, 1), device=dev)
-    gcol = torch.zeros(max(N, 1), 3, device=dev)
-    nws = B.gs_rasterize_bwd_workspace_size(f.K_capacity, deterministic)
+    dL_drgb = dL_drgb.contiguous().to(dt)
+    z = lambda *shape: torch.zeros(*shape, device=dev, dtype=dt)
+    g2, gc, go, gcol = z(max(P, 1), 2), z(max(P, 1), 3), z(max(N, 1)), z(max(N, 1), 3)
+    nws = B.gs_rasterize_bwd_workspace_size(f.K_capacity, deterministic, dt == torch.float64)
     ws = torch.empty(nws, dtype=torch.uint8, device=dev) if nws else None
     B.gs_rasterize_bwd(views, f.means2d, f.conics, p.opacities, p.colors, f.isect_ids, f.isect_pos, f.emit_start,
                        f.touched, f.tile_ranges, f.K, f.K_capacity, f.background, f.T_final, f.last_idx, dL_drgb,
                        deterministic, ws, g2, gc, go, gcol, config, stream)
-    gm = torch.zeros(max(N, 1), 3, device=dev)
-    gq = torch.zeros(max(N, 1), 4, device=dev)
-    gs = torch.zeros(max(N, 1), 3, device=dev)
+    gm, gq, gs = z(max(N, 1), 3), z(max(N, 1), 4), z(max(N, 1), 3)
     B.gs_project_bwd(views, p.means, p.quats, p.scales, f.eps2d, f.touched, g2, gc, gm, gq, gs, stream)
     return dict(means=gm[:N], quats=gq[:N], scales=gs[:N], opacities=go[:N], colors=gcol[:N], means2d=g2[:P],
                 conics=gc[:P])

@@ -48,14 +48,24 @@ inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Vector types for the fp32 and fp64 instantiations of the kernels: V2/V4 have
 // the size and alignment of 2/4 scalars, so they load and store as one vector.
-template <typename S>
-struct alignas(2 * sizeof(S)) V2 {
-    S x, y;
+// fp32 uses CUDA's own float2/float4; fp64 uses aligned structs.
+struct alignas(16) Double2 {
+    double x, y;
 };
-template <typename S>
-struct alignas(4 * sizeof(S)) V4 {
-    S x, y, z, w;
+struct alignas(32) Double4 {
+    double x, y, z, w;
 };
+template <typename S> struct VecOf;
+template <> struct VecOf<float> {
+    using V2 = float2;
+    using V4 = float4;
+};
+template <> struct VecOf<double> {
+    using V2 = Double2;
+    using V4 = Double4;
+};
+template <typename S> using V2 = typename VecOf<S>::V2;
+template <typename S> using V4 = typename VecOf<S>::V4;
 
 template <typename S>
 __device__ __forceinline__ V4<S> mk4(S x, S y, S z, S w)

@@ -186,11 +186,11 @@ __device__ __forceinline__ Staged<S> load_staged(const V4<S>* sh_xy, const V4<S>
     return Staged<S>{sh_xy[j], sh_q[j], sh_col[j], sh_cull[j]};
 }
 
-__device__ __forceinline__ void atomic_add2(V2<float>* a, float x, float y)
+__device__ __forceinline__ void atomic_add2(float2* a, float x, float y)
 {
-    atomicAdd(reinterpret_cast<float2*>(a), make_float2(x, y));
+    atomicAdd(a, make_float2(x, y));
 }
-__device__ __forceinline__ void atomic_add2(V2<double>* a, double x, double y)
+__device__ __forceinline__ void atomic_add2(Double2* a, double x, double y)
 {
     atomicAdd(&a->x, x);
     atomicAdd(&a->y, y);
@@ -249,7 +249,8 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
             for (int s = 0; s < n; s += 32) {
                 bool hit = s + lane < n;
                 if (kCull && hit)
-                    hit = reaches_box(load_staged(sh_xy, sh_q, sh_col, sh_cull, s + lane), t.wx0, t.wx1, t.wy0, t.wy1);
+                    hit = reaches_box(load_staged<S>(sh_xy, sh_q, sh_col, sh_cull, s + lane), t.wx0, t.wx1, t.wy0,
+                                      t.wy1);
                 unsigned m = __ballot_sync(kFull, hit);
                 while (m) {
                     const int j = s + __ffs(m) - 1;
@@ -425,8 +426,8 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                 if (s < nw) {
                     bool hit = s + lane < nw;
                     if (kCull && hit)
-                        hit = reaches_box(load_staged(sh_xy, sh_q, sh_col, sh_cull, s + lane), t.wx0, t.wx1, t.wy0,
-                                          t.wy1);
+                        hit = reaches_box(load_staged<S>(sh_xy, sh_q, sh_col, sh_cull, s + lane), t.wx0, t.wx1,
+                                          t.wy0, t.wy1);
                     unsigned m = __ballot_sync(kFull, hit);
                     while (m) {
                         const int hb = 31 - __clz(m);

@@ -45,7 +45,7 @@ FP32_LANES_PER_SM = 128
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -77,7 +77,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu_index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -119,6 +119,22 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["max"] for r in rows),
                 "reasons": sorted(reasons), "samples": len(rows),
                 "power_w_max": max(r["power"] for r in rows)}
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, if it
+    was captured from the current source of the raster kernels (else None)."""
+    import hashlib
+    try:
+        src = open(os.path.join(ROOT, "paper_2312_02121_gb300", "csrc", "gs_raster.cu"), "rb").read()
+        h = hashlib.sha256(src).hexdigest()
+        for line in open(os.path.join(ROOT, "profiles", "roofline_traffic.txt")):
+            f = line.split()
+            if len(f) == 3 and not line.startswith("#") and f[0] == kernel and f[1] == h:
+                return int(f[2])
+    except OSError:
+        pass
+    return None
 
 
 def measured_peaks():
@@ -369,18 +385,18 @@ def run_ours(args, rank, world, local_rank):
             step()
         torch.cuda.synchronize()
         return
-    for _ in range(max(args.warmup, 3)):
-        fl = step()
-    torch.cuda.synchronize()
-    assert int(fl.item()) == 0, "intersection capacity overflow"
-
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(args.steps)]
-    launches0 = B.gs_kernel_launches()
     with ClockSampler(local_rank) as clk:
+        time.sleep(0.3)  # let the sampler start; it covers warm-up and the timed steps
+        for _ in range(max(args.warmup, 3)):
+            fl = step()
+        torch.cuda.synchronize()
+        assert int(fl.item()) == 0, "intersection capacity overflow"
+        launches0 = B.gs_kernel_launches()
         barrier()
         torch.cuda.synchronize()
         wall0 = time.perf_counter()
@@ -451,7 +467,8 @@ def run_ours(args, rank, world, local_rank):
         work = contrib * flops_per_pair[dom] / 1e12
         achieved = work / (stage_ms[dom] / 1e3)
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None,
+                "frac": achieved / fp32_peak,
+                "traffic": recorded_traffic("k_raster_bwd" if dom == "rasterize_bwd" else "k_raster_fwd"),
                 "peak_source": f"FP32 FMA lanes: {SMS} SMs x {FP32_LANES_PER_SM} x 2 x {sm_mhz:.0f} MHz "
                                f"(max SM clock, {src})",
                 "work": f"{contrib} composited (pixel, Gaussian) pairs x {flops_per_pair[dom]} flops"}

@@ -31,10 +31,13 @@ class BatchRenderer:
     def __init__(self, params: Params, views: B.Views, K_capacity: int, targets: Optional[torch.Tensor] = None,
                  eps2d: float = 0.3, config: Optional[B.RasterConfig] = None, longest_first: bool = False,
                  deterministic: bool = False, background: Optional[torch.Tensor] = None,
-                 shared_grads: Optional[Dict[str, torch.Tensor]] = None):
+                 shared_grads: Optional[Dict[str, torch.Tensor]] = None, loss_pixels: Optional[int] = None):
         """``shared_grads``: per-Gaussian gradient buffers (means, quats,
         scales, opacities, colors) owned and zeroed by the caller, into which
-        this renderer accumulates; by default the renderer owns them."""
+        this renderer accumulates; by default the renderer owns them.
+        ``loss_pixels``: the pixel count the L2 loss is a mean over (default:
+        this renderer's own pixels; a rank rendering part of a larger job
+        passes the job's total)."""
         self.p, self.views, self.eps2d = params, views, eps2d
         self.cap = max(int(K_capacity), 1)
         self.config, self.longest_first, self.deterministic = config, longest_first, deterministic
@@ -57,6 +60,7 @@ class BatchRenderer:
         self.rgb, self.T_final = e(pix, 3), e(pix)
         self.last_idx = e(pix, dtype=torch.int32)
         self.targets = targets
+        self.loss_scale = 2.0 / (3 * (loss_pixels if loss_pixels is not None else max(pix, 1)))
         self.dL = e(pix, 3)
         nbw = B.gs_rasterize_bwd_workspace_size(self.cap, deterministic)
         self.bwd_ws = e(nbw, dtype=torch.uint8) if nbw else None
@@ -91,7 +95,7 @@ class BatchRenderer:
     def loss_grad(self):
         """dL/dC of L = mean((C - target)^2) over every pixel of every view."""
         torch.sub(self.rgb, self.targets, out=self.dL)
-        self.dL.mul_(2.0 / self.rgb.numel())
+        self.dL.mul_(self.loss_scale)
 
     def backward(self):
         v, p = self.views, self.p

@@ -88,7 +88,7 @@ def _load():
                                         _I64, _P, _P, _P, _P, _P, _P]),
                 "or_rasterize_bwd": (None, [_I64, _P, _P, _P, _P, _P, _P, _P, _I32, _I32, _I32, _P,
                                             _I64, _P, _P, _P, _P, _P, _P]),
-                "or_project_bwd": (None, [_P, _I64, _P, _P, _P, _D, _P, _P, _P, _P, _P, _P]),
+                "or_project_bwd": (None, [_P, _I64, _P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
                 "or_bin": (_I64, [_I64, _P, _P, _P, _I32, _I32, _P, _P]),
             }
             for name, (res, args) in sig.items():
@@ -271,16 +271,19 @@ def rasterize_bwd(proj: dict, opacities, colors, width: int, height: int, dL_drg
 
 
 def project_bwd(cam, means, quats, scales, valid, dL_dmeans2d, dL_dconics, eps2d: float = 0.3) -> dict:
-    """Sec. 3.2 / 3.2.1 (Eq. 16-20): dL/dmu, dL/dq (raw quaternion), dL/ds."""
+    """Sec. 3.2 / 3.2.1 (Eq. 16-20): dL/dmu, dL/dq (raw quaternion), dL/ds, and
+    dL/dT_cw [4,4] (Eq. 20 plus the covariance route through R_cw, Reading
+    O14; summed over the Gaussians)."""
     means, quats, scales = _d(means), _d(quats), _d(scales)
     n = means.shape[0]
     valid = np.ascontiguousarray(valid, dtype=np.int32)
     g2, gc = _d(dL_dmeans2d, (n, 2)), _d(dL_dconics, (n, 3))
-    out = dict(means=np.zeros((n, 3)), quats=np.zeros((n, 4)), scales=np.zeros((n, 3)))
+    out = dict(means=np.zeros((n, 3)), quats=np.zeros((n, 4)), scales=np.zeros((n, 3)), viewmat=np.zeros(16))
     c = _cam(cam)
     _load().or_project_bwd(ctypes.byref(c), n, _ptr(means), _ptr(quats), _ptr(scales), float(eps2d),
                            _ptr(valid), _ptr(g2), _ptr(gc), _ptr(out["means"]), _ptr(out["quats"]),
-                           _ptr(out["scales"]))
+                           _ptr(out["scales"]), _ptr(out["viewmat"]))
+    out["viewmat"] = out["viewmat"].reshape(4, 4)
     return out
 
 
@@ -313,14 +316,16 @@ def render(cam, scene, eps2d: float = 0.3, background=None, pixels=None) -> dict
 
 
 def backward(cam, scene, dL_drgb, eps2d: float = 0.3, background=None, pixels=None) -> dict:
-    """Backward of Sec. 3: returns dL/d{means, quats, scales, opacities, colors}
+    """Backward of Sec. 3: returns dL/d{means, quats, scales, opacities, colors},
+    dL/dT_cw (``viewmat``, [4,4])
     plus the 2D intermediates (means2d, conics)."""
     proj = project(cam, scene.means, scene.quats, scene.scales, eps2d)
     g2d = rasterize_bwd(proj, scene.opacities, scene.colors, cam.width, cam.height, dL_drgb, background, pixels)
     g3d = project_bwd(cam, scene.means, scene.quats, scene.scales, proj["valid"], g2d["means2d"],
                       g2d["conics"], eps2d)
     return dict(means=g3d["means"], quats=g3d["quats"], scales=g3d["scales"], opacities=g2d["opacities"],
-                colors=g2d["colors"], means2d=g2d["means2d"], conics=g2d["conics"], proj=proj)
+                colors=g2d["colors"], means2d=g2d["means2d"], conics=g2d["conics"], viewmat=g3d["viewmat"],
+                proj=proj)
 
 
 def finite_difference(cam, scene, dL_drgb, name: str, index, h: float = 1e-6, eps2d: float = 0.3,

@@ -49,6 +49,13 @@
  *   O12 equal depths are ordered by Gaussian index.
  *   O13 conics are packed (a, b, c) for Y = [[a, b], [b, c]]; the gradient of
  *       the packed b is dL/dY_01 + dL/dY_10.
+ *   O14 dL/dT_cw.  Eq. 20 gives dL/dT_cw = (dL/dt) [mu; 1]^T, which follows
+ *       T_cw through t only.  Sigma' = T Sigma T^T with T = J R_cw (Sec. 3.2)
+ *       also depends on R_cw, so the 3x3 rotation block gains
+ *       J^T dL/dT; the paper computes dL/dT but carries it only into J.
+ *       The 16 entries are treated as independent (no SE(3) projection);
+ *       the bottom row stays zero because d mu'/d t_w = 0 (O8) and
+ *       dJ/dt_w = 0.
  *
  * All arithmetic is double precision.  OpenMP (when available) only splits
  * independent pixels or Gaussians across threads.
@@ -603,9 +610,11 @@ void or_rasterize_bwd(int64_t N, const double* means2d, const double* conics, co
 void or_project_bwd(const or_camera* cam, int64_t N, const double* means, const double* quats,
                     const double* scales, double eps2d, const int32_t* valid,
                     const double* dL_dmeans2d, const double* dL_dconics,
-                    double* dL_dmeans, double* dL_dquats, double* dL_dscales)
+                    double* dL_dmeans, double* dL_dquats, double* dL_dscales, double* dL_dviewmat)
 {
     (void)eps2d; /* d Sigma' / d Sigma does not depend on the dilation (O11) */
+    /* per-Gaussian terms of dL/dT_cw (rows 0-2 of the 4x4), summed in index order below */
+    double* vterm = dL_dviewmat ? (double*)calloc((size_t)(N > 0 ? N : 1) * 12, sizeof(double)) : NULL;
 #pragma omp parallel for schedule(static)
     for (int64_t n = 0; n < N; ++n) {
         double* gm = dL_dmeans + 3 * n;
@@ -673,6 +682,19 @@ void or_project_bwd(const or_camera* cam, int64_t N, const double* means, const 
         for (int i = 0; i < 3; ++i)
             gm[i] = cam->R[0 * 3 + i] * gt[0] + cam->R[1 * 3 + i] * gt[1] + cam->R[2 * 3 + i] * gt[2];
 
+        /* Eq. 20 with Reading O14: dL/dT_cw = (dL/dt) [mu; 1]^T, plus J^T dL/dT in the R_cw block */
+        if (vterm) {
+            double JtGT[9], Jt[6];
+            tr(J, Jt, 2, 3);
+            mm(Jt, GT, JtGT, 3, 2, 3);
+            const double* mu = means + 3 * n;
+            double* v = vterm + 12 * n;
+            for (int i = 0; i < 3; ++i) {
+                for (int j = 0; j < 3; ++j) v[4 * i + j] = gt[i] * mu[j] + JtGT[3 * i + j];
+                v[4 * i + 3] = gt[i];
+            }
+        }
+
         /* Sec. 3.2.1: dL/dM = G M + G^T M ; dL/dR = dL/dM S^T ; dL/dS = R^T dL/dM */
         double GSt[9], GM1[9], GM2[9], GM[9], S[9] = {scales[3 * n], 0, 0, 0, scales[3 * n + 1], 0, 0, 0, scales[3 * n + 2]};
         double GR[9], GS[9], Rt[9];
@@ -696,6 +718,12 @@ void or_project_bwd(const or_camera* cam, int64_t N, const double* means, const 
         const double gqh[4] = {fprod(GR, dRw, 9), fprod(GR, dRx, 9), fprod(GR, dRy, 9), fprod(GR, dRz, 9)};
         const double dot = gqh[0] * qh[0] + gqh[1] * qh[1] + gqh[2] * qh[2] + gqh[3] * qh[3];
         for (int i = 0; i < 4; ++i) gq[i] = (gqh[i] - qh[i] * dot) / qn;
+    }
+    if (dL_dviewmat) {
+        for (int i = 0; i < 16; ++i) dL_dviewmat[i] = 0.0;
+        for (int64_t n = 0; n < N; ++n)
+            for (int i = 0; i < 12; ++i) dL_dviewmat[i] += vterm[12 * n + i];
+        free(vterm);
     }
 }
 

@@ -297,11 +297,20 @@ int gs_rasterize_bwd(const GsView* views, int32_t V, int64_t P, int32_t T_total,
  *        dL_dconics
  *   out (ACCUMULATED, summed over views): dL_dmeans[N,3], dL_dquats[N,4]
  *        (w.r.t. the raw quaternion), dL_dscales[N,3].
+ *   out (optional, may be NULL; ACCUMULATED): dL_dviewmats[V,4,4], dL/dT_cw of
+ *        each view, row-major, summed over the view's projections.  Eq. 20
+ *        gives dL/dT_cw = dL/dt [mu; 1]^T, which follows T_cw through t only;
+ *        because Sigma' = T Sigma T^T with T = J R_cw also depends on R_cw,
+ *        the rotation block adds J^T dL/dT.  The 16 entries are treated as
+ *        independent (the caller projects onto SE(3) if it wants a pose
+ *        update); row 3 stays zero.  Asking for it selects a kernel variant
+ *        that also reduces the 12 terms per view (one atomic per entry per
+ *        256 projections), so fp32 results vary in the last bits run to run.
  */
 int gs_project_bwd(const GsView* views, int32_t V, int64_t P, const float* means, const float* quats,
                    const float* scales, float eps2d, const int32_t* touched, const float* dL_dmeans2d,
                    const float* dL_dconics, float* dL_dmeans, float* dL_dquats, float* dL_dscales,
-                   void* stream);
+                   float* dL_dviewmats, void* stream);
 
 /*
  * FP64 instantiations of the four arithmetic stages, for checking the analytic
@@ -336,7 +345,7 @@ int gs_rasterize_bwd_f64(const GsView* views, int32_t V, int64_t P, int32_t T_to
 int gs_project_bwd_f64(const GsView* views, int32_t V, int64_t P, const double* means, const double* quats,
                        const double* scales, double eps2d, const int32_t* touched, const double* dL_dmeans2d,
                        const double* dL_dconics, double* dL_dmeans, double* dL_dquats, double* dL_dscales,
-                       void* stream);
+                       double* dL_dviewmats, void* stream);
 
 #ifdef __cplusplus
 }

@@ -80,13 +80,13 @@ SIGNATURES = {
     "gs_rasterize_bwd_workspace_size": (_SZ, [_I64, _I32]),
     "gs_rasterize_bwd": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P,
                                         _P, _P, _I32, _P, _SZ, _P, _P, _P, _P, _P, _P]),
-    "gs_project_bwd": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _F, _P, _P, _P, _P, _P, _P, _P]),
+    "gs_project_bwd": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _F, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gs_project_f64": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
     "gs_rasterize_fwd_f64": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gs_rasterize_bwd_f64_workspace_size": (_SZ, [_I64, _I32]),
     "gs_rasterize_bwd_f64": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I64, _P,
                                             _P, _P, _P, _I32, _P, _SZ, _P, _P, _P, _P, _P, _P]),
-    "gs_project_bwd_f64": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
+    "gs_project_bwd_f64": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -292,11 +292,13 @@ def gs_rasterize_bwd(views: Views, means2d, conics, opacities, colors, isect_ids
 
 
 def gs_project_bwd(views: Views, means, quats, scales, eps2d: float, touched, dL_dmeans2d, dL_dconics, dL_dmeans,
-                   dL_dquats, dL_dscales, stream=None):
+                   dL_dquats, dL_dscales, stream=None, dL_dviewmats=None):
+    """``dL_dviewmats``: optional [V, 4, 4] buffer (zeroed by the caller) that
+    receives dL/dT_cw of every view."""
     fn = load().gs_project_bwd_f64 if _f64(means) else load().gs_project_bwd
     _check(fn(_ptr(views.device), views.V, views.P, _ptr(means), _ptr(quats), _ptr(scales),
                                  float(eps2d), _ptr(touched), _ptr(dL_dmeans2d), _ptr(dL_dconics), _ptr(dL_dmeans),
-                                 _ptr(dL_dquats), _ptr(dL_dscales), _stream(stream)))
+                                 _ptr(dL_dquats), _ptr(dL_dscales), _ptr(dL_dviewmats), _stream(stream)))
 
 
 EXPORTED: List[str] = list(SIGNATURES)

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <climits>
 #include <stdint.h>
 
 #include "gsplat103.h"

@@ -176,17 +176,15 @@ k_project_fwd(const GsView* __restrict__ views, int V, int64_t P, const S* __res
     }
 }
 
-template <typename S>
-__global__ void __launch_bounds__(256)
-k_project_bwd(const GsView* __restrict__ views, int V, int64_t P, const S* __restrict__ means,
-              const V4<S>* __restrict__ quats, const S* __restrict__ scales, S eps2d,
-              const int32_t* __restrict__ touched, const V2<S>* __restrict__ dL_dmeans2d,
-              const S* __restrict__ dL_dconics, S* __restrict__ dL_dmeans, S* __restrict__ dL_dquats,
-              S* __restrict__ dL_dscales)
+// The backward of one projection p of view `view`.  With kView it also returns
+// this projection's share of dL/dT_cw (rows 0-2 of the 4x4, row-major) in vg.
+template <typename S, bool kView>
+__device__ __forceinline__ void project_bwd_one(const GsView& view, int64_t p, const S* __restrict__ means,
+                                                const V4<S>* __restrict__ quats, const S* __restrict__ scales,
+                                                S eps2d, const V2<S>* __restrict__ dL_dmeans2d,
+                                                const S* __restrict__ dL_dconics, S* __restrict__ dL_dmeans,
+                                                S* __restrict__ dL_dquats, S* __restrict__ dL_dscales, S vg[12])
 {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P || touched[p] == 0) return;
-    const GsView& view = views[view_of_projection(views, V, p)];
     const GsCamera& cam = view.cam;
     const int64_t g = view.g_begin + (p - view.proj_offset);
     Proj<S> o;
@@ -246,6 +244,21 @@ k_project_bwd(const GsView* __restrict__ views, int V, int64_t P, const S* __res
     atomicAdd(dL_dmeans + 3 * g + 0, W[0] * dtx + W[3] * dty + W[6] * dtz);
     atomicAdd(dL_dmeans + 3 * g + 1, W[1] * dtx + W[4] * dty + W[7] * dtz);
     atomicAdd(dL_dmeans + 3 * g + 2, W[2] * dtx + W[5] * dty + W[8] * dtz);
+    if constexpr (kView) {
+        // Eq. 20: dL/dT_cw = dL/dt [mu; 1]^T; the R_cw block also gains J^T dL/dT, the covariance route
+        // (Sigma' = T Sigma T^T with T = J R_cw), for which the rows of J are (J00, 0, J02), (0, J11, J12)
+        const S mu[3] = {means[3 * g + 0], means[3 * g + 1], means[3 * g + 2]};
+        const S dt[3] = {dtx, dty, dtz};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            vg[0 * 4 + j] = dt[0] * mu[j] + o.J00 * dT[j];
+            vg[1 * 4 + j] = dt[1] * mu[j] + o.J11 * dT[3 + j];
+            vg[2 * 4 + j] = dt[2] * mu[j] + o.J02 * dT[j] + o.J12 * dT[3 + j];
+        }
+        vg[3] = dtx;
+        vg[7] = dty;
+        vg[11] = dtz;
+    }
 
     // Sec. 3.2.1: dL/dM = (G + G^T) M = 2 dSigma M (dSigma is symmetric)
     S dM[9];
@@ -280,6 +293,87 @@ k_project_bwd(const GsView* __restrict__ views, int V, int64_t P, const S* __res
     atomicAdd(dL_dquats + 4 * g + 3, (gz - z * dot) * o.qinv);
 }
 
+template <typename S>
+__global__ void __launch_bounds__(256)
+k_project_bwd(const GsView* __restrict__ views, int V, int64_t P, const S* __restrict__ means,
+              const V4<S>* __restrict__ quats, const S* __restrict__ scales, S eps2d,
+              const int32_t* __restrict__ touched, const V2<S>* __restrict__ dL_dmeans2d,
+              const S* __restrict__ dL_dconics, S* __restrict__ dL_dmeans, S* __restrict__ dL_dquats,
+              S* __restrict__ dL_dscales)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P || touched[p] == 0) return;
+    project_bwd_one<S, false>(views[view_of_projection(views, V, p)], p, means, quats, scales, eps2d, dL_dmeans2d,
+                              dL_dconics, dL_dmeans, dL_dquats, dL_dscales, nullptr);
+}
+
+// The same, plus dL/dT_cw per view.  A view's projections are contiguous, so a
+// warp almost always lies in one view: it sums its 12 terms by shuffles and
+// hands them to the block, which adds each run of equal views to global
+// memory with one atomic per entry (about 12 atomics per 256 projections).
+// A warp that straddles a view boundary adds lane by lane instead.
+template <typename S>
+__global__ void __launch_bounds__(256)
+k_project_bwd_view(const GsView* __restrict__ views, int V, int64_t P, const S* __restrict__ means,
+                   const V4<S>* __restrict__ quats, const S* __restrict__ scales, S eps2d,
+                   const int32_t* __restrict__ touched, const V2<S>* __restrict__ dL_dmeans2d,
+                   const S* __restrict__ dL_dconics, S* __restrict__ dL_dmeans, S* __restrict__ dL_dquats,
+                   S* __restrict__ dL_dscales, S* __restrict__ dL_dviewmats)
+{
+    __shared__ S s_sum[8][12];
+    __shared__ int s_view[8];
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    S vg[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) vg[i] = S(0);
+    int vi = -1;
+    if (p < P && touched[p] != 0) {
+        vi = view_of_projection(views, V, p);
+        project_bwd_one<S, true>(views[vi], p, means, quats, scales, eps2d, dL_dmeans2d, dL_dconics, dL_dmeans,
+                                 dL_dquats, dL_dscales, vg);
+    }
+    const unsigned full = 0xffffffffu;
+    const int vlo = __reduce_min_sync(full, vi < 0 ? INT_MAX : vi);
+    const int vhi = __reduce_max_sync(full, vi);
+    if (vhi >= 0 && vlo == vhi) {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            S x = vg[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(full, x, o);
+            vg[i] = x;
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < 12; ++i) s_sum[warp][i] = vg[i];
+            s_view[warp] = vlo;
+        }
+    } else {
+        if (vi >= 0)
+#pragma unroll
+            for (int i = 0; i < 12; ++i) atomicAdd(dL_dviewmats + 16 * (int64_t)vi + i, vg[i]);
+        if (lane == 0) s_view[warp] = -1;
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        const int i = threadIdx.x;
+        int cur = -1;
+        S acc = S(0);
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const int v = s_view[w];
+            if (v < 0) continue;
+            if (v != cur) {
+                if (cur >= 0) atomicAdd(dL_dviewmats + 16 * (int64_t)cur + i, acc);
+                cur = v;
+                acc = S(0);
+            }
+            acc += s_sum[w][i];
+        }
+        if (cur >= 0) atomicAdd(dL_dviewmats + 16 * (int64_t)cur + i, acc);
+    }
+}
+
 static bool misaligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) != 0; }
 
 template <typename S>
@@ -310,7 +404,8 @@ static int project_impl(const char* who, const GsView* views, int32_t V, int64_t
 template <typename S>
 static int project_bwd_impl(const char* who, const GsView* views, int32_t V, int64_t P, const S* means,
                             const S* quats, const S* scales, S eps2d, const int32_t* touched, const S* dL_dmeans2d,
-                            const S* dL_dconics, S* dL_dmeans, S* dL_dquats, S* dL_dscales, void* stream)
+                            const S* dL_dconics, S* dL_dmeans, S* dL_dquats, S* dL_dscales, S* dL_dviewmats,
+                            void* stream)
 {
     if (V < 0 || P < 0 || (P > 0 && V == 0)) return fail(GS_ERR_INVALID_ARG, "%s: V=%d P=%lld", who, V, (long long)P);
     if (P > 0 && (!views || !means || !quats || !scales || !touched || !dL_dmeans2d || !dL_dconics || !dL_dmeans ||
@@ -322,9 +417,14 @@ static int project_bwd_impl(const char* who, const GsView* views, int32_t V, int
     if (P == 0) return GS_OK;
     const int threads = 256;
     const unsigned blocks = (unsigned)((P + threads - 1) / threads);
-    k_project_bwd<S><<<blocks, threads, 0, as_stream(stream)>>>(
-        views, V, P, means, reinterpret_cast<const V4<S>*>(quats), scales, eps2d, touched,
-        reinterpret_cast<const V2<S>*>(dL_dmeans2d), dL_dconics, dL_dmeans, dL_dquats, dL_dscales);
+    if (dL_dviewmats)
+        k_project_bwd_view<S><<<blocks, threads, 0, as_stream(stream)>>>(
+            views, V, P, means, reinterpret_cast<const V4<S>*>(quats), scales, eps2d, touched,
+            reinterpret_cast<const V2<S>*>(dL_dmeans2d), dL_dconics, dL_dmeans, dL_dquats, dL_dscales, dL_dviewmats);
+    else
+        k_project_bwd<S><<<blocks, threads, 0, as_stream(stream)>>>(
+            views, V, P, means, reinterpret_cast<const V4<S>*>(quats), scales, eps2d, touched,
+            reinterpret_cast<const V2<S>*>(dL_dmeans2d), dL_dconics, dL_dmeans, dL_dquats, dL_dscales);
     count_launches(1);
     return launch_status(who);
 }
@@ -352,17 +452,17 @@ extern "C" int gs_project_f64(const GsView* views, int32_t V, int64_t P, const d
 extern "C" int gs_project_bwd(const GsView* views, int32_t V, int64_t P, const float* means, const float* quats,
                               const float* scales, float eps2d, const int32_t* touched, const float* dL_dmeans2d,
                               const float* dL_dconics, float* dL_dmeans, float* dL_dquats, float* dL_dscales,
-                              void* stream)
+                              float* dL_dviewmats, void* stream)
 {
     return project_bwd_impl<float>("gs_project_bwd", views, V, P, means, quats, scales, eps2d, touched, dL_dmeans2d,
-                                   dL_dconics, dL_dmeans, dL_dquats, dL_dscales, stream);
+                                   dL_dconics, dL_dmeans, dL_dquats, dL_dscales, dL_dviewmats, stream);
 }
 
 extern "C" int gs_project_bwd_f64(const GsView* views, int32_t V, int64_t P, const double* means,
                                   const double* quats, const double* scales, double eps2d, const int32_t* touched,
                                   const double* dL_dmeans2d, const double* dL_dconics, double* dL_dmeans,
-                                  double* dL_dquats, double* dL_dscales, void* stream)
+                                  double* dL_dquats, double* dL_dscales, double* dL_dviewmats, void* stream)
 {
     return project_bwd_impl<double>("gs_project_bwd_f64", views, V, P, means, quats, scales, eps2d, touched,
-                                    dL_dmeans2d, dL_dconics, dL_dmeans, dL_dquats, dL_dscales, stream);
+                                    dL_dmeans2d, dL_dconics, dL_dmeans, dL_dquats, dL_dscales, dL_dviewmats, stream);
 }

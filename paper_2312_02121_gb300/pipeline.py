@@ -128,10 +128,11 @@ def forward(views: B.Views, p: Params, eps2d: float = 0.3, background: Optional[
 
 
 def backward(f: Frame, p: Params, dL_drgb: torch.Tensor, stream=None, deterministic: bool = False,
-             config: Optional[B.RasterConfig] = None) -> dict:
+             config: Optional[B.RasterConfig] = None, viewmats: bool = False) -> dict:
     """Gradients of L w.r.t. means, quats, scales, opacities, colors (and the
     2D intermediates means2d, conics) given dL/dC [pixels, 3].
-    ``deterministic`` selects the run-to-run identical reduction."""
+    ``deterministic`` selects the run-to-run identical reduction.  With
+    ``viewmats`` the result also holds dL/dT_cw of every view ([V, 4, 4])."""
     dev, dt = p.means.device, p.means.dtype
     views = f.views
     P, N = views.P, p.n
@@ -144,6 +145,10 @@ def backward(f: Frame, p: Params, dL_drgb: torch.Tensor, stream=None, determinis
                        f.touched, f.tile_ranges, f.K, f.K_capacity, f.background, f.T_final, f.last_idx, dL_drgb,
                        deterministic, ws, g2, gc, go, gcol, config, stream)
     gm, gq, gs = z(max(N, 1), 3), z(max(N, 1), 4), z(max(N, 1), 3)
-    B.gs_project_bwd(views, p.means, p.quats, p.scales, f.eps2d, f.touched, g2, gc, gm, gq, gs, stream)
-    return dict(means=gm[:N], quats=gq[:N], scales=gs[:N], opacities=go[:N], colors=gcol[:N], means2d=g2[:P],
-                conics=gc[:P])
+    gv = z(max(views.V, 1), 4, 4) if viewmats else None
+    B.gs_project_bwd(views, p.means, p.quats, p.scales, f.eps2d, f.touched, g2, gc, gm, gq, gs, stream, gv)
+    out = dict(means=gm[:N], quats=gq[:N], scales=gs[:N], opacities=go[:N], colors=gcol[:N], means2d=g2[:P],
+               conics=gc[:P])
+    if viewmats:
+        out["viewmats"] = gv[:views.V]
+    return out

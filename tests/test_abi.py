@@ -43,7 +43,7 @@ def test_binding_covers_every_declared_symbol():
 
 def test_version_and_struct_sizes(lib):
     from paper_2312_02121_gb300 import binding
-    assert binding.gs_version() == 100
+    assert binding.gs_version() == 101
     assert ctypes.sizeof(binding.GsView) == 120
 
 
@@ -88,4 +88,5 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.gs_tile_order(None, 5, None, 0, None, None) == 1
     assert lib.gs_bin_and_sort(None, 1, 10, 4, None, None, None, 100, None, 0, None, None, None, None, None, None,
                                None) == 1
-    assert lib.gs_project_bwd(None, 1, -5, None, None, None, 0.3, None, None, None, None, None, None, None) == 1
+    assert lib.gs_project_bwd(None, 1, -5, None, None, None, 0.3, None, None, None, None, None, None, None,
+                              None) == 1

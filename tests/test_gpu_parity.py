@@ -16,6 +16,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import oracle
+from paper_2312_02121_gb300 import binding as B
 from paper_2312_02121_gb300 import pipeline
 from paper_2312_02121_gb300 import workloads as wl
 from gpu_helpers import (gpu_projection, last_gaussian_ids, np_, rel_l2, run_gpu, uncertain_pixels, view_image)
@@ -55,7 +56,7 @@ def case(request):
     grads = pipeline.backward(frame, params, torch.as_tensor(Gm.reshape(-1, 3), device="cuda"))
     torch.cuda.synchronize()
     return dict(name=request.param, w=w, cam=cam, sc=sc, G=Gm, ofwd=ofwd, bad=bad, ogp=ogp, bad_gp=bad_gp,
-                frame=frame, grads=grads)
+                frame=frame, grads=grads, params=params)
 
 
 def test_projection(case):
@@ -136,6 +137,54 @@ def test_backward_end_to_end(case):
     ob = oracle.backward(cam, sc, case["G"], case["w"].eps2d)
     for k in ("means", "quats", "scales", "opacities", "colors"):
         assert rel_l2(np_(g[k]), ob[k]) <= GRAD_TOL, k
+
+
+def _project_bwd_with_viewmats(frame, params, g2, gc, eps2d):
+    z = lambda *shape: torch.zeros(*shape, device="cuda")
+    N = params.n
+    gm, gq, gs, gv = z(max(N, 1), 3), z(max(N, 1), 4), z(max(N, 1), 3), z(frame.views.V, 4, 4)
+    B.gs_project_bwd(frame.views, params.means, params.quats, params.scales, eps2d, frame.touched, g2, gc, gm, gq,
+                     gs, None, gv)
+    torch.cuda.synchronize()
+    return dict(means=gm[:N], quats=gq[:N], scales=gs[:N], viewmats=gv)
+
+
+def test_view_matrix_gradient_given_2d_gradients(case):
+    # projection backward with dL/dT_cw: the oracle maps the CUDA 2D gradients (Eq. 20, Reading O14)
+    cam, sc, f, g = case["cam"], case["sc"], case["frame"], case["grads"]
+    P = f.views.P
+    out = _project_bwd_with_viewmats(f, case["params"], g["means2d"][:P].contiguous(), g["conics"][:P].contiguous(),
+                                     case["w"].eps2d)
+    ob = oracle.project_bwd(cam, sc.means, sc.quats, sc.scales, gpu_projection(f)["valid"], np_(g["means2d"]),
+                            np_(g["conics"]), case["w"].eps2d)
+    gv = np_(out["viewmats"][0])
+    assert not gv[3].any()
+    assert rel_l2(gv, ob["viewmat"]) <= GRAD_TOL
+    for k in ("means", "quats", "scales"):  # the kernel variant leaves the per-Gaussian outputs as they were
+        assert rel_l2(np_(out[k]), np_(g[k])) <= 1e-6, k
+
+
+def test_view_matrix_gradient_end_to_end_rotated_cameras():
+    # three rotated cameras of uneven sizes on one scene; one batched call, per-view dL/dT_cw
+    base = wl.small_case(12, 2500, 64, 64, log_scale_mu=-2.6)
+    sc = base.scenes[0]
+    cams = wl.sphere_cameras(np.random.default_rng(13), 3, 4.0, [(80, 60), (47, 33), (64, 64)],
+                             focal_range=(60.0, 110.0))
+    w = wl.Workload("rotated", [sc], [wl.View(0, c) for c in cams], None)
+    rng = np.random.default_rng(14)
+    Gs = []
+    for c in cams:
+        o = oracle.render(c, sc, w.eps2d)
+        G = rng.standard_normal((c.height, c.width, 3)).astype(np.float32)
+        G[uncertain_pixels(o, o["proj"], c.width, c.height, sc.opacities)] = 0
+        Gs.append(G)
+    frame, params, _ = run_gpu(w)
+    g = pipeline.backward(frame, params, torch.as_tensor(np.concatenate([G.reshape(-1, 3) for G in Gs]),
+                                                         device="cuda"), viewmats=True)
+    torch.cuda.synchronize()
+    for i, (c, G) in enumerate(zip(cams, Gs)):
+        ob = oracle.backward(c, sc, G, w.eps2d)
+        assert rel_l2(np_(g["viewmats"][i]), ob["viewmat"]) <= GRAD_TOL, i
 
 
 def test_background():

@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target duration of the oracle sample")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-per-view measurement")
     ap.add_argument("--batched-steps", type=int, default=5)
+    ap.add_argument("--no-optim", action="store_true", help="skip the optimisation-loop measurement")
+    ap.add_argument("--optim-steps", type=int, default=20)
     ap.add_argument("--profile", action="store_true",
                     help="run warmup + steps untimed and exit (a fixed command line for ncu)")
     return ap.parse_args()
@@ -273,6 +275,69 @@ def batched_comparison(dev, steps: int):
     return out
 
 
+def optimisation_loop(dev, w, steps: int):
+    """The graph-captured training step (forward, fused L2 loss, backward, fused
+    Adam on the raw parameters) on the headline workload, from its scene toward
+    its target image."""
+    import numpy as np
+    import torch
+    from paper_2312_02121_gb300 import binding as B
+    from paper_2312_02121_gb300.train import Trainer
+    cam, sc = w.views[0].camera, w.scenes[0]
+    o = np.clip(np.asarray(sc.opacities, np.float64), 1e-6, 1 - 1e-6)
+    raw = {"means": sc.means, "quats": sc.quats, "log_scales": np.log(sc.scales),
+           "opacity_logits": np.log(o / (1 - o)), "colors": sc.colors}
+    raw = {k: torch.as_tensor(np.asarray(v, np.float32), device=dev).contiguous() for k, v in raw.items()}
+    views = B.Views([cam], [(0, sc.n)], device=dev)
+    tgt = torch.as_tensor(w.targets[0].reshape(-1, 3), device=dev)
+    t = Trainer(raw, views, tgt)
+    t.capture()
+    t.step()
+    torch.cuda.synchronize()
+    loss0 = t.loss()
+    l0 = B.gs_kernel_launches()
+    t.step_eager()
+    launches = B.gs_kernel_launches() - l0
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        t.step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    out = {"ms_per_step": ms, "mpix_s": views.pixels / ms / 1e3, "steps": steps, "cuda_graph": True,
+           "gpu_launches_per_step": int(launches), "loss_first": loss0, "loss_last": t.loss(),
+           "adam_steps_applied": t.steps_taken(), "overflowed": t.overflowed(), "capacity": t.capacity,
+           "l2": "inputs larger than L2 (params, moments, target: > 129 MB)"}
+    del t
+    torch.cuda.empty_cache()
+    return out
+
+
+def view_gradient_cost(dev, views, params, pr, g2, gc, eps2d: float, steps: int = 20):
+    """Device time of the projection backward with and without the per-view
+    dL/dT_cw output."""
+    import torch
+    from paper_2312_02121_gb300 import binding as B
+    N = params.n
+    z = lambda *shape: torch.zeros(*shape, device=dev)
+    gm, gq, gs, gv = z(N, 3), z(N, 4), z(N, 3), z(views.V, 4, 4)
+    res = {}
+    for name, vm in (("plain", None), ("with_viewmats", gv)):
+        for _ in range(3):
+            B.gs_project_bwd(views, params.means, params.quats, params.scales, eps2d, pr["touched"], g2, gc, gm, gq,
+                             gs, None, vm)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            B.gs_project_bwd(views, params.means, params.quats, params.scales, eps2d, pr["touched"], g2, gc, gm, gq,
+                             gs, None, vm)
+        b.record()
+        torch.cuda.synchronize()
+        res[name + "_ms"] = a.elapsed_time(b) / steps
+    return res
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
@@ -341,6 +406,7 @@ def run_ours(args, rank, world, local_rank):
     cap = K
     stream = torch.cuda.current_stream()
     stages = ["project", "bin_and_sort", "rasterize_fwd", "loss_grad", "rasterize_bwd", "project_bwd"]
+    last_state = {}
 
     def step(ev=None):
         def mark(i):
@@ -364,7 +430,8 @@ def run_ours(args, rank, world, local_rank):
         B.gs_rasterize_fwd(views, pr["means2d"], pr["conics"], params.opacities, params.colors, ids, tr, None, rgb,
                            Tf, last)
         mark(3)
-        dL = (rgb - target).mul_(2.0 / rgb.numel())
+        dL = torch.empty(pixels, 3, device=dev)
+        B.gs_l2_loss(rgb, target, 1.0 / rgb.numel(), dL, None)
         mark(4)
         g2 = torch.zeros(P, 2, device=dev)
         gc = torch.zeros(P, 3, device=dev)
@@ -378,6 +445,7 @@ def run_ours(args, rank, world, local_rank):
         gs = torch.zeros(sc.n, 3, device=dev)
         B.gs_project_bwd(views, params.means, params.quats, params.scales, w.eps2d, pr["touched"], g2, gc, gm, gq, gs)
         mark(6)
+        last_state.update(pr=pr, g2=g2, gc=gc)
         return fl
 
     if args.profile:
@@ -421,25 +489,29 @@ def run_ours(args, rank, world, local_rank):
         ms_step = float(t.item())
     value = world * pixels / (ms_step / 1e3) / 1e6
 
-    # --- end to end through the public API (host buffers, H2D + D2H inside the timed region)
+    # --- end to end through the public API, from host buffers: every step copies the Gaussian
+    # parameters and the target image from pinned host memory, lays out its view descriptor, renders
+    # through the autograd API, takes the fused L2 loss, runs the backward and reads the loss back.
     host = {k: torch.as_tensor(getattr(sc, k)).pin_memory() for k in ("means", "quats", "scales", "opacities", "colors")}
     host_tgt = torch.as_tensor(w.targets[0]).pin_memory()
     dev_bufs = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
     dev_tgt = torch.empty_like(host_tgt, device=dev)
     h2d = sum(v.numel() * v.element_size() for v in host.values()) + host_tgt.numel() * host_tgt.element_size()
+    h2d += 120  # one GsView
 
     def e2e_step():
         for k, v in host.items():
             dev_bufs[k].copy_(v, non_blocking=True)
         dev_tgt.copy_(host_tgt, non_blocking=True)
-        leaves = {k: v.detach().requires_grad_(True) for k, v in dev_bufs.items()}
+        v = B.Views([cam], [(0, sc.n)], device=dev)
+        leaves = {k: t.detach().requires_grad_(True) for k, t in dev_bufs.items()}
         img = ga.render(leaves["means"], leaves["quats"], leaves["scales"], leaves["opacities"], leaves["colors"],
-                        [cam], eps2d=w.eps2d, K_capacity=cap)[0]
-        loss = torch.mean((img - dev_tgt) ** 2)
+                        None, eps2d=w.eps2d, K_capacity=cap, views=v)[0]
+        loss = ga.l2_loss(img, dev_tgt)
         loss.backward()
         return float(loss.item())
 
-    for _ in range(2):
+    for _ in range(3):
         e2e_step()
     torch.cuda.synchronize()
     barrier()
@@ -452,7 +524,9 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e = {"value": world * pixels / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-           "d2h_bytes_per_step": 4, "ms_per_step": 1e3 * e2e_s}
+           "d2h_bytes_per_step": 4, "ms_per_step": 1e3 * e2e_s,
+           "inputs": "per step: Gaussian parameters, target image and view descriptor (host -> device); "
+                     "result: the loss (device -> host)"}
 
     if rank != 0:
         return
@@ -490,6 +564,10 @@ def run_ours(args, rank, world, local_rank):
         "stage_ms": stage_ms, "wall_s": wall, "gpu_launches": int(launches),
         "e2e": e2e, "roofline": roof, "clocks": clocks,
     }
+    line["project_bwd_view_gradient"] = view_gradient_cost(dev, views, params, last_state["pr"], last_state["g2"],
+                                                           last_state["gc"], w.eps2d)
+    if not args.no_optim:
+        line["optimisation_loop"] = optimisation_loop(dev, w, args.optim_steps)
     if not args.no_batched:
         line["batched"] = batched_comparison(dev, args.batched_steps)
     if not args.no_cpu_baseline and world == 1:

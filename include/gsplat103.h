@@ -313,6 +313,63 @@ int gs_project_bwd(const GsView* views, int32_t V, int64_t P, const float* means
                    float* dL_dviewmats, void* stream);
 
 /*
+ * Training-step helpers (the paper has no counterpart: it derives gradients
+ * only).  They let a whole optimisation step -- forward, loss, backward,
+ * update -- run on the GPU and be captured into one CUDA graph.
+ *
+ * gs_l2_loss: L = inv_norm * sum_i (rgb_i - target_i)^2 over n scalars and
+ * its gradient dL/drgb_i = 2 inv_norm (rgb_i - target_i), the dL/dC that
+ * gs_rasterize_bwd takes.  For the mean over all pixels and channels pass
+ * inv_norm = 1 / n.
+ *   in : rgb[n], target[n]
+ *   out: dL_drgb[n] (nullable), loss (device scalar, nullable; ACCUMULATED:
+ *        the caller zeroes it; blocks add with atomics, so fp32 sums vary in
+ *        the last bits run to run).  At least one output must be given.
+ */
+int gs_l2_loss(const float* rgb, const float* target, int64_t n, float inv_norm, float* dL_drgb, float* loss,
+               void* stream);
+int gs_l2_loss_f64(const double* rgb, const double* target, int64_t n, double inv_norm, double* dL_drgb,
+                   double* loss, void* stream);
+
+/* Adam hyper-parameters: one learning rate per parameter group (means,
+ * quaternions, log-scales, opacity logits, colours), the moment decay rates
+ * and the denominator offset. */
+typedef struct GsAdamConfig {
+    float lr[5];
+    float beta1, beta2, eps;
+} GsAdamConfig;
+
+/* Bytes of optimiser state for N Gaussians (a 256-byte header holding the step
+ * count, then the first and second moments, 14 floats per Gaussian each). */
+size_t gs_adam_state_size(int64_t N);
+
+/*
+ * One Adam step (Kingma & Ba, bias-corrected) on the raw parameters of N
+ * Gaussians, in place: means[N,3], quats[N,4] (raw; the renderer normalises
+ * them), log_scales[N,3], opacity_logits[N], colors[N,3].  The gradients are
+ * those of the projection and compositing backward, i.e. with respect to the
+ * ACTIVATED values scale = exp(log-scale) and opacity = sigmoid(logit); the
+ * step chains them through the activations using scales[N,3] and
+ * opacities[N] (the activated values the forward used) and then rewrites
+ * scales and opacities from the updated raw values, ready for the next
+ * forward.  `state` (gs_adam_state_size bytes, device) must be zeroed before
+ * the first step; the step count lives in it, so repeated launches (or graph
+ * replays) advance the bias correction.  When skip_if_set (device int32,
+ * nullable) is non-zero at run time -- e.g. the flags of gs_bin_and_sort after
+ * an intersection overflow made the gradients incomplete -- the step changes
+ * nothing, not even the step count.  Two kernels are enqueued.
+ */
+int gs_adam_step(int64_t N, const GsAdamConfig* cfg, void* state, size_t state_bytes, float* means, float* quats,
+                 float* log_scales, float* opacity_logits, float* colors, const float* dL_dmeans,
+                 const float* dL_dquats, const float* dL_dscales, const float* dL_dopacities,
+                 const float* dL_dcolors, float* scales, float* opacities, const int32_t* skip_if_set,
+                 void* stream);
+
+/* scales = exp(log_scales) [N,3], opacities = sigmoid(opacity_logits) [N]. */
+int gs_activate(int64_t N, const float* log_scales, const float* opacity_logits, float* scales, float* opacities,
+                void* stream);
+
+/*
  * FP64 instantiations of the four arithmetic stages, for checking the analytic
  * backward of Sec. 3 against finite differences (e.g. torch.autograd.gradcheck)
  * and against an fp64 reference.  Arguments are those of the fp32 entry points

@@ -58,19 +58,25 @@ def _posed(cam, T: np.ndarray):
 def render(means: torch.Tensor, quats: torch.Tensor, scales: torch.Tensor, opacities: torch.Tensor,
            colors: torch.Tensor, cameras: Sequence, g_ranges: Optional[Sequence[Tuple[int, int]]] = None,
            eps2d: float = 0.3, background: Optional[torch.Tensor] = None,
-           K_capacity: Optional[int] = None, viewmats: Optional[torch.Tensor] = None) -> List[torch.Tensor]:
+           K_capacity: Optional[int] = None, viewmats: Optional[torch.Tensor] = None,
+           views: Optional[B.Views] = None) -> List[torch.Tensor]:
     """Renders every camera; returns a list of [H, W, 3] images (views of one
     packed buffer).  ``g_ranges[i] = (g_begin, g_count)`` selects the scene
     camera i sees (default: all Gaussians).  ``viewmats`` (optional, [V, 4, 4])
-    overrides the cameras' extrinsics and is differentiable."""
-    if g_ranges is None:
-        g_ranges = [(0, int(means.shape[0]))] * len(cameras)
-    if viewmats is not None:
-        if tuple(viewmats.shape) != (len(cameras), 4, 4):
-            raise ValueError(f"viewmats must be [{len(cameras)}, 4, 4], got {tuple(viewmats.shape)}")
-        T = viewmats.detach().cpu().double().numpy()
-        cameras = [_posed(c, T[i]) for i, c in enumerate(cameras)]
-    views = B.Views(cameras, g_ranges, device=means.device)
+    overrides the cameras' extrinsics and is differentiable.  A prepared
+    ``views`` (``binding.Views``) may be passed instead of cameras and ranges.
+    With ``K_capacity`` given, nothing in the call waits for the device."""
+    if views is None:
+        if g_ranges is None:
+            g_ranges = [(0, int(means.shape[0]))] * len(cameras)
+        if viewmats is not None:
+            if tuple(viewmats.shape) != (len(cameras), 4, 4):
+                raise ValueError(f"viewmats must be [{len(cameras)}, 4, 4], got {tuple(viewmats.shape)}")
+            T = viewmats.detach().cpu().double().numpy()
+            cameras = [_posed(c, T[i]) for i, c in enumerate(cameras)]
+        views = B.Views(cameras, g_ranges, device=means.device)
+    elif viewmats is not None:
+        raise ValueError("pass viewmats with cameras, not with prepared views")
     rgb, _ = RasterizeGaussians.apply(means, quats, scales, opacities, colors, viewmats, views, eps2d, background,
                                       K_capacity)
     out = []
@@ -78,3 +84,28 @@ def render(means: torch.Tensor, quats: torch.Tensor, scales: torch.Tensor, opaci
         off, w, h, _ = views.image_slice(i)
         out.append(rgb[off:off + w * h].view(h, w, 3))
     return out
+
+
+class L2Loss(torch.autograd.Function):
+    """mean((rgb - target)^2) and its gradient in one kernel (gs_l2_loss)."""
+
+    @staticmethod
+    def forward(ctx, rgb, target):
+        rgb, target = rgb.contiguous(), target.contiguous()
+        loss = torch.zeros(1, dtype=rgb.dtype, device=rgb.device)
+        dL = torch.empty_like(rgb)
+        B.gs_l2_loss(rgb, target, 1.0 / max(rgb.numel(), 1), dL, loss)
+        ctx.save_for_backward(dL)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        (dL,) = ctx.saved_tensors
+        return dL * g, None
+
+
+def l2_loss(rgb: torch.Tensor, target: torch.Tensor) -> torch.Tensor:
+    """Mean squared error of an image against a target (no gradient to the target)."""
+    if rgb.shape != target.shape:
+        raise ValueError(f"shapes differ: {tuple(rgb.shape)} vs {tuple(target.shape)}")
+    return L2Loss.apply(rgb, target.detach())

@@ -60,8 +60,9 @@ class BatchRenderer:
         self.rgb, self.T_final = e(pix, 3), e(pix)
         self.last_idx = e(pix, dtype=torch.int32)
         self.targets = targets
-        self.loss_scale = 2.0 / (3 * (loss_pixels if loss_pixels is not None else max(pix, 1)))
+        self.inv_norm = 1.0 / (3 * (loss_pixels if loss_pixels is not None else max(pix, 1)))
         self.dL = e(pix, 3)
+        self.loss = e(1)
         nbw = B.gs_rasterize_bwd_workspace_size(self.cap, deterministic)
         self.bwd_ws = e(nbw, dtype=torch.uint8) if nbw else None
         self.g2, self.gc = e(max(P, 1), 2), e(max(P, 1), 3)
@@ -93,9 +94,10 @@ class BatchRenderer:
                            self.background, self.rgb, self.T_final, self.last_idx, None, self.config)
 
     def loss_grad(self):
-        """dL/dC of L = mean((C - target)^2) over every pixel of every view."""
-        torch.sub(self.rgb, self.targets, out=self.dL)
-        self.dL.mul_(self.loss_scale)
+        """L = mean((C - target)^2) over every pixel of every view (into
+        ``self.loss``, on the device) and dL/dC, in one kernel."""
+        self.loss.zero_()
+        B.gs_l2_loss(self.rgb, self.targets, self.inv_norm, self.dL, self.loss)
 
     def backward(self):
         v, p = self.views, self.p
@@ -181,8 +183,7 @@ class PerViewRenderer:
         for r in self.r:
             r.forward()
             # same loss as the batch: mean over every pixel of every view
-            torch.sub(r.rgb, r.targets, out=r.dL)
-            r.dL.mul_(2.0 / (3 * self.n_pix))
+            B.gs_l2_loss(r.rgb, r.targets, 1.0 / (3 * self.n_pix), r.dL, None)
             r.backward()
 
     def overflowed(self) -> bool:

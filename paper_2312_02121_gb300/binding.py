@@ -55,7 +55,13 @@ class GsRasterConfig(ctypes.Structure):
                 ("tile_order", ctypes.c_void_p), ("queue", ctypes.c_void_p)]
 
 
+class GsAdamConfig(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float * 5), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float)]
+
+
 assert ctypes.sizeof(GsCamera) == 80 and ctypes.sizeof(GsView) == 120 and ctypes.sizeof(GsRasterConfig) == 24
+assert ctypes.sizeof(GsAdamConfig) == 32
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -81,6 +87,11 @@ SIGNATURES = {
     "gs_rasterize_bwd": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P,
                                         _P, _P, _I32, _P, _SZ, _P, _P, _P, _P, _P, _P]),
     "gs_project_bwd": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _F, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gs_l2_loss": (ctypes.c_int, [_P, _P, _I64, _F, _P, _P, _P]),
+    "gs_l2_loss_f64": (ctypes.c_int, [_P, _P, _I64, _D, _P, _P, _P]),
+    "gs_adam_state_size": (_SZ, [_I64]),
+    "gs_adam_step": (ctypes.c_int, [_I64, _P, _P, _SZ] + [_P] * 14),
+    "gs_activate": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P]),
     "gs_project_f64": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
     "gs_rasterize_fwd_f64": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gs_rasterize_bwd_f64_workspace_size": (_SZ, [_I64, _I32]),
@@ -126,6 +137,8 @@ def _check(code: int):
 def _ptr(t: Optional[torch.Tensor]):
     if t is None:
         return None
+    if not t.is_cuda:
+        raise ValueError("gsplat103 takes device tensors only (got a host tensor)")
     if not t.is_contiguous():
         raise ValueError("gsplat103 needs contiguous tensors")
     return ctypes.c_void_p(t.data_ptr())
@@ -169,7 +182,9 @@ class Views:
         self.V, self.P, self.T, self.pixels = V, P.value, T.value, pix.value
         self.host = arr
         raw = bytes(ctypes.string_at(ctypes.addressof(arr), ctypes.sizeof(GsView) * max(V, 1)))
-        self.device = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
+        # an asynchronous copy on the current stream: the driver stages the (pageable) bytes
+        # before the call returns, and building views does not wait for work already queued
+        self.device = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device, non_blocking=True)
         self.cameras = list(cameras)
 
     def view(self, i: int) -> GsView:
@@ -302,3 +317,36 @@ def gs_project_bwd(views: Views, means, quats, scales, eps2d: float, touched, dL
 
 
 EXPORTED: List[str] = list(SIGNATURES)
+
+
+def gs_l2_loss(rgb, target, inv_norm: float, dL_drgb=None, loss=None, stream=None):
+    """fp32 or fp64 (gs_l2_loss_f64) by the dtype of ``rgb``; ``loss`` is accumulated."""
+    fn = load().gs_l2_loss_f64 if _f64(rgb) else load().gs_l2_loss
+    _check(fn(_ptr(rgb), _ptr(target), int(rgb.numel()), float(inv_norm), _ptr(dL_drgb), _ptr(loss),
+              _stream(stream)))
+
+
+def gs_adam_state_size(N: int) -> int:
+    return int(load().gs_adam_state_size(int(N)))
+
+
+def adam_config(lr: Sequence[float], beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> GsAdamConfig:
+    c = GsAdamConfig()
+    c.lr[:] = [float(x) for x in lr]
+    c.beta1, c.beta2, c.eps = float(beta1), float(beta2), float(eps)
+    return c
+
+
+def gs_adam_step(N: int, cfg: GsAdamConfig, state, means, quats, log_scales, opacity_logits, colors, dL_dmeans,
+                 dL_dquats, dL_dscales, dL_dopacities, dL_dcolors, scales, opacities, skip_if_set=None,
+                 stream=None):
+    nbytes = state.numel() * state.element_size()
+    _check(load().gs_adam_step(int(N), ctypes.byref(cfg), _ptr(state), nbytes, _ptr(means), _ptr(quats),
+                               _ptr(log_scales), _ptr(opacity_logits), _ptr(colors), _ptr(dL_dmeans),
+                               _ptr(dL_dquats), _ptr(dL_dscales), _ptr(dL_dopacities), _ptr(dL_dcolors),
+                               _ptr(scales), _ptr(opacities), _ptr(skip_if_set), _stream(stream)))
+
+
+def gs_activate(N: int, log_scales, opacity_logits, scales, opacities, stream=None):
+    _check(load().gs_activate(int(N), _ptr(log_scales), _ptr(opacity_logits), _ptr(scales), _ptr(opacities),
+                              _stream(stream)))

@@ -81,12 +81,12 @@ def _load():
                 "or_covariance3d": (None, [_P, _P, _P, _P, _P]),
                 "or_ewa_jacobian": (None, [_P, _P, _P]),
                 "or_ewa_jacobian_dt": (None, [_P, _P, _P]),
-                "or_pixel_trace": (_I64, [_I64, _P, _P, _P, _P, _P, _P, _P, _I32, _I32, _I32, _P, _P, _P, _P]),
+                "or_pixel_trace": (_I64, [_I64, _P, _P, _P, _P, _I32, _P, _P, _P, _I32, _I32, _I32, _P, _P, _P, _P]),
                 "or_world_to_pixel": (None, [_P, _P, _P, _P]),
                 "or_project": (None, [_P, _I64, _P, _P, _P, _D, _I32] + [_P] * 7),
-                "or_rasterize": (None, [_I64, _P, _P, _P, _P, _P, _P, _P, _I32, _I32, _I32, _P,
+                "or_rasterize": (None, [_I64, _P, _P, _P, _P, _I32, _P, _P, _P, _I32, _I32, _I32, _P,
                                         _I64, _P, _P, _P, _P, _P, _P]),
-                "or_rasterize_bwd": (None, [_I64, _P, _P, _P, _P, _P, _P, _P, _I32, _I32, _I32, _P,
+                "or_rasterize_bwd": (None, [_I64, _P, _P, _P, _P, _I32, _P, _P, _P, _I32, _I32, _I32, _P,
                                             _I64, _P, _P, _P, _P, _P, _P]),
                 "or_project_bwd": (None, [_P, _I64, _P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
                 "or_bin": (_I64, [_I64, _P, _P, _P, _I32, _I32, _P, _P]),
@@ -108,6 +108,14 @@ def _d(a, shape=None) -> np.ndarray:
     if shape is not None:
         a = a.reshape(shape)
     return a
+
+
+def _colors(colors, n: int) -> np.ndarray:
+    """[n, C] float64 colours (C = 3 when given as a flat array of 3n)."""
+    a = np.asarray(colors, dtype=np.float64)
+    if a.ndim == 1:
+        a = a.reshape(n, -1) if n else a.reshape(0, 3)
+    return np.ascontiguousarray(a.reshape(n, -1) if n else a)
 
 
 def _ptr(a: np.ndarray):
@@ -217,23 +225,26 @@ def rasterize(proj: dict, opacities, colors, width: int, height: int, background
     """Sec. 2.2, Eq. 7: front-to-back compositing over each pixel's tile list.
 
     ``proj`` needs means2d, conics, depths, rects, valid (oracle or any other
-    source).  ``pixels``: optional int64 array of linear pixel ids (y*W + x);
-    outputs then follow that order.  Returns rgb, T_final, last_id, n_contrib,
-    margin (smallest relative margin of any alpha / T threshold test)."""
+    source).  ``colors`` is [N, C] for any channel count C (default 3 when
+    given flat); ``background`` has C values.  ``pixels``: optional int64
+    array of linear pixel ids (y*W + x); outputs then follow that order.
+    Returns rgb [.., C], T_final, last_id, n_contrib, margin (smallest
+    relative margin of any alpha / T threshold test)."""
     m2, con, dep, rects, valid = _proj_arrays(proj)
     n = m2.shape[0]
-    op, col = _d(opacities, (n,)), _d(colors, (n, 3))
-    bg = None if background is None else _d(background, (3,))
+    op, col = _d(opacities, (n,)), _colors(colors, n)
+    nc = col.shape[1]
+    bg = None if background is None else _d(background, (nc,))
     pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int64)
     npix = width * height if pix is None else pix.shape[0]
-    out = dict(rgb=np.zeros((npix, 3)), T_final=np.zeros(npix), last_id=np.zeros(npix, np.int64),
+    out = dict(rgb=np.zeros((npix, nc)), T_final=np.zeros(npix), last_id=np.zeros(npix, np.int64),
                n_contrib=np.zeros(npix, np.int64), margin=np.zeros(npix))
-    _load().or_rasterize(n, _ptr(m2), _ptr(con), _ptr(op), _ptr(col), _ptr(dep), _ptr(rects), _ptr(valid),
+    _load().or_rasterize(n, _ptr(m2), _ptr(con), _ptr(op), _ptr(col), nc, _ptr(dep), _ptr(rects), _ptr(valid),
                          width, height, tile, _ptr(bg), npix, _ptr(pix),
                          _ptr(out["rgb"]), _ptr(out["T_final"]), _ptr(out["last_id"]), _ptr(out["n_contrib"]),
                          _ptr(out["margin"]))
     if pix is None:
-        out["rgb"] = out["rgb"].reshape(height, width, 3)
+        out["rgb"] = out["rgb"].reshape(height, width, nc)
         for k in ("T_final", "last_id", "n_contrib", "margin"):
             out[k] = out[k].reshape(height, width)
     return out
@@ -244,26 +255,28 @@ def pixel_trace(proj: dict, opacities, colors, px: int, py: int, tile: int = TIL
     product, before n) and the final transmittance."""
     m2, con, dep, rects, valid = _proj_arrays(proj)
     n = m2.shape[0]
-    op, col = _d(opacities, (n,)), _d(colors, (n, 3))
+    op, col = _d(opacities, (n,)), _colors(colors, n)
     ids, al, T, Tf = np.zeros(max(n, 1), np.int64), np.zeros(max(n, 1)), np.zeros(max(n, 1)), np.zeros(1)
-    c = _load().or_pixel_trace(n, _ptr(m2), _ptr(con), _ptr(op), _ptr(col), _ptr(dep), _ptr(rects), _ptr(valid),
-                               tile, px, py, _ptr(ids), _ptr(al), _ptr(T), _ptr(Tf))
+    c = _load().or_pixel_trace(n, _ptr(m2), _ptr(con), _ptr(op), _ptr(col), col.shape[1], _ptr(dep), _ptr(rects),
+                               _ptr(valid), tile, px, py, _ptr(ids), _ptr(al), _ptr(T), _ptr(Tf))
     return dict(ids=ids[:c], alpha=al[:c], T=T[:c], T_final=float(Tf[0]))
 
 
 def rasterize_bwd(proj: dict, opacities, colors, width: int, height: int, dL_drgb,
                   background=None, pixels=None, tile: int = TILE) -> dict:
-    """Sec. 3.1: dL/dmu', dL/dconic (packed, O13), dL/do, dL/dc from dL/dC."""
+    """Sec. 3.1: dL/dmu', dL/dconic (packed, O13), dL/do, dL/dc from dL/dC
+    (C channels, as in ``rasterize``)."""
     m2, con, dep, rects, valid = _proj_arrays(proj)
     n = m2.shape[0]
-    op, col = _d(opacities, (n,)), _d(colors, (n, 3))
-    bg = None if background is None else _d(background, (3,))
+    op, col = _d(opacities, (n,)), _colors(colors, n)
+    nc = col.shape[1]
+    bg = None if background is None else _d(background, (nc,))
     pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int64)
     npix = width * height if pix is None else pix.shape[0]
-    g = _d(dL_drgb, (npix, 3))
+    g = _d(dL_drgb, (npix, nc))
     out = dict(means2d=np.zeros((n, 2)), conics=np.zeros((n, 3)), opacities=np.zeros(n),
-               colors=np.zeros((n, 3)))
-    _load().or_rasterize_bwd(n, _ptr(m2), _ptr(con), _ptr(op), _ptr(col), _ptr(dep), _ptr(rects), _ptr(valid),
+               colors=np.zeros((n, nc)))
+    _load().or_rasterize_bwd(n, _ptr(m2), _ptr(con), _ptr(op), _ptr(col), nc, _ptr(dep), _ptr(rects), _ptr(valid),
                              width, height, tile, _ptr(bg), npix, _ptr(pix), _ptr(g),
                              _ptr(out["means2d"]), _ptr(out["conics"]), _ptr(out["opacities"]),
                              _ptr(out["colors"]))

@@ -343,12 +343,14 @@ typedef struct {
  * Fills out[] with the composited Gaussians (may be NULL), returns their count. */
 static int64_t composite_pixel(int px, int py, const int64_t* list, int64_t m,
                                const double* means2d, const double* conics, const double* opac,
-                               const double* colors, const double* bg,
+                               const double* colors, int nc, const double* bg,
                                double* rgb, double* T_final, int64_t* last_id, double* margin,
                                contrib* out)
 {
     const double x = px + 0.5, y = py + 0.5; /* Reading O2: pixel centres */
-    double T = 1.0, C[3] = {0, 0, 0}, mg = INFINITY;
+    double T = 1.0, mg = INFINITY;
+    if (rgb)
+        for (int k = 0; k < nc; ++k) rgb[k] = 0.0;
     int64_t last = -1, cnt = 0;
     for (int64_t i = 0; i < m; ++i) {
         const int64_t n = list[i];
@@ -364,7 +366,8 @@ static int64_t composite_pixel(int px, int py, const int64_t* list, int64_t m,
         const double Tn = T * (1.0 - alpha);
         mg = fmin(mg, fabs(Tn - OR_T_MIN) / OR_T_MIN);
         if (Tn < OR_T_MIN) break;
-        for (int k = 0; k < 3; ++k) C[k] += colors[3 * n + k] * alpha * T;
+        if (rgb)
+            for (int k = 0; k < nc; ++k) rgb[k] += colors[(int64_t)nc * n + k] * alpha * T;
         if (out) {
             out[cnt].id = n;
             out[cnt].alpha = alpha;
@@ -378,9 +381,8 @@ static int64_t composite_pixel(int px, int py, const int64_t* list, int64_t m,
         last = n;
         ++cnt;
     }
-    if (bg)
-        for (int k = 0; k < 3; ++k) C[k] += T * bg[k];
-    if (rgb) { rgb[0] = C[0]; rgb[1] = C[1]; rgb[2] = C[2]; }
+    if (bg && rgb)
+        for (int k = 0; k < nc; ++k) rgb[k] += T * bg[k];
     if (T_final) *T_final = T;
     if (last_id) *last_id = last;
     if (margin) *margin = mg;
@@ -433,7 +435,7 @@ static int64_t tile_list(const int64_t* order, int64_t m, const int32_t* rects, 
  * the running product) -- and the final transmittance.  Returns c.
  * Capacity of the output arrays: N. */
 int64_t or_pixel_trace(int64_t N, const double* means2d, const double* conics, const double* opac,
-                       const double* colors, const double* depths, const int32_t* rects,
+                       const double* colors, int32_t nc, const double* depths, const int32_t* rects,
                        const int32_t* valid, int32_t tile, int32_t px, int32_t py,
                        int64_t* ids, double* alpha, double* T, double* T_final)
 {
@@ -442,7 +444,7 @@ int64_t or_pixel_trace(int64_t N, const double* means2d, const double* conics, c
     contrib* cs = (contrib*)malloc(sizeof(contrib) * (N > 0 ? N : 1));
     const int64_t m = depth_order(N, depths, valid, order);
     const int64_t k = tile_list(order, m, rects, px / tile, py / tile, list);
-    const int64_t c = composite_pixel(px, py, list, k, means2d, conics, opac, colors, NULL,
+    const int64_t c = composite_pixel(px, py, list, k, means2d, conics, opac, colors, nc, NULL,
                                       NULL, T_final, NULL, NULL, cs);
     for (int64_t j = 0; j < c; ++j) { ids[j] = cs[j].id; alpha[j] = cs[j].alpha; T[j] = cs[j].T; }
     free(order); free(list); free(cs);
@@ -450,15 +452,16 @@ int64_t or_pixel_trace(int64_t N, const double* means2d, const double* conics, c
 }
 
 /*
- * Sec. 2.2, Eq. 7 (Readings O6, O7, O9, O12): front-to-back compositing.
+ * Sec. 2.2, Eq. 7 (Readings O6, O7, O9, O12): front-to-back compositing of
+ * nc channels (colors[N,nc]; Eq. 7 composites each channel alike).
  * Pixels rendered: pix[0..npix) (linear index y*W + x); pix == NULL means all
  * W*H pixels in order.  Outputs are indexed by position in that list:
- * rgb[npix,3], T_final[npix], last_id[npix] (index of the last composited
+ * rgb[npix,nc], T_final[npix], last_id[npix] (index of the last composited
  * Gaussian or -1), n_contrib[npix], margin[npix] (smallest relative margin
- * of any alpha/T threshold test met; +inf if none).  bg (3 values) may be NULL.
+ * of any alpha/T threshold test met; +inf if none).  bg (nc values) may be NULL.
  */
 void or_rasterize(int64_t N, const double* means2d, const double* conics, const double* opac,
-                  const double* colors, const double* depths, const int32_t* rects,
+                  const double* colors, int32_t nc, const double* depths, const int32_t* rects,
                   const int32_t* valid, int32_t W, int32_t H, int32_t tile, const double* bg,
                   int64_t npix, const int64_t* pix,
                   double* rgb, double* T_final, int64_t* last_id, int64_t* n_contrib, double* margin)
@@ -486,8 +489,8 @@ void or_rasterize(int64_t N, const double* means2d, const double* conics, const 
             const int64_t k = tile_list(order, m, rects, tx, ty, list);
             for (int64_t i = starts[g]; i < starts[g + 1]; ++i) {
                 const int64_t p = groups[i].pix, o = groups[i].pos;
-                const int64_t c = composite_pixel((int)(p % W), (int)(p / W), list, k, means2d, conics, opac, colors, bg,
-                                                  rgb ? rgb + 3 * o : NULL, T_final ? T_final + o : NULL,
+                const int64_t c = composite_pixel((int)(p % W), (int)(p / W), list, k, means2d, conics, opac, colors, nc,
+                                                  bg, rgb ? rgb + (int64_t)nc * o : NULL, T_final ? T_final + o : NULL,
                                                   last_id ? last_id + o : NULL, margin ? margin + o : NULL, NULL);
                 if (n_contrib) n_contrib[o] = c;
             }
@@ -499,7 +502,9 @@ void or_rasterize(int64_t N, const double* means2d, const double* conics, const 
 
 /*
  * Sec. 3.1: gradients of L w.r.t. the 2D parameters, given dL/dC for the
- * pixels pix[0..npix) (dL_drgb[npix,3], same order; pix == NULL = all).
+ * pixels pix[0..npix) (dL_drgb[npix,nc], same order; pix == NULL = all).
+ * Sec. 3.1 derives every term per channel k; dL/dalpha sums them over the nc
+ * channels.
  * Written as the plain definition: for each pixel the composited Gaussians,
  * their T_n as the running product of Eq. 7 and S_n = sum_{m>n} c_m alpha_m T_m
  * as an explicit suffix sum, then
@@ -508,10 +513,10 @@ void or_rasterize(int64_t N, const double* means2d, const double* conics, const 
  *   dalpha/do      = exp(-sigma),   dalpha/dsigma = -o exp(-sigma)   (0 if clamped)
  *   dsigma/dmu'    = Y Delta,       dsigma/dY = Delta Delta^T / 2   (packed: O13)
  * Outputs (accumulated, caller zeroes): dL_dmeans2d[N,2], dL_dconics[N,3],
- * dL_dopac[N], dL_dcolors[N,3].
+ * dL_dopac[N], dL_dcolors[N,nc].
  */
 void or_rasterize_bwd(int64_t N, const double* means2d, const double* conics, const double* opac,
-                      const double* colors, const double* depths, const int32_t* rects,
+                      const double* colors, int32_t nc, const double* depths, const int32_t* rects,
                       const int32_t* valid, int32_t W, int32_t H, int32_t tile, const double* bg,
                       int64_t npix, const int64_t* pix, const double* dL_drgb,
                       double* dL_dmeans2d, double* dL_dconics, double* dL_dopac, double* dL_dcolors)
@@ -530,18 +535,20 @@ void or_rasterize_bwd(int64_t N, const double* means2d, const double* conics, co
     int64_t* starts = (int64_t*)malloc(sizeof(int64_t) * (npix + 1));
     const int64_t ng = group_by_tile(npix, pix, W, tile, TX, groups, starts);
     const int nth = or_num_threads();
-    /* one private accumulator per thread, summed in thread order at the end */
-    double* acc = (double*)calloc((size_t)nth * (N > 0 ? N : 1) * 9, sizeof(double));
+    /* one private accumulator per thread (6 geometry terms + nc colours per
+     * Gaussian), summed in thread order at the end */
+    const int64_t R = 6 + nc;
+    double* acc = (double*)calloc((size_t)nth * (N > 0 ? N : 1) * R, sizeof(double));
 #pragma omp parallel
     {
         int tid = 0;
 #ifdef _OPENMP
         tid = omp_get_thread_num();
 #endif
-        double* my = acc + (size_t)tid * (N > 0 ? N : 1) * 9;
+        double* my = acc + (size_t)tid * (N > 0 ? N : 1) * R;
         int64_t* list = (int64_t*)malloc(sizeof(int64_t) * (m > 0 ? m : 1));
         contrib* cs = (contrib*)malloc(sizeof(contrib) * (m > 0 ? m : 1));
-        double* S = (double*)malloc(sizeof(double) * 3 * (m + 1));
+        double* S = (double*)malloc(sizeof(double) * nc * (m + 1));
 #pragma omp for schedule(dynamic, 1)
         for (int64_t gi = 0; gi < ng; ++gi) {
             const int64_t tl = groups[starts[gi]].tile;
@@ -550,49 +557,49 @@ void or_rasterize_bwd(int64_t N, const double* means2d, const double* conics, co
                 const int64_t p = groups[pi].pix, i = groups[pi].pos;
                 const int px = (int)(p % W), py = (int)(p / W);
                 double Tf;
-                const int64_t c = composite_pixel(px, py, list, k, means2d, conics, opac, colors, bg,
+                const int64_t c = composite_pixel(px, py, list, k, means2d, conics, opac, colors, nc, bg,
                                                   NULL, &Tf, NULL, NULL, cs);
-                const double* G = dL_drgb + 3 * i;
+                const double* G = dL_drgb + (int64_t)nc * i;
                 /* S_n as explicit suffix sums */
-                S[3 * c + 0] = S[3 * c + 1] = S[3 * c + 2] = 0.0;
+                for (int q = 0; q < nc; ++q) S[(int64_t)nc * c + q] = 0.0;
                 for (int64_t j = c - 1; j >= 0; --j)
-                    for (int q = 0; q < 3; ++q)
-                        S[3 * j + q] = S[3 * (j + 1) + q] + colors[3 * cs[j].id + q] * cs[j].alpha * cs[j].T;
+                    for (int q = 0; q < nc; ++q)
+                        S[nc * j + q] = S[nc * (j + 1) + q] + colors[(int64_t)nc * cs[j].id + q] * cs[j].alpha * cs[j].T;
                 for (int64_t j = 0; j < c; ++j) {
                     const contrib* e = cs + j;
                     const int64_t n = e->id;
                     double dL_dalpha = 0.0;
-                    for (int q = 0; q < 3; ++q) {
-                        double dC_dalpha = colors[3 * n + q] * e->T - S[3 * (j + 1) + q] / (1.0 - e->alpha);
+                    for (int q = 0; q < nc; ++q) {
+                        double dC_dalpha = colors[(int64_t)nc * n + q] * e->T - S[nc * (j + 1) + q] / (1.0 - e->alpha);
                         if (bg) dC_dalpha -= bg[q] * Tf / (1.0 - e->alpha);
                         dL_dalpha += G[q] * dC_dalpha;
-                        my[9 * n + 6 + q] += G[q] * e->alpha * e->T;
+                        my[R * n + 6 + q] += G[q] * e->alpha * e->T;
                     }
                     if (e->clamped) continue;
                     const double dL_do = e->g * dL_dalpha;
                     const double dL_dsigma = -opac[n] * e->g * dL_dalpha;
                     const double* Y = conics + 3 * n;
-                    my[9 * n + 0] += dL_dsigma * (Y[0] * e->dx + Y[1] * e->dy);
-                    my[9 * n + 1] += dL_dsigma * (Y[1] * e->dx + Y[2] * e->dy);
-                    my[9 * n + 2] += dL_dsigma * 0.5 * e->dx * e->dx;
-                    my[9 * n + 3] += dL_dsigma * e->dx * e->dy;
-                    my[9 * n + 4] += dL_dsigma * 0.5 * e->dy * e->dy;
-                    my[9 * n + 5] += dL_do;
+                    my[R * n + 0] += dL_dsigma * (Y[0] * e->dx + Y[1] * e->dy);
+                    my[R * n + 1] += dL_dsigma * (Y[1] * e->dx + Y[2] * e->dy);
+                    my[R * n + 2] += dL_dsigma * 0.5 * e->dx * e->dx;
+                    my[R * n + 3] += dL_dsigma * e->dx * e->dy;
+                    my[R * n + 4] += dL_dsigma * 0.5 * e->dy * e->dy;
+                    my[R * n + 5] += dL_do;
                 }
             }
         }
         free(list); free(cs); free(S);
     }
     for (int t = 0; t < nth; ++t) {
-        const double* my = acc + (size_t)t * (N > 0 ? N : 1) * 9;
+        const double* my = acc + (size_t)t * (N > 0 ? N : 1) * R;
         for (int64_t n = 0; n < N; ++n) {
-            dL_dmeans2d[2 * n + 0] += my[9 * n + 0];
-            dL_dmeans2d[2 * n + 1] += my[9 * n + 1];
-            dL_dconics[3 * n + 0] += my[9 * n + 2];
-            dL_dconics[3 * n + 1] += my[9 * n + 3];
-            dL_dconics[3 * n + 2] += my[9 * n + 4];
-            dL_dopac[n] += my[9 * n + 5];
-            for (int q = 0; q < 3; ++q) dL_dcolors[3 * n + q] += my[9 * n + 6 + q];
+            dL_dmeans2d[2 * n + 0] += my[R * n + 0];
+            dL_dmeans2d[2 * n + 1] += my[R * n + 1];
+            dL_dconics[3 * n + 0] += my[R * n + 2];
+            dL_dconics[3 * n + 1] += my[R * n + 3];
+            dL_dconics[3 * n + 2] += my[R * n + 4];
+            dL_dopac[n] += my[R * n + 5];
+            for (int q = 0; q < nc; ++q) dL_dcolors[(int64_t)nc * n + q] += my[R * n + 6 + q];
         }
     }
     free(acc); free(order); free(groups); free(starts); free(all);

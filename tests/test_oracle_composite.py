@@ -209,3 +209,72 @@ def test_binning_matches_python_enumeration():
     for t in range(TX * TY):
         s, e = ranges[t]
         assert all(pairs[i][0] == t for i in range(s, e))
+
+
+# -- any channel count (Sec. 3.1 derives every term per channel) --------------
+
+def _multichannel_case(C, seed=3):
+    w = wl.small_case(seed, 300, 48, 40, log_scale_mu=-2.5)
+    cam, sc = w.views[0].camera, w.scenes[0]
+    proj = oracle.project(cam, sc.means, sc.quats, sc.scales, w.eps2d)
+    col = np.random.default_rng(seed).uniform(size=(sc.n, C))
+    return cam, sc, proj, col
+
+
+def test_channels_are_composited_independently():
+    cam, sc, proj, col = _multichannel_case(5)
+    W, H = cam.width, cam.height
+    bg = np.array([0.1, 0.2, 0.3, 0.4, 0.5])
+    full = oracle.rasterize(proj, sc.opacities, col, W, H, background=bg)
+    a = oracle.rasterize(proj, sc.opacities, col[:, :3], W, H, background=bg[:3])
+    b = oracle.rasterize(proj, sc.opacities, col[:, 3:], W, H, background=bg[3:])
+    assert full["rgb"].shape == (H, W, 5)
+    np.testing.assert_array_equal(full["rgb"], np.concatenate([a["rgb"], b["rgb"]], axis=-1))
+    np.testing.assert_array_equal(full["T_final"], a["T_final"])
+    np.testing.assert_array_equal(full["last_id"], b["last_id"])
+
+
+def test_single_unit_channel_is_the_alpha_mask():
+    cam, sc, proj, _ = _multichannel_case(1)
+    out = oracle.rasterize(proj, sc.opacities, np.ones((sc.n, 1)), cam.width, cam.height)
+    np.testing.assert_allclose(out["rgb"][..., 0], 1.0 - out["T_final"], atol=1e-15)
+
+
+def test_multichannel_gradients_are_linear_in_the_channels():
+    cam, sc, proj, col = _multichannel_case(5, seed=4)
+    W, H = cam.width, cam.height
+    G = np.random.default_rng(9).standard_normal((H * W, 5))
+    bg = np.array([0.3, 0.1, 0.7, 0.2, 0.9])
+    full = oracle.rasterize_bwd(proj, sc.opacities, col, W, H, G, background=bg)
+    parts = [oracle.rasterize_bwd(proj, sc.opacities, col[:, s], W, H, G[:, s], background=bg[s])
+             for s in (slice(0, 2), slice(2, 5))]
+    for k in ("means2d", "conics", "opacities"):
+        np.testing.assert_allclose(full[k], parts[0][k] + parts[1][k], rtol=1e-12, atol=1e-15)
+    # (threads sum their tiles in a scheduling-dependent order: equal to rounding, not bit for bit)
+    np.testing.assert_allclose(full["colors"], np.concatenate([parts[0]["colors"], parts[1]["colors"]], 1),
+                               rtol=1e-12, atol=1e-15)
+
+
+def test_multichannel_gradients_match_finite_differences():
+    cam, sc, proj, col = _multichannel_case(2, seed=5)
+    W, H = cam.width, cam.height
+    G = np.random.default_rng(10).standard_normal((H * W, 2))
+    g = oracle.rasterize_bwd(proj, sc.opacities, col, W, H, G)
+    out = oracle.rasterize(proj, sc.opacities, col, W, H)
+    assert out["margin"].min() > 1e-6
+    hit = np.nonzero(g["opacities"])[0][:4]
+    h = 1e-7
+    for n in hit:
+        for j in range(2):
+            cp, cm = col.copy(), col.copy()
+            cp[n, j] += h
+            cm[n, j] -= h
+            fd = (np.sum(G * oracle.rasterize(proj, sc.opacities, cp, W, H)["rgb"].reshape(-1, 2)) -
+                  np.sum(G * oracle.rasterize(proj, sc.opacities, cm, W, H)["rgb"].reshape(-1, 2))) / (2 * h)
+            assert g["colors"][n, j] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+        op_p, op_m = np.array(sc.opacities, np.float64), np.array(sc.opacities, np.float64)
+        op_p[n] += h
+        op_m[n] -= h
+        fd = (np.sum(G * oracle.rasterize(proj, op_p, col, W, H)["rgb"].reshape(-1, 2)) -
+              np.sum(G * oracle.rasterize(proj, op_m, col, W, H)["rgb"].reshape(-1, 2))) / (2 * h)
+        assert g["opacities"][n] == pytest.approx(fd, rel=1e-5, abs=1e-9)

@@ -313,6 +313,32 @@ int gs_project_bwd(const GsView* views, int32_t V, int64_t P, const float* means
                    float* dL_dviewmats, void* stream);
 
 /*
+ * Sec. 2.2 (Eq. 7) and Sec. 3.1 for C channels per Gaussian (features, depth
+ * as a channel, ...): Eq. 7 composites every channel with the same alpha and
+ * T, and Sec. 3.1 derives every gradient term per channel, with dL/dalpha
+ * summed over the channels.  Arguments are those of gs_rasterize_fwd /
+ * gs_rasterize_bwd (fast mode) with colors[N,C], background[C] (nullable),
+ * out[pixels,C], dL_dout[pixels,C] and dL_dcolors[N,C]; T_final, last_idx and
+ * n_contrib as there.  C == 3 runs the 3-channel kernels.  Other C are
+ * composited in chunks of up to 32 channels, one launch per chunk and pass
+ * (each chunk rebuilds the same alpha and T); the backward adds every chunk's
+ * share with atomics, so its fp32 sums vary in the last bits run to run (there
+ * is no deterministic mode for C != 3).  Outputs of the backward are
+ * ACCUMULATED (the caller zeroes them).
+ */
+int gs_rasterize_fwd_nc(const GsView* views, int32_t V, int32_t T_total, int32_t C, const float* means2d,
+                        const float* conics, const float* opacities, const float* colors, const int32_t* isect_ids,
+                        const int32_t* tile_ranges, const float* background, float* out, float* T_final,
+                        int32_t* last_idx, int32_t* n_contrib, const GsRasterConfig* config, void* stream);
+
+int gs_rasterize_bwd_nc(const GsView* views, int32_t V, int64_t P, int32_t T_total, int32_t C,
+                        const float* means2d, const float* conics, const float* opacities, const float* colors,
+                        const int32_t* isect_ids, const int32_t* tile_ranges, const float* background,
+                        const float* T_final, const int32_t* last_idx, const float* dL_dout, float* dL_dmeans2d,
+                        float* dL_dconics, float* dL_dopacities, float* dL_dcolors, const GsRasterConfig* config,
+                        void* stream);
+
+/*
  * Training-step helpers (the paper has no counterpart: it derives gradients
  * only).  They let a whole optimisation step -- forward, loss, backward,
  * update -- run on the GPU and be captured into one CUDA graph.
@@ -339,14 +365,15 @@ typedef struct GsAdamConfig {
     float beta1, beta2, eps;
 } GsAdamConfig;
 
-/* Bytes of optimiser state for N Gaussians (a 256-byte header holding the step
- * count, then the first and second moments, 14 floats per Gaussian each). */
-size_t gs_adam_state_size(int64_t N);
+/* Bytes of optimiser state for N Gaussians of C colour channels (a 256-byte
+ * header holding the step count, then the first and second moments, 11 + C
+ * floats per Gaussian each). */
+size_t gs_adam_state_size(int64_t N, int32_t C);
 
 /*
  * One Adam step (Kingma & Ba, bias-corrected) on the raw parameters of N
  * Gaussians, in place: means[N,3], quats[N,4] (raw; the renderer normalises
- * them), log_scales[N,3], opacity_logits[N], colors[N,3].  The gradients are
+ * them), log_scales[N,3], opacity_logits[N], colors[N,C].  The gradients are
  * those of the projection and compositing backward, i.e. with respect to the
  * ACTIVATED values scale = exp(log-scale) and opacity = sigmoid(logit); the
  * step chains them through the activations using scales[N,3] and
@@ -359,7 +386,8 @@ size_t gs_adam_state_size(int64_t N);
  * an intersection overflow made the gradients incomplete -- the step changes
  * nothing, not even the step count.  Two kernels are enqueued.
  */
-int gs_adam_step(int64_t N, const GsAdamConfig* cfg, void* state, size_t state_bytes, float* means, float* quats,
+int gs_adam_step(int64_t N, int32_t C, const GsAdamConfig* cfg, void* state, size_t state_bytes, float* means,
+                 float* quats,
                  float* log_scales, float* opacity_logits, float* colors, const float* dL_dmeans,
                  const float* dL_dquats, const float* dL_dscales, const float* dL_dopacities,
                  const float* dL_dcolors, float* scales, float* opacities, const int32_t* skip_if_set,

@@ -44,6 +44,9 @@ class BatchRenderer:
         self.background = background
         dev = params.means.device
         P, T, pix, N = views.P, views.T, views.pixels, params.n
+        C = self.C = params.channels
+        if deterministic and C != 3:
+            raise ValueError("the deterministic backward composites 3 channels")
         e = lambda *shape, dtype=torch.float32: torch.empty(*shape, dtype=dtype, device=dev)
         self.means2d, self.conics, self.depths = e(max(P, 1), 2), e(max(P, 1), 3), e(max(P, 1))
         self.rects = e(max(P, 1), 4, dtype=torch.int16)
@@ -57,18 +60,18 @@ class BatchRenderer:
         self.flags = torch.zeros(1, dtype=torch.int32, device=dev)
         self.order_ws = e(max(B.gs_tile_order_workspace_size(T), 1), dtype=torch.uint8)
         self.tile_order = e(T, dtype=torch.int32)
-        self.rgb, self.T_final = e(pix, 3), e(pix)
+        self.rgb, self.T_final = e(pix, C), e(pix)
         self.last_idx = e(pix, dtype=torch.int32)
         self.targets = targets
-        self.inv_norm = 1.0 / (3 * (loss_pixels if loss_pixels is not None else max(pix, 1)))
-        self.dL = e(pix, 3)
+        self.inv_norm = 1.0 / (C * (loss_pixels if loss_pixels is not None else max(pix, 1)))
+        self.dL = e(pix, C)
         self.loss = e(1)
         nbw = B.gs_rasterize_bwd_workspace_size(self.cap, deterministic)
         self.bwd_ws = e(nbw, dtype=torch.uint8) if nbw else None
         self.g2, self.gc = e(max(P, 1), 2), e(max(P, 1), 3)
         self.owns_grads = shared_grads is None
         if self.owns_grads:
-            self.g_op, self.g_col = e(max(N, 1)), e(max(N, 1), 3)
+            self.g_op, self.g_col = e(max(N, 1)), e(max(N, 1), C)
             self.g_means, self.g_quats, self.g_scales = e(max(N, 1), 3), e(max(N, 1), 4), e(max(N, 1), 3)
         else:
             sg = shared_grads
@@ -90,8 +93,13 @@ class BatchRenderer:
                           self.flags)
         if self.longest_first:
             B.gs_tile_order(self.tile_ranges, v.T, self.order_ws, self.tile_order)
-        B.gs_rasterize_fwd(v, self.means2d, self.conics, p.opacities, p.colors, self.isect_ids, self.tile_ranges,
-                           self.background, self.rgb, self.T_final, self.last_idx, None, self.config)
+        if self.C == 3:
+            B.gs_rasterize_fwd(v, self.means2d, self.conics, p.opacities, p.colors, self.isect_ids, self.tile_ranges,
+                               self.background, self.rgb, self.T_final, self.last_idx, None, self.config)
+        else:
+            B.gs_rasterize_fwd_nc(v, self.C, self.means2d, self.conics, p.opacities, p.colors, self.isect_ids,
+                                  self.tile_ranges, self.background, self.rgb, self.T_final, self.last_idx, None,
+                                  self.config)
 
     def loss_grad(self):
         """L = mean((C - target)^2) over every pixel of every view (into
@@ -106,10 +114,15 @@ class BatchRenderer:
         if self.owns_grads:
             for t in (self.g_op, self.g_col, self.g_means, self.g_quats, self.g_scales):
                 t.zero_()
-        B.gs_rasterize_bwd(v, self.means2d, self.conics, p.opacities, p.colors, self.isect_ids, self.isect_pos,
-                           self.emit_start, self.touched, self.tile_ranges, self.K, self.cap, self.background,
-                           self.T_final, self.last_idx, self.dL, self.deterministic, self.bwd_ws, self.g2, self.gc,
-                           self.g_op, self.g_col, self.config)
+        if self.C == 3:
+            B.gs_rasterize_bwd(v, self.means2d, self.conics, p.opacities, p.colors, self.isect_ids, self.isect_pos,
+                               self.emit_start, self.touched, self.tile_ranges, self.K, self.cap, self.background,
+                               self.T_final, self.last_idx, self.dL, self.deterministic, self.bwd_ws, self.g2,
+                               self.gc, self.g_op, self.g_col, self.config)
+        else:
+            B.gs_rasterize_bwd_nc(v, self.C, self.means2d, self.conics, p.opacities, p.colors, self.isect_ids,
+                                  self.tile_ranges, self.background, self.T_final, self.last_idx, self.dL, self.g2,
+                                  self.gc, self.g_op, self.g_col, self.config)
         B.gs_project_bwd(v, p.means, p.quats, p.scales, self.eps2d, self.touched, self.g2, self.gc, self.g_means,
                          self.g_quats, self.g_scales)
 
@@ -149,7 +162,7 @@ class BatchRenderer:
 
     def image(self, i: int) -> torch.Tensor:
         off, w, h, _ = self.views.image_slice(i)
-        return self.rgb[off:off + w * h].view(h, w, 3)
+        return self.rgb[off:off + w * h].view(h, w, -1)
 
 
 class PerViewRenderer:
@@ -162,9 +175,10 @@ class PerViewRenderer:
         """``targets``: the packed [pixels, 3] targets of all views, in view order."""
         dev = params.means.device
         N = max(params.n, 1)
+        self.C = params.channels
         self.shared = dict(means=torch.empty(N, 3, device=dev), quats=torch.empty(N, 4, device=dev),
                            scales=torch.empty(N, 3, device=dev), opacities=torch.empty(N, device=dev),
-                           colors=torch.empty(N, 3, device=dev))
+                           colors=torch.empty(N, self.C, device=dev))
         self.n = params.n
         self.r: List[BatchRenderer] = []
         off = 0
@@ -183,7 +197,7 @@ class PerViewRenderer:
         for r in self.r:
             r.forward()
             # same loss as the batch: mean over every pixel of every view
-            B.gs_l2_loss(r.rgb, r.targets, 1.0 / (3 * self.n_pix), r.dL, None)
+            B.gs_l2_loss(r.rgb, r.targets, 1.0 / (self.C * self.n_pix), r.dL, None)
             r.backward()
 
     def overflowed(self) -> bool:

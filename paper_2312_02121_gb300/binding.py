@@ -87,10 +87,14 @@ SIGNATURES = {
     "gs_rasterize_bwd": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P,
                                         _P, _P, _I32, _P, _SZ, _P, _P, _P, _P, _P, _P]),
     "gs_project_bwd": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _F, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gs_rasterize_fwd_nc": (ctypes.c_int, [_P, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                           _P]),
+    "gs_rasterize_bwd_nc": (ctypes.c_int, [_P, _I32, _I64, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                           _P, _P, _P, _P, _P]),
     "gs_l2_loss": (ctypes.c_int, [_P, _P, _I64, _F, _P, _P, _P]),
     "gs_l2_loss_f64": (ctypes.c_int, [_P, _P, _I64, _D, _P, _P, _P]),
-    "gs_adam_state_size": (_SZ, [_I64]),
-    "gs_adam_step": (ctypes.c_int, [_I64, _P, _P, _SZ] + [_P] * 14),
+    "gs_adam_state_size": (_SZ, [_I64, _I32]),
+    "gs_adam_step": (ctypes.c_int, [_I64, _I32, _P, _P, _SZ] + [_P] * 14),
     "gs_activate": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P]),
     "gs_project_f64": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
     "gs_rasterize_fwd_f64": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -326,8 +330,8 @@ def gs_l2_loss(rgb, target, inv_norm: float, dL_drgb=None, loss=None, stream=Non
               _stream(stream)))
 
 
-def gs_adam_state_size(N: int) -> int:
-    return int(load().gs_adam_state_size(int(N)))
+def gs_adam_state_size(N: int, C: int = 3) -> int:
+    return int(load().gs_adam_state_size(int(N), int(C)))
 
 
 def adam_config(lr: Sequence[float], beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> GsAdamConfig:
@@ -341,7 +345,8 @@ def gs_adam_step(N: int, cfg: GsAdamConfig, state, means, quats, log_scales, opa
                  dL_dquats, dL_dscales, dL_dopacities, dL_dcolors, scales, opacities, skip_if_set=None,
                  stream=None):
     nbytes = state.numel() * state.element_size()
-    _check(load().gs_adam_step(int(N), ctypes.byref(cfg), _ptr(state), nbytes, _ptr(means), _ptr(quats),
+    C = int(colors.shape[1]) if colors.dim() == 2 else 3
+    _check(load().gs_adam_step(int(N), C, ctypes.byref(cfg), _ptr(state), nbytes, _ptr(means), _ptr(quats),
                                _ptr(log_scales), _ptr(opacity_logits), _ptr(colors), _ptr(dL_dmeans),
                                _ptr(dL_dquats), _ptr(dL_dscales), _ptr(dL_dopacities), _ptr(dL_dcolors),
                                _ptr(scales), _ptr(opacities), _ptr(skip_if_set), _stream(stream)))
@@ -350,3 +355,22 @@ def gs_adam_step(N: int, cfg: GsAdamConfig, state, means, quats, log_scales, opa
 def gs_activate(N: int, log_scales, opacity_logits, scales, opacities, stream=None):
     _check(load().gs_activate(int(N), _ptr(log_scales), _ptr(opacity_logits), _ptr(scales), _ptr(opacities),
                               _stream(stream)))
+
+
+def gs_rasterize_fwd_nc(views: Views, C: int, means2d, conics, opacities, colors, isect_ids, tile_ranges,
+                        background, out, T_final, last_idx, n_contrib=None, config: Optional[RasterConfig] = None,
+                        stream=None):
+    _check(load().gs_rasterize_fwd_nc(_ptr(views.device), views.V, views.T, int(C), _ptr(means2d), _ptr(conics),
+                                      _ptr(opacities), _ptr(colors), _ptr(isect_ids), _ptr(tile_ranges),
+                                      _ptr(background), _ptr(out), _ptr(T_final), _ptr(last_idx), _ptr(n_contrib),
+                                      _cfg(config), _stream(stream)))
+
+
+def gs_rasterize_bwd_nc(views: Views, C: int, means2d, conics, opacities, colors, isect_ids, tile_ranges,
+                        background, T_final, last_idx, dL_dout, dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors,
+                        config: Optional[RasterConfig] = None, stream=None):
+    _check(load().gs_rasterize_bwd_nc(_ptr(views.device), views.V, views.P, views.T, int(C), _ptr(means2d),
+                                      _ptr(conics), _ptr(opacities), _ptr(colors), _ptr(isect_ids),
+                                      _ptr(tile_ranges), _ptr(background), _ptr(T_final), _ptr(last_idx),
+                                      _ptr(dL_dout), _ptr(dL_dmeans2d), _ptr(dL_dconics), _ptr(dL_dopacities),
+                                      _ptr(dL_dcolors), _cfg(config), _stream(stream)))

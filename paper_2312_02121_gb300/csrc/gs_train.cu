@@ -86,13 +86,13 @@ static int l2_loss_impl(const char* who, const S* rgb, const S* target, int64_t 
 // ---------------------------------------------------------------------------
 
 // State header (first 256 bytes): the step count and the bias corrections of
-// the current step; then m and v, 14 floats per Gaussian each, field after
-// field (means 3, quats 4, log-scales 3, logits 1, colors 3).
+// the current step; then m and v, 11 + C floats per Gaussian each, field after
+// field (means 3, quats 4, log-scales 3, logits 1, colors C).
 struct AdamHeader {
     int32_t step;
     float bc1, bc2;  // 1 - beta1^t, 1 - beta2^t
 };
-constexpr int kAdamWidth = 14;
+constexpr int kAdamGeom = 11;  // means 3, quats 4, log-scales 3, logit 1
 
 __global__ void k_adam_prepare(AdamHeader* h, float beta1, float beta2, const int32_t* __restrict__ skip)
 {
@@ -117,9 +117,9 @@ __device__ __forceinline__ float adam_one(float& p, float g, float& m, float& v,
     return p;
 }
 
-// One thread per Gaussian: its 14 values, moments and activations.
+// One thread per Gaussian: its 11 + C values, moments and activations.
 __global__ void __launch_bounds__(256)
-k_adam_step(int64_t N, AdamArgs a, const AdamHeader* __restrict__ h, float* __restrict__ m, float* __restrict__ v,
+k_adam_step(int64_t N, int C, AdamArgs a, const AdamHeader* __restrict__ h, float* __restrict__ m, float* __restrict__ v,
             float* __restrict__ means, float* __restrict__ quats, float* __restrict__ log_scales,
             float* __restrict__ logits, float* __restrict__ colors, const float* __restrict__ g_means,
             const float* __restrict__ g_quats, const float* __restrict__ g_scales, const float* __restrict__ g_op,
@@ -160,9 +160,10 @@ k_adam_step(int64_t N, AdamArgs a, const AdamHeader* __restrict__ h, float* __re
         const float lg = adam_one(logits[n], g_op[n] * o * (1.f - o), m_op[n], v_op[n], a.lr[3], a, bc1, bc2);
         opacities[n] = 1.f / (1.f + expf(-lg));
     }
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-        adam_one(colors[3 * n + j], g_colors[3 * n + j], m_col[3 * n + j], v_col[3 * n + j], a.lr[4], a, bc1, bc2);
+    for (int j = 0; j < C; ++j) {
+        const int64_t i = (int64_t)C * n + j;
+        adam_one(colors[i], g_colors[i], m_col[i], v_col[i], a.lr[4], a, bc1, bc2);
+    }
 }
 
 __global__ void __launch_bounds__(256)
@@ -192,21 +193,23 @@ extern "C" int gs_l2_loss_f64(const double* rgb, const double* target, int64_t n
     return l2_loss_impl<double>("gs_l2_loss_f64", rgb, target, n, inv_norm, dL_drgb, loss, stream);
 }
 
-extern "C" size_t gs_adam_state_size(int64_t N)
+extern "C" size_t gs_adam_state_size(int64_t N, int32_t C)
 {
-    return N < 0 ? 0 : 256 + align256(sizeof(float) * kAdamWidth * (size_t)N) * 2;
+    return N < 0 || C < 1 ? 0 : 256 + align256(sizeof(float) * (kAdamGeom + C) * (size_t)N) * 2;
 }
 
-extern "C" int gs_adam_step(int64_t N, const GsAdamConfig* cfg, void* state, size_t state_bytes, float* means,
+extern "C" int gs_adam_step(int64_t N, int32_t C, const GsAdamConfig* cfg, void* state, size_t state_bytes, float* means,
                             float* quats, float* log_scales, float* opacity_logits, float* colors,
                             const float* dL_dmeans, const float* dL_dquats, const float* dL_dscales,
                             const float* dL_dopacities, const float* dL_dcolors, float* scales, float* opacities,
                             const int32_t* skip_if_set, void* stream)
 {
     const char* who = "gs_adam_step";
-    if (N < 0 || !cfg) return fail(GS_ERR_INVALID_ARG, "%s: N=%lld or null config", who, (long long)N);
-    if (!state || state_bytes < gs_adam_state_size(N))
-        return fail(GS_ERR_INVALID_ARG, "%s: state needs %zu bytes, got %zu", who, gs_adam_state_size(N), state_bytes);
+    if (N < 0 || C < 1 || !cfg)
+        return fail(GS_ERR_INVALID_ARG, "%s: N=%lld, C=%d or null config", who, (long long)N, C);
+    if (!state || state_bytes < gs_adam_state_size(N, C))
+        return fail(GS_ERR_INVALID_ARG, "%s: state needs %zu bytes, got %zu", who, gs_adam_state_size(N, C),
+                    state_bytes);
     if (N > 0 && (!means || !quats || !log_scales || !opacity_logits || !colors || !dL_dmeans || !dL_dquats ||
                   !dL_dscales || !dL_dopacities || !dL_dcolors || !scales || !opacities))
         return fail(GS_ERR_INVALID_ARG, "%s: null pointer argument", who);
@@ -215,7 +218,8 @@ extern "C" int gs_adam_step(int64_t N, const GsAdamConfig* cfg, void* state, siz
     cudaStream_t s = as_stream(stream);
     AdamHeader* h = reinterpret_cast<AdamHeader*>(state);
     float* m = reinterpret_cast<float*>(static_cast<char*>(state) + 256);
-    float* v = reinterpret_cast<float*>(static_cast<char*>(state) + 256 + align256(sizeof(float) * kAdamWidth * (size_t)N));
+    float* v = reinterpret_cast<float*>(static_cast<char*>(state) + 256 +
+                                        align256(sizeof(float) * (kAdamGeom + C) * (size_t)N));
     k_adam_prepare<<<1, 1, 0, s>>>(h, cfg->beta1, cfg->beta2, skip_if_set);
     AdamArgs a;
     for (int i = 0; i < 5; ++i) a.lr[i] = cfg->lr[i];
@@ -224,7 +228,7 @@ extern "C" int gs_adam_step(int64_t N, const GsAdamConfig* cfg, void* state, siz
     a.eps = cfg->eps;
     int launched = 1;
     if (N > 0) {
-        k_adam_step<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, a, h, m, v, means, quats, log_scales,
+        k_adam_step<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, C, a, h, m, v, means, quats, log_scales,
                                                                 opacity_logits, colors, dL_dmeans, dL_dquats,
                                                                 dL_dscales, dL_dopacities, dL_dcolors, scales,
                                                                 opacities, skip_if_set);

@@ -19,7 +19,8 @@ from . import binding as B
 @dataclasses.dataclass
 class Params:
     """Gaussian parameters on the device, fp32 contiguous: means [N,3],
-    quats [N,4] (w,x,y,z), scales [N,3], opacities [N], colors [N,3]."""
+    quats [N,4] (w,x,y,z), scales [N,3], opacities [N], colors [N,C] (C
+    channels per Gaussian, 3 for RGB; fp64 paths take C = 3)."""
 
     means: torch.Tensor
     quats: torch.Tensor
@@ -30,6 +31,10 @@ class Params:
     @property
     def n(self) -> int:
         return int(self.means.shape[0])
+
+    @property
+    def channels(self) -> int:
+        return int(self.colors.shape[1]) if self.colors.dim() == 2 else 3
 
     @staticmethod
     def from_scene(scene, device="cuda") -> "Params":
@@ -45,6 +50,10 @@ def _check_params(p: Params):
             raise RuntimeError(f"gsplat103 runs on CUDA only; {name} is on {x.device}")
         if x.dtype not in (torch.float32, torch.float64) or x.dtype != dt or not x.is_contiguous():
             raise ValueError(f"{name} must be contiguous float32 (or all float64)")
+    if p.colors.dim() != 2 or p.colors.shape[0] != p.n or p.colors.shape[1] < 1:
+        raise ValueError("colors must be [N, C]")
+    if dt == torch.float64 and p.channels != 3:
+        raise ValueError("the fp64 path composites 3 channels")
 
 
 @dataclasses.dataclass
@@ -77,7 +86,7 @@ class Frame:
 
     def image(self, i: int = 0) -> torch.Tensor:
         off, w, h, _ = self.views.image_slice(i)
-        return self.out_rgb[off:off + w * h].view(h, w, 3)
+        return self.out_rgb[off:off + w * h].view(h, w, -1)
 
 
 def project(views: B.Views, p: Params, eps2d: float, stream=None):
@@ -116,12 +125,17 @@ def forward(views: B.Views, p: Params, eps2d: float = 0.3, background: Optional[
                       tile_ranges, K, flags, stream)
     pix = views.pixels
     dt = p.means.dtype
-    out_rgb = torch.empty(pix, 3, device=dev, dtype=dt)
+    C = p.channels
+    out_rgb = torch.empty(pix, C, device=dev, dtype=dt)
     T_final = torch.empty(pix, device=dev, dtype=dt)
     last_idx = torch.empty(pix, dtype=torch.int32, device=dev)
     n_contrib = torch.empty(pix, dtype=torch.int32, device=dev) if count_contrib else None
-    B.gs_rasterize_fwd(views, pr["means2d"], pr["conics"], p.opacities, p.colors, isect_ids, tile_ranges, background,
-                       out_rgb, T_final, last_idx, n_contrib, config, stream)
+    if C == 3:
+        B.gs_rasterize_fwd(views, pr["means2d"], pr["conics"], p.opacities, p.colors, isect_ids, tile_ranges,
+                           background, out_rgb, T_final, last_idx, n_contrib, config, stream)
+    else:
+        B.gs_rasterize_fwd_nc(views, C, pr["means2d"], pr["conics"], p.opacities, p.colors, isect_ids, tile_ranges,
+                              background, out_rgb, T_final, last_idx, n_contrib, config, stream)
     return Frame(views, eps2d, background, cap, pr["means2d"], pr["conics"], pr["depths"], pr["rects"],
                  pr["touched"], pr["K_total"], isect_ids, isect_pos, emit_start, tile_ranges, K, flags, out_rgb,
                  T_final, last_idx, ws, n_contrib)
@@ -130,20 +144,28 @@ def forward(views: B.Views, p: Params, eps2d: float = 0.3, background: Optional[
 def backward(f: Frame, p: Params, dL_drgb: torch.Tensor, stream=None, deterministic: bool = False,
              config: Optional[B.RasterConfig] = None, viewmats: bool = False) -> dict:
     """Gradients of L w.r.t. means, quats, scales, opacities, colors (and the
-    2D intermediates means2d, conics) given dL/dC [pixels, 3].
-    ``deterministic`` selects the run-to-run identical reduction.  With
-    ``viewmats`` the result also holds dL/dT_cw of every view ([V, 4, 4])."""
+    2D intermediates means2d, conics) given dL/dC [pixels, C].
+    ``deterministic`` selects the run-to-run identical reduction (3 channels
+    only).  With ``viewmats`` the result also holds dL/dT_cw of every view
+    ([V, 4, 4])."""
     dev, dt = p.means.device, p.means.dtype
     views = f.views
     P, N = views.P, p.n
     dL_drgb = dL_drgb.contiguous().to(dt)
     z = lambda *shape: torch.zeros(*shape, device=dev, dtype=dt)
-    g2, gc, go, gcol = z(max(P, 1), 2), z(max(P, 1), 3), z(max(N, 1)), z(max(N, 1), 3)
-    nws = B.gs_rasterize_bwd_workspace_size(f.K_capacity, deterministic, dt == torch.float64)
-    ws = torch.empty(nws, dtype=torch.uint8, device=dev) if nws else None
-    B.gs_rasterize_bwd(views, f.means2d, f.conics, p.opacities, p.colors, f.isect_ids, f.isect_pos, f.emit_start,
-                       f.touched, f.tile_ranges, f.K, f.K_capacity, f.background, f.T_final, f.last_idx, dL_drgb,
-                       deterministic, ws, g2, gc, go, gcol, config, stream)
+    C = p.channels
+    g2, gc, go, gcol = z(max(P, 1), 2), z(max(P, 1), 3), z(max(N, 1)), z(max(N, 1), C)
+    if C == 3:
+        nws = B.gs_rasterize_bwd_workspace_size(f.K_capacity, deterministic, dt == torch.float64)
+        ws = torch.empty(nws, dtype=torch.uint8, device=dev) if nws else None
+        B.gs_rasterize_bwd(views, f.means2d, f.conics, p.opacities, p.colors, f.isect_ids, f.isect_pos,
+                           f.emit_start, f.touched, f.tile_ranges, f.K, f.K_capacity, f.background, f.T_final,
+                           f.last_idx, dL_drgb, deterministic, ws, g2, gc, go, gcol, config, stream)
+    else:
+        if deterministic:
+            raise ValueError("the deterministic backward composites 3 channels")
+        B.gs_rasterize_bwd_nc(views, C, f.means2d, f.conics, p.opacities, p.colors, f.isect_ids, f.tile_ranges,
+                              f.background, f.T_final, f.last_idx, dL_drgb, g2, gc, go, gcol, config, stream)
     gm, gq, gs = z(max(N, 1), 3), z(max(N, 1), 4), z(max(N, 1), 3)
     gv = z(max(views.V, 1), 4, 4) if viewmats else None
     B.gs_project_bwd(views, p.means, p.quats, p.scales, f.eps2d, f.touched, g2, gc, gm, gq, gs, stream, gv)

@@ -25,9 +25,14 @@ from typing import Dict, List, Optional, Sequence
 
 import torch
 
-# per-Gaussian gradient fields and their widths: 14 numbers per Gaussian
+# per-Gaussian gradient fields and their widths: 14 numbers per Gaussian for
+# 3 colour channels (11 + C for C channels)
 GRAD_FIELDS = (("means", 3), ("quats", 4), ("scales", 3), ("opacities", 1), ("colors", 3))
 GRAD_WIDTH = sum(k for _, k in GRAD_FIELDS)
+
+
+def grad_fields(channels: int = 3):
+    return GRAD_FIELDS[:-1] + (("colors", int(channels)),)
 
 
 def lpt_assign(costs: Sequence[float], world: int) -> List[List[int]]:
@@ -96,13 +101,14 @@ class GradBuffer:
     after field), which can be handed directly to the gradient outputs of the
     compositing and projection backward calls."""
 
-    def __init__(self, n: int, dtype=torch.float32, device="cpu"):
+    def __init__(self, n: int, dtype=torch.float32, device="cpu", channels: int = 3):
         self.n = int(n)
         rows = max(self.n, 1)
-        self.flat = torch.zeros(rows * GRAD_WIDTH, dtype=dtype, device=device)
+        fields = grad_fields(channels)
+        self.flat = torch.zeros(rows * sum(k for _, k in fields), dtype=dtype, device=device)
         self.fields: Dict[str, torch.Tensor] = {}
         off = 0
-        for name, k in GRAD_FIELDS:
+        for name, k in fields:
             v = self.flat[off:off + rows * k]
             self.fields[name] = v.view(rows) if k == 1 else v.view(rows, k)
             off += rows * k
@@ -140,7 +146,7 @@ class ShardedRenderer:
         self.plan = plan(scene_of_view, view_cost if view_cost is not None else pix, world, whole_scenes)
         self.rank, self.group = rank, group
         self.mine = self.plan.views_of_rank[rank]
-        self.buf = GradBuffer(params.n, params.means.dtype, dev)
+        self.buf = GradBuffer(params.n, params.means.dtype, dev, params.channels)
         starts = [0]
         for p_ in pix:
             starts.append(starts[-1] + p_)

@@ -33,8 +33,8 @@ class Trainer:
                  eps2d: float = 0.3, K_capacity: Optional[int] = None, headroom: float = 1.5,
                  config: Optional[B.RasterConfig] = None):
         """``raw``: device fp32 tensors means [N,3], quats [N,4], log_scales [N,3],
-        opacity_logits [N], colors [N,3]; they are updated in place.
-        ``targets``: packed [pixels, 3] target images of ``views``.
+        opacity_logits [N], colors [N,C]; they are updated in place.
+        ``targets``: packed [pixels, C] target images of ``views``.
         ``lr``: learning rates of the five groups, in that order."""
         for k in RAW:
             t = raw[k]
@@ -49,7 +49,7 @@ class Trainer:
         B.gs_activate(self.N, raw["log_scales"], raw["opacity_logits"], self.scales, self.opacities)
         self.params = Params(raw["means"], raw["quats"], self.scales[:self.N], self.opacities[:self.N], raw["colors"])
         self.adam = B.adam_config(lr, betas[0], betas[1], eps)
-        self.state = torch.zeros(B.gs_adam_state_size(self.N), dtype=torch.uint8, device=dev)
+        self.state = torch.zeros(B.gs_adam_state_size(self.N, self.params.channels), dtype=torch.uint8, device=dev)
         self.headroom = headroom
         if K_capacity is None:
             K_capacity = int(headroom * exact_capacity(self.params, views, eps2d)) + 1024

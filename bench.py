@@ -314,6 +314,40 @@ def optimisation_loop(dev, w, steps: int):
     return out
 
 
+def channel_cost(dev, views, params, pr, frame_ids, tile_ranges, K, cap, eps2d: float, channels=(1, 3, 4, 8, 16, 32),
+                 steps: int = 10):
+    """Device time of compositing forward + backward on the headline frame for
+    several channel counts (same projection and sorted lists)."""
+    import torch
+    from paper_2312_02121_gb300 import binding as B
+    N, pix = params.n, views.pixels
+    out = {}
+    for C in channels:
+        col = torch.rand(N, C, device=dev)
+        rgb, Tf = torch.empty(pix, C, device=dev), torch.empty(pix, device=dev)
+        last = torch.empty(pix, dtype=torch.int32, device=dev)
+        G = torch.randn(pix, C, device=dev)
+        g2, gc = torch.zeros(views.P, 2, device=dev), torch.zeros(views.P, 3, device=dev)
+        go, gcol = torch.zeros(N, device=dev), torch.zeros(N, C, device=dev)
+
+        def once():
+            B.gs_rasterize_fwd_nc(views, C, pr["means2d"], pr["conics"], params.opacities, col, frame_ids,
+                                  tile_ranges, None, rgb, Tf, last)
+            B.gs_rasterize_bwd_nc(views, C, pr["means2d"], pr["conics"], params.opacities, col, frame_ids,
+                                  tile_ranges, None, Tf, last, G, g2, gc, go, gcol)
+        for _ in range(2):
+            once()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            once()
+        b.record()
+        torch.cuda.synchronize()
+        out[str(C)] = {"fwd_bwd_ms": a.elapsed_time(b) / steps}
+        del col, rgb, Tf, last, G, g2, gc, go, gcol
+    return out
+
+
 def view_gradient_cost(dev, views, params, pr, g2, gc, eps2d: float, steps: int = 20):
     """Device time of the projection backward with and without the per-view
     dL/dT_cw output."""
@@ -445,7 +479,7 @@ def run_ours(args, rank, world, local_rank):
         gs = torch.zeros(sc.n, 3, device=dev)
         B.gs_project_bwd(views, params.means, params.quats, params.scales, w.eps2d, pr["touched"], g2, gc, gm, gq, gs)
         mark(6)
-        last_state.update(pr=pr, g2=g2, gc=gc)
+        last_state.update(pr=pr, g2=g2, gc=gc, ids=ids, tr=tr, Kd=Kd)
         return fl
 
     if args.profile:
@@ -566,6 +600,8 @@ def run_ours(args, rank, world, local_rank):
     }
     line["project_bwd_view_gradient"] = view_gradient_cost(dev, views, params, last_state["pr"], last_state["g2"],
                                                            last_state["gc"], w.eps2d)
+    line["channels"] = channel_cost(dev, views, params, last_state["pr"], last_state["ids"], last_state["tr"],
+                                    last_state["Kd"], cap, w.eps2d)
     if not args.no_optim:
         line["optimisation_loop"] = optimisation_loop(dev, w, args.optim_steps)
     if not args.no_batched:

@@ -170,13 +170,13 @@ __device__ __forceinline__ S warp_sum9(const S (&r)[kRec], S* buf, int lane, Red
     }
     row[8] = r[8];
     __syncwarp();
+    // lanes 27-31 sum a valid column too (their result is not used): no branch
+    const S* col = buf + rl.part * kRedStride + min(rl.q, kRec - 1);
     S acc = 0;
-    if (lane < 3 * kRec) {
-        const S* col = buf + rl.part * kRedStride + rl.q;
 #pragma unroll
-        for (int i = 0; i < 11; ++i)
-            if (rl.part + 3 * i < 32) acc += col[3 * i * kRedStride];
-    }
+    for (int i = 0; i < 10; ++i) acc += col[3 * i * kRedStride];
+    const S tail = col[(rl.part < 2 ? 30 : 27) * kRedStride];  // rows 30, 31 exist for residues 0, 1
+    acc += rl.part < 2 ? tail : S(0);
     __syncwarp();  // the buffer is free again
     const S a1 = __shfl_down_sync(kFull, acc, 1);
     const S a2 = __shfl_down_sync(kFull, acc, 2);
@@ -231,7 +231,9 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
             g2 = dL_drgb[3 * t.pix + 2];
             if (background) bgT = T * (background[0] * g0 + background[1] * g1 + background[2] * g2);
         }
-        S SdL = 0;  // S_n . dL/dC, S_n = sum_{m>n} c_m alpha_m T_m
+        // S_n . dL/dC + T_final b . dL/dC, with S_n = sum_{m>n} c_m alpha_m T_m: the numerator of the
+        // suffix term of dL/dalpha_n (the background part is constant per pixel, so it starts the sum)
+        S SdL = bgT;
         const RedLane rl = red_lane(lane);
 
         // the warp's and the tile's largest last index bound the work
@@ -293,18 +295,21 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                         const S Tn = T * inv1ma;  // T before this Gaussian
                         const S wgt = contrib ? alpha * Tn : S(0);
                         const S cdot = fma(col.x, g0, fma(col.y, g1, col.z * g2));
-                        const S dL_dalpha = fma(Tn, cdot, -(SdL + bgT) * inv1ma);
+                        const S dL_dalpha = fma(Tn, cdot, -SdL * inv1ma);
                         const S gd = (contrib && raw < RT<S>::alpha_max()) ? ge * dL_dalpha : S(0);  // dL/do
                         SdL = fma(wgt, cdot, SdL);
                         T = contrib ? Tn : T;
                         const S ds = -xy.z * gd;  // dL/dsigma
-                        const S hds = S(0.5) * ds;
+                        const S dsdx = ds * dx;
+                        // the sums the warp reduces; the flush turns them into the gradients:
+                        // dL/dmu' = sum ds Y Delta = (a sum ds u, b sum ds u + D sum ds dy) and
+                        // dL/dconic = (sum ds dx^2 / 2, sum ds dx dy, sum ds dy^2 / 2)
                         S r[kRec];
-                        r[0] = ds * (xy.w * u);                    // Y Delta = (a u, b u + D dy)
-                        r[1] = ds * fma(qq.w, u, col.w * dy);
-                        r[2] = hds * dx * dx;
-                        r[3] = ds * dx * dy;
-                        r[4] = hds * dy * dy;
+                        r[0] = ds * u;
+                        r[1] = ds * dy;
+                        r[2] = dsdx * dx;
+                        r[3] = dsdx * dy;
+                        r[4] = r[1] * dy;
                         r[5] = gd;
                         r[6] = wgt * g0;
                         r[7] = wgt * g1;
@@ -352,6 +357,15 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
 #pragma unroll
                         for (int q = 0; q < kRec; ++q) acc[q] += s_grad[ww][j][q];
                     }
+                {
+                    // from the reduced sums to dL/dmu' and the packed dL/dconic (see the walk)
+                    const S a = sh_xy[j].w, b = sh_q[j].w, D = sh_col[j].w;
+                    const S su = acc[0], sdy = acc[1];
+                    acc[0] = a * su;
+                    acc[1] = fma(b, su, D * sdy);
+                    acc[2] *= S(0.5);
+                    acc[4] *= S(0.5);
+                }
                 if (kAtomic) {
                     if (any) {
                         const int p = RT<S>::unstash(sh_cull[j].w);

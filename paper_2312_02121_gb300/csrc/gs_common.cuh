@@ -21,6 +21,32 @@ void count_launches(int n);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Programmatic dependent launch.  A kernel enqueued with launch_pdl may be
+// scheduled while the kernel before it in the stream is still draining, so
+// its launch latency and block start-up overlap that tail.  Every kernel of
+// the library therefore begins with pdl_wait() -- which returns once all work
+// it depends on has completed and its writes are visible -- before it reads
+// anything, and then calls pdl_trigger() so that the next kernel may be
+// scheduled in turn.  Both are no-ops for a kernel launched the usual way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t stream, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Index of the view that owns projection p: the largest v with
 // proj_offset <= p (views are laid out in increasing offsets; an empty view
 // shares its offset with the next one, so the largest match is the owner).

@@ -117,6 +117,8 @@ k_project_fwd(const GsView* __restrict__ views, int V, int64_t P, const S* __res
               S* __restrict__ conics, float* __restrict__ depths, short4* __restrict__ rects,
               int32_t* __restrict__ touched, unsigned long long* __restrict__ K_total)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int count = 0;
     if (p < P) {
@@ -301,6 +303,8 @@ k_project_bwd(const GsView* __restrict__ views, int V, int64_t P, const S* __res
               const S* __restrict__ dL_dconics, S* __restrict__ dL_dmeans, S* __restrict__ dL_dquats,
               S* __restrict__ dL_dscales)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P || touched[p] == 0) return;
     project_bwd_one<S, false>(views[view_of_projection(views, V, p)], p, means, quats, scales, eps2d, dL_dmeans2d,
@@ -320,6 +324,8 @@ k_project_bwd_view(const GsView* __restrict__ views, int V, int64_t P, const S* 
                    const S* __restrict__ dL_dconics, S* __restrict__ dL_dmeans, S* __restrict__ dL_dquats,
                    S* __restrict__ dL_dscales, S* __restrict__ dL_dviewmats)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ S s_sum[8][12];
     __shared__ int s_view[8];
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -393,7 +399,7 @@ static int project_impl(const char* who, const GsView* views, int32_t V, int64_t
     if (P == 0) return GS_OK;
     const int threads = 256;
     const unsigned blocks = (unsigned)((P + threads - 1) / threads);
-    k_project_fwd<S><<<blocks, threads, 0, s>>>(views, V, P, means, reinterpret_cast<const V4<S>*>(quats), scales,
+    launch_pdl(k_project_fwd<S>, blocks, threads, s, views, V, P, means, reinterpret_cast<const V4<S>*>(quats), scales,
                                                  eps2d, reinterpret_cast<V2<S>*>(means2d), conics, depths,
                                                  reinterpret_cast<short4*>(rects), touched,
                                                  reinterpret_cast<unsigned long long*>(K_total));
@@ -418,11 +424,11 @@ static int project_bwd_impl(const char* who, const GsView* views, int32_t V, int
     const int threads = 256;
     const unsigned blocks = (unsigned)((P + threads - 1) / threads);
     if (dL_dviewmats)
-        k_project_bwd_view<S><<<blocks, threads, 0, as_stream(stream)>>>(
+        launch_pdl(k_project_bwd_view<S>, blocks, threads, as_stream(stream),
             views, V, P, means, reinterpret_cast<const V4<S>*>(quats), scales, eps2d, touched,
             reinterpret_cast<const V2<S>*>(dL_dmeans2d), dL_dconics, dL_dmeans, dL_dquats, dL_dscales, dL_dviewmats);
     else
-        k_project_bwd<S><<<blocks, threads, 0, as_stream(stream)>>>(
+        launch_pdl(k_project_bwd<S>, blocks, threads, as_stream(stream),
             views, V, P, means, reinterpret_cast<const V4<S>*>(quats), scales, eps2d, touched,
             reinterpret_cast<const V2<S>*>(dL_dmeans2d), dL_dconics, dL_dmeans, dL_dquats, dL_dscales);
     count_launches(1);

@@ -54,6 +54,8 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
              const int2* __restrict__ tile_ranges, const S* __restrict__ background, S* __restrict__ out_rgb,
              S* __restrict__ T_final, int32_t* __restrict__ last_idx, int32_t* __restrict__ n_contrib)
 {
+    pdl_wait();
+    pdl_trigger();
     constexpr int kB = RT<S>::kFwdBatch;
     __shared__ V4<S> sh_xy[kB], sh_q[kB], sh_col[kB], sh_cull[kB];
     __shared__ int s_next;
@@ -197,6 +199,8 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
              V2<S>* __restrict__ dL_dmeans2d, S* __restrict__ dL_dconics, S* __restrict__ dL_dopacities,
              S* __restrict__ dL_dcolors)
 {
+    pdl_wait();
+    pdl_trigger();
     // deterministic: one partial slot per warp, summed in warp order; fast:
     // one slot per Gaussian, accumulated with shared-memory atomics (less
     // shared memory, so larger batches)
@@ -409,6 +413,8 @@ k_reduce_records(const GsView* __restrict__ views, int V, int64_t P, const int32
                  V2<S>* __restrict__ dL_dmeans2d, S* __restrict__ dL_dconics, S* __restrict__ dL_dopacities,
                  S* __restrict__ dL_dcolors)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
     const int n = touched[p];
@@ -461,7 +467,7 @@ static int rasterize_fwd_impl(const char* who, const GsView* views, int32_t V, i
     if (int rc = raster_grid(kern, config, T_total, &grid)) return rc;
     int* queue = pers ? config->queue : nullptr;
     if (pers && cudaMemsetAsync(queue, 0, sizeof(int), s) != cudaSuccess) return launch_status(who);
-    kern<<<grid, 256, 0, s>>>(views, V, T_total, config ? config->tile_order : nullptr, queue,
+    launch_pdl(kern, grid, 256, s, views, V, T_total, config ? config->tile_order : nullptr, queue,
                               reinterpret_cast<const V2<S>*>(means2d), conics, opacities, colors, isect_ids,
                               reinterpret_cast<const int2*>(tile_ranges), background, out_rgb, T_final, last_idx,
                               n_contrib);
@@ -515,13 +521,13 @@ static int rasterize_bwd_impl(const char* who, const GsView* views, int32_t V, i
     if (int rc = raster_grid(kern, config, T_total, &grid)) return rc;
     int* queue = pers ? config->queue : nullptr;
     if (pers && cudaMemsetAsync(queue, 0, sizeof(int), s) != cudaSuccess) return launch_status(who);
-    kern<<<grid, 256, 0, s>>>(views, V, T_total, config ? config->tile_order : nullptr, queue,
+    launch_pdl(kern, grid, 256, s, views, V, T_total, config ? config->tile_order : nullptr, queue,
                               reinterpret_cast<const V2<S>*>(means2d), conics, opacities, colors, isect_ids,
                               reinterpret_cast<const int2*>(tile_ranges), background, T_final, last_idx, dL_drgb,
                               records, reinterpret_cast<V2<S>*>(dL_dmeans2d), dL_dconics, dL_dopacities, dL_dcolors);
     count_launches(1);
     if (deterministic) {
-        k_reduce_records<S><<<(unsigned)((P + 255) / 256), 256, 0, s>>>(
+        launch_pdl(k_reduce_records<S>, (unsigned)((P + 255) / 256), 256, s,
             views, V, P, touched, emit_start, isect_pos, K, K_capacity, records,
             reinterpret_cast<V2<S>*>(dL_dmeans2d), dL_dconics, dL_dopacities, dL_dcolors);
         count_launches(1);

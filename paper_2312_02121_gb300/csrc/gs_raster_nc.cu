@@ -50,6 +50,8 @@ k_raster_fwd_nc(const GsView* __restrict__ views, int V, int T_total, const int3
                 const float* __restrict__ background, float* __restrict__ out, float* __restrict__ T_final,
                 int32_t* __restrict__ last_idx, int32_t* __restrict__ n_contrib)
 {
+    pdl_wait();
+    pdl_trigger();
     constexpr int kB = Nc<NC>::kB;
     __shared__ float4 sh_xy[kB], sh_q[kB], sh_col[kB], sh_cull[kB];
     __shared__ __align__(16) float sh_c[kB][NC];
@@ -141,6 +143,8 @@ k_raster_bwd_nc(const GsView* __restrict__ views, int V, int T_total, const int3
                 float2* __restrict__ dL_dmeans2d, float* __restrict__ dL_dconics, float* __restrict__ dL_dopacities,
                 float* __restrict__ dL_dcolors)
 {
+    pdl_wait();
+    pdl_trigger();
     constexpr int kB = Nc<NC>::kB, kR = Nc<NC>::kR;
     __shared__ float4 sh_xy[kB], sh_q[kB], sh_col[kB], sh_cull[kB];
     __shared__ __align__(16) float sh_c[kB][NC];
@@ -178,7 +182,7 @@ k_raster_bwd_nc(const GsView* __restrict__ views, int V, int T_total, const int3
                 }
             bgT *= T;
         }
-        float SdL = 0.f;  // S_n . dL/dC over the chunk's channels
+        float SdL = bgT;  // S_n . dL/dC + T_final b . dL/dC over the chunk's channels
 
         int wl = last;
 #pragma unroll
@@ -237,18 +241,20 @@ k_raster_bwd_nc(const GsView* __restrict__ views, int V, int T_total, const int3
                         float cdot = 0.f;
 #pragma unroll
                         for (int k = 0; k < NC; ++k) cdot = fmaf(sh_c[j][k], g[k], cdot);
-                        const float dL_dalpha = fmaf(Tn, cdot, -(SdL + bgT) * inv1ma);
+                        const float dL_dalpha = fmaf(Tn, cdot, -SdL * inv1ma);
                         const float gd = (contrib && raw < RT<float>::alpha_max()) ? ge * dL_dalpha : 0.f;
                         SdL = fmaf(wgt, cdot, SdL);
                         T = contrib ? Tn : T;
                         const float ds = -xy.z * gd;
-                        const float hds = 0.5f * ds;
+                        const float dsdx = ds * dx;
+                        // sums the flush turns into dL/dmu' = (a S_u, b S_u + D S_dy) and the packed
+                        // dL/dconic = (S_dx2 / 2, S_dxdy, S_dy2 / 2)
                         float r[kR];
-                        r[0] = ds * (xy.w * u);
-                        r[1] = ds * fmaf(qq.w, u, D * dy);
-                        r[2] = hds * dx * dx;
-                        r[3] = ds * dx * dy;
-                        r[4] = hds * dy * dy;
+                        r[0] = ds * u;
+                        r[1] = ds * dy;
+                        r[2] = dsdx * dx;
+                        r[3] = dsdx * dy;
+                        r[4] = r[1] * dy;
                         r[5] = gd;
 #pragma unroll
                         for (int k = 0; k < NC; ++k) r[6 + k] = wgt * g[k];
@@ -283,10 +289,11 @@ k_raster_bwd_nc(const GsView* __restrict__ views, int V, int T_total, const int3
                     const int p = RT<float>::unstash(sh_cull[j].w);
                     const int64_t gg = sh_g[j];
                     const float* a = s_grad[j];
-                    atomicAdd(dL_dmeans2d + p, make_float2(a[0], a[1]));
-                    atomicAdd(dL_dconics + 3 * p + 0, a[2]);
+                    const float ca = sh_xy[j].w, cb = sh_q[j].w, D = sh_col[j].w;
+                    atomicAdd(dL_dmeans2d + p, make_float2(ca * a[0], fmaf(cb, a[0], D * a[1])));
+                    atomicAdd(dL_dconics + 3 * p + 0, 0.5f * a[2]);
                     atomicAdd(dL_dconics + 3 * p + 1, a[3]);
-                    atomicAdd(dL_dconics + 3 * p + 2, a[4]);
+                    atomicAdd(dL_dconics + 3 * p + 2, 0.5f * a[4]);
                     atomicAdd(dL_dopacities + gg, a[5]);
                     float* dc = dL_dcolors + (int64_t)C * gg + c0;
                     for (int k = 0; k < nc; ++k) atomicAdd(dc + k, a[6 + k]);
@@ -336,7 +343,7 @@ static int launch_fwd(const ChunkArgs& a, const float* means2d, const float* con
     if (int rc = raster_grid(kern, a.cfg, a.T_total, &grid)) return rc;
     int* queue = pers ? a.cfg->queue : nullptr;
     if (pers && cudaMemsetAsync(queue, 0, sizeof(int), a.s) != cudaSuccess) return launch_status("gs_rasterize_fwd_nc");
-    kern<<<grid, 256, 0, a.s>>>(a.views, a.V, a.T_total, a.cfg ? a.cfg->tile_order : nullptr, queue,
+    launch_pdl(kern, grid, 256, a.s, a.views, a.V, a.T_total, a.cfg ? a.cfg->tile_order : nullptr, queue,
                                 reinterpret_cast<const float2*>(means2d), conics, opacities, colors, C, c0, nc,
                                 isect_ids, reinterpret_cast<const int2*>(tile_ranges), background, out, T_final,
                                 last_idx, n_contrib);
@@ -356,7 +363,7 @@ static int launch_bwd(const ChunkArgs& a, const float* means2d, const float* con
     if (int rc = raster_grid(kern, a.cfg, a.T_total, &grid)) return rc;
     int* queue = pers ? a.cfg->queue : nullptr;
     if (pers && cudaMemsetAsync(queue, 0, sizeof(int), a.s) != cudaSuccess) return launch_status("gs_rasterize_bwd_nc");
-    kern<<<grid, 256, 0, a.s>>>(a.views, a.V, a.T_total, a.cfg ? a.cfg->tile_order : nullptr, queue,
+    launch_pdl(kern, grid, 256, a.s, a.views, a.V, a.T_total, a.cfg ? a.cfg->tile_order : nullptr, queue,
                                 reinterpret_cast<const float2*>(means2d), conics, opacities, colors, C, c0, nc,
                                 isect_ids, reinterpret_cast<const int2*>(tile_ranges), background, T_final, last_idx,
                                 dL_dout, reinterpret_cast<float2*>(dL_dmeans2d), dL_dconics, dL_dopacities,

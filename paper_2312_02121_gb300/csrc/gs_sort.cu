@@ -80,6 +80,8 @@ __global__ void __launch_bounds__(kRT)
 k_radix_hist(const uint32_t* __restrict__ keys, const int32_t* __restrict__ count_dev, int64_t count_static,
              int64_t cap, int shift, int bits, uint32_t* __restrict__ hist)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t h[kRWarps][kMaxBins];
     const int count = item_count(count_dev, count_static, cap);
     const int nb = (count + kRTile - 1) / kRTile;
@@ -111,6 +113,8 @@ __global__ void __launch_bounds__(kRT)
 k_radix_scan_rows(uint32_t* __restrict__ hist, const int32_t* __restrict__ count_dev, int64_t count_static,
                   int64_t cap, uint32_t* __restrict__ digit_total)
 {
+    pdl_wait();
+    pdl_trigger();
     const int count = item_count(count_dev, count_static, cap);
     const int nb = (count + kRTile - 1) / kRTile;
     const int d = blockIdx.x;
@@ -137,6 +141,8 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
                 const int32_t* __restrict__ count_dev, int64_t count_static, int64_t cap, int shift, int bits,
                 const uint32_t* __restrict__ hist, const uint32_t* __restrict__ digit_total)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t s_keys[kRTile];
     __shared__ uint32_t s_vals[kRTile];
     __shared__ uint32_t s_warp[kRWarps][kMaxBins];  // per-warp digit counts, then per-warp offsets
@@ -250,9 +256,9 @@ static void lsd_sort(uint32_t* k1, uint32_t* k2, uint32_t* v1, uint32_t* v2, con
         const unsigned grid = (unsigned)((cap + kRTile - 1) / kRTile);
         for (int pass = 0, shift = 0; pass < passes; ++pass, shift += per) {
             const int bits = std::min(per, total_bits - shift);
-            k_radix_hist<<<grid, kRT, 0, s>>>(kin, count_dev, count_static, cap, shift, bits, rb.hist);
-            k_radix_scan_rows<<<1u << bits, kRT, 0, s>>>(rb.hist, count_dev, count_static, cap, rb.digit_total);
-            k_radix_scatter<<<grid, kRT, 0, s>>>(kin, vin, kout, vout, count_dev, count_static, cap, shift, bits,
+            launch_pdl(k_radix_hist, grid, kRT, s, kin, count_dev, count_static, cap, shift, bits, rb.hist);
+            launch_pdl(k_radix_scan_rows, 1u << bits, kRT, s, rb.hist, count_dev, count_static, cap, rb.digit_total);
+            launch_pdl(k_radix_scatter, grid, kRT, s, kin, vin, kout, vout, count_dev, count_static, cap, shift, bits,
                                                  rb.hist, rb.digit_total);
             count_launches(3);
             std::swap(kin, kout);
@@ -273,6 +279,8 @@ static void lsd_sort(uint32_t* k1, uint32_t* k2, uint32_t* v1, uint32_t* v2, con
 __global__ void k_depth_keys(int64_t P, const float* __restrict__ depths, const int32_t* __restrict__ touched,
                              uint32_t* __restrict__ keys)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p < P) keys[p] = touched[p] > 0 ? __float_as_uint(depths[p]) : 0x7fffffffu;
 }
@@ -282,6 +290,8 @@ __global__ void __launch_bounds__(256)
 k_touched_block_sums(int64_t P, const uint32_t* __restrict__ order, const int32_t* __restrict__ touched,
                      int64_t* __restrict__ block_sums)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t base = (int64_t)blockIdx.x * kEmitTile;
     int64_t s = 0;
 #pragma unroll
@@ -300,6 +310,8 @@ __global__ void __launch_bounds__(kScanThreads)
 k_scan_block_sums(int64_t nblk, int64_t* __restrict__ block_sums, int64_t cap, int32_t* __restrict__ K_out,
                   uint32_t* __restrict__ flags)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int64_t warp_tot[kScanThreads / 32];
     const int64_t per = (nblk + kScanThreads - 1) / kScanThreads;
     const int64_t lo = min(nblk, (int64_t)threadIdx.x * per), hi = min(nblk, lo + per);
@@ -343,6 +355,8 @@ k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __res
        const int32_t* __restrict__ touched, const short4* __restrict__ rects, const int64_t* __restrict__ block_prefix,
        int64_t cap, uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ owner, int32_t* __restrict__ emit_start)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int s_off[kEmitTile + 1];  // block-local first slot of each rank
     __shared__ uint32_t s_p[kEmitTile];
     __shared__ int s_x0[kEmitTile], s_w[kEmitTile];
@@ -408,6 +422,8 @@ __global__ void k_finalize(const int32_t* __restrict__ K_dev, int64_t cap, const
                            int32_t* __restrict__ isect_ids, int32_t* __restrict__ isect_pos,
                            int2* __restrict__ tile_ranges)
 {
+    pdl_wait();
+    pdl_trigger();
     const int K = item_count(K_dev, 0, cap);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= K) return;
@@ -422,6 +438,8 @@ __global__ void k_finalize(const int32_t* __restrict__ K_dev, int64_t cap, const
 // Longest-first key of each tile: 65535 - min(list length, 65535).
 __global__ void k_tile_len_keys(int32_t T, const int2* __restrict__ tile_ranges, uint32_t* __restrict__ keys)
 {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < T) {
         const int2 r = tile_ranges[i];
@@ -431,6 +449,8 @@ __global__ void k_tile_len_keys(int32_t T, const int2* __restrict__ tile_ranges,
 
 __global__ void k_copy_u32(int32_t n, const uint32_t* __restrict__ src, int32_t* __restrict__ dst)
 {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] = (int32_t)src[i];
 }
@@ -528,16 +548,16 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
     const RadixBufs rb{L.hist, L.digit_total};
 
     // 1. projections in (depth, p) order
-    k_depth_keys<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(P, depths, touched, L.dkey_a);
+    launch_pdl(k_depth_keys, (unsigned)((P + 255) / 256), 256, s, P, depths, touched, L.dkey_a);
     count_launches(1);
     uint32_t *dk, *order;
     lsd_sort(L.dkey_a, L.dkey_b, L.dval_a, L.dval_b, nullptr, P, P, 31, rb, s, &dk, &order);
 
     // 2. scan of touched in depth order, K, emission
     const int64_t nblk = (P + kEmitTile - 1) / kEmitTile;
-    k_touched_block_sums<<<(unsigned)nblk, 256, 0, s>>>(P, order, touched, L.block_sums);
-    k_scan_block_sums<<<1, kScanThreads, 0, s>>>(nblk, L.block_sums, K_capacity, K_out, flags);
-    k_emit<<<(unsigned)nblk, 256, 0, s>>>(views, V, P, order, touched, reinterpret_cast<const short4*>(rects),
+    launch_pdl(k_touched_block_sums, (unsigned)nblk, 256, s, P, order, touched, L.block_sums);
+    launch_pdl(k_scan_block_sums, 1, kScanThreads, s, nblk, L.block_sums, K_capacity, K_out, flags);
+    launch_pdl(k_emit, (unsigned)nblk, 256, s, views, V, P, order, touched, reinterpret_cast<const short4*>(rects),
                                           L.block_sums, K_capacity, L.tkey_a, L.owner, emit_start);
     count_launches(3);
     if (K_capacity == 0) return launch_status("gs_bin_and_sort");
@@ -547,7 +567,7 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
     lsd_sort(L.tkey_a, L.tkey_b, L.tval_a, L.tval_b, K_out, 0, K_capacity, bit_length((int64_t)T_total - 1), rb, s,
              &tk, &tv);
     // 4. projection ids, inverse positions, tile ranges
-    k_finalize<<<(unsigned)((K_capacity + 255) / 256), 256, 0, s>>>(K_out, K_capacity, tk, tv, L.owner, isect_ids,
+    launch_pdl(k_finalize, (unsigned)((K_capacity + 255) / 256), 256, s, K_out, K_capacity, tk, tv, L.owner, isect_ids,
                                                                       isect_pos, reinterpret_cast<int2*>(tile_ranges));
     count_launches(1);
     return launch_status("gs_bin_and_sort");
@@ -572,10 +592,10 @@ extern "C" int gs_tile_order(const int32_t* tile_ranges, int32_t T_total, void* 
     cudaStream_t s = as_stream(stream);
     const OrderLayout L = carve_order(workspace, T_total);
     const unsigned g = (unsigned)((T_total + 255) / 256);
-    k_tile_len_keys<<<g, 256, 0, s>>>(T_total, reinterpret_cast<const int2*>(tile_ranges), L.ka);
+    launch_pdl(k_tile_len_keys, g, 256, s, T_total, reinterpret_cast<const int2*>(tile_ranges), L.ka);
     uint32_t *k, *v;
     lsd_sort(L.ka, L.kb, L.va, L.vb, nullptr, T_total, T_total, 16, RadixBufs{L.hist, L.digit_total}, s, &k, &v);
-    k_copy_u32<<<g, 256, 0, s>>>(T_total, v, order);
+    launch_pdl(k_copy_u32, g, 256, s, T_total, v, order);
     count_launches(2);
     return launch_status("gs_tile_order");
 }

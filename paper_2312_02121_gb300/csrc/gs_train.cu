@@ -40,6 +40,8 @@ __global__ void __launch_bounds__(256)
 k_l2_loss(const S* __restrict__ rgb, const S* __restrict__ target, int64_t n, S inv_norm, S* __restrict__ dL,
           S* __restrict__ loss, bool vec)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ S sh[8];
     S acc = S(0);
     const S two = S(2) * inv_norm;
@@ -76,7 +78,7 @@ static int l2_loss_impl(const char* who, const S* rgb, const S* target, int64_t 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t groups = (n + 3) / 4;
     const unsigned blocks = (unsigned)std::min<int64_t>((groups + 255) / 256, (int64_t)std::max(sms, 1) * 8);
-    k_l2_loss<S><<<blocks, 256, 0, as_stream(stream)>>>(rgb, target, n, inv_norm, dL, loss, vec);
+    launch_pdl(k_l2_loss<S>, blocks, 256, as_stream(stream), rgb, target, n, inv_norm, dL, loss, vec);
     count_launches(1);
     return launch_status(who);
 }
@@ -96,6 +98,8 @@ constexpr int kAdamGeom = 11;  // means 3, quats 4, log-scales 3, logit 1
 
 __global__ void k_adam_prepare(AdamHeader* h, float beta1, float beta2, const int32_t* __restrict__ skip)
 {
+    pdl_wait();
+    pdl_trigger();
     if (skip && *skip) return;
     const int t = h->step + 1;
     h->step = t;
@@ -126,6 +130,8 @@ k_adam_step(int64_t N, int C, AdamArgs a, const AdamHeader* __restrict__ h, floa
             const float* __restrict__ g_colors, float* __restrict__ scales, float* __restrict__ opacities,
             const int32_t* __restrict__ skip)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N || (skip && *skip)) return;
     const float bc1 = h->bc1, bc2 = h->bc2;
@@ -170,6 +176,8 @@ __global__ void __launch_bounds__(256)
 k_activate(int64_t N, const float* __restrict__ log_scales, const float* __restrict__ logits,
            float* __restrict__ scales, float* __restrict__ opacities)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
 #pragma unroll
@@ -220,7 +228,7 @@ extern "C" int gs_adam_step(int64_t N, int32_t C, const GsAdamConfig* cfg, void*
     float* m = reinterpret_cast<float*>(static_cast<char*>(state) + 256);
     float* v = reinterpret_cast<float*>(static_cast<char*>(state) + 256 +
                                         align256(sizeof(float) * (kAdamGeom + C) * (size_t)N));
-    k_adam_prepare<<<1, 1, 0, s>>>(h, cfg->beta1, cfg->beta2, skip_if_set);
+    launch_pdl(k_adam_prepare, 1, 1, s, h, cfg->beta1, cfg->beta2, skip_if_set);
     AdamArgs a;
     for (int i = 0; i < 5; ++i) a.lr[i] = cfg->lr[i];
     a.beta1 = cfg->beta1;
@@ -228,7 +236,7 @@ extern "C" int gs_adam_step(int64_t N, int32_t C, const GsAdamConfig* cfg, void*
     a.eps = cfg->eps;
     int launched = 1;
     if (N > 0) {
-        k_adam_step<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, C, a, h, m, v, means, quats, log_scales,
+        launch_pdl(k_adam_step, (unsigned)((N + 255) / 256), 256, s, N, C, a, h, m, v, means, quats, log_scales,
                                                                 opacity_logits, colors, dL_dmeans, dL_dquats,
                                                                 dL_dscales, dL_dopacities, dL_dcolors, scales,
                                                                 opacities, skip_if_set);
@@ -245,7 +253,7 @@ extern "C" int gs_activate(int64_t N, const float* log_scales, const float* opac
     if (N == 0) return GS_OK;
     if (!log_scales || !opacity_logits || !scales || !opacities)
         return fail(GS_ERR_INVALID_ARG, "gs_activate: null pointer argument");
-    k_activate<<<(unsigned)((N + 255) / 256), 256, 0, as_stream(stream)>>>(N, log_scales, opacity_logits, scales,
+    launch_pdl(k_activate, (unsigned)((N + 255) / 256), 256, as_stream(stream), N, log_scales, opacity_logits, scales,
                                                                           opacities);
     count_launches(1);
     return launch_status("gs_activate");

@@ -452,11 +452,10 @@ def run_ours(args, rank, world, local_rank):
         P, T = views.P, views.T
         ws = torch.empty(B.gs_bin_and_sort_workspace_size(P, cap, T), dtype=torch.uint8, device=dev)
         ids = torch.empty(cap, dtype=torch.int32, device=dev)
-        es = torch.empty(P, dtype=torch.int32, device=dev)
         tr = torch.empty(T, 2, dtype=torch.int32, device=dev)
         Kd = torch.empty(1, dtype=torch.int32, device=dev)
         fl = torch.zeros(1, dtype=torch.int32, device=dev)
-        B.gs_bin_and_sort(views, pr["rects"], pr["depths"], pr["touched"], cap, ws, ids, None, es, tr, Kd, fl)
+        B.gs_bin_and_sort(views, pr["rects"], pr["depths"], pr["touched"], cap, ws, ids, None, None, tr, Kd, fl)
         mark(2)
         rgb = torch.empty(pixels, 3, device=dev)
         Tf = torch.empty(pixels, device=dev)
@@ -471,7 +470,7 @@ def run_ours(args, rank, world, local_rank):
         gc = torch.zeros(P, 3, device=dev)
         go = torch.zeros(sc.n, device=dev)
         gcol = torch.zeros(sc.n, 3, device=dev)
-        B.gs_rasterize_bwd(views, pr["means2d"], pr["conics"], params.opacities, params.colors, ids, None, es,
+        B.gs_rasterize_bwd(views, pr["means2d"], pr["conics"], params.opacities, params.colors, ids, None, None,
                            pr["touched"], tr, Kd, cap, None, Tf, last, dL, False, None, g2, gc, go, gcol, None)
         mark(5)
         gm = torch.zeros(sc.n, 3, device=dev)

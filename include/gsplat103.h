@@ -155,7 +155,9 @@ size_t gs_bin_and_sort_workspace_size(int64_t P, int64_t K_capacity, int32_t T_t
  *                                pair j of p is emission emit_start[p] + j);
  *                                nullable -- only the deterministic
  *                                gs_rasterize_bwd reads it
- *        emit_start[P]           first emission index of each projection
+ *        emit_start[P]           first emission index of each projection;
+ *                                nullable unless isect_pos is given (it is
+ *                                read only with it)
  *        tile_ranges[T_total,2]  [start, end) of each tile's sorted pairs
  *        K_out                   (device int32) number of pairs K
  *        flags                   (device uint32) GS_FLAG_CAPACITY is OR-ed in

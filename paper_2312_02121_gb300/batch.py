@@ -89,7 +89,8 @@ class BatchRenderer:
                      self.touched, self.K_total)
         self.flags.zero_()
         B.gs_bin_and_sort(v, self.rects, self.depths, self.touched, self.cap, self.sort_ws, self.isect_ids,
-                          self.isect_pos if self.deterministic else None, self.emit_start, self.tile_ranges, self.K,
+                          self.isect_pos if self.deterministic else None,
+                          self.emit_start if self.deterministic else None, self.tile_ranges, self.K,
                           self.flags)
         if self.longest_first:
             B.gs_tile_order(self.tile_ranges, v.T, self.order_ws, self.tile_order)

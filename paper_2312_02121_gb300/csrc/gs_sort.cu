@@ -241,15 +241,15 @@ struct RadixBufs {
 
 // Stable LSD sort of (key, value) pairs on key bits [0, total_bits), in
 // passes of at most 8 bits.  Keys ping-pong between k1 and k2, values between
-// v1 and v2; the first pass takes "value = input position".  The item count
-// is *count_dev (device, clamped to cap) or count_static.  Returns the
-// buffers holding the result.
-static void lsd_sort(uint32_t* k1, uint32_t* k2, uint32_t* v1, uint32_t* v2, const int32_t* count_dev,
-                     int64_t count_static, int64_t cap, int total_bits, const RadixBufs& rb, cudaStream_t s,
-                     uint32_t** keys_out, uint32_t** vals_out)
+// v1 and v2; the values start as vals0, or as the input positions when vals0
+// is null.  The item count is *count_dev (device, clamped to cap) or
+// count_static.  Returns the buffers holding the result.
+static void lsd_sort(uint32_t* k1, uint32_t* k2, uint32_t* v1, uint32_t* v2, const uint32_t* vals0,
+                     const int32_t* count_dev, int64_t count_static, int64_t cap, int total_bits,
+                     const RadixBufs& rb, cudaStream_t s, uint32_t** keys_out, uint32_t** vals_out)
 {
     uint32_t *kin = k1, *kout = k2, *vout = v1;
-    const uint32_t* vin = nullptr;
+    const uint32_t* vin = vals0;
     if (total_bits > 0 && cap > 0) {
         const int passes = (total_bits + 7) / 8;
         const int per = (total_bits + passes - 1) / passes;
@@ -267,7 +267,7 @@ static void lsd_sort(uint32_t* k1, uint32_t* k2, uint32_t* v1, uint32_t* v2, con
         }
     }
     *keys_out = kin;
-    *vals_out = const_cast<uint32_t*>(vin);
+    *vals_out = const_cast<uint32_t*>(vin);  // vals0 itself when no pass ran
 }
 
 // ---------------------------------------------------------------------------
@@ -285,10 +285,12 @@ __global__ void k_depth_keys(int64_t P, const float* __restrict__ depths, const 
     if (p < P) keys[p] = touched[p] > 0 ? __float_as_uint(depths[p]) : 0x7fffffffu;
 }
 
-// Per block of kEmitTile projections in depth order: sum of touched.
+// Per block of kEmitTile projections in depth order: sum of touched.  The
+// counts are also stored in depth order (cnt_sorted[r] = touched[order[r]]),
+// so that the emission reads them contiguously instead of gathering again.
 __global__ void __launch_bounds__(256)
 k_touched_block_sums(int64_t P, const uint32_t* __restrict__ order, const int32_t* __restrict__ touched,
-                     int64_t* __restrict__ block_sums)
+                     int64_t* __restrict__ block_sums, int32_t* __restrict__ cnt_sorted)
 {
     pdl_wait();
     pdl_trigger();
@@ -297,7 +299,11 @@ k_touched_block_sums(int64_t P, const uint32_t* __restrict__ order, const int32_
 #pragma unroll
     for (int k = 0; k < kEmitItems; ++k) {
         const int64_t r = base + k * 256 + threadIdx.x;
-        if (r < P) s += touched[order[r]];
+        if (r < P) {
+            const int32_t c = touched[order[r]];
+            cnt_sorted[r] = c;
+            s += c;
+        }
     }
     int64_t tot;
     block_exclusive_scan_256<int64_t>(s, &tot);
@@ -352,7 +358,7 @@ k_scan_block_sums(int64_t nblk, int64_t* __restrict__ block_sums, int64_t cap, i
 // warp are contiguous whatever the rectangle sizes.
 __global__ void __launch_bounds__(256)
 k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __restrict__ order,
-       const int32_t* __restrict__ touched, const short4* __restrict__ rects, const int64_t* __restrict__ block_prefix,
+       const int32_t* __restrict__ cnt_sorted, const short4* __restrict__ rects, const int64_t* __restrict__ block_prefix,
        int64_t cap, uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ owner, int32_t* __restrict__ emit_start)
 {
     pdl_wait();
@@ -374,7 +380,7 @@ k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __res
         cnt[k] = 0;
         if (r < P) {
             p = order[r];
-            cnt[k] = touched[p];
+            cnt[k] = cnt_sorted[r];
             if (cnt[k] > 0) {
                 const GsView& view = views[view_of_projection(views, V, (int64_t)p)];
                 const short4 rc = rects[p];
@@ -393,7 +399,7 @@ k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __res
     for (int k = 0; k < kEmitItems; ++k) {
         const int li = threadIdx.x * kEmitItems + k;
         s_off[li] = off;
-        if (cnt[k] > 0) emit_start[s_p[li]] = (int32_t)min(gbase + off, (int64_t)INT32_MAX);
+        if (emit_start && cnt[k] > 0) emit_start[s_p[li]] = (int32_t)min(gbase + off, (int64_t)INT32_MAX);
         off += cnt[k];
     }
     if (threadIdx.x == 0) s_off[kEmitTile] = total;
@@ -416,9 +422,12 @@ k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __res
     }
 }
 
-// Sorted pairs -> projection ids, inverse positions and per-tile ranges.
+// Sorted pairs -> projection ids, inverse positions and per-tile ranges.  The
+// sorted values are emission indices when isect_pos is wanted (their owners
+// are gathered and the inverse permutation is scattered), else the owners
+// themselves.
 __global__ void k_finalize(const int32_t* __restrict__ K_dev, int64_t cap, const uint32_t* __restrict__ keys,
-                           const uint32_t* __restrict__ emit_idx, const uint32_t* __restrict__ owner,
+                           const uint32_t* __restrict__ vals, const uint32_t* __restrict__ owner,
                            int32_t* __restrict__ isect_ids, int32_t* __restrict__ isect_pos,
                            int2* __restrict__ tile_ranges)
 {
@@ -427,9 +436,13 @@ __global__ void k_finalize(const int32_t* __restrict__ K_dev, int64_t cap, const
     const int K = item_count(K_dev, 0, cap);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= K) return;
-    const uint32_t e = emit_idx ? emit_idx[i] : (uint32_t)i;
-    isect_ids[i] = (int32_t)owner[e];
-    if (isect_pos) isect_pos[e] = i;
+    if (isect_pos) {
+        const uint32_t e = vals[i];
+        isect_ids[i] = (int32_t)owner[e];
+        isect_pos[e] = i;
+    } else {
+        isect_ids[i] = (int32_t)vals[i];
+    }
     const uint32_t t = keys[i];
     if (i == 0 || keys[i - 1] != t) tile_ranges[t].x = i;
     if (i == K - 1 || keys[i + 1] != t) tile_ranges[t].y = i + 1;
@@ -476,6 +489,7 @@ static OrderLayout carve_order(void* ws, int64_t T)
 
 struct SortLayout {
     uint32_t *dkey_a, *dkey_b, *dval_a, *dval_b;
+    int32_t* cnt_sorted;
     int64_t* block_sums;
     uint32_t *tkey_a, *tkey_b, *tval_a, *tval_b, *owner;
     uint32_t *hist, *digit_total;
@@ -490,6 +504,7 @@ static SortLayout carve(void* ws, int64_t P, int64_t cap)
     L.dkey_b = c.take<uint32_t>(P);
     L.dval_a = c.take<uint32_t>(P);
     L.dval_b = c.take<uint32_t>(P);
+    L.cnt_sorted = c.take<int32_t>(P);
     L.block_sums = c.take<int64_t>((P + kEmitTile - 1) / kEmitTile + 1);
     L.tkey_a = c.take<uint32_t>(cap);
     L.tkey_b = c.take<uint32_t>(cap);
@@ -530,8 +545,8 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
         K_capacity >= (int64_t(1) << 31))
         return fail(GS_ERR_INVALID_ARG, "gs_bin_and_sort: V=%d P=%lld T_total=%d K_capacity=%lld", V, (long long)P,
                     T_total, (long long)K_capacity);
-    if (!views || !tile_ranges || !K_out || !flags || (P > 0 && (!rects || !depths || !touched || !emit_start)) ||
-        (K_capacity > 0 && !isect_ids))
+    if (!views || !tile_ranges || !K_out || !flags || (P > 0 && (!rects || !depths || !touched)) ||
+        (K_capacity > 0 && !isect_ids) || (isect_pos && !emit_start))
         return fail(GS_ERR_INVALID_ARG, "gs_bin_and_sort: null pointer argument");
     if ((reinterpret_cast<uintptr_t>(rects) & 7) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7))
         return fail(GS_ERR_INVALID_ARG, "gs_bin_and_sort: rects and tile_ranges need 8-byte alignment");
@@ -551,24 +566,25 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
     launch_pdl(k_depth_keys, (unsigned)((P + 255) / 256), 256, s, P, depths, touched, L.dkey_a);
     count_launches(1);
     uint32_t *dk, *order;
-    lsd_sort(L.dkey_a, L.dkey_b, L.dval_a, L.dval_b, nullptr, P, P, 31, rb, s, &dk, &order);
+    lsd_sort(L.dkey_a, L.dkey_b, L.dval_a, L.dval_b, nullptr, nullptr, P, P, 31, rb, s, &dk, &order);
 
     // 2. scan of touched in depth order, K, emission
     const int64_t nblk = (P + kEmitTile - 1) / kEmitTile;
-    launch_pdl(k_touched_block_sums, (unsigned)nblk, 256, s, P, order, touched, L.block_sums);
+    launch_pdl(k_touched_block_sums, (unsigned)nblk, 256, s, P, order, touched, L.block_sums, L.cnt_sorted);
     launch_pdl(k_scan_block_sums, 1, kScanThreads, s, nblk, L.block_sums, K_capacity, K_out, flags);
-    launch_pdl(k_emit, (unsigned)nblk, 256, s, views, V, P, order, touched, reinterpret_cast<const short4*>(rects),
+    launch_pdl(k_emit, (unsigned)nblk, 256, s, views, V, P, order, L.cnt_sorted, reinterpret_cast<const short4*>(rects),
                                           L.block_sums, K_capacity, L.tkey_a, L.owner, emit_start);
     count_launches(3);
     if (K_capacity == 0) return launch_status("gs_bin_and_sort");
 
-    // 3. stable sort of the pairs by global tile id (values: emission index)
+    // 3. stable sort of the pairs by global tile id; the values are the emission indices when the
+    //    inverse positions are wanted, else directly the owning projections
     uint32_t *tk, *tv;
-    lsd_sort(L.tkey_a, L.tkey_b, L.tval_a, L.tval_b, K_out, 0, K_capacity, bit_length((int64_t)T_total - 1), rb, s,
-             &tk, &tv);
+    lsd_sort(L.tkey_a, L.tkey_b, L.tval_a, L.tval_b, isect_pos ? nullptr : L.owner, K_out, 0, K_capacity,
+             bit_length((int64_t)T_total - 1), rb, s, &tk, &tv);
     // 4. projection ids, inverse positions, tile ranges
-    launch_pdl(k_finalize, (unsigned)((K_capacity + 255) / 256), 256, s, K_out, K_capacity, tk, tv, L.owner, isect_ids,
-                                                                      isect_pos, reinterpret_cast<int2*>(tile_ranges));
+    launch_pdl(k_finalize, (unsigned)((K_capacity + 255) / 256), 256, s, K_out, K_capacity, tk, tv, L.owner,
+               isect_ids, isect_pos, reinterpret_cast<int2*>(tile_ranges));
     count_launches(1);
     return launch_status("gs_bin_and_sort");
 }
@@ -594,7 +610,8 @@ extern "C" int gs_tile_order(const int32_t* tile_ranges, int32_t T_total, void* 
     const unsigned g = (unsigned)((T_total + 255) / 256);
     launch_pdl(k_tile_len_keys, g, 256, s, T_total, reinterpret_cast<const int2*>(tile_ranges), L.ka);
     uint32_t *k, *v;
-    lsd_sort(L.ka, L.kb, L.va, L.vb, nullptr, T_total, T_total, 16, RadixBufs{L.hist, L.digit_total}, s, &k, &v);
+    lsd_sort(L.ka, L.kb, L.va, L.vb, nullptr, nullptr, T_total, T_total, 16, RadixBufs{L.hist, L.digit_total}, s, &k,
+             &v);
     launch_pdl(k_copy_u32, g, 256, s, T_total, v, order);
     count_launches(2);
     return launch_status("gs_tile_order");

@@ -94,6 +94,25 @@ def test_binning_bit_exact(case):
     np.testing.assert_array_equal(sid[pos[e]], owner)
 
 
+def test_binning_without_inverse_positions_is_the_same(case):
+    # without isect_pos (the fast backward's case) the tile sort carries the owners directly
+    f = case["frame"]
+    v, P, T = f.views, f.views.P, f.views.T
+    cap = f.K_capacity
+    dev = "cuda"
+    ws = torch.empty(B.gs_bin_and_sort_workspace_size(P, cap, T), dtype=torch.uint8, device=dev)
+    ids = torch.full((cap,), -7, dtype=torch.int32, device=dev)
+    tr = torch.full((T, 2), -7, dtype=torch.int32, device=dev)
+    K = torch.empty(1, dtype=torch.int32, device=dev)
+    fl = torch.zeros(1, dtype=torch.int32, device=dev)
+    B.gs_bin_and_sort(v, f.rects, f.depths, f.touched, cap, ws, ids, None, None, tr, K, fl)
+    torch.cuda.synchronize()
+    k = int(K.item())
+    assert k == int(np_(f.K)[0]) and int(fl.item()) == 0
+    np.testing.assert_array_equal(np_(ids)[:k], np_(f.isect_ids)[:k])
+    np.testing.assert_array_equal(np_(tr), np_(f.tile_ranges))
+
+
 def test_forward_given_projection(case):
     # compositing alone: the oracle composites the CUDA path's own fp32 projection
     cam, sc, f = case["cam"], case["sc"], case["frame"]

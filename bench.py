@@ -123,13 +123,24 @@ class ClockSampler:
                 "power_w_max": max(r["power"] for r in rows)}
 
 
+RASTER_SOURCES = ("gs_raster.cu", "gs_raster_common.cuh", "gs_common.cuh")
+
+
+def raster_source_hash() -> str:
+    """sha256 over the sources the 3-channel raster kernels are compiled from."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in RASTER_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2312_02121_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def recorded_traffic(kernel: str):
     """DRAM bytes per launch of ``kernel`` from the committed ncu summary, if it
     was captured from the current source of the raster kernels (else None)."""
     import hashlib
     try:
-        src = open(os.path.join(ROOT, "paper_2312_02121_gb300", "csrc", "gs_raster.cu"), "rb").read()
-        h = hashlib.sha256(src).hexdigest()
+        h = raster_source_hash()
         for line in open(os.path.join(ROOT, "profiles", "roofline_traffic.txt")):
             f = line.split()
             if len(f) == 3 and not line.startswith("#") and f[0] == kernel and f[1] == h:

@@ -81,10 +81,53 @@ class BatchRenderer:
             cfg = config or B.RasterConfig(device=dev)
             self.config = B.RasterConfig(cfg.persistent, cfg.ctas_per_sm, self.tile_order, device=dev)
         self.graph: Optional[torch.cuda.CUDAGraph] = None
+        self.host = None
+
+    # -- inputs from host memory ---------------------------------------------
+    def attach_host_inputs(self, params: Dict[str, torch.Tensor], targets: Optional[torch.Tensor] = None):
+        """Makes every step start by copying its inputs from pinned host
+        memory and end by copying the loss into the pinned host scalar
+        ``loss_host``.  ``params`` maps means, quats, scales, opacities and
+        colors to pinned host tensors shaped like the renderer's parameters;
+        ``targets`` is the pinned host [pixels, C] target.  The copies of what
+        compositing and the loss read (opacities, colours, target) run on a
+        second stream while projection and sorting run; the step waits for
+        them only where they are needed.  Attach before ``capture``: the
+        copies are then part of the graph, and each replay reads whatever the
+        host tensors hold at that time."""
+        for k in ("means", "quats", "scales", "opacities", "colors"):
+            h, d = params[k], getattr(self.p, k)
+            if not h.is_pinned() or h.shape != d.shape or h.dtype != d.dtype:
+                raise ValueError(f"host {k} must be pinned and shaped {tuple(d.shape)} {d.dtype}")
+        if targets is not None and (not targets.is_pinned() or targets.numel() != self.targets.numel()):
+            raise ValueError("host targets must be pinned and hold as many values as the device targets")
+        self.host = dict(params=params, targets=targets, stream=torch.cuda.Stream(),
+                         fork=torch.cuda.Event(), late=torch.cuda.Event(), tgt=torch.cuda.Event())
+        self.loss_host = torch.zeros(1, dtype=self.loss.dtype, pin_memory=True)
+
+    def _upload(self):
+        """Issues this step's host -> device copies; returns after the ones
+        the projection needs are enqueued on the current stream."""
+        h, p = self.host, self.p
+        main = torch.cuda.current_stream()
+        h["fork"].record(main)  # the previous step is done with every input buffer
+        side = h["stream"]
+        side.wait_event(h["fork"])
+        with torch.cuda.stream(side):
+            p.opacities.copy_(h["params"]["opacities"], non_blocking=True)
+            p.colors.copy_(h["params"]["colors"], non_blocking=True)
+            h["late"].record(side)
+            if h["targets"] is not None:
+                self.targets.view(-1).copy_(h["targets"].view(-1), non_blocking=True)
+            h["tgt"].record(side)
+        for k in ("means", "quats", "scales"):
+            getattr(p, k).copy_(h["params"][k], non_blocking=True)
 
     # -- one step, eagerly --------------------------------------------------
     def forward(self):
         v, p = self.views, self.p
+        if self.host is not None:
+            self._upload()
         B.gs_project(v, p.means, p.quats, p.scales, self.eps2d, self.means2d, self.conics, self.depths, self.rects,
                      self.touched, self.K_total)
         self.flags.zero_()
@@ -94,6 +137,8 @@ class BatchRenderer:
                           self.flags)
         if self.longest_first:
             B.gs_tile_order(self.tile_ranges, v.T, self.order_ws, self.tile_order)
+        if self.host is not None:
+            torch.cuda.current_stream().wait_event(self.host["late"])
         if self.C == 3:
             B.gs_rasterize_fwd(v, self.means2d, self.conics, p.opacities, p.colors, self.isect_ids, self.tile_ranges,
                                self.background, self.rgb, self.T_final, self.last_idx, None, self.config)
@@ -105,6 +150,8 @@ class BatchRenderer:
     def loss_grad(self):
         """L = mean((C - target)^2) over every pixel of every view (into
         ``self.loss``, on the device) and dL/dC, in one kernel."""
+        if self.host is not None:
+            torch.cuda.current_stream().wait_event(self.host["tgt"])
         self.loss.zero_()
         B.gs_l2_loss(self.rgb, self.targets, self.inv_norm, self.dL, self.loss)
 
@@ -126,6 +173,8 @@ class BatchRenderer:
                                   self.gc, self.g_op, self.g_col, self.config)
         B.gs_project_bwd(v, p.means, p.quats, p.scales, self.eps2d, self.touched, self.g2, self.gc, self.g_means,
                          self.g_quats, self.g_scales)
+        if self.host is not None:
+            self.loss_host.copy_(self.loss, non_blocking=True)
 
     def step_eager(self):
         self.forward()

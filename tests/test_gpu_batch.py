@@ -146,3 +146,33 @@ def test_batch_views_500k_64_sampled_parity():
 def test_batch_scenes_16x4_sampled_parity():
     w = wl.batch_scenes_16x4()
     _sampled_view_parity(w, [0, 21, 62])
+
+
+def test_host_inputs_are_uploaded_by_every_replay():
+    # a captured step that copies its inputs from pinned host memory, with the late copies on a
+    # second stream, renders exactly what the same step renders from device inputs; a change of the
+    # host tensors between replays reaches the next replay
+    w = _mixed_workload()
+    params, views, ranges, targets = GB.workload_views(w)
+    cap = GB.exact_capacity(params, views, w.eps2d) + 1000
+    ref = GB.BatchRenderer(params, views, cap, targets, w.eps2d, deterministic=True)
+    keys = ("means", "quats", "scales", "opacities", "colors")
+    dev = pipeline.Params(*[torch.full_like(getattr(params, k), 0.5) for k in keys])
+    r = GB.BatchRenderer(dev, views, cap, torch.zeros_like(targets), w.eps2d, deterministic=True)
+    host = {k: getattr(params, k).cpu().pin_memory() for k in keys}
+    r.attach_host_inputs(host, targets.cpu().pin_memory())
+    r.capture()
+    for trial in range(2):
+        if trial == 1:
+            host["colors"].mul_(0.5)
+            host["means"].add_(0.01)
+            params.colors.mul_(0.5)
+            params.means.add_(0.01)
+        ref.step_eager()
+        r.step()
+        torch.cuda.synchronize()
+        assert torch.equal(r.rgb, ref.rgb)
+        # the loss is summed with one atomic per block: equal up to the order of those sums
+        assert float(r.loss_host[0]) == pytest.approx(float(ref.loss.item()), rel=1e-6)
+        for k, g in ref.grads().items():
+            assert rel_l2(np_(r.grads()[k]), np_(g)) <= 1e-6, k

@@ -47,7 +47,7 @@ constexpr int kRec = 9;  // dmu'(2) dconic(3) dopacity(1) dcolor(3)
 // otherwise CTA i renders queue slot i.  Slot qi renders tile tile_order[qi]
 // (identity when tile_order is NULL).
 template <typename S, bool kCull, bool kPersistent>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 6)  // 6 CTAs per SM (40 registers) measured fastest
 k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t* __restrict__ tile_order,
              int* __restrict__ queue, const V2<S>* __restrict__ means2d, const S* __restrict__ conics,
              const S* __restrict__ opacities, const S* __restrict__ colors, const int32_t* __restrict__ isect_ids,

@@ -32,8 +32,9 @@
  *       unit quaternion and chained through the normalisation.
  *   O6  Delta = mu' - pixel centre, so that d sigma / d mu' = Y Delta holds as
  *       printed in Sec. 3.1.
- *   O7  alpha = min(ALPHA_MAX, o exp(-sigma)); a Gaussian with alpha <
- *       ALPHA_MIN is skipped; compositing stops before a Gaussian whose
+ *   O7  alpha = min(ALPHA_MAX, o exp(-sigma)); a Gaussian is skipped unless
+ *       o exp(-sigma) >= ALPHA_MIN (so a NaN opacity is skipped rather than
+ *       clamped to ALPHA_MAX); compositing stops before a Gaussian whose
  *       T (1 - alpha) would fall below T_MIN (that Gaussian is not
  *       composited); sigma < 0 is skipped.  d alpha/d(o, sigma) = 0 where the
  *       clamp is active.  Background b adds T_final * b.
@@ -362,7 +363,7 @@ static int64_t composite_pixel(int px, int py, const int64_t* list, int64_t m,
         const double alpha = raw < OR_ALPHA_MAX ? raw : OR_ALPHA_MAX;
         mg = fmin(mg, fabs(raw - OR_ALPHA_MIN) / OR_ALPHA_MIN);
         mg = fmin(mg, fabs(raw - OR_ALPHA_MAX) / OR_ALPHA_MAX);
-        if (alpha < OR_ALPHA_MIN) continue;
+        if (!(raw >= OR_ALPHA_MIN)) continue; /* O7: also skips a non-finite o e^-sigma */
         const double Tn = T * (1.0 - alpha);
         mg = fmin(mg, fabs(Tn - OR_T_MIN) / OR_T_MIN);
         if (Tn < OR_T_MIN) break;

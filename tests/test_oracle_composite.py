@@ -278,3 +278,24 @@ def test_multichannel_gradients_match_finite_differences():
         fd = (np.sum(G * oracle.rasterize(proj, op_p, col, W, H)["rgb"].reshape(-1, 2)) -
               np.sum(G * oracle.rasterize(proj, op_m, col, W, H)["rgb"].reshape(-1, 2))) / (2 * h)
         assert g["opacities"][n] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+
+
+def test_non_finite_opacity_is_skipped():
+    # Reading O7: a Gaussian is composited only if o exp(-sigma) >= 1/255, a test NaN fails; the
+    # clamp to 0.99 must not turn a NaN opacity into an opaque Gaussian
+    w = wl.small_case(14, 60, 40, 32, log_scale_mu=-2.0)
+    cam, sc = w.views[0].camera, w.scenes[0]
+    proj = oracle.project(cam, sc.means, sc.quats, sc.scales, w.eps2d)
+    op = np.array(sc.opacities, np.float64)
+    hit = int(np.argmax(proj["valid"]))
+    op_nan = op.copy()
+    op_nan[hit] = np.nan
+    op_zero = op.copy()
+    op_zero[hit] = 0.0
+    a = oracle.rasterize(proj, op_nan, sc.colors, cam.width, cam.height)
+    b = oracle.rasterize(proj, op_zero, sc.colors, cam.width, cam.height)
+    np.testing.assert_array_equal(a["rgb"], b["rgb"])
+    np.testing.assert_array_equal(a["T_final"], b["T_final"])
+    G = np.random.default_rng(2).standard_normal((cam.height, cam.width, 3))
+    ga = oracle.rasterize_bwd(proj, op_nan, sc.colors, cam.width, cam.height, G)
+    assert np.isfinite(ga["means2d"]).all() and ga["opacities"][hit] == 0.0

@@ -103,10 +103,12 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                     const V4<S> xy = sh_xy[j];
                     S u;
                     const S p2 = neg_sigma_log2(sh_q[j], xy.x - t.cx, xy.y - t.cy, u);
-                    const S alpha = fmin(RT<S>::alpha_max(), mul_rn(xy.z, RT<S>::ex2(p2)));
+                    const S raw = mul_rn(xy.z, RT<S>::ex2(p2));
+                    const S alpha = fmin(RT<S>::alpha_max(), raw);
                     const S Tn = T * (S(1) - alpha);
-                    // p2 > 0 means sigma < 0 (not a positive-definite conic): skipped
-                    const bool take = !done && p2 <= S(0) && alpha >= RT<S>::alpha_min();
+                    // p2 > 0 means sigma < 0 (not a positive-definite conic): skipped; the alpha test
+                    // is on o e^-sigma before the clamp, so a NaN opacity is skipped too
+                    const bool take = !done && p2 <= S(0) && raw >= RT<S>::alpha_min();
                     const bool stop = take && Tn < RT<S>::t_min();  // not composited; the pixel is finished
                     const bool comp = take && !stop;
                     done = done || stop;
@@ -292,7 +294,7 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                         const S ge = RT<S>::ex2(p2);  // exp(-sigma)
                         const S raw = mul_rn(xy.z, ge);
                         const S alpha = fmin(RT<S>::alpha_max(), raw);
-                        const bool contrib = (b0 + j <= last) && (p2 <= S(0)) && (alpha >= RT<S>::alpha_min());
+                        const bool contrib = (b0 + j <= last) && (p2 <= S(0)) && (raw >= RT<S>::alpha_min());
                         const unsigned cm = __ballot_sync(kFull, contrib);
                         if (cm == 0u) continue;
                         const S inv1ma = RT<S>::rcp(S(1) - alpha);

@@ -101,9 +101,10 @@ k_raster_fwd_nc(const GsView* __restrict__ views, int V, int T_total, const int3
                     const float4 xy = sh_xy[j];
                     float u;
                     const float p2 = neg_sigma_log2(sh_q[j], xy.x - t.cx, xy.y - t.cy, u);
-                    const float alpha = fminf(RT<float>::alpha_max(), mul_rn(xy.z, RT<float>::ex2(p2)));
+                    const float raw = mul_rn(xy.z, RT<float>::ex2(p2));
+                    const float alpha = fminf(RT<float>::alpha_max(), raw);
                     const float Tn = T * (1.f - alpha);
-                    const bool take = !done && p2 <= 0.f && alpha >= RT<float>::alpha_min();
+                    const bool take = !done && p2 <= 0.f && raw >= RT<float>::alpha_min();
                     const bool stop = take && Tn < RT<float>::t_min();
                     const bool comp = take && !stop;
                     done = done || stop;
@@ -232,7 +233,7 @@ k_raster_bwd_nc(const GsView* __restrict__ views, int V, int T_total, const int3
                         const float ge = RT<float>::ex2(p2);
                         const float raw = mul_rn(xy.z, ge);
                         const float alpha = fminf(RT<float>::alpha_max(), raw);
-                        const bool contrib = (b0 + j <= last) && (p2 <= 0.f) && (alpha >= RT<float>::alpha_min());
+                        const bool contrib = (b0 + j <= last) && (p2 <= 0.f) && (raw >= RT<float>::alpha_min());
                         const unsigned cm = __ballot_sync(kFull, contrib);
                         if (cm == 0u) continue;
                         const float inv1ma = RT<float>::rcp(1.f - alpha);

@@ -357,3 +357,37 @@ def test_full_size_1080p_sampled_pixels():
         assert rel_l2(np_(g2[k]), ob[k]) <= GRAD_TOL, k
     # properties at every pixel
     assert np.isfinite(img).all() and (Tf > 0).all() and (Tf <= 1).all()
+
+
+def test_non_finite_parameters_are_culled_or_skipped():
+    # NaN / Inf means and scales, a zero quaternion (culled at projection, Reading O1) and a NaN
+    # opacity (skipped at compositing, Reading O7) among ordinary Gaussians: the image equals the
+    # oracle's and the one without those Gaussians; every gradient is finite
+    w = wl.small_case(15, 400, 64, 48, log_scale_mu=-2.4)
+    cam, sc = w.views[0].camera, w.scenes[0]
+    bad_ids = [3, 17, 41, 77, 123]
+    for k in ("means", "quats", "scales", "opacities", "colors"):
+        setattr(sc, k, np.array(getattr(sc, k)))
+    sc.means[3] = np.nan
+    sc.scales[17] = [np.inf, 0.1, 0.1]
+    sc.quats[41] = 0.0
+    sc.opacities[77] = np.nan
+    sc.means[123, 2] = np.inf
+    G = np.random.default_rng(4).standard_normal((cam.height, cam.width, 3)).astype(np.float32)
+    f, p, g = run_gpu(w, dL_drgb=G.reshape(-1, 3))
+    touched = np_(f.touched)
+    assert all(touched[i] == 0 for i in (3, 17, 41, 123))
+    o = oracle.render(cam, sc, w.eps2d)
+    bad = uncertain_pixels(o, o["proj"], cam.width, cam.height, sc.opacities)
+    img, T, _ = view_image(f)
+    assert np.isfinite(img).all() and np.isfinite(T).all()
+    assert np.abs(img - o["rgb"])[~bad].max() <= IMG_TOL
+    keep = np.setdiff1d(np.arange(sc.n), bad_ids)
+    clean = wl.Workload("clean", [wl.Scene(*[np.ascontiguousarray(getattr(sc, k)[keep]) for k in
+                                              ("means", "quats", "scales", "opacities", "colors")])],
+                        w.views, None)
+    fc, _, _ = run_gpu(clean)
+    img_c, T_c, _ = view_image(fc)
+    assert np.abs(img - img_c).max() <= 1e-6
+    for k in ("means2d", "conics", "means", "quats", "scales", "opacities", "colors"):
+        assert np.isfinite(np_(g[k])[keep if g[k].shape[0] == sc.n else slice(None)]).all(), k

@@ -45,8 +45,10 @@ constexpr int kRec = 9;  // dmu'(2) dconic(3) dopacity(1) dcolor(3)
 // kPersistent: a grid of a few CTAs per SM pops tiles from the global queue
 // counter `queue` (zeroed before launch) until T_total tiles are taken;
 // otherwise CTA i renders queue slot i.  Slot qi renders tile tile_order[qi]
-// (identity when tile_order is NULL).
-template <typename S, bool kCull, bool kPersistent>
+// (identity when tile_order is NULL).  kCount: also count each pixel's
+// composited Gaussians into n_contrib (a separate instantiation, so that the
+// usual walk carries no counter).
+template <typename S, bool kCull, bool kPersistent, bool kCount>
 __global__ void __launch_bounds__(256, 6)  // 6 CTAs per SM (40 registers) measured fastest
 k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t* __restrict__ tile_order,
              int* __restrict__ queue, const V2<S>* __restrict__ means2d, const S* __restrict__ conics,
@@ -119,7 +121,7 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                     C2 = fma(wgt, c.z, C2);
                     T = comp ? Tn : T;
                     last = comp ? b0 + j : last;
-                    count += comp;
+                    if (kCount) count += comp;
                 }
                 if (__all_sync(kFull, done)) break;
             }
@@ -132,7 +134,7 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
             out_rgb[3 * t.pix + 2] = fma(T, bg2, C2);
             T_final[t.pix] = T;
             last_idx[t.pix] = last;
-            if (n_contrib) n_contrib[t.pix] = count;
+            if (kCount) n_contrib[t.pix] = count;
         }
         if (!kPersistent) break;
     }
@@ -463,8 +465,13 @@ static int rasterize_fwd_impl(const char* who, const GsView* views, int32_t V, i
     if (T_total == 0) return GS_OK;
     cudaStream_t s = as_stream(stream);
     const bool cull = cull_enabled(), pers = config && config->persistent;
-    auto kern = cull ? (pers ? k_raster_fwd<S, true, true> : k_raster_fwd<S, true, false>)
-                     : (pers ? k_raster_fwd<S, false, true> : k_raster_fwd<S, false, false>);
+    using KF = decltype(&k_raster_fwd<S, true, true, true>);
+    static const KF table[2][2][2] = {
+        {{k_raster_fwd<S, false, false, false>, k_raster_fwd<S, false, false, true>},
+         {k_raster_fwd<S, false, true, false>, k_raster_fwd<S, false, true, true>}},
+        {{k_raster_fwd<S, true, false, false>, k_raster_fwd<S, true, false, true>},
+         {k_raster_fwd<S, true, true, false>, k_raster_fwd<S, true, true, true>}}};
+    const KF kern = table[cull][pers][n_contrib != nullptr];
     unsigned grid;
     if (int rc = raster_grid(kern, config, T_total, &grid)) return rc;
     int* queue = pers ? config->queue : nullptr;

@@ -24,8 +24,10 @@
 namespace gs {
 
 constexpr int kRT = 256;              // threads per radix block
-constexpr int kRI = 16;               // items per thread
-constexpr int kRTile = kRT * kRI;     // items per radix block
+// Items per thread of a radix pass (a template parameter): 16 for long
+// sorts, 8 for short ones, whose blocks are then small enough to fill the GPU.
+constexpr int kRIShort = 8, kRILong = 16;
+constexpr int kRTileMin = kRT * kRIShort;  // the smallest radix block (sizes the histogram)
 constexpr int kRWarps = kRT / 32;
 constexpr int kMaxBins = 256;         // digits of at most 8 bits
 constexpr int kScanThreads = 1024;
@@ -76,10 +78,12 @@ __device__ __forceinline__ T block_exclusive_scan_256(T x, T* total)
 // radix sort passes (uint32 keys, uint32 values)
 // ---------------------------------------------------------------------------
 
+template <int kRI>
 __global__ void __launch_bounds__(kRT)
 k_radix_hist(const uint32_t* __restrict__ keys, const int32_t* __restrict__ count_dev, int64_t count_static,
              int64_t cap, int shift, int bits, uint32_t* __restrict__ hist)
 {
+    constexpr int kRTile = kRT * kRI;
     pdl_wait();
     pdl_trigger();
     __shared__ uint32_t h[kRWarps][kMaxBins];
@@ -109,10 +113,12 @@ k_radix_hist(const uint32_t* __restrict__ keys, const int32_t* __restrict__ coun
 
 // One block per digit: exclusive scan of that digit's per-block counts (in
 // place) and the digit total.
+template <int kRI>
 __global__ void __launch_bounds__(kRT)
 k_radix_scan_rows(uint32_t* __restrict__ hist, const int32_t* __restrict__ count_dev, int64_t count_static,
                   int64_t cap, uint32_t* __restrict__ digit_total)
 {
+    constexpr int kRTile = kRT * kRI;
     pdl_wait();
     pdl_trigger();
     const int count = item_count(count_dev, count_static, cap);
@@ -135,6 +141,7 @@ k_radix_scan_rows(uint32_t* __restrict__ hist, const int32_t* __restrict__ count
 
 // Stable scatter of one block of items by digit.  vals_in == nullptr means
 // "value = input position" (the first pass of a sort of indices).
+template <int kRI>
 __global__ void __launch_bounds__(kRT)
 k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
@@ -143,6 +150,7 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
 {
     pdl_wait();
     pdl_trigger();
+    constexpr int kRTile = kRT * kRI;
     __shared__ uint32_t s_keys[kRTile];
     __shared__ uint32_t s_vals[kRTile];
     __shared__ uint32_t s_warp[kRWarps][kMaxBins];  // per-warp digit counts, then per-warp offsets
@@ -244,10 +252,12 @@ struct RadixBufs {
 // v1 and v2; the values start as vals0, or as the input positions when vals0
 // is null.  The item count is *count_dev (device, clamped to cap) or
 // count_static.  Returns the buffers holding the result.
+template <int kRI>
 static void lsd_sort(uint32_t* k1, uint32_t* k2, uint32_t* v1, uint32_t* v2, const uint32_t* vals0,
                      const int32_t* count_dev, int64_t count_static, int64_t cap, int total_bits,
                      const RadixBufs& rb, cudaStream_t s, uint32_t** keys_out, uint32_t** vals_out)
 {
+    constexpr int kRTile = kRT * kRI;
     uint32_t *kin = k1, *kout = k2, *vout = v1;
     const uint32_t* vin = vals0;
     if (total_bits > 0 && cap > 0) {
@@ -256,9 +266,11 @@ static void lsd_sort(uint32_t* k1, uint32_t* k2, uint32_t* v1, uint32_t* v2, con
         const unsigned grid = (unsigned)((cap + kRTile - 1) / kRTile);
         for (int pass = 0, shift = 0; pass < passes; ++pass, shift += per) {
             const int bits = std::min(per, total_bits - shift);
-            launch_pdl(k_radix_hist, grid, kRT, s, kin, count_dev, count_static, cap, shift, bits, rb.hist);
-            launch_pdl(k_radix_scan_rows, 1u << bits, kRT, s, rb.hist, count_dev, count_static, cap, rb.digit_total);
-            launch_pdl(k_radix_scatter, grid, kRT, s, kin, vin, kout, vout, count_dev, count_static, cap, shift, bits,
+            launch_pdl(k_radix_hist<kRI>, grid, kRT, s, kin, count_dev, count_static, cap, shift, bits, rb.hist);
+            launch_pdl(k_radix_scan_rows<kRI>, 1u << bits, kRT, s, rb.hist, count_dev, count_static, cap,
+                       rb.digit_total);
+            launch_pdl(k_radix_scatter<kRI>, grid, kRT, s, kin, vin, kout, vout, count_dev, count_static, cap, shift,
+                       bits,
                                                  rb.hist, rb.digit_total);
             count_launches(3);
             std::swap(kin, kout);
@@ -481,7 +493,7 @@ static OrderLayout carve_order(void* ws, int64_t T)
     L.kb = c.take<uint32_t>(T);
     L.va = c.take<uint32_t>(T);
     L.vb = c.take<uint32_t>(T);
-    L.hist = c.take<uint32_t>((size_t)((T + kRTile - 1) / kRTile) * kMaxBins + 1);
+    L.hist = c.take<uint32_t>((size_t)((T + kRTileMin - 1) / kRTileMin) * kMaxBins + 1);
     L.digit_total = c.take<uint32_t>(kMaxBins);
     L.bytes = c.used;
     return L;
@@ -511,7 +523,8 @@ static SortLayout carve(void* ws, int64_t P, int64_t cap)
     L.tval_a = c.take<uint32_t>(cap);
     L.tval_b = c.take<uint32_t>(cap);
     L.owner = c.take<uint32_t>(cap);
-    const int64_t nb = (std::max(P, cap) + kRTile - 1) / kRTile;
+    // radix blocks of the depth sort (short blocks) and of the tile sort (long blocks)
+    const int64_t nb = std::max((P + kRTileMin - 1) / kRTileMin, (cap + kRT * kRILong - 1) / (kRT * kRILong));
     L.hist = c.take<uint32_t>((size_t)nb * kMaxBins + 1);
     L.digit_total = c.take<uint32_t>(kMaxBins);
     L.bytes = c.used;
@@ -566,7 +579,7 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
     launch_pdl(k_depth_keys, (unsigned)((P + 255) / 256), 256, s, P, depths, touched, L.dkey_a);
     count_launches(1);
     uint32_t *dk, *order;
-    lsd_sort(L.dkey_a, L.dkey_b, L.dval_a, L.dval_b, nullptr, nullptr, P, P, 31, rb, s, &dk, &order);
+    lsd_sort<kRIShort>(L.dkey_a, L.dkey_b, L.dval_a, L.dval_b, nullptr, nullptr, P, P, 31, rb, s, &dk, &order);
 
     // 2. scan of touched in depth order, K, emission
     const int64_t nblk = (P + kEmitTile - 1) / kEmitTile;
@@ -580,7 +593,7 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
     // 3. stable sort of the pairs by global tile id; the values are the emission indices when the
     //    inverse positions are wanted, else directly the owning projections
     uint32_t *tk, *tv;
-    lsd_sort(L.tkey_a, L.tkey_b, L.tval_a, L.tval_b, isect_pos ? nullptr : L.owner, K_out, 0, K_capacity,
+    lsd_sort<kRILong>(L.tkey_a, L.tkey_b, L.tval_a, L.tval_b, isect_pos ? nullptr : L.owner, K_out, 0, K_capacity,
              bit_length((int64_t)T_total - 1), rb, s, &tk, &tv);
     // 4. projection ids, inverse positions, tile ranges
     launch_pdl(k_finalize, (unsigned)((K_capacity + 255) / 256), 256, s, K_out, K_capacity, tk, tv, L.owner,
@@ -610,7 +623,7 @@ extern "C" int gs_tile_order(const int32_t* tile_ranges, int32_t T_total, void* 
     const unsigned g = (unsigned)((T_total + 255) / 256);
     launch_pdl(k_tile_len_keys, g, 256, s, T_total, reinterpret_cast<const int2*>(tile_ranges), L.ka);
     uint32_t *k, *v;
-    lsd_sort(L.ka, L.kb, L.va, L.vb, nullptr, nullptr, T_total, T_total, 16, RadixBufs{L.hist, L.digit_total}, s, &k,
+    lsd_sort<kRIShort>(L.ka, L.kb, L.va, L.vb, nullptr, nullptr, T_total, T_total, 16, RadixBufs{L.hist, L.digit_total}, s, &k,
              &v);
     launch_pdl(k_copy_u32, g, 256, s, T_total, v, order);
     count_launches(2);

@@ -97,11 +97,16 @@ k_radix_hist(const uint32_t* __restrict__ keys, const int32_t* __restrict__ coun
     for (int i = threadIdx.x; i < kRWarps * kMaxBins; i += kRT) (&h[0][0])[i] = 0;
     __syncthreads();
     const int base = b * kRTile;
-#pragma unroll 4
+    // all loads first (kRI in flight per thread), then the shared-memory counts
+    uint32_t key[kRI];
+#pragma unroll
     for (int k = 0; k < kRI; ++k) {
         const int idx = base + k * kRT + threadIdx.x;
-        if (idx < count) atomicAdd(&h[w][(keys[idx] >> shift) & mask], 1u);
+        key[k] = idx < count ? keys[idx] : 0u;
     }
+#pragma unroll
+    for (int k = 0; k < kRI; ++k)
+        if (base + k * kRT + (int)threadIdx.x < count) atomicAdd(&h[w][(key[k] >> shift) & mask], 1u);
     __syncthreads();
     for (int d = threadIdx.x; d < bins; d += kRT) {
         uint32_t s = 0;
@@ -364,10 +369,12 @@ k_scan_block_sums(int64_t nblk, int64_t* __restrict__ block_sums, int64_t cap, i
 // Emission of the (tile, projection) pairs in depth order: pair j of the
 // projection at depth rank r gets emission index off[r] + j; its key is the
 // global tile id (row-major inside the rectangle), its owner the projection.
-// A block takes kEmitTile consecutive ranks, scans their pair counts into
-// shared memory, and then its threads write consecutive output slots, each
-// finding the rank that owns its slot by binary search -- so the stores of a
-// warp are contiguous whatever the rectangle sizes.
+// A block takes kEmitTile consecutive ranks and scans their pair counts into
+// shared memory.  Each warp then writes the slots of its ranks, 32 ranks at a
+// time: lane L holds the first slot of rank L, and the lanes write 32
+// consecutive slots per round, each finding its owner among the 32 ranks by a
+// five-step shuffle search -- so the stores of a warp are contiguous whatever
+// the rectangle sizes.
 __global__ void __launch_bounds__(256)
 k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __restrict__ order,
        const int32_t* __restrict__ cnt_sorted, const short4* __restrict__ rects, const int64_t* __restrict__ block_prefix,
@@ -380,6 +387,7 @@ k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __res
     __shared__ int s_x0[kEmitTile], s_w[kEmitTile];
     __shared__ int s_row0[kEmitTile];      // tile id of the rectangle's first row start (x = 0)
     __shared__ int s_tx[kEmitTile];        // tiles_x of the projection's view
+    __shared__ float s_iw[kEmitTile];      // 1 / rectangle width
     const int64_t base = (int64_t)blockIdx.x * kEmitTile;
     const int64_t gbase = block_prefix[blockIdx.x];
     int cnt[kEmitItems];
@@ -398,6 +406,7 @@ k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __res
                 const short4 rc = rects[p];
                 s_x0[li] = rc.x;
                 s_w[li] = rc.z - rc.x;
+                s_iw[li] = 1.f / (float)(rc.z - rc.x);
                 s_row0[li] = view.tile_offset + rc.y * view.tiles_x;
                 s_tx[li] = view.tiles_x;
             }
@@ -416,21 +425,36 @@ k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __res
     }
     if (threadIdx.x == 0) s_off[kEmitTile] = total;
     __syncthreads();
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int64_t ge = gbase + e;
-        if (ge >= cap) break;
-        // last rank whose first slot is <= e (ranks with no pairs share it with
-        // the next one; the last of them owns the slot)
-        int lo = 0, hi = kEmitTile - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_off[mid] <= e) lo = mid; else hi = mid - 1;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    constexpr int kPerWarp = kEmitTile / 8;  // ranks per warp
+#pragma unroll 1
+    for (int c = 0; c < kPerWarp; c += 32) {
+        const int r0 = wp * kPerWarp + c;
+        const int my_start = s_off[r0 + lane];
+        const int e_begin = s_off[r0], e_end = s_off[r0 + 32];
+        for (int e = e_begin + lane; e - lane < e_end; e += 32) {
+            // the last of the 32 ranks whose first slot is <= e (ranks with no pairs share it with the
+            // next one; the last of them owns the slot)
+            int lo = 0;
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1) {
+                const int st = __shfl_sync(kFull, my_start, lo + d);
+                if (st <= e) lo += d;
+            }
+            const int64_t ge = gbase + e;
+            if (e < e_end && ge < cap) {
+                const int r = r0 + lo;
+                const int j = e - s_off[r];
+                const int w = s_w[r];
+                // j / w through the reciprocal: the estimate is within one of the quotient (j / w is at
+                // most the rectangle height, < 2^15), and the two integer checks make it exact
+                int dy = (int)((float)j * s_iw[r]);
+                dy -= dy * w > j;
+                dy += (dy + 1) * w <= j;
+                tile_keys[ge] = (uint32_t)(s_row0[r] + dy * s_tx[r] + s_x0[r] + (j - dy * w));
+                owner[ge] = s_p[r];
+            }
         }
-        const int j = e - s_off[lo];
-        const int w = s_w[lo];
-        const int dy = j / w;
-        tile_keys[ge] = (uint32_t)(s_row0[lo] + dy * s_tx[lo] + s_x0[lo] + (j - dy * w));
-        owner[ge] = s_p[lo];
     }
 }
 

@@ -68,12 +68,20 @@ class BatchRenderer:
         self.loss = e(1)
         nbw = B.gs_rasterize_bwd_workspace_size(self.cap, deterministic)
         self.bwd_ws = e(nbw, dtype=torch.uint8) if nbw else None
-        self.g2, self.gc = e(max(P, 1), 2), e(max(P, 1), 3)
+        # every gradient buffer the step zeroes lives in one allocation, cleared by one fill
         self.owns_grads = shared_grads is None
+        Pm, Nm = max(P, 1), max(N, 1)
+        shapes = [("g2", (Pm, 2)), ("gc", (Pm, 3))]
         if self.owns_grads:
-            self.g_op, self.g_col = e(max(N, 1)), e(max(N, 1), C)
-            self.g_means, self.g_quats, self.g_scales = e(max(N, 1), 3), e(max(N, 1), 4), e(max(N, 1), 3)
-        else:
+            shapes += [("g_op", (Nm,)), ("g_col", (Nm, C)), ("g_means", (Nm, 3)), ("g_quats", (Nm, 4)),
+                       ("g_scales", (Nm, 3))]
+        self.grad_flat = e(sum(int(np.prod(sh)) for _, sh in shapes))
+        off = 0
+        for name, sh in shapes:
+            n = int(np.prod(sh))
+            setattr(self, name, self.grad_flat[off:off + n].view(*sh))
+            off += n
+        if not self.owns_grads:
             sg = shared_grads
             self.g_op, self.g_col = sg["opacities"], sg["colors"]
             self.g_means, self.g_quats, self.g_scales = sg["means"], sg["quats"], sg["scales"]
@@ -157,11 +165,7 @@ class BatchRenderer:
 
     def backward(self):
         v, p = self.views, self.p
-        self.g2.zero_()
-        self.gc.zero_()
-        if self.owns_grads:
-            for t in (self.g_op, self.g_col, self.g_means, self.g_quats, self.g_scales):
-                t.zero_()
+        self.grad_flat.zero_()
         if self.C == 3:
             B.gs_rasterize_bwd(v, self.means2d, self.conics, p.opacities, p.colors, self.isect_ids, self.isect_pos,
                                self.emit_start, self.touched, self.tile_ranges, self.K, self.cap, self.background,

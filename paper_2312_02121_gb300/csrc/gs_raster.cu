@@ -22,12 +22,12 @@
 // The backward walks the same batches in reverse from each pixel's last
 // composited Gaussian, rebuilding T_n from the saved T_final (Sec. 3.1).  The
 // nine per-pixel gradient terms of a Gaussian are summed over the warp
-// through a shared-memory transpose, then over the tile's warps -- with
-// shared atomics (fast mode) or per-warp slots summed in a fixed order
-// (deterministic mode) -- giving one partial per (tile, Gaussian).  The fast
-// mode adds the partials straight into the per-projection outputs with
-// global atomics; the deterministic mode writes them as records that a
-// second kernel sums per projection in emission order.
+// through a shared-memory transpose into the warp's own slot for that
+// Gaussian (plain stores), and the slots of the tile's warps are summed in a
+// fixed order, giving one partial per (tile, Gaussian).  The fast mode adds
+// the partials straight into the per-projection outputs with global atomics;
+// the deterministic mode writes them as records that a second kernel sums per
+// projection in emission order.
 //
 // Everything is templated on the scalar type: fp32 is the fast path, fp64
 // (smaller batches, exp2 instead of the SFU) serves the gs_*_f64 entry points
@@ -205,11 +205,10 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
 {
     pdl_wait();
     pdl_trigger();
-    // deterministic: one partial slot per warp, summed in warp order; fast:
-    // one slot per Gaussian, accumulated with shared-memory atomics (less
-    // shared memory, so larger batches)
-    constexpr int kB = kAtomic ? RT<S>::kBwdFast : RT<S>::kBwdDet;
-    constexpr int kSlots = kAtomic ? 1 : kWarps;
+    // one partial slot per (warp, Gaussian), written with plain stores and summed in warp order at
+    // the flush (shared-memory atomics into one slot per Gaussian were measured 8 % slower)
+    constexpr int kB = RT<S>::kBwdBatch;
+    constexpr int kSlots = kWarps;
     __shared__ V4<S> sh_xy[kB], sh_q[kB], sh_col[kB], sh_cull[kB];
     __shared__ S s_grad[kSlots][kB][kRec];
     __shared__ unsigned s_mask[kSlots][(kB + 31) / 32];
@@ -258,10 +257,6 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
         for (int k = nbatch - 1; k >= 0; --k) {
             const int b0 = range.x + k * kB;
             const int n = min(kB, maxlast - b0 + 1);
-            if (kAtomic) {
-                for (int i = threadIdx.x; i < kB * kRec; i += blockDim.x) (&s_grad[0][0][0])[i] = S(0);
-                if (threadIdx.x < (kB + 31) / 32) s_mask[0][threadIdx.x] = 0u;
-            }
             if (threadIdx.x < n) {
                 const int p = isect_ids[b0 + threadIdx.x];
                 const int64_t g = p + t.g_shift;
@@ -323,32 +318,14 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                         r[7] = wgt * g1;
                         r[8] = wgt * g2;
                         chunk_mask |= 1u << hb;
-                        S* slot = s_grad[kAtomic ? 0 : w][j];
-                        if (__popc(cm) == 1) {
-                            // one contributing pixel: its terms are the warp's sum
-                            if (contrib) {
-#pragma unroll
-                                for (int q = 0; q < kRec; ++q) {
-                                    if (kAtomic) atomicAdd(slot + q, r[q]);
-                                    else slot[q] = r[q];
-                                }
-                            }
-                        } else {
-                            const S tot = warp_sum9<S>(r, s_red[w], lane, rl);
-                            if (lane < 3 * kRec && rl.part == 0) {
-                                if (kAtomic) atomicAdd(slot + rl.q, tot);
-                                else slot[rl.q] = tot;
-                            }
-                        }
+                        // the warp's sum of each term, into the warp's own slot for this Gaussian (a
+                        // lone contributing lane is not special-cased: the transpose is cheaper than its
+                        // nine dependent stores)
+                        const S tot = warp_sum9<S>(r, s_red[w], lane, rl);
+                        if (lane < 3 * kRec && rl.part == 0) s_grad[w][j][rl.q] = tot;
                     }
                 }
-                if (lane == 0) {
-                    if (kAtomic) {
-                        if (chunk_mask) atomicOr(&s_mask[0][s >> 5], chunk_mask);
-                    } else {
-                        s_mask[w][s >> 5] = chunk_mask;
-                    }
-                }
+                if (lane == 0) s_mask[w][s >> 5] = chunk_mask;
             }
             __syncthreads();
             // fixed-order sum over warps: one (tile, Gaussian) partial

@@ -16,8 +16,7 @@ constexpr int kWarps = 8;
 template <typename S> struct RT;  // per-scalar constants and primitives
 template <> struct RT<float> {
     static constexpr int kFwdBatch = 256;
-    static constexpr int kBwdFast = 256;   // Gaussians per batch, fast backward
-    static constexpr int kBwdDet = 64;     // deterministic backward (per-warp slots)
+    static constexpr int kBwdBatch = 96;   // Gaussians per backward batch (per-warp partial slots)
     static constexpr float kLog2e = 1.4426950408889634f;
     __device__ static float alpha_min() { return GS_ALPHA_MIN; }
     __device__ static float alpha_max() { return GS_ALPHA_MAX; }
@@ -35,8 +34,7 @@ template <> struct RT<float> {
 };
 template <> struct RT<double> {
     static constexpr int kFwdBatch = 128;
-    static constexpr int kBwdFast = 64;
-    static constexpr int kBwdDet = 32;
+    static constexpr int kBwdBatch = 32;
     static constexpr double kLog2e = 1.4426950408889634;
     __device__ static double alpha_min() { return 1.0 / 255.0; }
     __device__ static double alpha_max() { return 0.99; }

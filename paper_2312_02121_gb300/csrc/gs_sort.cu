@@ -256,11 +256,13 @@ struct RadixBufs {
 // passes of at most 8 bits.  Keys ping-pong between k1 and k2, values between
 // v1 and v2; the values start as vals0, or as the input positions when vals0
 // is null.  The item count is *count_dev (device, clamped to cap) or
-// count_static.  Returns the buffers holding the result.
+// count_static.  The last pass writes its values to vals_last when that is
+// given.  Returns the buffers holding the result.
 template <int kRI>
 static void lsd_sort(uint32_t* k1, uint32_t* k2, uint32_t* v1, uint32_t* v2, const uint32_t* vals0,
                      const int32_t* count_dev, int64_t count_static, int64_t cap, int total_bits,
-                     const RadixBufs& rb, cudaStream_t s, uint32_t** keys_out, uint32_t** vals_out)
+                     const RadixBufs& rb, cudaStream_t s, uint32_t** keys_out, uint32_t** vals_out,
+                     uint32_t* vals_last = nullptr)
 {
     constexpr int kRTile = kRT * kRI;
     uint32_t *kin = k1, *kout = k2, *vout = v1;
@@ -271,12 +273,12 @@ static void lsd_sort(uint32_t* k1, uint32_t* k2, uint32_t* v1, uint32_t* v2, con
         const unsigned grid = (unsigned)((cap + kRTile - 1) / kRTile);
         for (int pass = 0, shift = 0; pass < passes; ++pass, shift += per) {
             const int bits = std::min(per, total_bits - shift);
+            if (vals_last && pass == passes - 1) vout = vals_last;
             launch_pdl(k_radix_hist<kRI>, grid, kRT, s, kin, count_dev, count_static, cap, shift, bits, rb.hist);
             launch_pdl(k_radix_scan_rows<kRI>, 1u << bits, kRT, s, rb.hist, count_dev, count_static, cap,
                        rb.digit_total);
             launch_pdl(k_radix_scatter<kRI>, grid, kRT, s, kin, vin, kout, vout, count_dev, count_static, cap, shift,
-                       bits,
-                                                 rb.hist, rb.digit_total);
+                       bits, rb.hist, rb.digit_total);
             count_launches(3);
             std::swap(kin, kout);
             vin = vout;
@@ -461,7 +463,7 @@ k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __res
 // Sorted pairs -> projection ids, inverse positions and per-tile ranges.  The
 // sorted values are emission indices when isect_pos is wanted (their owners
 // are gathered and the inverse permutation is scattered), else the owners
-// themselves.
+// themselves, which the last radix pass already wrote into isect_ids.
 __global__ void k_finalize(const int32_t* __restrict__ K_dev, int64_t cap, const uint32_t* __restrict__ keys,
                            const uint32_t* __restrict__ vals, const uint32_t* __restrict__ owner,
                            int32_t* __restrict__ isect_ids, int32_t* __restrict__ isect_pos,
@@ -476,8 +478,8 @@ __global__ void k_finalize(const int32_t* __restrict__ K_dev, int64_t cap, const
         const uint32_t e = vals[i];
         isect_ids[i] = (int32_t)owner[e];
         isect_pos[e] = i;
-    } else {
-        isect_ids[i] = (int32_t)vals[i];
+    } else if (vals != reinterpret_cast<const uint32_t*>(isect_ids)) {
+        isect_ids[i] = (int32_t)vals[i];  // only when no pass ran (a single tile: zero key bits)
     }
     const uint32_t t = keys[i];
     if (i == 0 || keys[i - 1] != t) tile_ranges[t].x = i;
@@ -616,9 +618,11 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
 
     // 3. stable sort of the pairs by global tile id; the values are the emission indices when the
     //    inverse positions are wanted, else directly the owning projections
+    //    (in the latter case the last pass writes them straight into isect_ids)
     uint32_t *tk, *tv;
     lsd_sort<kRILong>(L.tkey_a, L.tkey_b, L.tval_a, L.tval_b, isect_pos ? nullptr : L.owner, K_out, 0, K_capacity,
-             bit_length((int64_t)T_total - 1), rb, s, &tk, &tv);
+                      bit_length((int64_t)T_total - 1), rb, s, &tk, &tv,
+                      isect_pos ? nullptr : reinterpret_cast<uint32_t*>(isect_ids));
     // 4. projection ids, inverse positions, tile ranges
     launch_pdl(k_finalize, (unsigned)((K_capacity + 255) / 256), 256, s, K_out, K_capacity, tk, tv, L.owner,
                isect_ids, isect_pos, reinterpret_cast<int2*>(tile_ranges));

@@ -189,6 +189,54 @@ __device__ __forceinline__ S warp_sum9(const S (&r)[kRec], S* buf, int lane, Red
     return acc + (a1 + a2);  // lane 3q: part 0 + (part 1 + part 2)
 }
 
+// One (tile, Gaussian) partial of a walked batch: the fixed-order sum of the
+// warps' slots, turned into dL/dmu' and the packed dL/dconic, added to the
+// outputs (fast mode) or written as a record (deterministic mode).  fl holds
+// the Gaussian's (a, b, D, stashed projection) from its staging.
+template <typename S, bool kAtomic, int kB>
+__device__ __forceinline__ void flush_partial(int j, int b0, const S (*s_grad)[kB][kRec],
+                                              const unsigned (*s_mask)[(kB + 31) / 32], V4<S> fl,
+                                              int64_t g_shift, S* __restrict__ records,
+                                              V2<S>* __restrict__ dL_dmeans2d, S* __restrict__ dL_dconics,
+                                              S* __restrict__ dL_dopacities, S* __restrict__ dL_dcolors)
+{
+    S acc[kRec];
+#pragma unroll
+    for (int q = 0; q < kRec; ++q) acc[q] = S(0);
+    bool any = false;
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww)
+        if (s_mask[ww][j >> 5] & (1u << (j & 31))) {
+            any = true;
+#pragma unroll
+            for (int q = 0; q < kRec; ++q) acc[q] += s_grad[ww][j][q];
+        }
+    // from the reduced sums to dL/dmu' and the packed dL/dconic (see the walk)
+    const S su = acc[0], sdy = acc[1];
+    acc[0] = fl.x * su;
+    acc[1] = fma(fl.y, su, fl.z * sdy);
+    acc[2] *= S(0.5);
+    acc[4] *= S(0.5);
+    if (kAtomic) {
+        if (any) {
+            const int p = RT<S>::unstash(fl.w);
+            const int64_t g = p + g_shift;
+            atomic_add2(dL_dmeans2d + p, acc[0], acc[1]);
+            atomicAdd(dL_dconics + 3 * p + 0, acc[2]);
+            atomicAdd(dL_dconics + 3 * p + 1, acc[3]);
+            atomicAdd(dL_dconics + 3 * p + 2, acc[4]);
+            atomicAdd(dL_dopacities + g, acc[5]);
+            atomicAdd(dL_dcolors + 3 * g + 0, acc[6]);
+            atomicAdd(dL_dcolors + 3 * g + 1, acc[7]);
+            atomicAdd(dL_dcolors + 3 * g + 2, acc[8]);
+        }
+    } else {
+        S* rec = records + (size_t)(b0 + j) * kRec;
+#pragma unroll
+        for (int q = 0; q < kRec; ++q) rec[q] = acc[q];
+    }
+}
+
 // kAtomic: each (tile, Gaussian) partial is added straight into the
 // per-projection outputs with reduction atomics (fast; the summation order
 // across tiles varies).  Otherwise it is written as a record for
@@ -212,6 +260,7 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
     __shared__ V4<S> sh_xy[kB], sh_q[kB], sh_col[kB], sh_cull[kB];
     __shared__ S s_grad[kSlots][kB][kRec];
     __shared__ unsigned s_mask[kSlots][(kB + 31) / 32];
+    __shared__ V4<S> s_fl[2][kB];  // (a, b, D, projection) of the last two staged batches, for the flush
     __shared__ __align__(16) S s_red[kWarps][32 * kRedStride];
     __shared__ int s_maxlast[kWarps];
     __shared__ int s_next;
@@ -253,7 +302,11 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
 #pragma unroll
         for (int i = 1; i < kWarps; ++i) maxlast = max(maxlast, s_maxlast[i]);
 
+        // batches walk back to front; the flush of a walked batch runs on threads [kB, 2 kB) while
+        // threads [0, kB) stage the next one, so that it costs no barrier of its own
+        static_assert(2 * kB <= 256, "staging and flush share the block");
         const int nbatch = maxlast >= range.x ? (maxlast - range.x) / kB + 1 : 0;
+        int prev_b0 = 0, prev_n = 0;
         for (int k = nbatch - 1; k >= 0; --k) {
             const int b0 = range.x + k * kB;
             const int n = min(kB, maxlast - b0 + 1);
@@ -263,7 +316,12 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                 stage_gaussian<S>(sh_xy, sh_q, sh_col, sh_cull, threadIdx.x, means2d[p], conics[3 * p],
                                   conics[3 * p + 1], conics[3 * p + 2], opacities[g], colors[3 * g],
                                   colors[3 * g + 1], colors[3 * g + 2]);
-                sh_cull[threadIdx.x].w = RT<S>::stash(p);  // the projection, for the atomic flush
+                s_fl[k & 1][threadIdx.x] = mk4<S>(sh_xy[threadIdx.x].w, sh_q[threadIdx.x].w, sh_col[threadIdx.x].w,
+                                                  RT<S>::stash(p));
+            } else if (threadIdx.x >= kB && threadIdx.x < kB + prev_n) {
+                const int j = threadIdx.x - kB;
+                flush_partial<S, kAtomic, kB>(j, prev_b0, s_grad, s_mask, s_fl[(k + 1) & 1][j], t.g_shift, records,
+                                              dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors);
             }
             __syncthreads();
             // this warp only needs entries up to its own last index
@@ -328,50 +386,13 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                 if (lane == 0) s_mask[w][s >> 5] = chunk_mask;
             }
             __syncthreads();
-            // fixed-order sum over warps: one (tile, Gaussian) partial
-            if (threadIdx.x < n) {
-                const int j = threadIdx.x;
-                S acc[kRec];
-#pragma unroll
-                for (int q = 0; q < kRec; ++q) acc[q] = S(0);
-                bool any = false;
-#pragma unroll
-                for (int ww = 0; ww < kSlots; ++ww)
-                    if (s_mask[ww][j >> 5] & (1u << (j & 31))) {
-                        any = true;
-#pragma unroll
-                        for (int q = 0; q < kRec; ++q) acc[q] += s_grad[ww][j][q];
-                    }
-                {
-                    // from the reduced sums to dL/dmu' and the packed dL/dconic (see the walk)
-                    const S a = sh_xy[j].w, b = sh_q[j].w, D = sh_col[j].w;
-                    const S su = acc[0], sdy = acc[1];
-                    acc[0] = a * su;
-                    acc[1] = fma(b, su, D * sdy);
-                    acc[2] *= S(0.5);
-                    acc[4] *= S(0.5);
-                }
-                if (kAtomic) {
-                    if (any) {
-                        const int p = RT<S>::unstash(sh_cull[j].w);
-                        const int64_t g = p + t.g_shift;
-                        atomic_add2(dL_dmeans2d + p, acc[0], acc[1]);
-                        atomicAdd(dL_dconics + 3 * p + 0, acc[2]);
-                        atomicAdd(dL_dconics + 3 * p + 1, acc[3]);
-                        atomicAdd(dL_dconics + 3 * p + 2, acc[4]);
-                        atomicAdd(dL_dopacities + g, acc[5]);
-                        atomicAdd(dL_dcolors + 3 * g + 0, acc[6]);
-                        atomicAdd(dL_dcolors + 3 * g + 1, acc[7]);
-                        atomicAdd(dL_dcolors + 3 * g + 2, acc[8]);
-                    }
-                } else {
-                    S* rec = records + (size_t)(b0 + j) * kRec;
-#pragma unroll
-                    for (int q = 0; q < kRec; ++q) rec[q] = acc[q];
-                }
-            }
             __syncthreads();
+            prev_b0 = b0;
+            prev_n = n;
         }
+        if (threadIdx.x < prev_n)  // the last walked batch (batch 0)
+            flush_partial<S, kAtomic, kB>(threadIdx.x, prev_b0, s_grad, s_mask, s_fl[0][threadIdx.x], t.g_shift,
+                                          records, dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors);
         if (!kAtomic) {
             // Gaussians after every pixel's last one received nothing
             const int first_unused = max(range.x, maxlast + 1);

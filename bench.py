@@ -452,6 +452,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     stages = ["project", "bin_and_sort", "rasterize_fwd", "loss_grad", "rasterize_bwd", "project_bwd"]
     last_state = {}
+    # the forward hands its per-pair warp-box cull to the backward through this buffer
+    hits_cfg = B.RasterConfig(device=dev, warp_hits=torch.empty(cap, dtype=torch.int32, device=dev))
 
     def step(ev=None):
         def mark(i):
@@ -472,7 +474,7 @@ def run_ours(args, rank, world, local_rank):
         Tf = torch.empty(pixels, device=dev)
         last = torch.empty(pixels, dtype=torch.int32, device=dev)
         B.gs_rasterize_fwd(views, pr["means2d"], pr["conics"], params.opacities, params.colors, ids, tr, None, rgb,
-                           Tf, last)
+                           Tf, last, None, hits_cfg)
         mark(3)
         dL = torch.empty(pixels, 3, device=dev)
         B.gs_l2_loss(rgb, target, 1.0 / rgb.numel(), dL, None)
@@ -485,7 +487,7 @@ def run_ours(args, rank, world, local_rank):
         gm, gq = gz[5 * P + 4 * N:5 * P + 7 * N].view(N, 3), gz[5 * P + 7 * N:5 * P + 11 * N].view(N, 4)
         gs = gz[5 * P + 11 * N:].view(N, 3)
         B.gs_rasterize_bwd(views, pr["means2d"], pr["conics"], params.opacities, params.colors, ids, None, None,
-                           pr["touched"], tr, Kd, cap, None, Tf, last, dL, False, None, g2, gc, go, gcol, None)
+                           pr["touched"], tr, Kd, cap, None, Tf, last, dL, False, None, g2, gc, go, gcol, hits_cfg)
         mark(5)
         B.gs_project_bwd(views, params.means, params.quats, params.scales, w.eps2d, pr["touched"], g2, gc, gm, gq, gs)
         mark(6)

@@ -213,6 +213,14 @@ typedef struct GsRasterConfig {
                                    NULL = tile id order */
     int32_t* queue;             /* device int32 counter the persistent grid pops from; required
                                    when persistent; the call zeroes it on its stream */
+    uint32_t* warp_hits;        /* device [K_capacity] 32-bit words, nullable (3-channel
+                                   kernels): the forward records, for every chunk of 32 sorted
+                                   pairs of a tile, which of them each of the tile's 8 warp boxes
+                                   (8x4 pixels each) can be reached by (word w of the chunk holds
+                                   box w's 32 bits), and the backward reads that instead of
+                                   repeating the same test.  Give the backward the buffer the
+                                   forward of the same frame filled; words the forward had no
+                                   use for are left as they were. */
 } GsRasterConfig;
 
 /* Bytes of scratch gs_tile_order needs for T_total tiles. */

@@ -85,9 +85,12 @@ class BatchRenderer:
             sg = shared_grads
             self.g_op, self.g_col = sg["opacities"], sg["colors"]
             self.g_means, self.g_quats, self.g_scales = sg["means"], sg["quats"], sg["scales"]
-        if longest_first:
-            cfg = config or B.RasterConfig(device=dev)
-            self.config = B.RasterConfig(cfg.persistent, cfg.ctas_per_sm, self.tile_order, device=dev)
+        # the forward hands its per-pair warp-box cull to the backward (3-channel kernels)
+        self.warp_hits = e(self.cap, dtype=torch.int32) if C == 3 else None
+        cfg = config or B.RasterConfig(device=dev)
+        self.config = B.RasterConfig(cfg.persistent, cfg.ctas_per_sm,
+                                     self.tile_order if longest_first else cfg.tile_order, device=dev,
+                                     warp_hits=self.warp_hits)
         self.graph: Optional[torch.cuda.CUDAGraph] = None
         self.host = None
 

@@ -54,7 +54,8 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
              int* __restrict__ queue, const V2<S>* __restrict__ means2d, const S* __restrict__ conics,
              const S* __restrict__ opacities, const S* __restrict__ colors, const int32_t* __restrict__ isect_ids,
              const int2* __restrict__ tile_ranges, const S* __restrict__ background, S* __restrict__ out_rgb,
-             S* __restrict__ T_final, int32_t* __restrict__ last_idx, int32_t* __restrict__ n_contrib)
+             S* __restrict__ T_final, int32_t* __restrict__ last_idx, int32_t* __restrict__ n_contrib,
+             uint32_t* __restrict__ warp_hits)
 {
     pdl_wait();
     pdl_trigger();
@@ -77,7 +78,7 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
         S T = 1, C0 = 0, C1 = 0, C2 = 0;
         int last = range.x - 1, count = 0;
         bool done = !t.inside;
-
+        const int w = threadIdx.x >> 5;
         for (int b0 = range.x; b0 < range.y; b0 += kB) {
             if (__syncthreads_count(done) == (int)blockDim.x) break;  // also guards the stage below
             if (threadIdx.x < kB) {
@@ -98,6 +99,9 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                     hit = reaches_box(load_staged<S>(sh_xy, sh_q, sh_col, sh_cull, s + lane), t.wx0, t.wx1, t.wy0,
                                       t.wy1);
                 unsigned m = __ballot_sync(kFull, hit);
+                // the chunk's ballot of warp w goes to word w of the chunk (a chunk shorter than 8
+                // entries has room for the first warps' words only)
+                if (warp_hits && lane == 0 && w < n - s) warp_hits[b0 + s + w] = m;
                 while (m) {
                     const int j = s + __ffs(m) - 1;
                     m &= m - 1;
@@ -247,7 +251,8 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
              int* __restrict__ queue, const V2<S>* __restrict__ means2d, const S* __restrict__ conics,
              const S* __restrict__ opacities, const S* __restrict__ colors, const int32_t* __restrict__ isect_ids,
              const int2* __restrict__ tile_ranges, const S* __restrict__ background, const S* __restrict__ T_final,
-             const int32_t* __restrict__ last_idx, const S* __restrict__ dL_drgb, S* __restrict__ records,
+             const int32_t* __restrict__ last_idx, const uint32_t* __restrict__ warp_hits,
+             const S* __restrict__ dL_drgb, S* __restrict__ records,
              V2<S>* __restrict__ dL_dmeans2d, S* __restrict__ dL_dconics, S* __restrict__ dL_dopacities,
              S* __restrict__ dL_dcolors)
 {
@@ -261,6 +266,7 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
     __shared__ S s_grad[kSlots][kB][kRec];
     __shared__ unsigned s_mask[kSlots][(kB + 31) / 32];
     __shared__ V4<S> s_fl[2][kB];  // (a, b, D, projection) of the last two staged batches, for the flush
+    __shared__ uint32_t s_hitw[(kB + 31) / 32][kWarps];  // the forward's cull ballots of the staged chunks
     __shared__ __align__(16) S s_red[kWarps][32 * kRedStride];
     __shared__ int s_maxlast[kWarps];
     __shared__ int s_next;
@@ -310,6 +316,15 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
         for (int k = nbatch - 1; k >= 0; --k) {
             const int b0 = range.x + k * kB;
             const int n = min(kB, maxlast - b0 + 1);
+            // word ww of a chunk is warp ww's forward ballot; a chunk of fewer than 8 entries kept the
+            // first warps' words only, and the other warps walk all of it (loaded first, so that its
+            // latency overlaps the staging loads)
+            const bool put_hits = warp_hits && threadIdx.x < kWarps * ((n + 31) >> 5);
+            uint32_t hw = kFull;
+            if (put_hits) {
+                const int e0 = b0 + 32 * (threadIdx.x / kWarps), ww = threadIdx.x % kWarps;
+                if (ww < range.y - e0) hw = warp_hits[e0 + ww];
+            }
             if (threadIdx.x < n) {
                 const int p = isect_ids[b0 + threadIdx.x];
                 const int64_t g = p + t.g_shift;
@@ -323,6 +338,7 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                 flush_partial<S, kAtomic, kB>(j, prev_b0, s_grad, s_mask, s_fl[(k + 1) & 1][j], t.g_shift, records,
                                               dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors);
             }
+            if (put_hits) (&s_hitw[0][0])[threadIdx.x] = hw;
             __syncthreads();
             // this warp only needs entries up to its own last index
             const int nw = min(n, wl - b0 + 1);
@@ -330,7 +346,9 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                 unsigned chunk_mask = 0u;  // Gaussians of this chunk the warp wrote a partial for
                 if (s < nw) {
                     bool hit = s + lane < nw;
-                    if (kCull && hit)
+                    if (warp_hits)  // the forward's cull of the same entry against the same box
+                        hit = hit && ((s_hitw[s >> 5][w] >> lane) & 1u);
+                    else if (kCull && hit)
                         hit = reaches_box(load_staged<S>(sh_xy, sh_q, sh_col, sh_cull, s + lane), t.wx0, t.wx1,
                                           t.wy0, t.wy1);
                     unsigned m = __ballot_sync(kFull, hit);
@@ -451,7 +469,8 @@ template <typename S>
 static int rasterize_fwd_impl(const char* who, const GsView* views, int32_t V, int32_t T_total, const S* means2d,
                               const S* conics, const S* opacities, const S* colors, const int32_t* isect_ids,
                               const int32_t* tile_ranges, const S* background, S* out_rgb, S* T_final,
-                              int32_t* last_idx, int32_t* n_contrib, const GsRasterConfig* config, void* stream)
+                              int32_t* last_idx, int32_t* n_contrib, uint32_t* warp_hits,
+                              const GsRasterConfig* config, void* stream)
 {
     if (V <= 0 || T_total < 0) return fail(GS_ERR_INVALID_ARG, "%s: V=%d T_total=%d", who, V, T_total);
     if (!views || !tile_ranges || !out_rgb || !T_final || !last_idx)
@@ -477,7 +496,7 @@ static int rasterize_fwd_impl(const char* who, const GsView* views, int32_t V, i
     launch_pdl(kern, grid, 256, s, views, V, T_total, config ? config->tile_order : nullptr, queue,
                               reinterpret_cast<const V2<S>*>(means2d), conics, opacities, colors, isect_ids,
                               reinterpret_cast<const int2*>(tile_ranges), background, out_rgb, T_final, last_idx,
-                              n_contrib);
+                              n_contrib, warp_hits);
     count_launches(1);
     return launch_status(who);
 }
@@ -494,7 +513,8 @@ static int rasterize_bwd_impl(const char* who, const GsView* views, int32_t V, i
                               const S* means2d, const S* conics, const S* opacities, const S* colors,
                               const int32_t* isect_ids, const int32_t* isect_pos, const int32_t* emit_start,
                               const int32_t* touched, const int32_t* tile_ranges, const int32_t* K, int64_t K_capacity,
-                              const S* background, const S* T_final, const int32_t* last_idx, const S* dL_drgb,
+                              const S* background, const S* T_final, const int32_t* last_idx,
+                              const uint32_t* warp_hits, const S* dL_drgb,
                               int32_t deterministic, void* workspace, size_t workspace_bytes, S* dL_dmeans2d,
                               S* dL_dconics, S* dL_dopacities, S* dL_dcolors, const GsRasterConfig* config,
                               void* stream)
@@ -530,7 +550,8 @@ static int rasterize_bwd_impl(const char* who, const GsView* views, int32_t V, i
     if (pers && cudaMemsetAsync(queue, 0, sizeof(int), s) != cudaSuccess) return launch_status(who);
     launch_pdl(kern, grid, 256, s, views, V, T_total, config ? config->tile_order : nullptr, queue,
                               reinterpret_cast<const V2<S>*>(means2d), conics, opacities, colors, isect_ids,
-                              reinterpret_cast<const int2*>(tile_ranges), background, T_final, last_idx, dL_drgb,
+                              reinterpret_cast<const int2*>(tile_ranges), background, T_final, last_idx, warp_hits,
+                              dL_drgb,
                               records, reinterpret_cast<V2<S>*>(dL_dmeans2d), dL_dconics, dL_dopacities, dL_dcolors);
     count_launches(1);
     if (deterministic) {
@@ -553,8 +574,8 @@ extern "C" int gs_rasterize_fwd(const GsView* views, int32_t V, int32_t T_total,
                                 const GsRasterConfig* config, void* stream)
 {
     return rasterize_fwd_impl<float>("gs_rasterize_fwd", views, V, T_total, means2d, conics, opacities, colors,
-                                     isect_ids, tile_ranges, background, out_rgb, T_final, last_idx, n_contrib, config,
-                                     stream);
+                                     isect_ids, tile_ranges, background, out_rgb, T_final, last_idx, n_contrib,
+                                     config ? config->warp_hits : nullptr, config, stream);
 }
 
 extern "C" int gs_rasterize_fwd_f64(const GsView* views, int32_t V, int32_t T_total, const double* means2d,
@@ -565,7 +586,7 @@ extern "C" int gs_rasterize_fwd_f64(const GsView* views, int32_t V, int32_t T_to
 {
     return rasterize_fwd_impl<double>("gs_rasterize_fwd_f64", views, V, T_total, means2d, conics, opacities, colors,
                                       isect_ids, tile_ranges, background, out_rgb, T_final, last_idx, n_contrib,
-                                      config, stream);
+                                      config ? config->warp_hits : nullptr, config, stream);
 }
 
 extern "C" size_t gs_rasterize_bwd_workspace_size(int64_t K_capacity, int32_t deterministic)
@@ -589,7 +610,8 @@ extern "C" int gs_rasterize_bwd(const GsView* views, int32_t V, int64_t P, int32
 {
     return rasterize_bwd_impl<float>("gs_rasterize_bwd", views, V, P, T_total, means2d, conics, opacities, colors,
                                      isect_ids, isect_pos, emit_start, touched, tile_ranges, K, K_capacity,
-                                     background, T_final, last_idx, dL_drgb, deterministic, workspace,
+                                     background, T_final, last_idx, config ? config->warp_hits : nullptr, dL_drgb,
+                                     deterministic, workspace,
                                      workspace_bytes, dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors, config,
                                      stream);
 }
@@ -606,7 +628,8 @@ extern "C" int gs_rasterize_bwd_f64(const GsView* views, int32_t V, int64_t P, i
 {
     return rasterize_bwd_impl<double>("gs_rasterize_bwd_f64", views, V, P, T_total, means2d, conics, opacities,
                                       colors, isect_ids, isect_pos, emit_start, touched, tile_ranges, K, K_capacity,
-                                      background, T_final, last_idx, dL_drgb, deterministic, workspace,
+                                      background, T_final, last_idx, config ? config->warp_hits : nullptr, dL_drgb,
+                                      deterministic, workspace,
                                       workspace_bytes, dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors, config,
                                       stream);
 }

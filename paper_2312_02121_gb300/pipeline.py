@@ -79,6 +79,7 @@ class Frame:
     last_idx: torch.Tensor
     sort_ws: torch.Tensor
     n_contrib: Optional[torch.Tensor] = None
+    config: Optional[B.RasterConfig] = None  # the forward's tile walk, reused by the backward
 
     def overflowed(self) -> bool:
         """Reads the device error word (synchronises)."""
@@ -130,6 +131,9 @@ def forward(views: B.Views, p: Params, eps2d: float = 0.3, background: Optional[
     T_final = torch.empty(pix, device=dev, dtype=dt)
     last_idx = torch.empty(pix, dtype=torch.int32, device=dev)
     n_contrib = torch.empty(pix, dtype=torch.int32, device=dev) if count_contrib else None
+    if config is None and C == 3:
+        # the forward records its per-pair warp-box cull for the backward
+        config = B.RasterConfig(device=dev, warp_hits=torch.empty(cap, dtype=torch.int32, device=dev))
     if C == 3:
         B.gs_rasterize_fwd(views, pr["means2d"], pr["conics"], p.opacities, p.colors, isect_ids, tile_ranges,
                            background, out_rgb, T_final, last_idx, n_contrib, config, stream)
@@ -138,7 +142,7 @@ def forward(views: B.Views, p: Params, eps2d: float = 0.3, background: Optional[
                               background, out_rgb, T_final, last_idx, n_contrib, config, stream)
     return Frame(views, eps2d, background, cap, pr["means2d"], pr["conics"], pr["depths"], pr["rects"],
                  pr["touched"], pr["K_total"], isect_ids, isect_pos, emit_start, tile_ranges, K, flags, out_rgb,
-                 T_final, last_idx, ws, n_contrib)
+                 T_final, last_idx, ws, n_contrib, config)
 
 
 def backward(f: Frame, p: Params, dL_drgb: torch.Tensor, stream=None, deterministic: bool = False,
@@ -151,6 +155,8 @@ def backward(f: Frame, p: Params, dL_drgb: torch.Tensor, stream=None, determinis
     dev, dt = p.means.device, p.means.dtype
     views = f.views
     P, N = views.P, p.n
+    if config is None:
+        config = f.config
     dL_drgb = dL_drgb.contiguous().to(dt)
     z = lambda *shape: torch.zeros(*shape, device=dev, dtype=dt)
     C = p.channels

@@ -148,7 +148,8 @@ size_t gs_bin_and_sort_workspace_size(int64_t P, int64_t K_capacity, int32_t T_t
  * p) -- exactly, equal depths by p.
  *   in : views (device), P, T_total, rects, depths, touched (from gs_project),
  *        K_capacity (size of the isect arrays), workspace (device, >=
- *        gs_bin_and_sort_workspace_size bytes, contents irrelevant)
+ *        gs_bin_and_sort_workspace_size bytes, 16-byte aligned, contents
+ *        irrelevant)
  *   out: isect_ids[K_capacity]   projection of each sorted pair
  *        isect_pos[K_capacity]   sorted position of each pair in emission
  *                                order (the order p's pairs are generated:

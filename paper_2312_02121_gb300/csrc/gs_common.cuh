@@ -94,6 +94,41 @@ template <> struct VecOf<double> {
 template <typename S> using V2 = typename VecOf<S>::V2;
 template <typename S> using V4 = typename VecOf<S>::V4;
 
+// d[0..2] += (x, y, z) and d[0..3] += (x, y, z, w) with reduction atomics: in
+// fp32 an 8-byte (16-byte) aligned run goes as one 2-vector (4-vector) atomic,
+// each component still added on its own, so the results are those of the
+// scalar atomics.
+__device__ __forceinline__ void atomic_add3(float* d, float x, float y, float z)
+{
+    if ((reinterpret_cast<uintptr_t>(d) & 7u) == 0) {
+        atomicAdd(reinterpret_cast<float2*>(d), make_float2(x, y));
+        atomicAdd(d + 2, z);
+    } else {
+        atomicAdd(d, x);
+        atomicAdd(reinterpret_cast<float2*>(d + 1), make_float2(y, z));
+    }
+}
+__device__ __forceinline__ void atomic_add3(double* d, double x, double y, double z)
+{
+    atomicAdd(d, x);
+    atomicAdd(d + 1, y);
+    atomicAdd(d + 2, z);
+}
+__device__ __forceinline__ void atomic_add4(float* d, float x, float y, float z, float w)
+{
+    if ((reinterpret_cast<uintptr_t>(d) & 15u) == 0) {
+        atomicAdd(reinterpret_cast<float4*>(d), make_float4(x, y, z, w));
+    } else {
+        atomic_add3(d, x, y, z);
+        atomicAdd(d + 3, w);
+    }
+}
+__device__ __forceinline__ void atomic_add4(double* d, double x, double y, double z, double w)
+{
+    atomic_add3(d, x, y, z);
+    atomicAdd(d + 3, w);
+}
+
 template <typename S>
 __device__ __forceinline__ V4<S> mk4(S x, S y, S z, S w)
 {

@@ -243,9 +243,8 @@ __device__ __forceinline__ void project_bwd_one(const GsView& view, int64_t p, c
     const S dtz = -fx * rz2 * dJ00 + S(2) * fx * o.t[0] * rz3 * dJ02 - fy * rz2 * dJ11 +
                   S(2) * fy * o.t[1] * rz3 * dJ12 + o.J02 * gm.x + o.J12 * gm.y;
     // Eq. 20: dL/dmu = R_cw^T dL/dt
-    atomicAdd(dL_dmeans + 3 * g + 0, W[0] * dtx + W[3] * dty + W[6] * dtz);
-    atomicAdd(dL_dmeans + 3 * g + 1, W[1] * dtx + W[4] * dty + W[7] * dtz);
-    atomicAdd(dL_dmeans + 3 * g + 2, W[2] * dtx + W[5] * dty + W[8] * dtz);
+    atomic_add3(dL_dmeans + 3 * g, W[0] * dtx + W[3] * dty + W[6] * dtz, W[1] * dtx + W[4] * dty + W[7] * dtz,
+                W[2] * dtx + W[5] * dty + W[8] * dtz);
     if constexpr (kView) {
         // Eq. 20: dL/dT_cw = dL/dt [mu; 1]^T; the R_cw block also gains J^T dL/dT, the covariance route
         // (Sigma' = T Sigma T^T with T = J R_cw), for which the rows of J are (J00, 0, J02), (0, J11, J12)
@@ -275,9 +274,10 @@ __device__ __forceinline__ void project_bwd_one(const GsView& view, int64_t p, c
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) dR[3 * i + j] = dM[3 * i + j] * s[j];
+    S ds3[3];
 #pragma unroll
-    for (int j = 0; j < 3; ++j)
-        atomicAdd(dL_dscales + 3 * g + j, o.R[j] * dM[j] + o.R[3 + j] * dM[3 + j] + o.R[6 + j] * dM[6 + j]);
+    for (int j = 0; j < 3; ++j) ds3[j] = o.R[j] * dM[j] + o.R[3 + j] * dM[3 + j] + o.R[6 + j] * dM[6 + j];
+    atomic_add3(dL_dscales + 3 * g, ds3[0], ds3[1], ds3[2]);
     // <dL/dR, dR/dq> with the four Jacobians of Sec. 3.2.1 at the unit quaternion
     const S w = o.q[0], x = o.q[1], y = o.q[2], z = o.q[3];
     const S gw = S(2) * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
@@ -289,10 +289,8 @@ __device__ __forceinline__ void project_bwd_one(const GsView& view, int64_t p, c
                          x * dR[6] + y * dR[7]);
     // through q_hat = q / |q|: dq = (I - q_hat q_hat^T) dq_hat / |q|
     const S dot = gw * w + gx * x + gy * y + gz * z;
-    atomicAdd(dL_dquats + 4 * g + 0, (gw - w * dot) * o.qinv);
-    atomicAdd(dL_dquats + 4 * g + 1, (gx - x * dot) * o.qinv);
-    atomicAdd(dL_dquats + 4 * g + 2, (gy - y * dot) * o.qinv);
-    atomicAdd(dL_dquats + 4 * g + 3, (gz - z * dot) * o.qinv);
+    atomic_add4(dL_dquats + 4 * g, (gw - w * dot) * o.qinv, (gx - x * dot) * o.qinv, (gy - y * dot) * o.qinv,
+                (gz - z * dot) * o.qinv);
 }
 
 template <typename S>

@@ -463,7 +463,9 @@ k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __res
 // Sorted pairs -> projection ids, inverse positions and per-tile ranges.  The
 // sorted values are emission indices when isect_pos is wanted (their owners
 // are gathered and the inverse permutation is scattered), else the owners
-// themselves, which the last radix pass already wrote into isect_ids.
+// themselves, which the last radix pass already wrote into isect_ids.  Each
+// thread takes kFinItems consecutive pairs (one 16-byte load of their keys).
+constexpr int kFinItems = 4;
 __global__ void k_finalize(const int32_t* __restrict__ K_dev, int64_t cap, const uint32_t* __restrict__ keys,
                            const uint32_t* __restrict__ vals, const uint32_t* __restrict__ owner,
                            int32_t* __restrict__ isect_ids, int32_t* __restrict__ isect_pos,
@@ -472,18 +474,40 @@ __global__ void k_finalize(const int32_t* __restrict__ K_dev, int64_t cap, const
     pdl_wait();
     pdl_trigger();
     const int K = item_count(K_dev, 0, cap);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= K) return;
-    if (isect_pos) {
-        const uint32_t e = vals[i];
-        isect_ids[i] = (int32_t)owner[e];
-        isect_pos[e] = i;
-    } else if (vals != reinterpret_cast<const uint32_t*>(isect_ids)) {
-        isect_ids[i] = (int32_t)vals[i];  // only when no pass ran (a single tile: zero key bits)
+    const int i0 = kFinItems * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (i0 >= K) return;
+    const int n = min(kFinItems, K - i0);
+    uint32_t t[kFinItems];
+    if (n == kFinItems) {  // keys comes from the workspace (256-byte aligned) and i0 is a multiple of 4
+        const uint4 v = *reinterpret_cast<const uint4*>(keys + i0);
+        t[0] = v.x;
+        t[1] = v.y;
+        t[2] = v.z;
+        t[3] = v.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kFinItems; ++k) t[k] = k < n ? keys[i0 + k] : 0u;
     }
-    const uint32_t t = keys[i];
-    if (i == 0 || keys[i - 1] != t) tile_ranges[t].x = i;
-    if (i == K - 1 || keys[i + 1] != t) tile_ranges[t].y = i + 1;
+    // tile ids are below 2^31, so ~0 marks "no neighbour"
+    uint32_t prev = i0 > 0 ? keys[i0 - 1] : ~0u;
+    const uint32_t next = i0 + n < K ? keys[i0 + n] : ~0u;
+#pragma unroll
+    for (int k = 0; k < kFinItems; ++k) {
+        if (k >= n) break;
+        const int i = i0 + k;
+        if (isect_pos) {
+            const uint32_t e = vals[i];
+            isect_ids[i] = (int32_t)owner[e];
+            isect_pos[e] = i;
+        } else if (vals != reinterpret_cast<const uint32_t*>(isect_ids)) {
+            isect_ids[i] = (int32_t)vals[i];  // only when no pass ran (a single tile: zero key bits)
+        }
+        const uint32_t cur = t[k];
+        const uint32_t nx = k + 1 < n ? t[k + 1] : next;
+        if (cur != prev) tile_ranges[cur].x = i;
+        if (nx != cur) tile_ranges[cur].y = i + 1;
+        prev = cur;
+    }
 }
 
 // Longest-first key of each tile: 65535 - min(list length, 65535).
@@ -593,6 +617,8 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
     if (!workspace || workspace_bytes < need.bytes)
         return fail(GS_ERR_INVALID_ARG, "gs_bin_and_sort: workspace of %zu bytes, need %zu", workspace_bytes,
                     need.bytes);
+    if (reinterpret_cast<uintptr_t>(workspace) & 15)
+        return fail(GS_ERR_INVALID_ARG, "gs_bin_and_sort: workspace needs 16-byte alignment");
     cudaStream_t s = as_stream(stream);
     const SortLayout L = carve(workspace, P, K_capacity);
     if (cudaMemsetAsync(tile_ranges, 0, sizeof(int32_t) * 2 * (size_t)T_total, s) != cudaSuccess ||
@@ -624,7 +650,7 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
                       bit_length((int64_t)T_total - 1), rb, s, &tk, &tv,
                       isect_pos ? nullptr : reinterpret_cast<uint32_t*>(isect_ids));
     // 4. projection ids, inverse positions, tile ranges
-    launch_pdl(k_finalize, (unsigned)((K_capacity + 255) / 256), 256, s, K_out, K_capacity, tk, tv, L.owner,
+    launch_pdl(k_finalize, (unsigned)((K_capacity + 256 * kFinItems - 1) / (256 * kFinItems)), 256, s, K_out, K_capacity, tk, tv, L.owner,
                isect_ids, isect_pos, reinterpret_cast<int2*>(tile_ranges));
     count_launches(1);
     return launch_status("gs_bin_and_sort");

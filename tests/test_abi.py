@@ -90,3 +90,18 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
                                None) == 1
     assert lib.gs_project_bwd(None, 1, -5, None, None, None, 0.3, None, None, None, None, None, None, None,
                               None) == 1
+
+
+def test_bin_and_sort_rejects_a_misaligned_workspace(lib):
+    # fake (never dereferenced) addresses: every check before the first CUDA call passes except the
+    # workspace alignment
+    from paper_2312_02121_gb300 import binding
+    P, cap, T = 10, 100, 4
+    need = binding.gs_bin_and_sort_workspace_size(P, cap, T)
+    fake = 1 << 20
+    args = (fake, 1, P, T, fake, fake, fake, cap)
+    outs = (fake, None, None, fake, fake, fake, None)
+    assert lib.gs_bin_and_sort(*args, fake + 8, need, *outs) == binding.GS_ERR_INVALID_ARG
+    assert b"16-byte alignment" in lib.gs_last_error()
+    assert lib.gs_bin_and_sort(*args, fake, need - 1, *outs) == binding.GS_ERR_INVALID_ARG
+    assert b"workspace of" in lib.gs_last_error()

@@ -40,6 +40,7 @@ UNIT = "Mpixel/s"
 WORKLOAD = "fwdbwd_1m_1080p"
 SMS = 152
 FP32_LANES_PER_SM = 128
+SFU_LANES_PER_SM = 16  # MUFU (ex2, rcp) lanes per SM: 4 per SM sub-partition
 
 
 def parse_args():
@@ -148,6 +149,18 @@ def recorded_traffic(kernel: str):
     except OSError:
         pass
     return None
+
+
+def walked_pairs(f, cam, dev) -> int:
+    """(pixel, Gaussian) pairs the backward of Sec. 3.1 evaluates: for every pixel the entries of its
+    tile's sorted list from the first through the pixel's last composited one (none when nothing was
+    composited), counted exactly from last_idx and the tile ranges."""
+    import torch
+    W, H = cam.width, cam.height
+    tx = (W + 15) // 16
+    tile = ((torch.arange(H, device=dev).view(H, 1) // 16) * tx + torch.arange(W, device=dev).view(1, W) // 16)
+    start = f.tile_ranges[tile.reshape(-1), 0].long()
+    return int((f.last_idx.reshape(-1).long() - start + 1).clamp_min(0).sum().item())
 
 
 def measured_peaks():
@@ -448,9 +461,10 @@ def run_ours(args, rank, world, local_rank):
     f0 = pipeline.forward(views, params, w.eps2d, count_contrib=True)
     K = int(f0.K_total.item())
     contrib = int(f0.n_contrib.sum().item())
+    walked = walked_pairs(f0, cam, dev)
     cap = K
     stream = torch.cuda.current_stream()
-    stages = ["project", "bin_and_sort", "rasterize_fwd", "loss_grad", "rasterize_bwd", "project_bwd"]
+    stages = ["project", "bin_and_sort", "rasterize_fwd", "loss_grad", "zero_grads", "rasterize_bwd", "project_bwd"]
     last_state = {}
     # the forward hands its per-pair warp-box cull to the backward through this buffer
     hits_cfg = B.RasterConfig(device=dev, warp_hits=torch.empty(cap, dtype=torch.int32, device=dev))
@@ -486,11 +500,12 @@ def run_ours(args, rank, world, local_rank):
         go, gcol = gz[5 * P:5 * P + N], gz[5 * P + N:5 * P + 4 * N].view(N, 3)
         gm, gq = gz[5 * P + 4 * N:5 * P + 7 * N].view(N, 3), gz[5 * P + 7 * N:5 * P + 11 * N].view(N, 4)
         gs = gz[5 * P + 11 * N:].view(N, 3)
+        mark(5)
         B.gs_rasterize_bwd(views, pr["means2d"], pr["conics"], params.opacities, params.colors, ids, None, None,
                            pr["touched"], tr, Kd, cap, None, Tf, last, dL, False, None, g2, gc, go, gcol, hits_cfg)
-        mark(5)
-        B.gs_project_bwd(views, params.means, params.quats, params.scales, w.eps2d, pr["touched"], g2, gc, gm, gq, gs)
         mark(6)
+        B.gs_project_bwd(views, params.means, params.quats, params.scales, w.eps2d, pr["touched"], g2, gc, gm, gq, gs)
+        mark(7)
         last_state.update(pr=pr, g2=g2, gc=gc, ids=ids, tr=tr, Kd=Kd)
         return fl
 
@@ -627,16 +642,28 @@ def run_ours(args, rank, world, local_rank):
     dom = max(("rasterize_fwd", "rasterize_bwd", "bin_and_sort", "project", "project_bwd"), key=lambda s: stage_ms[s])
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
+    # algorithmic flops: per evaluated (pixel, Gaussian) pair of the backward, 40 FP32 flops (plus an
+    # ex2 and a reciprocal); the stricter count over composited pairs only (49 flops each) rides along
     flops_per_pair = {"rasterize_fwd": 20, "rasterize_bwd": 49}
     if dom in flops_per_pair:
-        work = contrib * flops_per_pair[dom] / 1e12
-        achieved = work / (stage_ms[dom] / 1e3)
+        t_dom = stage_ms[dom] / 1e3
+        strict = contrib * flops_per_pair[dom] / 1e12 / t_dom
+        if dom == "rasterize_bwd":
+            achieved = walked * 40 / 1e12 / t_dom
+            work = f"{walked} evaluated (pixel, Gaussian) pairs x 40 FP32 flops"
+        else:
+            achieved, work = strict, f"{contrib} composited (pixel, Gaussian) pairs x {flops_per_pair[dom]} flops"
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak,
                 "traffic": recorded_traffic("k_raster_bwd" if dom == "rasterize_bwd" else "k_raster_fwd"),
                 "peak_source": f"FP32 FMA lanes: {SMS} SMs x {FP32_LANES_PER_SM} x 2 x {sm_mhz:.0f} MHz "
                                f"(max SM clock, {src})",
-                "work": f"{contrib} composited (pixel, Gaussian) pairs x {flops_per_pair[dom]} flops"}
+                "work": work, "launch_ms": stage_ms[dom],
+                "sfu": {"achieved": 2 * walked / t_dom / 1e12, "unit": "Tops/s",
+                        "peak": SMS * SFU_LANES_PER_SM * sm_mhz * 1e6 / 1e12,
+                        "note": "ex2 + reciprocal per evaluated pair against 16 MUFU lanes per SM"},
+                "composited_only": {"achieved": strict, "frac": strict / fp32_peak,
+                                    "work": f"{contrib} composited pairs x {flops_per_pair[dom]} flops"}}
     else:
         hbm = peaks["hbm_gbs"]
         bytes_ = {"bin_and_sort": K * 164.0, "project": sc.n * 80.0, "project_bwd": sc.n * 88.0}[dom]
@@ -649,7 +676,7 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "gaussians": sc.n, "width": cam.width, "height": cam.height,
-                   "views": 1, "intersections": K, "composited_pairs": contrib,
+                   "views": 1, "intersections": K, "composited_pairs": contrib, "evaluated_pairs_bwd": walked,
                    "l2": "flushed (256 MiB write) before every timed step, outside its events",
                    "per_rank": "independent frame (seed = rank)"},
         "stage_ms": stage_ms, "eager_ms_per_step": eager_ms,

@@ -193,7 +193,7 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
         key[k] = valid ? keys_in[idx] : 0u;
         val[k] = valid ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
         const uint32_t d = (key[k] >> shift) & mask;
-        // lanes holding the same digit, via one ballot per digit bit
+        // lanes holding the same digit, via one ballot per digit bit (__match_any_sync was measured slower)
         unsigned peers = __ballot_sync(kFull, valid);
         for (int bit = 0; bit < bits; ++bit) {
             const unsigned bal = __ballot_sync(kFull, (d >> bit) & 1u);
@@ -372,11 +372,10 @@ k_scan_block_sums(int64_t nblk, int64_t* __restrict__ block_sums, int64_t cap, i
 // projection at depth rank r gets emission index off[r] + j; its key is the
 // global tile id (row-major inside the rectangle), its owner the projection.
 // A block takes kEmitTile consecutive ranks and scans their pair counts into
-// shared memory.  Each warp then writes the slots of its ranks, 32 ranks at a
-// time: lane L holds the first slot of rank L, and the lanes write 32
-// consecutive slots per round, each finding its owner among the 32 ranks by a
-// five-step shuffle search -- so the stores of a warp are contiguous whatever
-// the rectangle sizes.
+// shared memory.  Its threads then write the block's slots round-robin, each
+// finding the slot's owner by a ten-step binary search over the block's first
+// slots -- so the stores are contiguous and the work is spread over the block
+// whatever the rectangle sizes.
 __global__ void __launch_bounds__(256)
 k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __restrict__ order,
        const int32_t* __restrict__ cnt_sorted, const short4* __restrict__ rects, const int64_t* __restrict__ block_prefix,
@@ -427,36 +426,30 @@ k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __res
     }
     if (threadIdx.x == 0) s_off[kEmitTile] = total;
     __syncthreads();
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    constexpr int kPerWarp = kEmitTile / 8;  // ranks per warp
+    // the block's slots go round-robin over all its threads (consecutive threads, consecutive slots),
+    // so that a projection with thousands of tiles is shared by the block instead of one warp
 #pragma unroll 1
-    for (int c = 0; c < kPerWarp; c += 32) {
-        const int r0 = wp * kPerWarp + c;
-        const int my_start = s_off[r0 + lane];
-        const int e_begin = s_off[r0], e_end = s_off[r0 + 32];
-        for (int e = e_begin + lane; e - lane < e_end; e += 32) {
-            // the last of the 32 ranks whose first slot is <= e (ranks with no pairs share it with the
-            // next one; the last of them owns the slot)
-            int lo = 0;
+    for (int e = threadIdx.x; e < total; e += 256) {
+        const int64_t ge = gbase + e;
+        if (ge >= cap) break;
+        // the last rank whose first slot is <= e (ranks with no pairs share it with the next one; the last
+        // of them owns the slot): s_off[lo] <= e < s_off[hi] throughout
+        int lo = 0, hi = kEmitTile;
 #pragma unroll
-            for (int d = 16; d >= 1; d >>= 1) {
-                const int st = __shfl_sync(kFull, my_start, lo + d);
-                if (st <= e) lo += d;
-            }
-            const int64_t ge = gbase + e;
-            if (e < e_end && ge < cap) {
-                const int r = r0 + lo;
-                const int j = e - s_off[r];
-                const int w = s_w[r];
-                // j / w through the reciprocal: the estimate is within one of the quotient (j / w is at
-                // most the rectangle height, < 2^15), and the two integer checks make it exact
-                int dy = (int)((float)j * s_iw[r]);
-                dy -= dy * w > j;
-                dy += (dy + 1) * w <= j;
-                tile_keys[ge] = (uint32_t)(s_row0[r] + dy * s_tx[r] + s_x0[r] + (j - dy * w));
-                owner[ge] = s_p[r];
-            }
+        for (int step = 0; step < 10; ++step) {  // kEmitTile = 2^10
+            const int mid = (lo + hi) >> 1;
+            if (s_off[mid] <= e) lo = mid; else hi = mid;
         }
+        const int r = lo;
+        const int j = e - s_off[r];
+        const int w = s_w[r];
+        // j / w through the reciprocal: the estimate is within one of the quotient (j / w is at most the
+        // rectangle height, < 2^15), and the two integer checks make it exact
+        int dy = (int)((float)j * s_iw[r]);
+        dy -= dy * w > j;
+        dy += (dy + 1) * w <= j;
+        tile_keys[ge] = (uint32_t)(s_row0[r] + dy * s_tx[r] + s_x0[r] + (j - dy * w));
+        owner[ge] = s_p[r];
     }
 }
 
@@ -464,8 +457,9 @@ k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __res
 // sorted values are emission indices when isect_pos is wanted (their owners
 // are gathered and the inverse permutation is scattered), else the owners
 // themselves, which the last radix pass already wrote into isect_ids.  Each
-// thread takes kFinItems consecutive pairs (one 16-byte load of their keys).
-constexpr int kFinItems = 4;
+// thread takes kFinItems consecutive pairs (16-byte loads of their keys, all
+// issued before any is used).
+constexpr int kFinItems = 16;
 __global__ void k_finalize(const int32_t* __restrict__ K_dev, int64_t cap, const uint32_t* __restrict__ keys,
                            const uint32_t* __restrict__ vals, const uint32_t* __restrict__ owner,
                            int32_t* __restrict__ isect_ids, int32_t* __restrict__ isect_pos,
@@ -478,12 +472,15 @@ __global__ void k_finalize(const int32_t* __restrict__ K_dev, int64_t cap, const
     if (i0 >= K) return;
     const int n = min(kFinItems, K - i0);
     uint32_t t[kFinItems];
-    if (n == kFinItems) {  // keys comes from the workspace (256-byte aligned) and i0 is a multiple of 4
-        const uint4 v = *reinterpret_cast<const uint4*>(keys + i0);
-        t[0] = v.x;
-        t[1] = v.y;
-        t[2] = v.z;
-        t[3] = v.w;
+    if (n == kFinItems) {  // keys comes from the workspace (16-byte aligned) and i0 is a multiple of 4
+#pragma unroll
+        for (int q = 0; q < kFinItems / 4; ++q) {
+            const uint4 v = reinterpret_cast<const uint4*>(keys + i0)[q];
+            t[4 * q + 0] = v.x;
+            t[4 * q + 1] = v.y;
+            t[4 * q + 2] = v.z;
+            t[4 * q + 3] = v.w;
+        }
     } else {
 #pragma unroll
         for (int k = 0; k < kFinItems; ++k) t[k] = k < n ? keys[i0 + k] : 0u;

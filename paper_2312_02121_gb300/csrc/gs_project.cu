@@ -294,7 +294,7 @@ __device__ __forceinline__ void project_bwd_one(const GsView& view, int64_t p, c
 }
 
 template <typename S>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)  // 4 CTAs per SM (64 registers): 8 % faster than 3
 k_project_bwd(const GsView* __restrict__ views, int V, int64_t P, const S* __restrict__ means,
               const V4<S>* __restrict__ quats, const S* __restrict__ scales, S eps2d,
               const int32_t* __restrict__ touched, const V2<S>* __restrict__ dL_dmeans2d,

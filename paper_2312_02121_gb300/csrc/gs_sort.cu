@@ -78,14 +78,37 @@ __device__ __forceinline__ T block_exclusive_scan_256(T x, T* total)
 // radix sort passes (uint32 keys, uint32 values)
 // ---------------------------------------------------------------------------
 
+// What pass `pass` of `passes` does.  With a key range krange = {smallest key,
+// ~largest key} in device memory (an adaptive sort), the keys are sorted
+// relative to the smallest, on the bits their spread needs, in passes of 8
+// bits: the first pass subtracts the smallest key, passes past the needed ones
+// do nothing, and the last needed one writes its values to the final buffer.
+// At least one pass runs, so the values always come out as a permutation.
+struct PassPlan {
+    bool run, last;
+    uint32_t sub;
+};
+
+__device__ __forceinline__ PassPlan pass_plan(const uint32_t* krange, int pass, int passes)
+{
+    if (!krange) return PassPlan{true, pass == passes - 1, 0u};
+    const uint32_t lo = krange[0], hi = ~krange[1];
+    const int need = hi > lo ? 32 - __clz(hi - lo) : 1;  // bits of the spread
+    const int np = min((need + 7) / 8, passes);
+    return PassPlan{pass < np, pass == np - 1, pass == 0 ? lo : 0u};
+}
+
 template <int kRI>
 __global__ void __launch_bounds__(kRT)
 k_radix_hist(const uint32_t* __restrict__ keys, const int32_t* __restrict__ count_dev, int64_t count_static,
-             int64_t cap, int shift, int bits, uint32_t* __restrict__ hist)
+             int64_t cap, int shift, int bits, uint32_t* __restrict__ hist, const uint32_t* __restrict__ krange,
+             int pass, int passes)
 {
     constexpr int kRTile = kRT * kRI;
     pdl_wait();
     pdl_trigger();
+    const PassPlan plan = pass_plan(krange, pass, passes);
+    if (!plan.run) return;
     __shared__ uint32_t h[kRWarps][kMaxBins];
     const int count = item_count(count_dev, count_static, cap);
     const int nb = (count + kRTile - 1) / kRTile;
@@ -102,7 +125,7 @@ k_radix_hist(const uint32_t* __restrict__ keys, const int32_t* __restrict__ coun
 #pragma unroll
     for (int k = 0; k < kRI; ++k) {
         const int idx = base + k * kRT + threadIdx.x;
-        key[k] = idx < count ? keys[idx] : 0u;
+        key[k] = idx < count ? keys[idx] - plan.sub : 0u;
     }
 #pragma unroll
     for (int k = 0; k < kRI; ++k)
@@ -121,11 +144,13 @@ k_radix_hist(const uint32_t* __restrict__ keys, const int32_t* __restrict__ coun
 template <int kRI>
 __global__ void __launch_bounds__(kRT)
 k_radix_scan_rows(uint32_t* __restrict__ hist, const int32_t* __restrict__ count_dev, int64_t count_static,
-                  int64_t cap, uint32_t* __restrict__ digit_total)
+                  int64_t cap, uint32_t* __restrict__ digit_total, const uint32_t* __restrict__ krange, int pass,
+                  int passes)
 {
     constexpr int kRTile = kRT * kRI;
     pdl_wait();
     pdl_trigger();
+    if (!pass_plan(krange, pass, passes).run) return;
     const int count = item_count(count_dev, count_static, cap);
     const int nb = (count + kRTile - 1) / kRTile;
     const int d = blockIdx.x;
@@ -151,10 +176,14 @@ __global__ void __launch_bounds__(kRT)
 k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                 const int32_t* __restrict__ count_dev, int64_t count_static, int64_t cap, int shift, int bits,
-                const uint32_t* __restrict__ hist, const uint32_t* __restrict__ digit_total)
+                const uint32_t* __restrict__ hist, const uint32_t* __restrict__ digit_total,
+                const uint32_t* __restrict__ krange, int pass, int passes, uint32_t* __restrict__ vals_last)
 {
     pdl_wait();
     pdl_trigger();
+    const PassPlan plan = pass_plan(krange, pass, passes);
+    if (!plan.run) return;
+    if (plan.last && vals_last) vals_out = vals_last;
     constexpr int kRTile = kRT * kRI;
     __shared__ uint32_t s_keys[kRTile];
     __shared__ uint32_t s_vals[kRTile];
@@ -190,7 +219,7 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
         const int li = w * (kRI * 32) + k * 32 + lane;
         const int idx = base + li;
         const bool valid = li < n_here;
-        key[k] = valid ? keys_in[idx] : 0u;
+        key[k] = valid ? keys_in[idx] - plan.sub : 0u;
         val[k] = valid ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
         const uint32_t d = (key[k] >> shift) & mask;
         // lanes holding the same digit, via one ballot per digit bit (__match_any_sync was measured slower)
@@ -257,12 +286,15 @@ struct RadixBufs {
 // v1 and v2; the values start as vals0, or as the input positions when vals0
 // is null.  The item count is *count_dev (device, clamped to cap) or
 // count_static.  The last pass writes its values to vals_last when that is
-// given.  Returns the buffers holding the result.
+// given.  With krange (device {smallest key, ~largest key}) the sort is
+// adaptive (see pass_plan): it needs vals_last, which then always receives
+// the values.  Returns the buffers holding the result (for an adaptive sort
+// only the values: the keys are left relative and in either buffer).
 template <int kRI>
 static void lsd_sort(uint32_t* k1, uint32_t* k2, uint32_t* v1, uint32_t* v2, const uint32_t* vals0,
                      const int32_t* count_dev, int64_t count_static, int64_t cap, int total_bits,
                      const RadixBufs& rb, cudaStream_t s, uint32_t** keys_out, uint32_t** vals_out,
-                     uint32_t* vals_last = nullptr)
+                     uint32_t* vals_last = nullptr, const uint32_t* krange = nullptr)
 {
     constexpr int kRTile = kRT * kRI;
     uint32_t *kin = k1, *kout = k2, *vout = v1;
@@ -273,20 +305,21 @@ static void lsd_sort(uint32_t* k1, uint32_t* k2, uint32_t* v1, uint32_t* v2, con
         const unsigned grid = (unsigned)((cap + kRTile - 1) / kRTile);
         for (int pass = 0, shift = 0; pass < passes; ++pass, shift += per) {
             const int bits = std::min(per, total_bits - shift);
-            if (vals_last && pass == passes - 1) vout = vals_last;
-            launch_pdl(k_radix_hist<kRI>, grid, kRT, s, kin, count_dev, count_static, cap, shift, bits, rb.hist);
+            // the device picks vals_last for the last pass that runs (the host's last one when not adaptive)
+            launch_pdl(k_radix_hist<kRI>, grid, kRT, s, kin, count_dev, count_static, cap, shift, bits, rb.hist, krange,
+                       pass, passes);
             launch_pdl(k_radix_scan_rows<kRI>, 1u << bits, kRT, s, rb.hist, count_dev, count_static, cap,
-                       rb.digit_total);
+                       rb.digit_total, krange, pass, passes);
             launch_pdl(k_radix_scatter<kRI>, grid, kRT, s, kin, vin, kout, vout, count_dev, count_static, cap, shift,
-                       bits, rb.hist, rb.digit_total);
+                       bits, rb.hist, rb.digit_total, krange, pass, passes, vals_last);
             count_launches(3);
             std::swap(kin, kout);
-            vin = vout;
+            vin = (vals_last && pass == passes - 1) ? vals_last : vout;
             vout = (vout == v1) ? v2 : v1;
         }
     }
     *keys_out = kin;
-    *vals_out = const_cast<uint32_t*>(vin);  // vals0 itself when no pass ran
+    *vals_out = const_cast<uint32_t*>(krange ? vals_last : vin);  // vals0 itself when no pass ran
 }
 
 // ---------------------------------------------------------------------------
@@ -294,14 +327,53 @@ static void lsd_sort(uint32_t* k1, uint32_t* k2, uint32_t* v1, uint32_t* v2, con
 // ---------------------------------------------------------------------------
 
 // Depth keys: the fp32 bit pattern of t_z (> near > 0, so monotone in 31
-// bits); culled projections get the largest key.
-__global__ void k_depth_keys(int64_t P, const float* __restrict__ depths, const int32_t* __restrict__ touched,
-                             uint32_t* __restrict__ keys)
+// bits); culled projections get the largest key.  The smallest key and the
+// complement of the largest one over the visible projections go to krange
+// (both by atomicMin, one pair per block of kKeyItems x 256 keys; the caller
+// sets both words to ~0 first): the depth sort then sorts only the bits their
+// spread needs.  A culled projection's key may fall outside that range; its
+// place in the order does not matter, as it has no pairs.
+constexpr int kKeyItems = 8;
+__global__ void __launch_bounds__(256)
+k_depth_keys(int64_t P, const float* __restrict__ depths, const int32_t* __restrict__ touched,
+             uint32_t* __restrict__ keys, uint32_t* __restrict__ krange)
 {
     pdl_wait();
     pdl_trigger();
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < P) keys[p] = touched[p] > 0 ? __float_as_uint(depths[p]) : 0x7fffffffu;
+    __shared__ uint32_t s_lo[8], s_hi[8];
+    uint32_t lo = 0xffffffffu, hi_c = 0xffffffffu;
+    const int64_t base = (int64_t)blockIdx.x * (256 * kKeyItems) + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < kKeyItems; ++k) {
+        const int64_t p = base + k * 256;
+        if (p < P) {
+            const bool vis = touched[p] > 0;
+            const uint32_t key = vis ? __float_as_uint(depths[p]) : 0x7fffffffu;
+            keys[p] = key;
+            if (vis) {
+                lo = min(lo, key);
+                hi_c = min(hi_c, ~key);
+            }
+        }
+    }
+    lo = __reduce_min_sync(kFull, lo);
+    hi_c = __reduce_min_sync(kFull, hi_c);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_lo[w] = lo;
+        s_hi[w] = hi_c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < 8; ++i) {
+            lo = min(lo, s_lo[i]);
+            hi_c = min(hi_c, s_hi[i]);
+        }
+        if (lo != 0xffffffffu) {
+            atomicMin(krange, lo);
+            atomicMin(krange + 1, hi_c);
+        }
+    }
 }
 
 // Per block of kEmitTile projections in depth order: sum of touched.  The
@@ -547,7 +619,7 @@ static OrderLayout carve_order(void* ws, int64_t T)
 }
 
 struct SortLayout {
-    uint32_t *dkey_a, *dkey_b, *dval_a, *dval_b;
+    uint32_t *dkey_a, *dkey_b, *dval_a, *dval_b, *order, *krange;
     int32_t* cnt_sorted;
     int64_t* block_sums;
     uint32_t *tkey_a, *tkey_b, *tval_a, *tval_b, *owner;
@@ -563,6 +635,8 @@ static SortLayout carve(void* ws, int64_t P, int64_t cap)
     L.dkey_b = c.take<uint32_t>(P);
     L.dval_a = c.take<uint32_t>(P);
     L.dval_b = c.take<uint32_t>(P);
+    L.order = c.take<uint32_t>(P);
+    L.krange = c.take<uint32_t>(2);
     L.cnt_sorted = c.take<int32_t>(P);
     L.block_sums = c.take<int64_t>((P + kEmitTile - 1) / kEmitTile + 1);
     L.tkey_a = c.take<uint32_t>(cap);
@@ -624,11 +698,15 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
     if (P == 0) return launch_status("gs_bin_and_sort");
     const RadixBufs rb{L.hist, L.digit_total};
 
-    // 1. projections in (depth, p) order
-    launch_pdl(k_depth_keys, (unsigned)((P + 255) / 256), 256, s, P, depths, touched, L.dkey_a);
+    // 1. projections in (depth, p) order: an adaptive sort on the spread of the visible depth keys
+    if (cudaMemsetAsync(L.krange, 0xff, 2 * sizeof(uint32_t), s) != cudaSuccess)
+        return launch_status("gs_bin_and_sort memset");
+    launch_pdl(k_depth_keys, (unsigned)((P + 256 * kKeyItems - 1) / (256 * kKeyItems)), 256, s, P, depths, touched,
+               L.dkey_a, L.krange);
     count_launches(1);
     uint32_t *dk, *order;
-    lsd_sort<kRIShort>(L.dkey_a, L.dkey_b, L.dval_a, L.dval_b, nullptr, nullptr, P, P, 31, rb, s, &dk, &order);
+    lsd_sort<kRIShort>(L.dkey_a, L.dkey_b, L.dval_a, L.dval_b, nullptr, nullptr, P, P, 31, rb, s, &dk, &order, L.order,
+                       L.krange);
 
     // 2. scan of touched in depth order, K, emission
     const int64_t nblk = (P + kEmitTile - 1) / kEmitTile;

@@ -105,3 +105,16 @@ def test_bin_and_sort_rejects_a_misaligned_workspace(lib):
     assert b"16-byte alignment" in lib.gs_last_error()
     assert lib.gs_bin_and_sort(*args, fake, need - 1, *outs) == binding.GS_ERR_INVALID_ARG
     assert b"workspace of" in lib.gs_last_error()
+
+
+def test_static_scratch_covers_the_static_limits(lib):
+    # at the documented limits the workspace check passes; the call then fails only at its first CUDA
+    # call (there is no GPU here), not with "needs ... bytes of scratch"
+    import re
+    hdr = open(HEADER).read()
+    P = int(re.search(r"#define GS_STATIC_MAX_PROJECTIONS (\d+)", hdr).group(1))
+    K = int(re.search(r"#define GS_STATIC_MAX_INTERSECTIONS (\d+)", hdr).group(1))
+    fake = 1 << 20
+    rc = lib.gs_bin_and_sort_static(fake, 1, P, 65536, fake, fake, fake, K, fake, None, None, fake, fake, fake, None)
+    assert b"bytes of scratch" not in lib.gs_last_error(), lib.gs_last_error()
+    assert rc != 0  # no device in this container

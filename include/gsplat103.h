@@ -214,7 +214,7 @@ typedef struct GsRasterConfig {
                                    NULL = tile id order */
     int32_t* queue;             /* device int32 counter the persistent grid pops from; required
                                    when persistent; the call zeroes it on its stream */
-    uint32_t* warp_hits;        /* device [K_capacity] 32-bit words, nullable (3-channel
+    uint32_t* warp_hits;        /* device [K_capacity] 32-bit words, nullable (up to 3-channel
                                    kernels): the forward records, for every chunk of 32 sorted
                                    pairs of a tile, which of them each of the tile's 8 warp boxes
                                    (8x4 pixels each) can be reached by (word w of the chunk holds
@@ -330,12 +330,15 @@ int gs_project_bwd(const GsView* views, int32_t V, int64_t P, const float* means
  * summed over the channels.  Arguments are those of gs_rasterize_fwd /
  * gs_rasterize_bwd (fast mode) with colors[N,C], background[C] (nullable),
  * out[pixels,C], dL_dout[pixels,C] and dL_dcolors[N,C]; T_final, last_idx and
- * n_contrib as there.  C == 3 runs the 3-channel kernels.  Other C are
- * composited in chunks of up to 32 channels, one launch per chunk and pass
- * (each chunk rebuilds the same alpha and T); the backward adds every chunk's
- * share with atomics, so its fp32 sums vary in the last bits run to run (there
- * is no deterministic mode for C != 3).  Outputs of the backward are
- * ACCUMULATED (the caller zeroes them).
+ * n_contrib as there.  C <= 3 runs the kernels of gs_rasterize_fwd /
+ * gs_rasterize_bwd with a channel stride of C (missing channels count as zero
+ * colour and zero dL/dC, which adds nothing), GsRasterConfig.warp_hits
+ * included.  Larger C are composited in chunks of up to 32 channels, one
+ * launch per chunk and pass (each chunk rebuilds the same alpha and T; these
+ * kernels ignore warp_hits); the backward adds every chunk's share with
+ * atomics.  Either way the backward's fp32 sums vary in the last bits run to
+ * run (the deterministic mode is gs_rasterize_bwd's).  Outputs of the
+ * backward are ACCUMULATED (the caller zeroes them).
  */
 int gs_rasterize_fwd_nc(const GsView* views, int32_t V, int32_t T_total, int32_t C, const float* means2d,
                         const float* conics, const float* opacities, const float* colors, const int32_t* isect_ids,

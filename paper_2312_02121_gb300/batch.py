@@ -85,8 +85,8 @@ class BatchRenderer:
             sg = shared_grads
             self.g_op, self.g_col = sg["opacities"], sg["colors"]
             self.g_means, self.g_quats, self.g_scales = sg["means"], sg["quats"], sg["scales"]
-        # the forward hands its per-pair warp-box cull to the backward (3-channel kernels)
-        self.warp_hits = e(self.cap, dtype=torch.int32) if C == 3 else None
+        # the forward hands its per-pair warp-box cull to the backward (kernels of up to 3 channels)
+        self.warp_hits = e(self.cap, dtype=torch.int32) if C <= 3 else None
         cfg = config or B.RasterConfig(device=dev)
         self.config = B.RasterConfig(cfg.persistent, cfg.ctas_per_sm,
                                      self.tile_order if longest_first else cfg.tile_order, device=dev,

@@ -38,6 +38,18 @@ namespace gs {
 
 constexpr int kRec = 9;  // dmu'(2) dconic(3) dopacity(1) dcolor(3)
 
+// The colours of these kernels have C = 1, 2 or 3 channels (3: the RGB of Eq. 7): the values of a
+// Gaussian or a pixel are C apart; a missing channel reads as zero (zero colour, zero dL/dC, so it
+// adds nothing to alpha's gradient) and is never written.
+template <typename S>
+__device__ __forceinline__ void load_c3(const S* __restrict__ a, int64_t i, int C, S& x, S& y, S& z)
+{
+    const S* b = a + (int64_t)C * i;
+    x = b[0];
+    y = C > 1 ? b[1] : S(0);
+    z = C > 2 ? b[2] : S(0);
+}
+
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
@@ -47,18 +59,21 @@ constexpr int kRec = 9;  // dmu'(2) dconic(3) dopacity(1) dcolor(3)
 // otherwise CTA i renders queue slot i.  Slot qi renders tile tile_order[qi]
 // (identity when tile_order is NULL).  kCount: also count each pixel's
 // composited Gaussians into n_contrib (a separate instantiation, so that the
-// usual walk carries no counter).
-template <typename S, bool kCull, bool kPersistent, bool kCount>
+// usual walk carries no counter).  kAnyC: colours of C_arg = 1, 2 or 3
+// channels; otherwise 3 (a separate instantiation: the runtime stride cost
+// the 3-channel walk 2 %).
+template <typename S, bool kCull, bool kPersistent, bool kCount, bool kAnyC>
 __global__ void __launch_bounds__(256, 6)  // 6 CTAs per SM (40 registers) measured fastest
 k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t* __restrict__ tile_order,
              int* __restrict__ queue, const V2<S>* __restrict__ means2d, const S* __restrict__ conics,
              const S* __restrict__ opacities, const S* __restrict__ colors, const int32_t* __restrict__ isect_ids,
              const int2* __restrict__ tile_ranges, const S* __restrict__ background, S* __restrict__ out_rgb,
              S* __restrict__ T_final, int32_t* __restrict__ last_idx, int32_t* __restrict__ n_contrib,
-             uint32_t* __restrict__ warp_hits)
+             uint32_t* __restrict__ warp_hits, int C_arg)
 {
     pdl_wait();
     pdl_trigger();
+    const int C = kAnyC ? C_arg : 3;
     constexpr int kB = RT<S>::kFwdBatch;
     __shared__ V4<S> sh_xy[kB], sh_q[kB], sh_col[kB], sh_cull[kB];
     __shared__ int s_next;
@@ -86,9 +101,10 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                 if (i < range.y) {
                     const int p = isect_ids[i];
                     const int64_t g = p + t.g_shift;
+                    S c0, c1, c2;
+                    load_c3(colors, g, C, c0, c1, c2);
                     stage_gaussian<S>(sh_xy, sh_q, sh_col, sh_cull, threadIdx.x, means2d[p], conics[3 * p],
-                                      conics[3 * p + 1], conics[3 * p + 2], opacities[g], colors[3 * g],
-                                      colors[3 * g + 1], colors[3 * g + 2]);
+                                      conics[3 * p + 1], conics[3 * p + 2], opacities[g], c0, c1, c2);
                 }
             }
             __syncthreads();
@@ -132,10 +148,11 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
         }
         if (t.inside) {
             S bg0 = 0, bg1 = 0, bg2 = 0;
-            if (background) { bg0 = background[0]; bg1 = background[1]; bg2 = background[2]; }
-            out_rgb[3 * t.pix + 0] = fma(T, bg0, C0);
-            out_rgb[3 * t.pix + 1] = fma(T, bg1, C1);
-            out_rgb[3 * t.pix + 2] = fma(T, bg2, C2);
+            if (background) load_c3(background, 0, C, bg0, bg1, bg2);
+            S* o = out_rgb + (int64_t)C * t.pix;
+            o[0] = fma(T, bg0, C0);
+            if (C > 1) o[1] = fma(T, bg1, C1);
+            if (C > 2) o[2] = fma(T, bg2, C2);
             T_final[t.pix] = T;
             last_idx[t.pix] = last;
             if (kCount) n_contrib[t.pix] = count;
@@ -202,7 +219,7 @@ __device__ __forceinline__ void flush_partial(int j, int b0, const S (*s_grad)[k
                                               const unsigned (*s_mask)[(kB + 31) / 32], V4<S> fl,
                                               int64_t g_shift, S* __restrict__ records,
                                               V2<S>* __restrict__ dL_dmeans2d, S* __restrict__ dL_dconics,
-                                              S* __restrict__ dL_dopacities, S* __restrict__ dL_dcolors)
+                                              S* __restrict__ dL_dopacities, S* __restrict__ dL_dcolors, int C)
 {
     S acc[kRec];
 #pragma unroll
@@ -231,9 +248,10 @@ __device__ __forceinline__ void flush_partial(int j, int b0, const S (*s_grad)[k
             atomicAdd(dL_dconics + 3 * p + 1, acc[3]);
             atomicAdd(dL_dconics + 3 * p + 2, acc[4]);
             atomicAdd(dL_dopacities + g, acc[5]);
-            atomicAdd(dL_dcolors + 3 * g + 0, acc[6]);
-            atomicAdd(dL_dcolors + 3 * g + 1, acc[7]);
-            atomicAdd(dL_dcolors + 3 * g + 2, acc[8]);
+            S* dc = dL_dcolors + (int64_t)C * g;
+            atomicAdd(dc, acc[6]);
+            if (C > 1) atomicAdd(dc + 1, acc[7]);
+            if (C > 2) atomicAdd(dc + 2, acc[8]);
         }
     } else {
         S* rec = records + (size_t)(b0 + j) * kRec;
@@ -245,8 +263,8 @@ __device__ __forceinline__ void flush_partial(int j, int b0, const S (*s_grad)[k
 // kAtomic: each (tile, Gaussian) partial is added straight into the
 // per-projection outputs with reduction atomics (fast; the summation order
 // across tiles varies).  Otherwise it is written as a record for
-// k_reduce_records (deterministic).
-template <typename S, bool kCull, bool kAtomic, bool kPersistent>
+// k_reduce_records (deterministic).  kAnyC as for the forward.
+template <typename S, bool kCull, bool kAtomic, bool kPersistent, bool kAnyC>
 __global__ void __launch_bounds__(256, 4)
 k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t* __restrict__ tile_order,
              int* __restrict__ queue, const V2<S>* __restrict__ means2d, const S* __restrict__ conics,
@@ -255,10 +273,11 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
              const int32_t* __restrict__ last_idx, const uint32_t* __restrict__ warp_hits,
              const S* __restrict__ dL_drgb, S* __restrict__ records,
              V2<S>* __restrict__ dL_dmeans2d, S* __restrict__ dL_dconics, S* __restrict__ dL_dopacities,
-             S* __restrict__ dL_dcolors)
+             S* __restrict__ dL_dcolors, int C_arg)
 {
     pdl_wait();
     pdl_trigger();
+    const int C = kAnyC ? C_arg : 3;
     // one partial slot per (warp, Gaussian), written with plain stores and summed in warp order at
     // the flush (shared-memory atomics into one slot per Gaussian were measured 8 % slower)
     constexpr int kB = RT<S>::kBwdBatch;
@@ -289,10 +308,12 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
         if (t.inside) {
             T = T_final[t.pix];
             last = last_idx[t.pix];
-            g0 = dL_drgb[3 * t.pix + 0];
-            g1 = dL_drgb[3 * t.pix + 1];
-            g2 = dL_drgb[3 * t.pix + 2];
-            if (background) bgT = T * (background[0] * g0 + background[1] * g1 + background[2] * g2);
+            load_c3(dL_drgb, t.pix, C, g0, g1, g2);
+            if (background) {
+                S b0, b1, b2;
+                load_c3(background, 0, C, b0, b1, b2);
+                bgT = T * (b0 * g0 + b1 * g1 + b2 * g2);
+            }
         }
         // S_n . dL/dC + T_final b . dL/dC, with S_n = sum_{m>n} c_m alpha_m T_m: the numerator of the
         // suffix term of dL/dalpha_n (the background part is constant per pixel, so it starts the sum)
@@ -329,15 +350,16 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
             if (threadIdx.x < n) {
                 const int p = isect_ids[b0 + threadIdx.x];
                 const int64_t g = p + t.g_shift;
+                S c0, c1, c2;
+                load_c3(colors, g, C, c0, c1, c2);
                 stage_gaussian<S>(sh_xy, sh_q, sh_col, sh_cull, threadIdx.x, means2d[p], conics[3 * p],
-                                  conics[3 * p + 1], conics[3 * p + 2], opacities[g], colors[3 * g],
-                                  colors[3 * g + 1], colors[3 * g + 2]);
+                                  conics[3 * p + 1], conics[3 * p + 2], opacities[g], c0, c1, c2);
                 s_fl[k & 1][threadIdx.x] = mk4<S>(sh_xy[threadIdx.x].w, sh_q[threadIdx.x].w, sh_col[threadIdx.x].w,
                                                   RT<S>::stash(p));
             } else if (threadIdx.x >= kB && threadIdx.x < kB + prev_n) {
                 const int j = threadIdx.x - kB;
                 flush_partial<S, kAtomic, kB>(j, prev_b0, s_grad, s_mask, s_fl[(k + 1) & 1][j], t.g_shift, records,
-                                              dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors);
+                                              dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors, C);
             }
             if (put_hits) (&s_hitw[0][0])[threadIdx.x] = hw;
             __syncthreads();
@@ -411,7 +433,7 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
         }
         if (threadIdx.x < prev_n)  // the last walked batch (batch 0)
             flush_partial<S, kAtomic, kB>(threadIdx.x, prev_b0, s_grad, s_mask, s_fl[0][threadIdx.x], t.g_shift,
-                                          records, dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors);
+                                          records, dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors, C);
         if (!kAtomic) {
             // Gaussians after every pixel's last one received nothing
             const int first_unused = max(range.x, maxlast + 1);
@@ -432,7 +454,7 @@ k_reduce_records(const GsView* __restrict__ views, int V, int64_t P, const int32
                  const int32_t* __restrict__ emit_start, const int32_t* __restrict__ isect_pos,
                  const int32_t* __restrict__ K_dev, int64_t cap, const S* __restrict__ records,
                  V2<S>* __restrict__ dL_dmeans2d, S* __restrict__ dL_dconics, S* __restrict__ dL_dopacities,
-                 S* __restrict__ dL_dcolors)
+                 S* __restrict__ dL_dcolors, int C)
 {
     pdl_wait();
     pdl_trigger();
@@ -461,17 +483,24 @@ k_reduce_records(const GsView* __restrict__ views, int V, int64_t P, const int32
     const GsView& view = views[view_of_projection(views, V, p)];
     const int64_t g = view.g_begin + (p - view.proj_offset);
     atomicAdd(dL_dopacities + g, acc[5]);
-    atomic_add3(dL_dcolors + 3 * g, acc[6], acc[7], acc[8]);
+    S* dc = dL_dcolors + (int64_t)C * g;
+    if (C == 3) {
+        atomic_add3(dc, acc[6], acc[7], acc[8]);
+    } else {
+        atomicAdd(dc, acc[6]);
+        if (C > 1) atomicAdd(dc + 1, acc[7]);
+    }
 }
 
 template <typename S>
-static int rasterize_fwd_impl(const char* who, const GsView* views, int32_t V, int32_t T_total, const S* means2d,
+static int rasterize_fwd_impl(const char* who, int C, const GsView* views, int32_t V, int32_t T_total, const S* means2d,
                               const S* conics, const S* opacities, const S* colors, const int32_t* isect_ids,
                               const int32_t* tile_ranges, const S* background, S* out_rgb, S* T_final,
                               int32_t* last_idx, int32_t* n_contrib, uint32_t* warp_hits,
                               const GsRasterConfig* config, void* stream)
 {
-    if (V <= 0 || T_total < 0) return fail(GS_ERR_INVALID_ARG, "%s: V=%d T_total=%d", who, V, T_total);
+    if (V <= 0 || T_total < 0 || C < 1 || C > 3)
+        return fail(GS_ERR_INVALID_ARG, "%s: V=%d T_total=%d C=%d", who, V, T_total, C);
     if (!views || !tile_ranges || !out_rgb || !T_final || !last_idx)
         return fail(GS_ERR_INVALID_ARG, "%s: null pointer argument", who);
     if ((reinterpret_cast<uintptr_t>(means2d) & (2 * sizeof(S) - 1)) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7))
@@ -481,13 +510,19 @@ static int rasterize_fwd_impl(const char* who, const GsView* views, int32_t V, i
     if (T_total == 0) return GS_OK;
     cudaStream_t s = as_stream(stream);
     const bool cull = cull_enabled(), pers = config && config->persistent;
-    using KF = decltype(&k_raster_fwd<S, true, true, true>);
-    static const KF table[2][2][2] = {
-        {{k_raster_fwd<S, false, false, false>, k_raster_fwd<S, false, false, true>},
-         {k_raster_fwd<S, false, true, false>, k_raster_fwd<S, false, true, true>}},
-        {{k_raster_fwd<S, true, false, false>, k_raster_fwd<S, true, false, true>},
-         {k_raster_fwd<S, true, true, false>, k_raster_fwd<S, true, true, true>}}};
-    const KF kern = table[cull][pers][n_contrib != nullptr];
+    // the any-channel instantiations exist for fp32 only (the fp64 entry points composite 3 channels)
+    constexpr bool kA = std::is_same<S, float>::value;
+    using KF = decltype(&k_raster_fwd<S, true, true, true, false>);
+    static const KF table[2][2][2][2] = {
+        {{{k_raster_fwd<S, false, false, false, false>, k_raster_fwd<S, false, false, false, kA>},
+          {k_raster_fwd<S, false, false, true, false>, k_raster_fwd<S, false, false, true, kA>}},
+         {{k_raster_fwd<S, false, true, false, false>, k_raster_fwd<S, false, true, false, kA>},
+          {k_raster_fwd<S, false, true, true, false>, k_raster_fwd<S, false, true, true, kA>}}},
+        {{{k_raster_fwd<S, true, false, false, false>, k_raster_fwd<S, true, false, false, kA>},
+          {k_raster_fwd<S, true, false, true, false>, k_raster_fwd<S, true, false, true, kA>}},
+         {{k_raster_fwd<S, true, true, false, false>, k_raster_fwd<S, true, true, false, kA>},
+          {k_raster_fwd<S, true, true, true, false>, k_raster_fwd<S, true, true, true, kA>}}}};
+    const KF kern = table[cull][pers][n_contrib != nullptr][C != 3];
     unsigned grid;
     if (int rc = raster_grid(kern, config, T_total, &grid)) return rc;
     int* queue = pers ? config->queue : nullptr;
@@ -495,7 +530,7 @@ static int rasterize_fwd_impl(const char* who, const GsView* views, int32_t V, i
     launch_pdl(kern, grid, 256, s, views, V, T_total, config ? config->tile_order : nullptr, queue,
                               reinterpret_cast<const V2<S>*>(means2d), conics, opacities, colors, isect_ids,
                               reinterpret_cast<const int2*>(tile_ranges), background, out_rgb, T_final, last_idx,
-                              n_contrib, warp_hits);
+                              n_contrib, warp_hits, C);
     count_launches(1);
     return launch_status(who);
 }
@@ -508,7 +543,7 @@ static size_t bwd_workspace(int64_t K_capacity, int32_t deterministic)
 }
 
 template <typename S>
-static int rasterize_bwd_impl(const char* who, const GsView* views, int32_t V, int64_t P, int32_t T_total,
+static int rasterize_bwd_impl(const char* who, int C, const GsView* views, int32_t V, int64_t P, int32_t T_total,
                               const S* means2d, const S* conics, const S* opacities, const S* colors,
                               const int32_t* isect_ids, const int32_t* isect_pos, const int32_t* emit_start,
                               const int32_t* touched, const int32_t* tile_ranges, const int32_t* K, int64_t K_capacity,
@@ -518,9 +553,9 @@ static int rasterize_bwd_impl(const char* who, const GsView* views, int32_t V, i
                               S* dL_dconics, S* dL_dopacities, S* dL_dcolors, const GsRasterConfig* config,
                               void* stream)
 {
-    if (V <= 0 || P < 0 || T_total < 0 || K_capacity < 0 || K_capacity >= (int64_t(1) << 31))
-        return fail(GS_ERR_INVALID_ARG, "%s: V=%d P=%lld T_total=%d K_capacity=%lld", who, V, (long long)P, T_total,
-                    (long long)K_capacity);
+    if (V <= 0 || P < 0 || T_total < 0 || K_capacity < 0 || K_capacity >= (int64_t(1) << 31) || C < 1 || C > 3)
+        return fail(GS_ERR_INVALID_ARG, "%s: V=%d P=%lld T_total=%d K_capacity=%lld C=%d", who, V, (long long)P,
+                    T_total, (long long)K_capacity, C);
     if (!views || !tile_ranges || !T_final || !last_idx || !dL_drgb ||
         (P > 0 && (!dL_dmeans2d || !dL_dconics || !dL_dopacities || !dL_dcolors)) ||
         (deterministic && P > 0 && (!K || !touched || !emit_start || !isect_pos)))
@@ -536,13 +571,18 @@ static int rasterize_bwd_impl(const char* who, const GsView* views, int32_t V, i
     cudaStream_t s = as_stream(stream);
     S* records = static_cast<S*>(workspace);
     const bool cull = cull_enabled(), pers = config && config->persistent;
-    using KB = decltype(&k_raster_bwd<S, true, true, true>);
-    static const KB table[2][2][2] = {
-        {{k_raster_bwd<S, false, false, false>, k_raster_bwd<S, false, false, true>},
-         {k_raster_bwd<S, false, true, false>, k_raster_bwd<S, false, true, true>}},
-        {{k_raster_bwd<S, true, false, false>, k_raster_bwd<S, true, false, true>},
-         {k_raster_bwd<S, true, true, false>, k_raster_bwd<S, true, true, true>}}};
-    const KB kern = table[cull][!deterministic][pers];
+    constexpr bool kA = std::is_same<S, float>::value;
+    using KB = decltype(&k_raster_bwd<S, true, true, true, false>);
+    static const KB table[2][2][2][2] = {
+        {{{k_raster_bwd<S, false, false, false, false>, k_raster_bwd<S, false, false, false, kA>},
+          {k_raster_bwd<S, false, false, true, false>, k_raster_bwd<S, false, false, true, kA>}},
+         {{k_raster_bwd<S, false, true, false, false>, k_raster_bwd<S, false, true, false, kA>},
+          {k_raster_bwd<S, false, true, true, false>, k_raster_bwd<S, false, true, true, kA>}}},
+        {{{k_raster_bwd<S, true, false, false, false>, k_raster_bwd<S, true, false, false, kA>},
+          {k_raster_bwd<S, true, false, true, false>, k_raster_bwd<S, true, false, true, kA>}},
+         {{k_raster_bwd<S, true, true, false, false>, k_raster_bwd<S, true, true, false, kA>},
+          {k_raster_bwd<S, true, true, true, false>, k_raster_bwd<S, true, true, true, kA>}}}};
+    const KB kern = table[cull][!deterministic][pers][C != 3];
     unsigned grid;
     if (int rc = raster_grid(kern, config, T_total, &grid)) return rc;
     int* queue = pers ? config->queue : nullptr;
@@ -551,15 +591,38 @@ static int rasterize_bwd_impl(const char* who, const GsView* views, int32_t V, i
                               reinterpret_cast<const V2<S>*>(means2d), conics, opacities, colors, isect_ids,
                               reinterpret_cast<const int2*>(tile_ranges), background, T_final, last_idx, warp_hits,
                               dL_drgb,
-                              records, reinterpret_cast<V2<S>*>(dL_dmeans2d), dL_dconics, dL_dopacities, dL_dcolors);
+                              records, reinterpret_cast<V2<S>*>(dL_dmeans2d), dL_dconics, dL_dopacities, dL_dcolors, C);
     count_launches(1);
     if (deterministic) {
         launch_pdl(k_reduce_records<S>, (unsigned)((P + 255) / 256), 256, s,
             views, V, P, touched, emit_start, isect_pos, K, K_capacity, records,
-            reinterpret_cast<V2<S>*>(dL_dmeans2d), dL_dconics, dL_dopacities, dL_dcolors);
+            reinterpret_cast<V2<S>*>(dL_dmeans2d), dL_dconics, dL_dopacities, dL_dcolors, C);
         count_launches(1);
     }
     return launch_status(who);
+}
+
+int rasterize_fwd_upto3(const char* who, int C, const GsView* views, int32_t V, int32_t T_total, const float* means2d,
+                        const float* conics, const float* opacities, const float* colors, const int32_t* isect_ids,
+                        const int32_t* tile_ranges, const float* background, float* out, float* T_final,
+                        int32_t* last_idx, int32_t* n_contrib, const GsRasterConfig* config, void* stream)
+{
+    return rasterize_fwd_impl<float>(who, C, views, V, T_total, means2d, conics, opacities, colors, isect_ids,
+                                     tile_ranges, background, out, T_final, last_idx, n_contrib,
+                                     config ? config->warp_hits : nullptr, config, stream);
+}
+
+int rasterize_bwd_upto3(const char* who, int C, const GsView* views, int32_t V, int64_t P, int32_t T_total,
+                        const float* means2d, const float* conics, const float* opacities, const float* colors,
+                        const int32_t* isect_ids, const int32_t* tile_ranges, const float* background,
+                        const float* T_final, const int32_t* last_idx, const float* dL_dout, float* dL_dmeans2d,
+                        float* dL_dconics, float* dL_dopacities, float* dL_dcolors, const GsRasterConfig* config,
+                        void* stream)
+{
+    return rasterize_bwd_impl<float>(who, C, views, V, P, T_total, means2d, conics, opacities, colors, isect_ids,
+                                     nullptr, nullptr, nullptr, tile_ranges, nullptr, 0, background, T_final, last_idx,
+                                     config ? config->warp_hits : nullptr, dL_dout, 0, nullptr, 0, dL_dmeans2d,
+                                     dL_dconics, dL_dopacities, dL_dcolors, config, stream);
 }
 
 }  // namespace gs
@@ -572,7 +635,7 @@ extern "C" int gs_rasterize_fwd(const GsView* views, int32_t V, int32_t T_total,
                                 float* out_rgb, float* T_final, int32_t* last_idx, int32_t* n_contrib,
                                 const GsRasterConfig* config, void* stream)
 {
-    return rasterize_fwd_impl<float>("gs_rasterize_fwd", views, V, T_total, means2d, conics, opacities, colors,
+    return rasterize_fwd_impl<float>("gs_rasterize_fwd", 3, views, V, T_total, means2d, conics, opacities, colors,
                                      isect_ids, tile_ranges, background, out_rgb, T_final, last_idx, n_contrib,
                                      config ? config->warp_hits : nullptr, config, stream);
 }
@@ -583,7 +646,7 @@ extern "C" int gs_rasterize_fwd_f64(const GsView* views, int32_t V, int32_t T_to
                                     double* out_rgb, double* T_final, int32_t* last_idx, int32_t* n_contrib,
                                     const GsRasterConfig* config, void* stream)
 {
-    return rasterize_fwd_impl<double>("gs_rasterize_fwd_f64", views, V, T_total, means2d, conics, opacities, colors,
+    return rasterize_fwd_impl<double>("gs_rasterize_fwd_f64", 3, views, V, T_total, means2d, conics, opacities, colors,
                                       isect_ids, tile_ranges, background, out_rgb, T_final, last_idx, n_contrib,
                                       config ? config->warp_hits : nullptr, config, stream);
 }
@@ -607,7 +670,7 @@ extern "C" int gs_rasterize_bwd(const GsView* views, int32_t V, int64_t P, int32
                                 void* workspace, size_t workspace_bytes, float* dL_dmeans2d, float* dL_dconics,
                                 float* dL_dopacities, float* dL_dcolors, const GsRasterConfig* config, void* stream)
 {
-    return rasterize_bwd_impl<float>("gs_rasterize_bwd", views, V, P, T_total, means2d, conics, opacities, colors,
+    return rasterize_bwd_impl<float>("gs_rasterize_bwd", 3, views, V, P, T_total, means2d, conics, opacities, colors,
                                      isect_ids, isect_pos, emit_start, touched, tile_ranges, K, K_capacity,
                                      background, T_final, last_idx, config ? config->warp_hits : nullptr, dL_drgb,
                                      deterministic, workspace,
@@ -625,7 +688,7 @@ extern "C" int gs_rasterize_bwd_f64(const GsView* views, int32_t V, int64_t P, i
                                     double* dL_dmeans2d, double* dL_dconics, double* dL_dopacities,
                                     double* dL_dcolors, const GsRasterConfig* config, void* stream)
 {
-    return rasterize_bwd_impl<double>("gs_rasterize_bwd_f64", views, V, P, T_total, means2d, conics, opacities,
+    return rasterize_bwd_impl<double>("gs_rasterize_bwd_f64", 3, views, V, P, T_total, means2d, conics, opacities,
                                       colors, isect_ids, isect_pos, emit_start, touched, tile_ranges, K, K_capacity,
                                       background, T_final, last_idx, config ? config->warp_hits : nullptr, dL_drgb,
                                       deterministic, workspace,

@@ -438,9 +438,9 @@ extern "C" int gs_rasterize_fwd_nc(const GsView* views, int32_t V, int32_t T_tot
 {
     const char* who = "gs_rasterize_fwd_nc";
     if (V <= 0 || T_total < 0 || C <= 0) return fail(GS_ERR_INVALID_ARG, "%s: V=%d T_total=%d C=%d", who, V, T_total, C);
-    if (C == 3)  // the tuned 3-channel kernels compute the same
-        return gs_rasterize_fwd(views, V, T_total, means2d, conics, opacities, colors, isect_ids, tile_ranges,
-                                background, out, T_final, last_idx, n_contrib, config, stream);
+    if (C <= 3)  // the tuned kernels take up to 3 channels
+        return rasterize_fwd_upto3(who, C, views, V, T_total, means2d, conics, opacities, colors, isect_ids,
+                                   tile_ranges, background, out, T_final, last_idx, n_contrib, config, stream);
     if (!views || !tile_ranges || !out || !T_final || !last_idx)
         return fail(GS_ERR_INVALID_ARG, "%s: null pointer argument", who);
     if (misaligned8(means2d) || misaligned8(tile_ranges))
@@ -462,10 +462,10 @@ extern "C" int gs_rasterize_bwd_nc(const GsView* views, int32_t V, int64_t P, in
     const char* who = "gs_rasterize_bwd_nc";
     if (V <= 0 || P < 0 || T_total < 0 || C <= 0)
         return fail(GS_ERR_INVALID_ARG, "%s: V=%d P=%lld T_total=%d C=%d", who, V, (long long)P, T_total, C);
-    if (C == 3)
-        return gs_rasterize_bwd(views, V, P, T_total, means2d, conics, opacities, colors, isect_ids, nullptr,
-                                nullptr, nullptr, tile_ranges, nullptr, 0, background, T_final, last_idx, dL_dout, 0,
-                                nullptr, 0, dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors, config, stream);
+    if (C <= 3)
+        return rasterize_bwd_upto3(who, C, views, V, P, T_total, means2d, conics, opacities, colors, isect_ids,
+                                   tile_ranges, background, T_final, last_idx, dL_dout, dL_dmeans2d, dL_dconics,
+                                   dL_dopacities, dL_dcolors, config, stream);
     if (!views || !tile_ranges || !T_final || !last_idx || !dL_dout ||
         (P > 0 && (!dL_dmeans2d || !dL_dconics || !dL_dopacities || !dL_dcolors)))
         return fail(GS_ERR_INVALID_ARG, "%s: null pointer argument", who);

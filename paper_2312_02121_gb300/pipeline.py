@@ -131,7 +131,7 @@ def forward(views: B.Views, p: Params, eps2d: float = 0.3, background: Optional[
     T_final = torch.empty(pix, device=dev, dtype=dt)
     last_idx = torch.empty(pix, dtype=torch.int32, device=dev)
     n_contrib = torch.empty(pix, dtype=torch.int32, device=dev) if count_contrib else None
-    if config is None and C == 3:
+    if config is None and C <= 3:
         # the forward records its per-pair warp-box cull for the backward
         config = B.RasterConfig(device=dev, warp_hits=torch.empty(cap, dtype=torch.int32, device=dev))
     if C == 3:

@@ -1,6 +1,7 @@
 """Any number of channels per Gaussian (gs_rasterize_fwd_nc / _bwd_nc): parity
 with the FP64 oracle for 1 to 40 channels, including several 32-channel chunks
-and their ragged tails; agreement with the tuned 3-channel kernels; invariance
+and their ragged tails; agreement with the tuned 3-channel kernels (which also
+run 1 and 2 channels); invariance
 under the pair cull and the persistent tile queue; the optimisation loop on a
 4-channel scene."""
 import os
@@ -81,6 +82,30 @@ def test_multichannel_kernels_agree_with_the_three_channel_kernels():
         assert rel_l2(np_(g4[k]), np_(g3[k])) <= 1e-5, k
     assert rel_l2(np_(g4["colors"])[:, :3], np_(g3["colors"])) <= 1e-6
     assert not np_(g4["colors"])[:, 3].any()
+
+
+@pytest.mark.parametrize("C", [1, 2])
+def test_one_or_two_channels_run_as_three_with_zero_channels(C):
+    # C < 3 runs the tuned kernels with the missing channels read as zero colour and zero dL/dC: the
+    # same arithmetic as three channels whose extra ones are zero
+    w = wl.small_case(63 + C, 3000, 150, 110, log_scale_mu=-2.4, opacity_logit_mu=0.8)
+    s3 = _scene(w, 3, 7)
+    s3.colors[:, C:] = 0
+    sC = types.SimpleNamespace(**{**vars(s3), "colors": np.ascontiguousarray(s3.colors[:, :C])})
+    views = B.Views([w.views[0].camera], [(0, s3.n)], device="cuda")
+    p3, pC = _params(s3), _params(sC)
+    f3 = pipeline.forward(views, p3, w.eps2d)
+    fC = pipeline.forward(views, pC, w.eps2d)
+    np.testing.assert_array_equal(np_(fC.out_rgb), np_(f3.out_rgb)[:, :C])
+    np.testing.assert_array_equal(np_(fC.T_final), np_(f3.T_final))
+    np.testing.assert_array_equal(np_(fC.last_idx), np_(f3.last_idx))
+    G3 = np.random.default_rng(8).standard_normal((views.pixels, 3)).astype(np.float32)
+    G3[:, C:] = 0
+    g3 = pipeline.backward(f3, p3, torch.tensor(G3, device="cuda"))
+    gC = pipeline.backward(fC, pC, torch.tensor(np.ascontiguousarray(G3[:, :C]), device="cuda"))
+    for k in ("means2d", "conics", "means", "quats", "scales", "opacities"):
+        assert rel_l2(np_(gC[k]), np_(g3[k])) <= 1e-5, k
+    assert rel_l2(np_(gC["colors"]), np_(g3["colors"])[:, :C]) <= 1e-6
 
 
 def test_multichannel_cull_and_persistent_queue_change_nothing():

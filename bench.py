@@ -297,6 +297,7 @@ def batched_comparison(dev, steps: int):
         del rd, pvd
         out[name] = {"views": views.V, "scenes": len(w.scenes), "gaussians": params.n, "pixels": views.pixels,
                      "intersections": cap, "batched_mpix_s": views.pixels / ms_b / 1e3,
+                     "batched_intersections_per_s": cap / (ms_b / 1e3),
                      "per_view_mpix_s": views.pixels / ms_v / 1e3, "speedup": ms_v / ms_b,
                      "batched_ms_per_step": ms_b, "per_view_ms_per_step": ms_v,
                      "batched_launches_per_step": int(launches_b), "per_view_launches_per_step": int(launches_v),
@@ -686,7 +687,8 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "gaussians": sc.n, "width": cam.width, "height": cam.height,
-                   "views": 1, "intersections": K, "composited_pairs": contrib, "evaluated_pairs_bwd": walked,
+                   "views": 1, "intersections": K, "intersections_per_s": K / (ms_step / 1e3),
+                   "composited_pairs": contrib, "evaluated_pairs_bwd": walked,
                    "l2": "flushed (256 MiB write) before every timed step, outside its events",
                    "per_rank": "independent frame (seed = rank)"},
         "stage_ms": stage_ms, "eager_ms_per_step": eager_ms,

@@ -51,7 +51,6 @@ class BatchRenderer:
         self.means2d, self.conics, self.depths = e(max(P, 1), 2), e(max(P, 1), 3), e(max(P, 1))
         self.rects = e(max(P, 1), 4, dtype=torch.int16)
         self.touched = e(max(P, 1), dtype=torch.int32)
-        self.K_total = e(1, dtype=torch.int64)
         self.sort_ws = e(B.gs_bin_and_sort_workspace_size(P, self.cap, T), dtype=torch.uint8)
         self.isect_ids, self.isect_pos = e(self.cap, dtype=torch.int32), e(self.cap, dtype=torch.int32)
         self.emit_start = e(max(P, 1), dtype=torch.int32)
@@ -144,7 +143,7 @@ class BatchRenderer:
         if self.host is not None:
             self._upload()
         B.gs_project(v, p.means, p.quats, p.scales, self.eps2d, self.means2d, self.conics, self.depths, self.rects,
-                     self.touched, self.K_total)
+                     self.touched, None)  # the pair count comes from the sort (no per-block atomics here)
         self.flags.zero_()
         B.gs_bin_and_sort(v, self.rects, self.depths, self.touched, self.cap, self.sort_ws, self.isect_ids,
                           self.isect_pos if self.deterministic else None,

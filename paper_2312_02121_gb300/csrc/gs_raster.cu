@@ -38,16 +38,17 @@ namespace gs {
 
 constexpr int kRec = 9;  // dmu'(2) dconic(3) dopacity(1) dcolor(3)
 
-// The colours of these kernels have C = 1, 2 or 3 channels (3: the RGB of Eq. 7): the values of a
-// Gaussian or a pixel are C apart; a missing channel reads as zero (zero colour, zero dL/dC, so it
-// adds nothing to alpha's gradient) and is never written.
+// These kernels composite up to 3 channels (the RGB of Eq. 7) of colours whose values are C apart
+// per Gaussian or pixel: CW = 1, 2 or 3 of them, from the pointers given (a chunk of a C-channel
+// image starts at an offset).  A channel past CW reads as zero (zero colour, zero dL/dC, so it adds
+// nothing to alpha's gradient) and is never written.
 template <typename S>
-__device__ __forceinline__ void load_c3(const S* __restrict__ a, int64_t i, int C, S& x, S& y, S& z)
+__device__ __forceinline__ void load_c3(const S* __restrict__ a, int64_t i, int C, int CW, S& x, S& y, S& z)
 {
     const S* b = a + (int64_t)C * i;
     x = b[0];
-    y = C > 1 ? b[1] : S(0);
-    z = C > 2 ? b[2] : S(0);
+    y = CW > 1 ? b[1] : S(0);
+    z = CW > 2 ? b[2] : S(0);
 }
 
 // ---------------------------------------------------------------------------
@@ -59,9 +60,9 @@ __device__ __forceinline__ void load_c3(const S* __restrict__ a, int64_t i, int 
 // otherwise CTA i renders queue slot i.  Slot qi renders tile tile_order[qi]
 // (identity when tile_order is NULL).  kCount: also count each pixel's
 // composited Gaussians into n_contrib (a separate instantiation, so that the
-// usual walk carries no counter).  kAnyC: colours of C_arg = 1, 2 or 3
-// channels; otherwise 3 (a separate instantiation: the runtime stride cost
-// the 3-channel walk 2 %).
+// usual walk carries no counter).  kAnyC: W_arg channels of colours C_arg
+// apart; otherwise 3 channels 3 apart (a separate instantiation: the runtime
+// stride cost the 3-channel walk 2 %).
 template <typename S, bool kCull, bool kPersistent, bool kCount, bool kAnyC>
 __global__ void __launch_bounds__(256, 6)  // 6 CTAs per SM (40 registers) measured fastest
 k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t* __restrict__ tile_order,
@@ -69,11 +70,11 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
              const S* __restrict__ opacities, const S* __restrict__ colors, const int32_t* __restrict__ isect_ids,
              const int2* __restrict__ tile_ranges, const S* __restrict__ background, S* __restrict__ out_rgb,
              S* __restrict__ T_final, int32_t* __restrict__ last_idx, int32_t* __restrict__ n_contrib,
-             uint32_t* __restrict__ warp_hits, int C_arg)
+             uint32_t* __restrict__ warp_hits, int C_arg, int W_arg)
 {
     pdl_wait();
     pdl_trigger();
-    const int C = kAnyC ? C_arg : 3;
+    const int C = kAnyC ? C_arg : 3, CW = kAnyC ? W_arg : 3;
     constexpr int kB = RT<S>::kFwdBatch;
     __shared__ V4<S> sh_xy[kB], sh_q[kB], sh_col[kB], sh_cull[kB];
     __shared__ int s_next;
@@ -102,7 +103,7 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                     const int p = isect_ids[i];
                     const int64_t g = p + t.g_shift;
                     S c0, c1, c2;
-                    load_c3(colors, g, C, c0, c1, c2);
+                    load_c3(colors, g, C, CW, c0, c1, c2);
                     stage_gaussian<S>(sh_xy, sh_q, sh_col, sh_cull, threadIdx.x, means2d[p], conics[3 * p],
                                       conics[3 * p + 1], conics[3 * p + 2], opacities[g], c0, c1, c2);
                 }
@@ -148,11 +149,11 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
         }
         if (t.inside) {
             S bg0 = 0, bg1 = 0, bg2 = 0;
-            if (background) load_c3(background, 0, C, bg0, bg1, bg2);
+            if (background) load_c3(background, 0, C, CW, bg0, bg1, bg2);
             S* o = out_rgb + (int64_t)C * t.pix;
             o[0] = fma(T, bg0, C0);
-            if (C > 1) o[1] = fma(T, bg1, C1);
-            if (C > 2) o[2] = fma(T, bg2, C2);
+            if (CW > 1) o[1] = fma(T, bg1, C1);
+            if (CW > 2) o[2] = fma(T, bg2, C2);
             T_final[t.pix] = T;
             last_idx[t.pix] = last;
             if (kCount) n_contrib[t.pix] = count;
@@ -219,7 +220,8 @@ __device__ __forceinline__ void flush_partial(int j, int b0, const S (*s_grad)[k
                                               const unsigned (*s_mask)[(kB + 31) / 32], V4<S> fl,
                                               int64_t g_shift, S* __restrict__ records,
                                               V2<S>* __restrict__ dL_dmeans2d, S* __restrict__ dL_dconics,
-                                              S* __restrict__ dL_dopacities, S* __restrict__ dL_dcolors, int C)
+                                              S* __restrict__ dL_dopacities, S* __restrict__ dL_dcolors, int C,
+                                              int CW)
 {
     S acc[kRec];
 #pragma unroll
@@ -250,8 +252,8 @@ __device__ __forceinline__ void flush_partial(int j, int b0, const S (*s_grad)[k
             atomicAdd(dL_dopacities + g, acc[5]);
             S* dc = dL_dcolors + (int64_t)C * g;
             atomicAdd(dc, acc[6]);
-            if (C > 1) atomicAdd(dc + 1, acc[7]);
-            if (C > 2) atomicAdd(dc + 2, acc[8]);
+            if (CW > 1) atomicAdd(dc + 1, acc[7]);
+            if (CW > 2) atomicAdd(dc + 2, acc[8]);
         }
     } else {
         S* rec = records + (size_t)(b0 + j) * kRec;
@@ -273,11 +275,11 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
              const int32_t* __restrict__ last_idx, const uint32_t* __restrict__ warp_hits,
              const S* __restrict__ dL_drgb, S* __restrict__ records,
              V2<S>* __restrict__ dL_dmeans2d, S* __restrict__ dL_dconics, S* __restrict__ dL_dopacities,
-             S* __restrict__ dL_dcolors, int C_arg)
+             S* __restrict__ dL_dcolors, int C_arg, int W_arg)
 {
     pdl_wait();
     pdl_trigger();
-    const int C = kAnyC ? C_arg : 3;
+    const int C = kAnyC ? C_arg : 3, CW = kAnyC ? W_arg : 3;
     // one partial slot per (warp, Gaussian), written with plain stores and summed in warp order at
     // the flush (shared-memory atomics into one slot per Gaussian were measured 8 % slower)
     constexpr int kB = RT<S>::kBwdBatch;
@@ -308,10 +310,10 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
         if (t.inside) {
             T = T_final[t.pix];
             last = last_idx[t.pix];
-            load_c3(dL_drgb, t.pix, C, g0, g1, g2);
+            load_c3(dL_drgb, t.pix, C, CW, g0, g1, g2);
             if (background) {
                 S b0, b1, b2;
-                load_c3(background, 0, C, b0, b1, b2);
+                load_c3(background, 0, C, CW, b0, b1, b2);
                 bgT = T * (b0 * g0 + b1 * g1 + b2 * g2);
             }
         }
@@ -351,7 +353,7 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                 const int p = isect_ids[b0 + threadIdx.x];
                 const int64_t g = p + t.g_shift;
                 S c0, c1, c2;
-                load_c3(colors, g, C, c0, c1, c2);
+                load_c3(colors, g, C, CW, c0, c1, c2);
                 stage_gaussian<S>(sh_xy, sh_q, sh_col, sh_cull, threadIdx.x, means2d[p], conics[3 * p],
                                   conics[3 * p + 1], conics[3 * p + 2], opacities[g], c0, c1, c2);
                 s_fl[k & 1][threadIdx.x] = mk4<S>(sh_xy[threadIdx.x].w, sh_q[threadIdx.x].w, sh_col[threadIdx.x].w,
@@ -359,7 +361,7 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
             } else if (threadIdx.x >= kB && threadIdx.x < kB + prev_n) {
                 const int j = threadIdx.x - kB;
                 flush_partial<S, kAtomic, kB>(j, prev_b0, s_grad, s_mask, s_fl[(k + 1) & 1][j], t.g_shift, records,
-                                              dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors, C);
+                                              dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors, C, CW);
             }
             if (put_hits) (&s_hitw[0][0])[threadIdx.x] = hw;
             __syncthreads();
@@ -433,7 +435,7 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
         }
         if (threadIdx.x < prev_n)  // the last walked batch (batch 0)
             flush_partial<S, kAtomic, kB>(threadIdx.x, prev_b0, s_grad, s_mask, s_fl[0][threadIdx.x], t.g_shift,
-                                          records, dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors, C);
+                                          records, dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors, C, CW);
         if (!kAtomic) {
             // Gaussians after every pixel's last one received nothing
             const int first_unused = max(range.x, maxlast + 1);
@@ -454,7 +456,7 @@ k_reduce_records(const GsView* __restrict__ views, int V, int64_t P, const int32
                  const int32_t* __restrict__ emit_start, const int32_t* __restrict__ isect_pos,
                  const int32_t* __restrict__ K_dev, int64_t cap, const S* __restrict__ records,
                  V2<S>* __restrict__ dL_dmeans2d, S* __restrict__ dL_dconics, S* __restrict__ dL_dopacities,
-                 S* __restrict__ dL_dcolors, int C)
+                 S* __restrict__ dL_dcolors, int C, int CW)
 {
     pdl_wait();
     pdl_trigger();
@@ -484,22 +486,22 @@ k_reduce_records(const GsView* __restrict__ views, int V, int64_t P, const int32
     const int64_t g = view.g_begin + (p - view.proj_offset);
     atomicAdd(dL_dopacities + g, acc[5]);
     S* dc = dL_dcolors + (int64_t)C * g;
-    if (C == 3) {
+    if (CW == 3) {
         atomic_add3(dc, acc[6], acc[7], acc[8]);
     } else {
         atomicAdd(dc, acc[6]);
-        if (C > 1) atomicAdd(dc + 1, acc[7]);
+        if (CW > 1) atomicAdd(dc + 1, acc[7]);
     }
 }
 
 template <typename S>
-static int rasterize_fwd_impl(const char* who, int C, const GsView* views, int32_t V, int32_t T_total, const S* means2d,
+static int rasterize_fwd_impl(const char* who, int C, int CW, const GsView* views, int32_t V, int32_t T_total, const S* means2d,
                               const S* conics, const S* opacities, const S* colors, const int32_t* isect_ids,
                               const int32_t* tile_ranges, const S* background, S* out_rgb, S* T_final,
                               int32_t* last_idx, int32_t* n_contrib, uint32_t* warp_hits,
                               const GsRasterConfig* config, void* stream)
 {
-    if (V <= 0 || T_total < 0 || C < 1 || C > 3)
+    if (V <= 0 || T_total < 0 || CW < 1 || CW > 3 || C < CW)
         return fail(GS_ERR_INVALID_ARG, "%s: V=%d T_total=%d C=%d", who, V, T_total, C);
     if (!views || !tile_ranges || !out_rgb || !T_final || !last_idx)
         return fail(GS_ERR_INVALID_ARG, "%s: null pointer argument", who);
@@ -522,7 +524,7 @@ static int rasterize_fwd_impl(const char* who, int C, const GsView* views, int32
           {k_raster_fwd<S, true, false, true, false>, k_raster_fwd<S, true, false, true, kA>}},
          {{k_raster_fwd<S, true, true, false, false>, k_raster_fwd<S, true, true, false, kA>},
           {k_raster_fwd<S, true, true, true, false>, k_raster_fwd<S, true, true, true, kA>}}}};
-    const KF kern = table[cull][pers][n_contrib != nullptr][C != 3];
+    const KF kern = table[cull][pers][n_contrib != nullptr][C != 3 || CW != 3];
     unsigned grid;
     if (int rc = raster_grid(kern, config, T_total, &grid)) return rc;
     int* queue = pers ? config->queue : nullptr;
@@ -530,7 +532,7 @@ static int rasterize_fwd_impl(const char* who, int C, const GsView* views, int32
     launch_pdl(kern, grid, 256, s, views, V, T_total, config ? config->tile_order : nullptr, queue,
                               reinterpret_cast<const V2<S>*>(means2d), conics, opacities, colors, isect_ids,
                               reinterpret_cast<const int2*>(tile_ranges), background, out_rgb, T_final, last_idx,
-                              n_contrib, warp_hits, C);
+                              n_contrib, warp_hits, C, CW);
     count_launches(1);
     return launch_status(who);
 }
@@ -543,7 +545,7 @@ static size_t bwd_workspace(int64_t K_capacity, int32_t deterministic)
 }
 
 template <typename S>
-static int rasterize_bwd_impl(const char* who, int C, const GsView* views, int32_t V, int64_t P, int32_t T_total,
+static int rasterize_bwd_impl(const char* who, int C, int CW, const GsView* views, int32_t V, int64_t P, int32_t T_total,
                               const S* means2d, const S* conics, const S* opacities, const S* colors,
                               const int32_t* isect_ids, const int32_t* isect_pos, const int32_t* emit_start,
                               const int32_t* touched, const int32_t* tile_ranges, const int32_t* K, int64_t K_capacity,
@@ -553,7 +555,8 @@ static int rasterize_bwd_impl(const char* who, int C, const GsView* views, int32
                               S* dL_dconics, S* dL_dopacities, S* dL_dcolors, const GsRasterConfig* config,
                               void* stream)
 {
-    if (V <= 0 || P < 0 || T_total < 0 || K_capacity < 0 || K_capacity >= (int64_t(1) << 31) || C < 1 || C > 3)
+    if (V <= 0 || P < 0 || T_total < 0 || K_capacity < 0 || K_capacity >= (int64_t(1) << 31) || CW < 1 || CW > 3 ||
+        C < CW)
         return fail(GS_ERR_INVALID_ARG, "%s: V=%d P=%lld T_total=%d K_capacity=%lld C=%d", who, V, (long long)P,
                     T_total, (long long)K_capacity, C);
     if (!views || !tile_ranges || !T_final || !last_idx || !dL_drgb ||
@@ -582,7 +585,7 @@ static int rasterize_bwd_impl(const char* who, int C, const GsView* views, int32
           {k_raster_bwd<S, true, false, true, false>, k_raster_bwd<S, true, false, true, kA>}},
          {{k_raster_bwd<S, true, true, false, false>, k_raster_bwd<S, true, true, false, kA>},
           {k_raster_bwd<S, true, true, true, false>, k_raster_bwd<S, true, true, true, kA>}}}};
-    const KB kern = table[cull][!deterministic][pers][C != 3];
+    const KB kern = table[cull][!deterministic][pers][C != 3 || CW != 3];
     unsigned grid;
     if (int rc = raster_grid(kern, config, T_total, &grid)) return rc;
     int* queue = pers ? config->queue : nullptr;
@@ -591,38 +594,58 @@ static int rasterize_bwd_impl(const char* who, int C, const GsView* views, int32
                               reinterpret_cast<const V2<S>*>(means2d), conics, opacities, colors, isect_ids,
                               reinterpret_cast<const int2*>(tile_ranges), background, T_final, last_idx, warp_hits,
                               dL_drgb,
-                              records, reinterpret_cast<V2<S>*>(dL_dmeans2d), dL_dconics, dL_dopacities, dL_dcolors, C);
+                              records, reinterpret_cast<V2<S>*>(dL_dmeans2d), dL_dconics, dL_dopacities, dL_dcolors, C,
+                              CW);
     count_launches(1);
     if (deterministic) {
         launch_pdl(k_reduce_records<S>, (unsigned)((P + 255) / 256), 256, s,
             views, V, P, touched, emit_start, isect_pos, K, K_capacity, records,
-            reinterpret_cast<V2<S>*>(dL_dmeans2d), dL_dconics, dL_dopacities, dL_dcolors, C);
+            reinterpret_cast<V2<S>*>(dL_dmeans2d), dL_dconics, dL_dopacities, dL_dcolors, C, CW);
         count_launches(1);
     }
     return launch_status(who);
 }
 
-int rasterize_fwd_upto3(const char* who, int C, const GsView* views, int32_t V, int32_t T_total, const float* means2d,
-                        const float* conics, const float* opacities, const float* colors, const int32_t* isect_ids,
-                        const int32_t* tile_ranges, const float* background, float* out, float* T_final,
-                        int32_t* last_idx, int32_t* n_contrib, const GsRasterConfig* config, void* stream)
+int rasterize_fwd_chunks3(const char* who, int C, const GsView* views, int32_t V, int32_t T_total,
+                          const float* means2d, const float* conics, const float* opacities, const float* colors,
+                          const int32_t* isect_ids, const int32_t* tile_ranges, const float* background, float* out,
+                          float* T_final, int32_t* last_idx, int32_t* n_contrib, const GsRasterConfig* config,
+                          void* stream)
 {
-    return rasterize_fwd_impl<float>(who, C, views, V, T_total, means2d, conics, opacities, colors, isect_ids,
-                                     tile_ranges, background, out, T_final, last_idx, n_contrib,
-                                     config ? config->warp_hits : nullptr, config, stream);
+    if (C < 1) return fail(GS_ERR_INVALID_ARG, "%s: C=%d", who, C);
+    // every chunk rebuilds the same alpha, T, last index and warp-box ballots
+    for (int c0 = 0; c0 < C; c0 += 3) {
+        const int cw = std::min(3, C - c0);
+        if (int rc = rasterize_fwd_impl<float>(who, C, cw, views, V, T_total, means2d, conics, opacities,
+                                               colors ? colors + c0 : nullptr, isect_ids, tile_ranges,
+                                               background ? background + c0 : nullptr, out ? out + c0 : nullptr,
+                                               T_final, last_idx, n_contrib, config ? config->warp_hits : nullptr,
+                                               config, stream))
+            return rc;
+    }
+    return GS_OK;
 }
 
-int rasterize_bwd_upto3(const char* who, int C, const GsView* views, int32_t V, int64_t P, int32_t T_total,
-                        const float* means2d, const float* conics, const float* opacities, const float* colors,
-                        const int32_t* isect_ids, const int32_t* tile_ranges, const float* background,
-                        const float* T_final, const int32_t* last_idx, const float* dL_dout, float* dL_dmeans2d,
-                        float* dL_dconics, float* dL_dopacities, float* dL_dcolors, const GsRasterConfig* config,
-                        void* stream)
+int rasterize_bwd_chunks3(const char* who, int C, const GsView* views, int32_t V, int64_t P, int32_t T_total,
+                          const float* means2d, const float* conics, const float* opacities, const float* colors,
+                          const int32_t* isect_ids, const int32_t* tile_ranges, const float* background,
+                          const float* T_final, const int32_t* last_idx, const float* dL_dout, float* dL_dmeans2d,
+                          float* dL_dconics, float* dL_dopacities, float* dL_dcolors, const GsRasterConfig* config,
+                          void* stream)
 {
-    return rasterize_bwd_impl<float>(who, C, views, V, P, T_total, means2d, conics, opacities, colors, isect_ids,
-                                     nullptr, nullptr, nullptr, tile_ranges, nullptr, 0, background, T_final, last_idx,
-                                     config ? config->warp_hits : nullptr, dL_dout, 0, nullptr, 0, dL_dmeans2d,
-                                     dL_dconics, dL_dopacities, dL_dcolors, config, stream);
+    if (C < 1) return fail(GS_ERR_INVALID_ARG, "%s: C=%d", who, C);
+    // each chunk adds its channels' share of every gradient (dL/dalpha is a sum over the channels)
+    for (int c0 = 0; c0 < C; c0 += 3) {
+        const int cw = std::min(3, C - c0);
+        if (int rc = rasterize_bwd_impl<float>(
+                who, C, cw, views, V, P, T_total, means2d, conics, opacities, colors ? colors + c0 : nullptr,
+                isect_ids, nullptr, nullptr, nullptr, tile_ranges, nullptr, 0, background ? background + c0 : nullptr,
+                T_final, last_idx, config ? config->warp_hits : nullptr, dL_dout ? dL_dout + c0 : nullptr, 0,
+                nullptr, 0, dL_dmeans2d, dL_dconics, dL_dopacities, dL_dcolors ? dL_dcolors + c0 : nullptr, config,
+                stream))
+            return rc;
+    }
+    return GS_OK;
 }
 
 }  // namespace gs
@@ -635,7 +658,7 @@ extern "C" int gs_rasterize_fwd(const GsView* views, int32_t V, int32_t T_total,
                                 float* out_rgb, float* T_final, int32_t* last_idx, int32_t* n_contrib,
                                 const GsRasterConfig* config, void* stream)
 {
-    return rasterize_fwd_impl<float>("gs_rasterize_fwd", 3, views, V, T_total, means2d, conics, opacities, colors,
+    return rasterize_fwd_impl<float>("gs_rasterize_fwd", 3, 3, views, V, T_total, means2d, conics, opacities, colors,
                                      isect_ids, tile_ranges, background, out_rgb, T_final, last_idx, n_contrib,
                                      config ? config->warp_hits : nullptr, config, stream);
 }
@@ -646,7 +669,7 @@ extern "C" int gs_rasterize_fwd_f64(const GsView* views, int32_t V, int32_t T_to
                                     double* out_rgb, double* T_final, int32_t* last_idx, int32_t* n_contrib,
                                     const GsRasterConfig* config, void* stream)
 {
-    return rasterize_fwd_impl<double>("gs_rasterize_fwd_f64", 3, views, V, T_total, means2d, conics, opacities, colors,
+    return rasterize_fwd_impl<double>("gs_rasterize_fwd_f64", 3, 3, views, V, T_total, means2d, conics, opacities, colors,
                                       isect_ids, tile_ranges, background, out_rgb, T_final, last_idx, n_contrib,
                                       config ? config->warp_hits : nullptr, config, stream);
 }
@@ -670,7 +693,7 @@ extern "C" int gs_rasterize_bwd(const GsView* views, int32_t V, int64_t P, int32
                                 void* workspace, size_t workspace_bytes, float* dL_dmeans2d, float* dL_dconics,
                                 float* dL_dopacities, float* dL_dcolors, const GsRasterConfig* config, void* stream)
 {
-    return rasterize_bwd_impl<float>("gs_rasterize_bwd", 3, views, V, P, T_total, means2d, conics, opacities, colors,
+    return rasterize_bwd_impl<float>("gs_rasterize_bwd", 3, 3, views, V, P, T_total, means2d, conics, opacities, colors,
                                      isect_ids, isect_pos, emit_start, touched, tile_ranges, K, K_capacity,
                                      background, T_final, last_idx, config ? config->warp_hits : nullptr, dL_drgb,
                                      deterministic, workspace,
@@ -688,7 +711,7 @@ extern "C" int gs_rasterize_bwd_f64(const GsView* views, int32_t V, int64_t P, i
                                     double* dL_dmeans2d, double* dL_dconics, double* dL_dopacities,
                                     double* dL_dcolors, const GsRasterConfig* config, void* stream)
 {
-    return rasterize_bwd_impl<double>("gs_rasterize_bwd_f64", 3, views, V, P, T_total, means2d, conics, opacities,
+    return rasterize_bwd_impl<double>("gs_rasterize_bwd_f64", 3, 3, views, V, P, T_total, means2d, conics, opacities,
                                       colors, isect_ids, isect_pos, emit_start, touched, tile_ranges, K, K_capacity,
                                       background, T_final, last_idx, config ? config->warp_hits : nullptr, dL_drgb,
                                       deterministic, workspace,

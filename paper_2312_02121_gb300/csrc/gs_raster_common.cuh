@@ -113,18 +113,19 @@ __device__ __forceinline__ bool reaches_box(const Staged<S>& g, S X0, S X1, S Y0
     return smin <= thr;
 }
 
-// The tuned 3-channel compositing kernels for C = 1, 2 or 3 channels (gs_raster.cu); the channel
-// entry points hand such C to them.
-int rasterize_fwd_upto3(const char* who, int C, const GsView* views, int32_t V, int32_t T_total, const float* means2d,
-                        const float* conics, const float* opacities, const float* colors, const int32_t* isect_ids,
-                        const int32_t* tile_ranges, const float* background, float* out, float* T_final,
-                        int32_t* last_idx, int32_t* n_contrib, const GsRasterConfig* config, void* stream);
-int rasterize_bwd_upto3(const char* who, int C, const GsView* views, int32_t V, int64_t P, int32_t T_total,
-                        const float* means2d, const float* conics, const float* opacities, const float* colors,
-                        const int32_t* isect_ids, const int32_t* tile_ranges, const float* background,
-                        const float* T_final, const int32_t* last_idx, const float* dL_dout, float* dL_dmeans2d,
-                        float* dL_dconics, float* dL_dopacities, float* dL_dcolors, const GsRasterConfig* config,
-                        void* stream);
+// The tuned compositing kernels for C channels, run on chunks of up to 3 of them (gs_raster.cu); the
+// channel entry points hand small C to them.
+int rasterize_fwd_chunks3(const char* who, int C, const GsView* views, int32_t V, int32_t T_total,
+                          const float* means2d, const float* conics, const float* opacities, const float* colors,
+                          const int32_t* isect_ids, const int32_t* tile_ranges, const float* background, float* out,
+                          float* T_final, int32_t* last_idx, int32_t* n_contrib, const GsRasterConfig* config,
+                          void* stream);
+int rasterize_bwd_chunks3(const char* who, int C, const GsView* views, int32_t V, int64_t P, int32_t T_total,
+                          const float* means2d, const float* conics, const float* opacities, const float* colors,
+                          const int32_t* isect_ids, const int32_t* tile_ranges, const float* background,
+                          const float* T_final, const int32_t* last_idx, const float* dL_dout, float* dL_dmeans2d,
+                          float* dL_dconics, float* dL_dopacities, float* dL_dcolors, const GsRasterConfig* config,
+                          void* stream);
 
 template <typename S>
 struct TileCtx {

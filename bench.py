@@ -352,7 +352,7 @@ def optimisation_loop(dev, w, steps: int):
 
 
 def channel_cost(dev, views, params, pr, frame_ids, tile_ranges, K, cap, eps2d: float,
-                 channels=(1, 3, 4, 6, 8, 12, 13, 16, 32),
+                 channels=(1, 3, 4, 8, 12, 16, 32),
                  steps: int = 10):
     """Device time of compositing forward + backward on the headline frame for
     several channel counts (same projection and sorted lists)."""

@@ -330,13 +330,13 @@ int gs_project_bwd(const GsView* views, int32_t V, int64_t P, const float* means
  * summed over the channels.  Arguments are those of gs_rasterize_fwd /
  * gs_rasterize_bwd (fast mode) with colors[N,C], background[C] (nullable),
  * out[pixels,C], dL_dout[pixels,C] and dL_dcolors[N,C]; T_final, last_idx and
- * n_contrib as there.  C <= 12 runs the kernels of gs_rasterize_fwd /
- * gs_rasterize_bwd once per chunk of up to 3 channels, with a channel stride
- * of C (a chunk's missing channels count as zero colour and zero dL/dC, which
- * adds nothing), GsRasterConfig.warp_hits included.  Larger C are composited
- * in chunks of up to 32 channels on kernels with a lane per channel (these
- * ignore warp_hits).  Either way every chunk rebuilds the same alpha and T,
- * and the backward adds every chunk's share with atomics.  Either way the backward's fp32 sums vary in the last bits run to
+ * n_contrib as there.  C <= 3 runs the kernels of gs_rasterize_fwd /
+ * gs_rasterize_bwd with a channel stride of C (missing channels count as zero
+ * colour and zero dL/dC, which adds nothing), GsRasterConfig.warp_hits
+ * included.  Larger C are composited in chunks of up to 32 channels on
+ * kernels with a lane per channel (these ignore warp_hits): every chunk
+ * rebuilds the same alpha and T, and the backward adds every chunk's share
+ * with atomics.  Either way the backward's fp32 sums vary in the last bits run to
  * run (the deterministic mode is gs_rasterize_bwd's).  Outputs of the
  * backward are ACCUMULATED (the caller zeroes them).
  */

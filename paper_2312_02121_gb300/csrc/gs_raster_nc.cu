@@ -15,9 +15,10 @@
 // tile, one pixel per thread, warps on 8x4 pixel boxes, the exact per-warp box
 // cull, branchless bodies.  Colours are staged in shared memory beside the
 // geometry.  The backward sums a Gaussian's 6 + NC per-pixel terms over the
-// warp with butterfly shuffles (or takes the lone contributing lane's terms),
-// adds them into a per-(tile, Gaussian) slot with shared atomics, and flushes
-// the slots to the outputs with global atomics.  The deterministic reduction
+// warp through a shared-memory transpose, 16 terms at a time (or takes the
+// lone contributing lane's terms), adds them into a per-(tile, Gaussian) slot
+// with shared atomics, and flushes the slots to the outputs with global
+// atomics.  The deterministic reduction
 // of the 3-channel path is not offered here.
 #include "gs_raster_common.cuh"
 
@@ -25,9 +26,43 @@ namespace gs {
 
 template <int NC>
 struct Nc {
-    static constexpr int kB = NC >= 16 ? 128 : 256;  // Gaussians per staged batch
+    static constexpr int kB = NC >= 16 ? 128 : 256;  // Gaussians per staged batch (forward)
+    // backward batches: smaller, so that the per-warp reduction buffers fit the 48 KB of static
+    // shared memory beside the slots
+    static constexpr int kBwdB = NC >= 32 ? 64 : NC >= 4 ? 128 : 256;
     static constexpr int kR = 6 + NC;                // dmu'(2) dconic(3) dopacity(1) dcolor(NC)
 };
+
+// The warp's sums of r[0..kR) added into slot[0..kR) (shared memory, shared by the CTA's warps),
+// kG terms at a time through the warp's 32 x kGS buffer: every lane stores its kG terms as a row,
+// lane L then sums column L % kG over rows 16 (L / 16) .. +15, and one shuffle adds the two halves.
+// With rows kGS = 17 floats apart the row stores and the column loads are conflict-free.  The
+// order is fixed within the warp: 16 adds, then the other half.  (Butterfly shuffles cost 5
+// shuffles and 5 adds per term.)
+constexpr int kG = 16, kGS = 17;
+
+template <int kR>
+__device__ __forceinline__ void warp_add_terms(const float (&r)[kR], float* buf, float* slot, int lane)
+{
+    float* row = buf + lane * kGS;
+    const int col = lane & 15, half = lane >> 4;
+    const float* colp = buf + half * 16 * kGS + col;
+#pragma unroll
+    for (int g0 = 0; g0 < kR; g0 += kG) {
+#pragma unroll
+        for (int q = 0; q < kG; ++q)
+            if (g0 + q < kR) row[q] = r[g0 + q];
+        __syncwarp();
+        float acc = 0.f;
+        if (g0 + col < kR) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc += colp[i * kGS];
+        }
+        acc += __shfl_xor_sync(kFull, acc, 16);
+        if (half == 0 && g0 + col < kR) atomicAdd(slot + g0 + col, acc);
+        __syncwarp();  // the buffer is free again
+    }
+}
 
 // Stages the colour chunk [c0, c0 + nc) of the batch's Gaussians (sh_g holds
 // their Gaussian indices) into sh_c[j][0..NC), zero-padded; coalesced over k.
@@ -146,8 +181,9 @@ k_raster_bwd_nc(const GsView* __restrict__ views, int V, int T_total, const int3
 {
     pdl_wait();
     pdl_trigger();
-    constexpr int kB = Nc<NC>::kB, kR = Nc<NC>::kR;
+    constexpr int kB = Nc<NC>::kBwdB, kR = Nc<NC>::kR;
     __shared__ float4 sh_xy[kB], sh_q[kB], sh_col[kB], sh_cull[kB];
+    __shared__ float s_red[kWarps][32 * kGS];
     __shared__ __align__(16) float sh_c[kB][NC];
     __shared__ int sh_g[kB];
     __shared__ float s_grad[kB][kR];
@@ -267,17 +303,7 @@ k_raster_bwd_nc(const GsView* __restrict__ views, int V, int T_total, const int3
                                 for (int q = 0; q < kR; ++q) atomicAdd(slot + q, r[q]);
                             }
                         } else {
-#pragma unroll
-                            for (int q = 0; q < kR; ++q) {
-                                float x = r[q];
-#pragma unroll
-                                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-                                r[q] = x;
-                            }
-                            // every lane holds the totals; lane q % 32 adds term q
-#pragma unroll
-                            for (int q = 0; q < kR; ++q)
-                                if ((q & 31) == lane) atomicAdd(slot + q, r[q]);
+                            warp_add_terms<kR>(r, s_red[w], slot, lane);
                         }
                     }
                 }
@@ -430,10 +456,10 @@ struct BwdChunks {
 
 using namespace gs;
 
-// Up to this many channels the tuned 3-channel kernels, run once per chunk of 3, beat the lane-per-
-// channel kernels below (fwd+bwd at 1080p, 1M Gaussians: 4 channels 2.62 against 3.06 ms, 8 channels
-// 4.08 against 4.19, 12 channels 5.52 against about 6.9; 13 channels take 6.88 here).
-constexpr int kChunked3MaxC = 12;
+// Up to this many channels the tuned 3-channel kernels run the image (one chunk).  Beyond, the kernels
+// below are faster than the tuned ones run once per chunk of 3 (fwd+bwd at 1080p, 1M Gaussians:
+// 4 channels 1.52 against 2.62 ms, 8 channels 1.83 against 4.08, 12 channels 2.88 against 5.51).
+constexpr int kChunked3MaxC = 3;
 
 extern "C" int gs_rasterize_fwd_nc(const GsView* views, int32_t V, int32_t T_total, int32_t C, const float* means2d,
                                    const float* conics, const float* opacities, const float* colors,

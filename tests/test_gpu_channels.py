@@ -1,7 +1,7 @@
 """Any number of channels per Gaussian (gs_rasterize_fwd_nc / _bwd_nc): parity
 with the FP64 oracle for 1 to 40 channels, including several 32-channel chunks
 and their ragged tails; agreement with the tuned 3-channel kernels (which also
-run up to 12 channels, in chunks of 3); invariance
+run 1 and 2 channels); invariance
 under the pair cull and the persistent tile queue; the optimisation loop on a
 4-channel scene."""
 import os

@@ -9,6 +9,7 @@ alpha, which the backward kernels rebuild on the fly.
 from __future__ import annotations
 
 import dataclasses
+import math
 from typing import Optional
 
 import torch
@@ -158,9 +159,19 @@ def backward(f: Frame, p: Params, dL_drgb: torch.Tensor, stream=None, determinis
     if config is None:
         config = f.config
     dL_drgb = dL_drgb.contiguous().to(dt)
-    z = lambda *shape: torch.zeros(*shape, device=dev, dtype=dt)
     C = p.channels
-    g2, gc, go, gcol = z(max(P, 1), 2), z(max(P, 1), 3), z(max(N, 1)), z(max(N, 1), C)
+    # every gradient in one allocation, zeroed by one fill (the outputs are views of it)
+    Pm, Nm = max(P, 1), max(N, 1)
+    shapes = [(Pm, 2), (Pm, 3), (Nm,), (Nm, C), (Nm, 3), (Nm, 4), (Nm, 3)]
+    if viewmats:
+        shapes.append((max(views.V, 1), 4, 4))
+    sizes = [math.prod(sh) for sh in shapes]
+    flat = torch.zeros(sum(sizes), device=dev, dtype=dt)
+    parts, off = [], 0
+    for sh, n in zip(shapes, sizes):
+        parts.append(flat[off:off + n].view(*sh))
+        off += n
+    g2, gc, go, gcol, gm, gq, gs = parts[:7]
     if C == 3:
         nws = B.gs_rasterize_bwd_workspace_size(f.K_capacity, deterministic, dt == torch.float64)
         ws = torch.empty(nws, dtype=torch.uint8, device=dev) if nws else None
@@ -172,8 +183,7 @@ def backward(f: Frame, p: Params, dL_drgb: torch.Tensor, stream=None, determinis
             raise ValueError("the deterministic backward composites 3 channels")
         B.gs_rasterize_bwd_nc(views, C, f.means2d, f.conics, p.opacities, p.colors, f.isect_ids, f.tile_ranges,
                               f.background, f.T_final, f.last_idx, dL_drgb, g2, gc, go, gcol, config, stream)
-    gm, gq, gs = z(max(N, 1), 3), z(max(N, 1), 4), z(max(N, 1), 3)
-    gv = z(max(views.V, 1), 4, 4) if viewmats else None
+    gv = parts[7] if viewmats else None
     B.gs_project_bwd(views, p.means, p.quats, p.scales, f.eps2d, f.touched, g2, gc, gm, gq, gs, stream, gv)
     out = dict(means=gm[:N], quats=gq[:N], scales=gs[:N], opacities=go[:N], colors=gcol[:N], means2d=g2[:P],
                conics=gc[:P])

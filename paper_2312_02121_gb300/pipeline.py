@@ -70,8 +70,8 @@ class Frame:
     touched: torch.Tensor
     K_total: torch.Tensor
     isect_ids: torch.Tensor
-    isect_pos: torch.Tensor
-    emit_start: torch.Tensor
+    isect_pos: Optional[torch.Tensor]  # deterministic frames only
+    emit_start: Optional[torch.Tensor]
     tile_ranges: torch.Tensor
     K: torch.Tensor
     flags: torch.Tensor
@@ -105,9 +105,12 @@ def project(views: B.Views, p: Params, eps2d: float, stream=None):
 
 def forward(views: B.Views, p: Params, eps2d: float = 0.3, background: Optional[torch.Tensor] = None,
             K_capacity: Optional[int] = None, stream=None, count_contrib: bool = False,
-            config: Optional[B.RasterConfig] = None) -> Frame:
+            config: Optional[B.RasterConfig] = None, deterministic: bool = False) -> Frame:
     """Projection, binning + sort and compositing of every view.  Without
-    ``K_capacity`` the exact intersection count is read back (one sync)."""
+    ``K_capacity`` the exact intersection count is read back (one sync).
+    ``deterministic`` also keeps what the deterministic backward needs (the
+    sorted position of every pair in emission order); the fast backward does
+    without it."""
     _check_params(p)
     dev = p.means.device
     if background is not None:
@@ -118,8 +121,8 @@ def forward(views: B.Views, p: Params, eps2d: float = 0.3, background: Optional[
     P, T = views.P, views.T
     ws = torch.empty(B.gs_bin_and_sort_workspace_size(P, cap, T), dtype=torch.uint8, device=dev)
     isect_ids = torch.empty(cap, dtype=torch.int32, device=dev)
-    isect_pos = torch.empty(cap, dtype=torch.int32, device=dev)
-    emit_start = torch.empty(max(P, 1), dtype=torch.int32, device=dev)
+    isect_pos = torch.empty(cap, dtype=torch.int32, device=dev) if deterministic else None
+    emit_start = torch.empty(max(P, 1), dtype=torch.int32, device=dev) if deterministic else None
     tile_ranges = torch.empty(T, 2, dtype=torch.int32, device=dev)
     K = torch.empty(1, dtype=torch.int32, device=dev)
     flags = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -172,6 +175,8 @@ def backward(f: Frame, p: Params, dL_drgb: torch.Tensor, stream=None, determinis
         parts.append(flat[off:off + n].view(*sh))
         off += n
     g2, gc, go, gcol, gm, gq, gs = parts[:7]
+    if deterministic and f.isect_pos is None:
+        raise ValueError("the deterministic backward needs a frame from forward(..., deterministic=True)")
     if C == 3:
         nws = B.gs_rasterize_bwd_workspace_size(f.K_capacity, deterministic, dt == torch.float64)
         ws = torch.empty(nws, dtype=torch.uint8, device=dev) if nws else None

@@ -10,7 +10,8 @@ from paper_2312_02121_gb300 import pipeline
 
 def run_gpu(workload, dL_drgb=None, background=None, K_capacity=None, views_subset=None, deterministic=False):
     """Forward (and backward when dL_drgb is given) of every view of the workload.
-    Returns (frame, params, grads or None)."""
+    ``deterministic``: the deterministic backward, and a frame that keeps the
+    pairs' inverse positions.  Returns (frame, params, grads or None)."""
     B.load()
     dev = "cuda"
     offs = np.cumsum([0] + [s.n for s in workload.scenes])
@@ -20,7 +21,7 @@ def run_gpu(workload, dL_drgb=None, background=None, K_capacity=None, views_subs
     vs = workload.views if views_subset is None else [workload.views[i] for i in views_subset]
     views = B.Views([v.camera for v in vs], [(int(offs[v.scene]), workload.scenes[v.scene].n) for v in vs], device=dev)
     bg = None if background is None else torch.as_tensor(background, dtype=torch.float32, device=dev)
-    frame = pipeline.forward(views, params, workload.eps2d, bg, K_capacity)
+    frame = pipeline.forward(views, params, workload.eps2d, bg, K_capacity, deterministic=deterministic)
     grads = None
     if dL_drgb is not None:
         grads = pipeline.backward(frame, params, torch.as_tensor(dL_drgb, dtype=torch.float32, device=dev),

@@ -47,7 +47,7 @@ def case(request):
     rng = np.random.default_rng(42)
     G = rng.standard_normal((cam.height, cam.width, 3)).astype(np.float32)
     ofwd = oracle.render(cam, sc, w.eps2d)
-    frame, params, _ = run_gpu(w)
+    frame, params, _ = run_gpu(w, deterministic=True)  # the binning tests read the inverse positions
     # uncertain pixels: end to end (oracle projection) or given the CUDA projection
     bad = uncertain_pixels(ofwd, ofwd["proj"], cam.width, cam.height, sc.opacities)
     ogp = oracle.rasterize(gpu_projection(frame), sc.opacities, sc.colors, cam.width, cam.height)
@@ -403,7 +403,7 @@ def test_backward_with_forward_warp_hits_is_identical():
     G = torch.tensor(np.random.default_rng(5).standard_normal((views.pixels, 3)).astype(np.float32), device="cuda")
     for persistent in (False, True):
         plain = B.RasterConfig(persistent, 2)
-        f1 = pipeline.forward(views, params, w.eps2d, config=plain)
+        f1 = pipeline.forward(views, params, w.eps2d, config=plain, deterministic=True)
         g1 = pipeline.backward(f1, params, G, deterministic=True, config=plain)
         K = int(f1.K.item())
         # words the forward does not write (chunks past a warp's last pixel) must never be read:
@@ -411,7 +411,7 @@ def test_backward_with_forward_warp_hits_is_identical():
         hits = torch.randint(-2**31, 2**31 - 1, (f1.K_capacity,), dtype=torch.int32,
                              generator=torch.Generator().manual_seed(9)).cuda()
         with_hits = B.RasterConfig(persistent, 2, warp_hits=hits)
-        f2 = pipeline.forward(views, params, w.eps2d, config=with_hits)
+        f2 = pipeline.forward(views, params, w.eps2d, config=with_hits, deterministic=True)
         g2 = pipeline.backward(f2, params, G, deterministic=True, config=with_hits)
         torch.cuda.synchronize()
         assert int(hits[:K].count_nonzero()) > 0

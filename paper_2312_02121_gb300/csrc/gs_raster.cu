@@ -354,8 +354,9 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                 const int64_t g = p + t.g_shift;
                 S c0, c1, c2;
                 load_c3(colors, g, C, CW, c0, c1, c2);
+                // with the forward's ballots the backward never reads the cull thresholds
                 stage_gaussian<S>(sh_xy, sh_q, sh_col, sh_cull, threadIdx.x, means2d[p], conics[3 * p],
-                                  conics[3 * p + 1], conics[3 * p + 2], opacities[g], c0, c1, c2);
+                                  conics[3 * p + 1], conics[3 * p + 2], opacities[g], c0, c1, c2, !warp_hits);
                 s_fl[k & 1][threadIdx.x] = mk4<S>(sh_xy[threadIdx.x].w, sh_q[threadIdx.x].w, sh_col[threadIdx.x].w,
                                                   RT<S>::stash(p));
             } else if (threadIdx.x >= kB && threadIdx.x < kB + prev_n) {

@@ -67,7 +67,7 @@ __device__ __forceinline__ S neg_sigma_log2(const V4<S>& q, S dx, S dy, S& u)
 
 template <typename S>
 __device__ __forceinline__ void stage_gaussian(V4<S>* sh_xy, V4<S>* sh_q, V4<S>* sh_col, V4<S>* sh_cull, int j,
-                                               V2<S> m, S a, S b, S c, S o, S r, S g, S bl)
+                                               V2<S> m, S a, S b, S c, S o, S r, S g, S bl, bool need_cull = true)
 {
     // det with the rounding error of b^2 compensated (Kahan's 2x2 determinant)
     const S bb = b * b;
@@ -77,6 +77,7 @@ __device__ __forceinline__ void stage_gaussian(V4<S>* sh_xy, V4<S>* sh_q, V4<S>*
     sh_xy[j] = mk4<S>(m.x, m.y, o, a);
     sh_q[j] = mk4<S>(S(-0.5) * RT<S>::kLog2e * a, k, S(-0.5) * RT<S>::kLog2e * D, b);
     sh_col[j] = mk4<S>(r, g, bl, D);
+    if (!need_cull) return;  // a walk that takes its cull from elsewhere
     S thr;
     if (!(o >= RT<S>::alpha_min())) {
         thr = S(-1);  // o e^-sigma < 1/255 everywhere

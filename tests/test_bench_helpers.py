@@ -1,0 +1,71 @@
+"""Host-side helpers of bench.py that its reported numbers rest on: the exact
+count of (pixel, Gaussian) pairs the backward of Sec. 3.1 evaluates, the SFU
+roofline arithmetic, and the DRAM-traffic record keyed by the raster sources."""
+import importlib.util
+import os
+import sys
+import types
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    saved = sys.argv
+    sys.argv = ["bench.py"]
+    try:
+        spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+        mod = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(mod)
+    finally:
+        sys.argv = saved
+    return mod
+
+
+def test_walked_pairs_counts_each_pixels_entries_through_its_last(bench):
+    # a 40 x 20 image: 3 x 2 tiles, the last column and row of tiles partial
+    W, H = 40, 20
+    TX, TY = 3, 2
+    rng = np.random.default_rng(0)
+    lens = rng.integers(0, 9, TX * TY)
+    starts = np.concatenate([[0], np.cumsum(lens)[:-1]])
+    ranges = np.stack([starts, starts + lens], 1).astype(np.int32)
+    last = np.empty((H, W), np.int32)
+    expected = 0
+    for y in range(H):
+        for x in range(W):
+            t = (y // 16) * TX + x // 16
+            s, e = ranges[t]
+            # no composited Gaussian: last = start - 1, else an entry of the tile's list
+            last[y, x] = rng.integers(s - 1, e) if e > s else s - 1
+            expected += last[y, x] - s + 1
+    f = types.SimpleNamespace(tile_ranges=torch.tensor(ranges), last_idx=torch.tensor(last.reshape(-1)))
+    cam = types.SimpleNamespace(width=W, height=H)
+    assert bench.walked_pairs(f, cam, "cpu") == expected
+
+
+def test_sfu_roof_charges_one_ex2_and_one_rcp_per_pair(bench):
+    r = bench.sfu_roof(10**9, 1e-3, 2000.0)
+    per_pair_clk = 1 / bench.MUFU_EX2_PER_SM_CLK + 1 / bench.MUFU_RCP_PER_SM_CLK
+    assert r["peak"] == pytest.approx(bench.SMS * 2000e6 / per_pair_clk / 1e9)
+    assert r["achieved"] == pytest.approx(1000.0)  # 1e9 pairs in 1 ms = 1000 G pairs/s
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+
+
+def test_traffic_record_matches_only_the_current_raster_sources(bench):
+    h = bench.raster_source_hash()
+    assert len(h) == 64
+    rec = {}
+    for line in open(os.path.join(ROOT, "profiles", "roofline_traffic.txt")):
+        f = line.split()
+        if len(f) == 3 and not line.startswith("#"):
+            rec[f[0]] = (f[1], int(f[2]))
+    for k in ("k_raster_fwd", "k_raster_bwd"):
+        want = rec[k][1] if rec.get(k, ("", 0))[0] == h else None
+        assert bench.recorded_traffic(k) == want
+    assert bench.recorded_traffic("no_such_kernel") is None

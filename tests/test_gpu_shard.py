@@ -5,7 +5,6 @@ and no kernel waits on another).  The images of each rank's views must equal
 the whole batch's bit for bit.  The ranks' partial gradients must sum to the
 whole batch's gradients.  Both sides use the deterministic backward, so only
 the order of the final per-scene sum differs."""
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")

@@ -2,7 +2,6 @@
 differences of the oracle's forward (Sec. 2), stage by stage and end to end,
 plus the matrix-calculus rule of Sec. 3 the derivation rests on."""
 import numpy as np
-import pytest
 
 import oracle
 from paper_2312_02121_gb300 import workloads as wl

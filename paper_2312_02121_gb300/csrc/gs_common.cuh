@@ -7,6 +7,8 @@
 
 #include "gsplat103.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace gs {
 
 constexpr int kTile = GS_TILE;
@@ -72,6 +74,16 @@ __device__ __forceinline__ int view_of_tile(const GsView* __restrict__ views, in
 }
 
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// An NVTX range over one C-ABI call, named after it: profilers that collect NVTX
+// (Nsight Systems, ncu's --nvtx filters) see every stage; without one attached
+// the push and pop return at once.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Vector types for the fp32 and fp64 instantiations of the kernels: V2/V4 have
 // the size and alignment of 2/4 scalars, so they load and store as one vector.

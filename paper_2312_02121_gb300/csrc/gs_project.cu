@@ -441,6 +441,7 @@ extern "C" int gs_project(const GsView* views, int32_t V, int64_t P, const float
                           const float* scales, float eps2d, float* means2d, float* conics, float* depths,
                           int16_t* rects, int32_t* touched, int64_t* K_total, void* stream)
 {
+    gs::NvtxRange nvtx("gs_project");
     return project_impl<float>("gs_project", views, V, P, means, quats, scales, eps2d, means2d, conics, depths, rects,
                                 touched, K_total, stream);
 }
@@ -449,6 +450,7 @@ extern "C" int gs_project_f64(const GsView* views, int32_t V, int64_t P, const d
                               const double* scales, double eps2d, double* means2d, double* conics, float* depths,
                               int16_t* rects, int32_t* touched, int64_t* K_total, void* stream)
 {
+    gs::NvtxRange nvtx("gs_project_f64");
     return project_impl<double>("gs_project_f64", views, V, P, means, quats, scales, eps2d, means2d, conics, depths,
                                  rects, touched, K_total, stream);
 }
@@ -458,6 +460,7 @@ extern "C" int gs_project_bwd(const GsView* views, int32_t V, int64_t P, const f
                               const float* dL_dconics, float* dL_dmeans, float* dL_dquats, float* dL_dscales,
                               float* dL_dviewmats, void* stream)
 {
+    gs::NvtxRange nvtx("gs_project_bwd");
     return project_bwd_impl<float>("gs_project_bwd", views, V, P, means, quats, scales, eps2d, touched, dL_dmeans2d,
                                    dL_dconics, dL_dmeans, dL_dquats, dL_dscales, dL_dviewmats, stream);
 }
@@ -467,6 +470,7 @@ extern "C" int gs_project_bwd_f64(const GsView* views, int32_t V, int64_t P, con
                                   const double* dL_dmeans2d, const double* dL_dconics, double* dL_dmeans,
                                   double* dL_dquats, double* dL_dscales, double* dL_dviewmats, void* stream)
 {
+    gs::NvtxRange nvtx("gs_project_bwd_f64");
     return project_bwd_impl<double>("gs_project_bwd_f64", views, V, P, means, quats, scales, eps2d, touched,
                                     dL_dmeans2d, dL_dconics, dL_dmeans, dL_dquats, dL_dscales, dL_dviewmats, stream);
 }

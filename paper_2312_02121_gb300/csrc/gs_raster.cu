@@ -659,6 +659,7 @@ extern "C" int gs_rasterize_fwd(const GsView* views, int32_t V, int32_t T_total,
                                 float* out_rgb, float* T_final, int32_t* last_idx, int32_t* n_contrib,
                                 const GsRasterConfig* config, void* stream)
 {
+    gs::NvtxRange nvtx("gs_rasterize_fwd");
     return rasterize_fwd_impl<float>("gs_rasterize_fwd", 3, 3, views, V, T_total, means2d, conics, opacities, colors,
                                      isect_ids, tile_ranges, background, out_rgb, T_final, last_idx, n_contrib,
                                      config ? config->warp_hits : nullptr, config, stream);
@@ -670,6 +671,7 @@ extern "C" int gs_rasterize_fwd_f64(const GsView* views, int32_t V, int32_t T_to
                                     double* out_rgb, double* T_final, int32_t* last_idx, int32_t* n_contrib,
                                     const GsRasterConfig* config, void* stream)
 {
+    gs::NvtxRange nvtx("gs_rasterize_fwd_f64");
     return rasterize_fwd_impl<double>("gs_rasterize_fwd_f64", 3, 3, views, V, T_total, means2d, conics, opacities, colors,
                                       isect_ids, tile_ranges, background, out_rgb, T_final, last_idx, n_contrib,
                                       config ? config->warp_hits : nullptr, config, stream);
@@ -694,6 +696,7 @@ extern "C" int gs_rasterize_bwd(const GsView* views, int32_t V, int64_t P, int32
                                 void* workspace, size_t workspace_bytes, float* dL_dmeans2d, float* dL_dconics,
                                 float* dL_dopacities, float* dL_dcolors, const GsRasterConfig* config, void* stream)
 {
+    gs::NvtxRange nvtx("gs_rasterize_bwd");
     return rasterize_bwd_impl<float>("gs_rasterize_bwd", 3, 3, views, V, P, T_total, means2d, conics, opacities, colors,
                                      isect_ids, isect_pos, emit_start, touched, tile_ranges, K, K_capacity,
                                      background, T_final, last_idx, config ? config->warp_hits : nullptr, dL_drgb,
@@ -712,6 +715,7 @@ extern "C" int gs_rasterize_bwd_f64(const GsView* views, int32_t V, int64_t P, i
                                     double* dL_dmeans2d, double* dL_dconics, double* dL_dopacities,
                                     double* dL_dcolors, const GsRasterConfig* config, void* stream)
 {
+    gs::NvtxRange nvtx("gs_rasterize_bwd_f64");
     return rasterize_bwd_impl<double>("gs_rasterize_bwd_f64", 3, 3, views, V, P, T_total, means2d, conics, opacities,
                                       colors, isect_ids, isect_pos, emit_start, touched, tile_ranges, K, K_capacity,
                                       background, T_final, last_idx, config ? config->warp_hits : nullptr, dL_drgb,

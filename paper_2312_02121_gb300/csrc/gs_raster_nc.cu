@@ -467,6 +467,7 @@ extern "C" int gs_rasterize_fwd_nc(const GsView* views, int32_t V, int32_t T_tot
                                    float* out, float* T_final, int32_t* last_idx, int32_t* n_contrib,
                                    const GsRasterConfig* config, void* stream)
 {
+    gs::NvtxRange nvtx("gs_rasterize_fwd_nc");
     const char* who = "gs_rasterize_fwd_nc";
     if (V <= 0 || T_total < 0 || C <= 0) return fail(GS_ERR_INVALID_ARG, "%s: V=%d T_total=%d C=%d", who, V, T_total, C);
     if (C <= kChunked3MaxC)  // the tuned kernels, on chunks of up to 3 channels
@@ -490,6 +491,7 @@ extern "C" int gs_rasterize_bwd_nc(const GsView* views, int32_t V, int64_t P, in
                                    const float* dL_dout, float* dL_dmeans2d, float* dL_dconics, float* dL_dopacities,
                                    float* dL_dcolors, const GsRasterConfig* config, void* stream)
 {
+    gs::NvtxRange nvtx("gs_rasterize_bwd_nc");
     const char* who = "gs_rasterize_bwd_nc";
     if (V <= 0 || P < 0 || T_total < 0 || C <= 0)
         return fail(GS_ERR_INVALID_ARG, "%s: V=%d P=%lld T_total=%d C=%d", who, V, (long long)P, T_total, C);

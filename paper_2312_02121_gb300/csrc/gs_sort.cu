@@ -675,6 +675,7 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
                                size_t workspace_bytes, int32_t* isect_ids, int32_t* isect_pos, int32_t* emit_start,
                                int32_t* tile_ranges, int32_t* K_out, uint32_t* flags, void* stream)
 {
+    gs::NvtxRange nvtx("gs_bin_and_sort");
     if (V <= 0 || P < 0 || T_total <= 0 || K_capacity < 0 || P >= (int64_t(1) << 31) ||
         K_capacity >= (int64_t(1) << 31))
         return fail(GS_ERR_INVALID_ARG, "gs_bin_and_sort: V=%d P=%lld T_total=%d K_capacity=%lld", V, (long long)P,
@@ -739,6 +740,7 @@ extern "C" size_t gs_tile_order_workspace_size(int32_t T_total)
 extern "C" int gs_tile_order(const int32_t* tile_ranges, int32_t T_total, void* workspace, size_t workspace_bytes,
                              int32_t* order, void* stream)
 {
+    gs::NvtxRange nvtx("gs_tile_order");
     if (T_total < 0) return fail(GS_ERR_INVALID_ARG, "gs_tile_order: T_total=%d", T_total);
     if (T_total == 0) return GS_OK;
     if (!tile_ranges || !order || (reinterpret_cast<uintptr_t>(tile_ranges) & 7))

@@ -48,6 +48,7 @@ extern "C" int gs_bin_and_sort_static(const GsView* views, int32_t V, int64_t P,
                                       int32_t* isect_ids, int32_t* isect_pos, int32_t* emit_start,
                                       int32_t* tile_ranges, int32_t* K_out, uint32_t* flags, void* stream)
 {
+    gs::NvtxRange nvtx("gs_bin_and_sort_static");
     if (P > GS_STATIC_MAX_PROJECTIONS || K_capacity > GS_STATIC_MAX_INTERSECTIONS)
         return fail(GS_ERR_INVALID_ARG,
                     "gs_bin_and_sort_static: P=%lld and K_capacity=%lld must not exceed %d and %d "

@@ -192,12 +192,14 @@ using namespace gs;
 extern "C" int gs_l2_loss(const float* rgb, const float* target, int64_t n, float inv_norm, float* dL_drgb,
                           float* loss, void* stream)
 {
+    gs::NvtxRange nvtx("gs_l2_loss");
     return l2_loss_impl<float>("gs_l2_loss", rgb, target, n, inv_norm, dL_drgb, loss, stream);
 }
 
 extern "C" int gs_l2_loss_f64(const double* rgb, const double* target, int64_t n, double inv_norm, double* dL_drgb,
                               double* loss, void* stream)
 {
+    gs::NvtxRange nvtx("gs_l2_loss_f64");
     return l2_loss_impl<double>("gs_l2_loss_f64", rgb, target, n, inv_norm, dL_drgb, loss, stream);
 }
 
@@ -212,6 +214,7 @@ extern "C" int gs_adam_step(int64_t N, int32_t C, const GsAdamConfig* cfg, void*
                             const float* dL_dopacities, const float* dL_dcolors, float* scales, float* opacities,
                             const int32_t* skip_if_set, void* stream)
 {
+    gs::NvtxRange nvtx("gs_adam_step");
     const char* who = "gs_adam_step";
     if (N < 0 || C < 1 || !cfg)
         return fail(GS_ERR_INVALID_ARG, "%s: N=%lld, C=%d or null config", who, (long long)N, C);
@@ -249,6 +252,7 @@ extern "C" int gs_adam_step(int64_t N, int32_t C, const GsAdamConfig* cfg, void*
 extern "C" int gs_activate(int64_t N, const float* log_scales, const float* opacity_logits, float* scales,
                            float* opacities, void* stream)
 {
+    gs::NvtxRange nvtx("gs_activate");
     if (N < 0) return fail(GS_ERR_INVALID_ARG, "gs_activate: N=%lld", (long long)N);
     if (N == 0) return GS_OK;
     if (!log_scales || !opacity_logits || !scales || !opacities)

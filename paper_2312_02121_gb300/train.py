@@ -98,6 +98,34 @@ class Trainer:
         """The loss of the last step's forward (one device read)."""
         return float(self.r.loss.item())
 
+    def state_dict(self) -> Dict[str, torch.Tensor]:
+        """Host copies of everything a later run resumes from: the raw
+        parameters, the Adam state (both moments and the count of applied
+        steps) and the Adam constants (five learning rates, beta1, beta2, eps)."""
+        out = {k: self.raw[k].detach().cpu().clone() for k in RAW}
+        out["adam_state"] = self.state.detach().cpu().clone()
+        a = self.adam
+        out["adam_config"] = torch.tensor([*a.lr, a.beta1, a.beta2, a.eps], dtype=torch.float64)
+        return out
+
+    def load_state_dict(self, sd: Dict[str, torch.Tensor]) -> None:
+        """Resumes from ``state_dict()`` of a trainer over as many Gaussians
+        and channels.  The values go into this trainer's own buffers and the
+        activated scales and opacities are rebuilt; the step graph is captured
+        again at the next ``run`` (it holds the Adam constants)."""
+        for k in RAW:
+            if tuple(sd[k].shape) != tuple(self.raw[k].shape):
+                raise ValueError(f"{k}: shape {tuple(sd[k].shape)} in the checkpoint, {tuple(self.raw[k].shape)} here")
+        if sd["adam_state"].numel() != self.state.numel():
+            raise ValueError("the checkpoint's Adam state has another size (Gaussian or channel count)")
+        for k in RAW:
+            self.raw[k].copy_(sd[k])
+        self.state.copy_(sd["adam_state"])
+        c = [float(x) for x in sd["adam_config"]]
+        self.adam = B.adam_config(c[:5], c[5], c[6], c[7])
+        B.gs_activate(self.N, self.raw["log_scales"], self.raw["opacity_logits"], self.scales, self.opacities)
+        self.graph = None
+
     def steps_taken(self) -> int:
         """Adam steps applied so far (skipped steps excluded; one device read)."""
         return int(self.state[:4].view(torch.int32).item())

@@ -187,3 +187,35 @@ def test_overflow_skips_updates_and_run_grows_the_capacity():
     t.run(6, check_every=1)
     assert t.capacity > 50 and not t.overflowed()
     assert t.steps_taken() >= 1
+
+
+def test_checkpoint_resume_continues_the_same_loop(tmp_path):
+    # 4 steps, a checkpoint through torch.save, a fresh trainer that loads it and takes 4 more:
+    # the same loop as 8 steps in one trainer (up to the backward's fp32 summation order)
+    w = wl.small_case(44, 1500, 96, 80, log_scale_mu=-2.6)
+    cam, sc = w.views[0].camera, w.scenes[0]
+    raw = _scene_raw(sc)
+    tgt = torch.tensor(w.targets[0].reshape(-1, 3), device="cuda")
+    views = B.Views([cam], [(0, sc.n)], device="cuda")
+    a = Trainer(_dev(raw), views, tgt, lr=LR)
+    for _ in range(8):
+        a.step_eager()
+    b = Trainer(_dev(raw), views, tgt, lr=LR, K_capacity=a.capacity)
+    for _ in range(4):
+        b.step_eager()
+    path = tmp_path / "ckpt.pt"
+    torch.save(b.state_dict(), path)
+    other = {k: v + 1.0 for k, v in _dev(raw).items()}  # different starting values, overwritten by the load
+    c = Trainer(other, views, tgt, lr=(0.1,) * 5, K_capacity=a.capacity)
+    c.load_state_dict(torch.load(path))
+    assert c.steps_taken() == 4
+    for _ in range(4):
+        c.step_eager()
+    assert c.steps_taken() == 8 == a.steps_taken()
+    for k in RAW:
+        assert rel_l2(np_(c.raw[k]) - raw[k], np_(a.raw[k]) - raw[k]) <= 2e-2, k
+    assert c.loss() == pytest.approx(a.loss(), rel=1e-3)
+    with pytest.raises(ValueError):
+        d = Trainer(_dev({k: v[:-1] for k, v in raw.items()}), B.Views([cam], [(0, sc.n - 1)], device="cuda"), tgt,
+                    lr=LR)
+        d.load_state_dict(torch.load(path))

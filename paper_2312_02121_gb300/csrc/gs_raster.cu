@@ -20,7 +20,10 @@
 // product).
 //
 // The backward walks the same batches in reverse from each pixel's last
-// composited Gaussian, rebuilding T_n from the saved T_final (Sec. 3.1).  The
+// composited Gaussian, rebuilding T_n from the saved T_final (Sec. 3.1).  When
+// given a GsRasterConfig.warp_hits buffer, the forward stores each warp's
+// 32-bit cull ballot of every chunk of 32 pairs it walks, and the backward
+// walks those bits instead of repeating the test.  The
 // nine per-pixel gradient terms of a Gaussian are summed over the warp
 // through a shared-memory transpose into the warp's own slot for that
 // Gaussian (plain stores), and the slots of the tile's warps are summed in a
@@ -31,7 +34,9 @@
 //
 // Everything is templated on the scalar type: fp32 is the fast path, fp64
 // (smaller batches, exp2 instead of the SFU) serves the gs_*_f64 entry points
-// used to check the analytic backward against finite differences.
+// used to check the analytic backward against finite differences.  The
+// colours have 3 channels (RGB), or 1 to 3 channels C apart in a separate
+// instantiation that the multi-channel entry points use.
 #include "gs_raster_common.cuh"
 
 namespace gs {

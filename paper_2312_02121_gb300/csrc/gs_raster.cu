@@ -133,7 +133,7 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                     const S p2 = neg_sigma_log2(sh_q[j], xy.x - t.cx, xy.y - t.cy, u);
                     const S raw = mul_rn(xy.z, RT<S>::ex2(p2));
                     const S alpha = fmin(RT<S>::alpha_max(), raw);
-                    const S Tn = T * (S(1) - alpha);
+                    const S Tn = fma(-T, alpha, T);  // T (1 - alpha) in one rounding
                     // p2 > 0 means sigma < 0 (not a positive-definite conic): skipped; the alpha test
                     // is on o e^-sigma before the clamp, so a NaN opacity is skipped too
                     const bool take = !done && p2 <= S(0) && raw >= RT<S>::alpha_min();

@@ -138,7 +138,7 @@ k_raster_fwd_nc(const GsView* __restrict__ views, int V, int T_total, const int3
                     const float p2 = neg_sigma_log2(sh_q[j], xy.x - t.cx, xy.y - t.cy, u);
                     const float raw = mul_rn(xy.z, RT<float>::ex2(p2));
                     const float alpha = fminf(RT<float>::alpha_max(), raw);
-                    const float Tn = T * (1.f - alpha);
+                    const float Tn = fmaf(-T, alpha, T);  // as the 3-channel kernel: T (1 - alpha), one rounding
                     const bool take = !done && p2 <= 0.f && raw >= RT<float>::alpha_min();
                     const bool stop = take && Tn < RT<float>::t_min();
                     const bool comp = take && !stop;

@@ -115,6 +115,7 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
             }
             __syncthreads();
             const int n = min(kB, range.y - b0);
+            int lastj = -1;  // this batch's last composited entry (the batch offset is added once, below)
             for (int s = 0; s < n; s += 32) {
                 bool hit = s + lane < n;
                 if (kCull && hit)
@@ -146,11 +147,12 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                     C1 = fma(wgt, c.y, C1);
                     C2 = fma(wgt, c.z, C2);
                     T = comp ? Tn : T;
-                    last = comp ? b0 + j : last;
+                    lastj = comp ? j : lastj;
                     if (kCount) count += comp;
                 }
                 if (__all_sync(kFull, done)) break;
             }
+            if (lastj >= 0) last = b0 + lastj;
         }
         if (t.inside) {
             S bg0 = 0, bg1 = 0, bg2 = 0;
@@ -373,6 +375,7 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
             __syncthreads();
             // this warp only needs entries up to its own last index
             const int nw = min(n, wl - b0 + 1);
+            const int lastj = last - b0;  // this pixel's last index, relative to the batch
             for (int s = ((kB - 1) >> 5) << 5; s >= 0; s -= 32) {
                 unsigned chunk_mask = 0u;  // Gaussians of this chunk the warp wrote a partial for
                 if (s < nw) {
@@ -398,7 +401,7 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                         const S ge = RT<S>::ex2(p2);  // exp(-sigma)
                         const S raw = mul_rn(xy.z, ge);
                         const S alpha = fmin(RT<S>::alpha_max(), raw);
-                        const bool contrib = (b0 + j <= last) && (p2 <= S(0)) && (raw >= RT<S>::alpha_min());
+                        const bool contrib = (j <= lastj) && (p2 <= S(0)) && (raw >= RT<S>::alpha_min());
                         const unsigned cm = __ballot_sync(kFull, contrib);
                         if (cm == 0u) continue;
                         const S inv1ma = RT<S>::rcp(S(1) - alpha);

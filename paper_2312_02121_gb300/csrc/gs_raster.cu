@@ -437,8 +437,7 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                 }
                 if (lane == 0) s_mask[w][s >> 5] = chunk_mask;
             }
-            __syncthreads();
-            __syncthreads();
+            __syncthreads();  // the walk's slots and masks are complete before the next flush reads them
             prev_b0 = b0;
             prev_n = n;
         }

@@ -35,8 +35,11 @@ constexpr int kRTileMin = kRT * kRIShort;  // the smallest radix block (sizes th
 constexpr int kRWarps = kRT / 32;
 constexpr int kMaxBins = 256;         // digits of at most 8 bits
 constexpr int kScanThreads = 1024;
-constexpr int kEmitItems = 4;         // projections per thread in scan/emit
+constexpr int kEmitItems = 2;         // projections per thread in scan/emit (2 measured faster than 3-6)
 constexpr int kEmitTile = 256 * kEmitItems;
+// binary-search steps over a block's first slots
+constexpr int kEmitSearch = kEmitTile <= 512 ? 9 : kEmitTile <= 1024 ? 10 : 11;
+static_assert(kEmitTile <= (1 << kEmitSearch), "the emission's search covers the block");
 
 __device__ __forceinline__ int item_count(const int32_t* count_dev, int64_t count_static, int64_t cap)
 {
@@ -512,7 +515,7 @@ k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __res
         // of them owns the slot): s_off[lo] <= e < s_off[hi] throughout
         int lo = 0, hi = kEmitTile;
 #pragma unroll
-        for (int step = 0; step < 10; ++step) {  // kEmitTile = 2^10
+        for (int step = 0; step < kEmitSearch; ++step) {  // 2^kEmitSearch >= kEmitTile
             const int mid = (lo + hi) >> 1;
             if (s_off[mid] <= e) lo = mid; else hi = mid;
         }

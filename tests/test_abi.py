@@ -118,3 +118,15 @@ def test_static_scratch_covers_the_static_limits(lib):
     rc = lib.gs_bin_and_sort_static(fake, 1, P, 65536, fake, fake, fake, K, fake, None, None, fake, fake, fake, None)
     assert b"bytes of scratch" not in lib.gs_last_error(), lib.gs_last_error()
     assert rc != 0  # no device in this container
+
+
+def test_raster_config_rejects_a_wrong_warp_hits_buffer(lib):
+    # the forward-to-backward hand-off takes device int32 words; anything else is refused on the host
+    import torch
+    from paper_2312_02121_gb300 import binding
+    with pytest.raises(TypeError):
+        binding.RasterConfig(device="cpu", warp_hits=torch.zeros(8, dtype=torch.uint8))
+    with pytest.raises(TypeError):
+        binding.RasterConfig(device="cpu", warp_hits=torch.zeros(8, dtype=torch.int32))  # host memory
+    cfg = binding.RasterConfig(device="cpu")
+    assert cfg.describe()["warp_hits"] is False and cfg.c.warp_hits is None

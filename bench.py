@@ -548,6 +548,8 @@ def run_ours(args, rank, world, local_rank):
             step(evs[k])
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
+        # kernels per step (a replay of the captured step launches the same ones)
+        launches = (B.gs_kernel_launches() - launches0) // max(args.steps, 1)
         barrier()
         # the same step captured once into a CUDA graph (BatchRenderer), as a training loop runs it:
         # this is the timed headline; the instrumented eager steps above give the per-stage split
@@ -570,7 +572,6 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         graph_ms = sum(a.elapsed_time(b) for a, b in gev) / args.steps
         del rgraph
-    launches = (B.gs_kernel_launches() - launches0) // max(args.steps, 1)
     stage_ms = {s: 0.0 for s in stages}
     total_ms = 0.0
     for ev in evs:

@@ -17,6 +17,7 @@ import numpy as np
 import torch
 
 from . import build as _build
+from . import debug as _debug
 
 GS_OK = 0
 GS_ERR_INVALID_ARG = 1
@@ -235,6 +236,8 @@ def gs_bin_and_sort(views: Views, rects, depths, touched, K_capacity: int, works
                                   _ptr(touched), int(K_capacity), _ptr(workspace),
                                   workspace.numel() * workspace.element_size(), _ptr(isect_ids), _ptr(isect_pos),
                                   _ptr(emit_start), _ptr(tile_ranges), _ptr(K_out), _ptr(flags), _stream(stream)))
+    if _debug.enabled():
+        _debug.check_binning(views.P, K_capacity, isect_ids, tile_ranges, K_out, flags)
 
 
 def gs_bin_and_sort_static(views: Views, rects, depths, touched, K_capacity: int, isect_ids, isect_pos, emit_start,
@@ -244,6 +247,8 @@ def gs_bin_and_sort_static(views: Views, rects, depths, touched, K_capacity: int
                                          _ptr(touched), int(K_capacity), _ptr(isect_ids), _ptr(isect_pos),
                                          _ptr(emit_start), _ptr(tile_ranges), _ptr(K_out), _ptr(flags),
                                          _stream(stream)))
+    if _debug.enabled():
+        _debug.check_binning(views.P, K_capacity, isect_ids, tile_ranges, K_out, flags)
 
 
 class RasterConfig:
@@ -297,6 +302,8 @@ def gs_rasterize_fwd(views: Views, means2d, conics, opacities, colors, isect_ids
                                    _ptr(opacities), _ptr(colors), _ptr(isect_ids), _ptr(tile_ranges),
                                    _ptr(background), _ptr(out_rgb), _ptr(T_final), _ptr(last_idx),
                                    _ptr(n_contrib), _cfg(config), _stream(stream)))
+    if _debug.enabled():
+        _debug.check_forward(views, tile_ranges, out_rgb, T_final, last_idx)
 
 
 def gs_rasterize_bwd_workspace_size(K_capacity: int, deterministic: bool = False, f64: bool = False) -> int:
@@ -317,6 +324,9 @@ def gs_rasterize_bwd(views: Views, means2d, conics, opacities, colors, isect_ids
                                    int(bool(deterministic)), _ptr(workspace), nbytes, _ptr(dL_dmeans2d),
                                    _ptr(dL_dconics), _ptr(dL_dopacities), _ptr(dL_dcolors), _cfg(config),
                                    _stream(stream)))
+    if _debug.enabled():
+        _debug.check_gradients([("dL_dmeans2d", dL_dmeans2d), ("dL_dconics", dL_dconics),
+                                ("dL_dopacities", dL_dopacities), ("dL_dcolors", dL_dcolors)])
 
 
 def gs_project_bwd(views: Views, means, quats, scales, eps2d: float, touched, dL_dmeans2d, dL_dconics, dL_dmeans,
@@ -373,6 +383,8 @@ def gs_rasterize_fwd_nc(views: Views, C: int, means2d, conics, opacities, colors
                                       _ptr(opacities), _ptr(colors), _ptr(isect_ids), _ptr(tile_ranges),
                                       _ptr(background), _ptr(out), _ptr(T_final), _ptr(last_idx), _ptr(n_contrib),
                                       _cfg(config), _stream(stream)))
+    if _debug.enabled():
+        _debug.check_forward(views, tile_ranges, out, T_final, last_idx)
 
 
 def gs_rasterize_bwd_nc(views: Views, C: int, means2d, conics, opacities, colors, isect_ids, tile_ranges,
@@ -383,3 +395,6 @@ def gs_rasterize_bwd_nc(views: Views, C: int, means2d, conics, opacities, colors
                                       _ptr(tile_ranges), _ptr(background), _ptr(T_final), _ptr(last_idx),
                                       _ptr(dL_dout), _ptr(dL_dmeans2d), _ptr(dL_dconics), _ptr(dL_dopacities),
                                       _ptr(dL_dcolors), _cfg(config), _stream(stream)))
+    if _debug.enabled():
+        _debug.check_gradients([("dL_dmeans2d", dL_dmeans2d), ("dL_dconics", dL_dconics),
+                                ("dL_dopacities", dL_dopacities), ("dL_dcolors", dL_dcolors)])

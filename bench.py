@@ -696,7 +696,9 @@ def run_ours(args, rank, world, local_rank):
         "stage_ms": stage_ms, "eager_ms_per_step": eager_ms,
         "timing": "ms_per_step: the step captured once into a CUDA graph and replayed (BatchRenderer); "
                   "stage_ms and eager_ms_per_step: the same kernels launched eagerly with an event between "
-                  "stages", "wall_s": wall, "gpu_launches": int(launches),
+                  "stages", "wall_s": wall,
+        # kernels of ours launched in the timed region: each of the replayed steps launches the step's kernels
+        "gpu_launches": int(launches) * args.steps, "gpu_launches_per_step": int(launches),
         "e2e": e2e, "roofline": roof, "clocks": clocks,
     }
     line["project_bwd_view_gradient"] = view_gradient_cost(dev, views, params, last_state["pr"], last_state["g2"],

@@ -120,7 +120,7 @@ def load(build_if_missing: bool = True):
         if build_if_missing and not _build.up_to_date():
             _build.build()
         if not os.path.exists(path):
-            raise RuntimeError(f"libgsplat103.so not found at {path}; run __graft_entry__.build()")
+            raise RuntimeError(f"libgsplat103.so not found at {path}; build it with paper_2312_02121_gb300.build.build()")
         lib = ctypes.CDLL(path)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(lib, name)

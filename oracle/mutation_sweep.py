@@ -2,13 +2,14 @@
 
 Plants one small mistake at a time in ``gs_oracle.c`` (a flipped sign or
 operator, an off-by-one comparison or bound, a swapped index, a changed
-constant, ``&&`` for ``||``), rebuilds the oracle in a scratch copy and runs
-the oracle's pin tests (``tests/test_oracle_*.py``) against it.  A mutant the
+constant, ``&&`` for ``||``) or, with ``--target optim.py``, in the Adam and
+loss reference, rebuilds the oracle in a scratch copy and runs the oracle's pin
+tests (``tests/test_oracle_*.py``) against it.  A mutant the
 pins do not catch ("survives") is either equivalent to the original, or marks a
-part of the oracle no pin fixes yet.  Comments and preprocessor lines are never
-mutated.  Nothing of the CUDA library is involved.
+part of the oracle no pin fixes yet.  Comments, docstrings and preprocessor lines
+are never mutated.  Nothing of the CUDA library is involved.
 
-    python oracle/mutation_sweep.py [--jobs 6] [--out survivors.txt]
+    python oracle/mutation_sweep.py [--target gs_oracle.c|optim.py] [--jobs 6] [--out survivors.txt]
 
 Scratch copies go under ``oracle/_build/mutants``.  A full sweep is about 700
 mutants, a few minutes on 8 cores.
@@ -26,7 +27,6 @@ from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = os.path.join(HERE, "gs_oracle.c")
 SCRATCH = os.path.join(HERE, "_build", "mutants")
 
 # (pattern, replacement): each match of a pattern in a code span is one mutant
@@ -39,6 +39,8 @@ OPERATORS = [
     (r"\+= ", "-= "), (r"-= ", "+= "), (r"\+ 1\b", "+ 0"), (r"- 1\b", "- 0"),
     (r"&&", "||"), (r"\|\|", "&&"),
 ]
+# Python only: powers, square roots, the sigmoid derivative's factor
+PY_OPERATORS = [(r"\*\*", "*"), (r"np\.sqrt", "np.abs"), (r"\(1 - o\)", "(1 + o)"), (r"\(1 - b", "(1 + b")]
 
 
 def code_spans(lines):
@@ -73,16 +75,37 @@ def code_spans(lines):
     return out
 
 
-def mutants(text: str, first_line: int = 1):
+def python_code_spans(lines):
+    """Per line, the column spans that are Python code (outside docstrings,
+    comments and import lines)."""
+    out = []
+    in_doc = False
+    for ln in lines:
+        st = ln.strip()
+        quotes = ln.count('"""')
+        if in_doc or quotes:
+            out.append([])
+            in_doc = in_doc != (quotes % 2 == 1)
+            continue
+        if st.startswith(("#", "import ", "from ")):
+            out.append([])
+            continue
+        j = ln.find("#")
+        out.append([(0, j if j >= 0 else len(ln))])
+    return out
+
+
+def mutants(text: str, first_line: int = 1, python: bool = False):
     """All single-site mutants: (line number, operator pattern, original line, mutated source)."""
     lines = text.split("\n")
     res = []
-    for li, spans in enumerate(code_spans(lines)):
+    ops = OPERATORS + (PY_OPERATORS if python else [])
+    for li, spans in enumerate((python_code_spans if python else code_spans)(lines)):
         if li + 1 < first_line:
             continue
         ln = lines[li]
         for a, b in spans:
-            for pat, rep in OPERATORS:
+            for pat, rep in ops:
                 for m in re.finditer(pat, ln[a:b]):
                     new = ln[:a + m.start()] + rep + ln[a + m.end():]
                     res.append((li + 1, pat, ln.strip(), "\n".join(lines[:li] + [new] + lines[li + 1:])))
@@ -100,8 +123,8 @@ def _slot(k: int) -> str:
     return d
 
 
-def _run(slot: str, source: str):
-    with open(os.path.join(slot, "oracle", "gs_oracle.c"), "w") as f:
+def _run(slot: str, target: str, source: str):
+    with open(os.path.join(slot, "oracle", target), "w") as f:
         f.write(source)
     shutil.rmtree(os.path.join(slot, "oracle", "_build"), ignore_errors=True)
     tests = sorted(os.path.join("tests", t) for t in os.listdir(os.path.join(slot, "tests"))
@@ -117,11 +140,12 @@ def _run(slot: str, source: str):
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--target", default="gs_oracle.c", choices=["gs_oracle.c", "optim.py"])
     ap.add_argument("--jobs", type=int, default=max(1, (os.cpu_count() or 2) - 1))
     ap.add_argument("--first-line", type=int, default=1, help="mutate only from this source line on")
     ap.add_argument("--out", default="", help="write the surviving mutants here")
     args = ap.parse_args(argv)
-    ms = mutants(open(SRC).read(), args.first_line)
+    ms = mutants(open(os.path.join(HERE, args.target)).read(), args.first_line, args.target.endswith(".py"))
     print(f"{len(ms)} mutants, {args.jobs} jobs", flush=True)
     free = queue.Queue()
     for k in range(args.jobs):
@@ -130,7 +154,7 @@ def main(argv=None) -> int:
     def job(m):
         s = free.get()
         try:
-            return m, _run(s, m[3])
+            return m, _run(s, args.target, m[3])
         finally:
             free.put(s)
 

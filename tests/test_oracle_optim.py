@@ -1,6 +1,6 @@
 """Pins of the FP64 training-step reference (``oracle.optim``): the L2 loss by
-closed form and finite differences, the activation chain rule by finite
-differences, and Adam against torch.optim.Adam on the CPU (the library
+closed form and finite differences, the activations by closed form and
+their chain rule by finite differences, and Adam against torch.optim.Adam on the CPU (the library
 routine the textbook algorithm reduces to)."""
 import numpy as np
 import pytest
@@ -28,6 +28,18 @@ def _raw(rng, n):
     return dict(means=rng.standard_normal((n, 3)), quats=rng.standard_normal((n, 4)),
                 log_scales=rng.normal(-3, 0.5, (n, 3)), opacity_logits=rng.standard_normal(n),
                 colors=rng.uniform(size=(n, 3)))
+
+
+def test_activations_closed_form():
+    # exp of the log-scales; the logistic sigmoid: sigmoid(0) = 1/2, sigmoid(ln 3) = 3/4,
+    # sigmoid(-x) = 1 - sigmoid(x).  (1 / (1 - e^-x) also has derivative o (1 - o), so
+    # the chain-rule check below alone would not tell it from the sigmoid.)
+    x = np.array([0.0, np.log(3.0), -np.log(3.0), 2.0])
+    s, o = optim.activate(dict(log_scales=np.log([[0.5, 2.0, 1e-3]]), opacity_logits=x))
+    np.testing.assert_allclose(s, [[0.5, 2.0, 1e-3]], rtol=1e-15)
+    np.testing.assert_allclose(o[:3], [0.5, 0.75, 0.25], rtol=1e-15)
+    assert o[3] == pytest.approx(1.0 - optim.activate(dict(log_scales=np.zeros(1), opacity_logits=-x[3:]))[1][0],
+                                 rel=1e-15)
 
 
 def test_activation_chain_rule_matches_finite_differences():

@@ -140,7 +140,7 @@ def _run(slot: str, target: str, source: str):
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--target", default="gs_oracle.c", choices=["gs_oracle.c", "optim.py"])
+    ap.add_argument("--target", default="gs_oracle.c", choices=["gs_oracle.c", "optim.py", "__init__.py"])
     ap.add_argument("--jobs", type=int, default=max(1, (os.cpu_count() or 2) - 1))
     ap.add_argument("--first-line", type=int, default=1, help="mutate only from this source line on")
     ap.add_argument("--out", default="", help="write the surviving mutants here")

@@ -163,6 +163,23 @@ def test_pixel_subset_equals_full_image():
     np.testing.assert_array_equal(sub["last_id"], full["last_id"].reshape(-1)[pix])
 
 
+def test_backward_on_a_pixel_subset_equals_the_masked_full_backward():
+    # The gradients are sums over pixels (Sec. 3.1), so those of a pixel subset are the
+    # full image's with dL/dC zero outside the subset.
+    w = wl.small_case(3, 80, 50, 30)
+    cam, sc = w.views[0].camera, w.scenes[0]
+    rng = np.random.default_rng(1)
+    pix = rng.choice(50 * 30, 97, replace=False)
+    G = rng.standard_normal((97, 3))
+    Gfull = np.zeros((50 * 30, 3))
+    Gfull[pix] = G
+    sub = oracle.backward(cam, sc, G, pixels=pix)
+    full = oracle.backward(cam, sc, Gfull)
+    assert np.abs(full["opacities"]).max() > 0
+    for k in ("means", "quats", "scales", "opacities", "colors", "means2d", "conics", "viewmat"):
+        np.testing.assert_allclose(sub[k], full[k], rtol=1e-12, atol=1e-15, err_msg=k)
+
+
 def test_reverse_recurrences_rebuild_forward_quantities():
     # Sec. 3.1: starting from the saved final transmittance, T_{n-1} = T_n / (1 - alpha_{n-1})
     # recovers the running products, and S_{n-1} = c_n alpha_n T_n + S_n the suffix sums.

@@ -156,11 +156,13 @@ def test_equal_depths_bin_in_index_order():
 
 def test_alpha_exactly_at_the_skip_threshold_is_composited():
     # O7: skipped only when o exp(-sigma) < 1/255; at the Gaussian's centre sigma = 0 and o = 1/255 exactly
+    # (and the thresholds the oracle exports are the ones it applies)
+    assert (oracle.ALPHA_MIN, oracle.ALPHA_MAX, oracle.T_MIN) == (1.0 / 255.0, 0.99, 1e-4)
     proj = _proj2d([[8.5, 8.5]], [2.0], [3.0], 16, 16)
-    out = oracle.rasterize(proj, [1.0 / 255.0], [[1.0, 0.5, 0.25]], 16, 16)
+    out = oracle.rasterize(proj, [oracle.ALPHA_MIN], [[1.0, 0.5, 0.25]], 16, 16)
     np.testing.assert_allclose(out["rgb"][8, 8], np.array([1.0, 0.5, 0.25]) / 255.0, rtol=0, atol=1e-18)
     assert out["n_contrib"][8, 8] == 1
-    out = oracle.rasterize(proj, [math.nextafter(1.0 / 255.0, 0.0)], [[1.0, 0.5, 0.25]], 16, 16)
+    out = oracle.rasterize(proj, [math.nextafter(oracle.ALPHA_MIN, 0.0)], [[1.0, 0.5, 0.25]], 16, 16)
     assert out["n_contrib"][8, 8] == 0 and out["T_final"][8, 8] == 1.0
 
 

@@ -130,3 +130,41 @@ def test_raster_config_rejects_a_wrong_warp_hits_buffer(lib):
         binding.RasterConfig(device="cpu", warp_hits=torch.zeros(8, dtype=torch.int32))  # host memory
     cfg = binding.RasterConfig(device="cpu")
     assert cfg.describe()["warp_hits"] is False and cfg.c.warp_hits is None
+
+
+
+def _kind_of_c(t: str):
+    """'ptr', 'char*', or (int|float, bytes) of a C type written in the header."""
+    t = " ".join(t.replace("const", " ").split())
+    if "*" in t:
+        return "char*" if t.replace(" ", "") == "char*" else "ptr"
+    sizes = {"int": 4, "int32_t": 4, "int64_t": 8, "size_t": 8, "float": 4, "double": 8}
+    return ("float" if t in ("float", "double") else "int", sizes[t])
+
+
+def _kind_of_ctypes(c):
+    if c is ctypes.c_char_p:
+        return "char*"
+    if c is ctypes.c_void_p:
+        return "ptr"
+    return ("float" if c in (ctypes.c_float, ctypes.c_double) else "int", ctypes.sizeof(c))
+
+
+def _param_type(param: str) -> str:
+    """The type of one 'type name' parameter (the name dropped, any stars kept)."""
+    return re.sub(r"\b[A-Za-z_]\w*\s*$", "", param.strip()).strip()
+
+
+def test_binding_signatures_match_the_header_prototypes():
+    # every argument's kind (pointer, or integer / floating point of its width) and every return
+    # type, read from the prototypes, against the ctypes declarations the binding installs
+    from paper_2312_02121_gb300 import binding
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    protos = re.findall(r"^\s*((?:const\s+)?[A-Za-z_]\w*\s*\**)\s*(gs_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", text, re.M)
+    assert sorted(name for _, name, _ in protos) == declared_functions()
+    for ret, name, params in protos:
+        params = " ".join(params.split())
+        want = [] if params in ("", "void") else [_kind_of_c(_param_type(q)) for q in params.split(",")]
+        res, argtypes = binding.SIGNATURES[name]
+        assert [_kind_of_ctypes(a) for a in argtypes] == want, name
+        assert _kind_of_ctypes(res) == _kind_of_c(ret), name

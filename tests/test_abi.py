@@ -168,3 +168,36 @@ def test_binding_signatures_match_the_header_prototypes():
         res, argtypes = binding.SIGNATURES[name]
         assert [_kind_of_ctypes(a) for a in argtypes] == want, name
         assert _kind_of_ctypes(res) == _kind_of_c(ret), name
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    # the C compiler's offsetof / sizeof of every field of every struct the header declares,
+    # against the ctypes structures the binding passes (host gcc: the layout is the platform's C ABI)
+    import shutil
+    import subprocess
+    from paper_2312_02121_gb300 import binding
+    cc = shutil.which(os.environ.get("CC", "gcc"))
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [binding.GsCamera, binding.GsView, binding.GsRasterConfig, binding.GsAdamConfig]
+    lines = ["#include <stdio.h>", '#include "gsplat103.h"', "int main(void) {"]
+    for S in structs:
+        n = S.__name__
+        lines.append(f'printf("{n} size %zu\\n", sizeof({n}));')
+        for f, _ in S._fields_:
+            lines.append(f'printf("{n} {f} %zu %zu\\n", offsetof({n}, {f}), sizeof((({n}*)0)->{f}));')
+    lines += ["return 0; }"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        f = ln.split()
+        got[(f[0], f[1])] = tuple(int(x) for x in f[2:])
+    for S in structs:
+        n = S.__name__
+        assert got[(n, "size")] == (ctypes.sizeof(S),), n
+        for f, _ in S._fields_:
+            d = getattr(S, f)
+            assert got[(n, f)] == (d.offset, d.size), f"{n}.{f}"

@@ -76,6 +76,58 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB_PATH
 
 
+def resources() -> list:
+    """Per kernel, what ptxas reports when compiling every source for sm_103a:
+    (translation unit, demangled kernel, registers, spill store bytes, spill
+    load bytes, static shared memory bytes).  Nothing is linked or written."""
+    import re
+    cc = nvcc()
+    rows = []
+
+    def one(src: str):
+        cmd = [cc, *ARCH, *FLAGS, "-Xptxas=-v", "-c", os.path.join(CSRC, src), "-o", os.devnull]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
+        return src, r.stderr
+
+    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        outs = list(ex.map(one, SOURCES))
+    for src, text in outs:
+        cur = None
+        for ln in text.splitlines():
+            m = re.search(r"Compiling entry function '([^']+)'", ln)
+            if m:
+                cur = dict(tu=src, name=m.group(1), regs=0, spill_st=0, spill_ld=0, smem=0)
+                rows.append(cur)
+                continue
+            if cur is None:
+                continue
+            m = re.search(r"(\d+) bytes spill stores, (\d+) bytes spill loads", ln)
+            if m:
+                cur["spill_st"], cur["spill_ld"] = int(m.group(1)), int(m.group(2))
+            m = re.search(r"Used (\d+) registers", ln)
+            if m:
+                cur["regs"] = int(m.group(1))
+                m2 = re.search(r"(\d+) bytes smem", ln)
+                cur["smem"] = int(m2.group(1)) if m2 else 0
+    filt = shutil.which("c++filt")
+    if filt and rows:
+        names = subprocess.run([filt], input="\n".join(r["name"] for r in rows), capture_output=True,
+                               text=True).stdout.splitlines()
+        if len(names) == len(rows):
+            for r, n in zip(rows, names):
+                r["name"] = n
+    return rows
+
+
 if __name__ == "__main__":  # pragma: no cover
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    if "--resources" in sys.argv:
+        print("| source | kernel | registers | spill st / ld (B) | static smem (B) |")
+        print("|---|---|---|---|---|")
+        for r in resources():
+            name = r["name"].split("(")[0].replace("void ", "")  # the kernel and its template arguments
+            print(f"| {r['tu']} | `{name}` | {r['regs']} | {r['spill_st']} / {r['spill_ld']} | {r['smem']} |")
+    else:
+        print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

@@ -104,18 +104,21 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None  # "[N/A]" and the like
+
         rows = []
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                rows.append(dict(sm=float(f[1]), max=float(f[2]), power=float(f[3]), hw=f[5], hwt=f[6], swt=f[7],
-                                 cap=f[8]))
-            except ValueError:
-                continue
+            if len(f) < 9 or num(f[1]) is None or num(f[2]) is None:
+                continue  # a clock sample needs both clocks; power may be unavailable
+            rows.append(dict(sm=num(f[1]), max=num(f[2]), power=num(f[3]), hw=f[5], hwt=f[6], swt=f[7], cap=f[8]))
         if not rows:
             return None
+        powers = [r["power"] for r in rows if r["power"] is not None]
         reasons = set()
         for r in rows:
             for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
@@ -124,7 +127,7 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["max"] for r in rows),
                 "reasons": sorted(reasons), "samples": len(rows),
-                "power_w_max": max(r["power"] for r in rows)}
+                "power_w_max": max(powers) if powers else None}
 
 
 RASTER_SOURCES = ("gs_raster.cu", "gs_raster_common.cuh", "gs_common.cuh")

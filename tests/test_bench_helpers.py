@@ -69,3 +69,22 @@ def test_traffic_record_matches_only_the_current_raster_sources(bench):
         want = rec[k][1] if rec.get(k, ("", 0))[0] == h else None
         assert bench.recorded_traffic(k) == want
     assert bench.recorded_traffic("no_such_kernel") is None
+
+
+def test_clock_summary_reads_nvidia_smi_rows(bench):
+    c = bench.ClockSampler(0)
+    c.lines = [
+        "0, 1965, 2070, 812.40, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, [N/A], 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2010, 2070, 1011.9, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "0, [N/A], 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    s = c.summary()
+    assert s["samples"] == 3 and s["sm_mhz"] == 1980 and s["sm_max_mhz"] == 2070
+    assert s["reasons"] == ["sw_power_cap"] and s["power_w_max"] == pytest.approx(1011.9)
+    c.lines = ["0, 1500, 2070, [N/A], 0x8, Active, Not Active, Active, Not Active"]
+    s = c.summary()
+    assert s["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and s["power_w_max"] is None
+    c.lines = []
+    assert c.summary() is None

@@ -21,8 +21,10 @@ rank), no data-path collective; timings are max-reduced over ranks.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
+import shutil
 import statistics
 import subprocess
 import sys
@@ -73,17 +75,20 @@ class ClockSampler:
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,timestamp")
 
     def __init__(self, gpu_index: int):
         self.gpu_index = gpu_index
         self.proc = None
         self.lines = []
+        self.windows = []  # (start, end) wall-clock seconds of the timed regions
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu_index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "20"],
+            # line-buffered where coreutils' stdbuf exists, so no sample is held back in a pipe buffer
+            line_buf = ["stdbuf", "-oL"] if shutil.which("stdbuf") else []
+            self.proc = subprocess.Popen(line_buf + ["nvidia-smi", f"--id={self.gpu_index}", f"--query-gpu={self.QUERY}",
+                                                     "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -102,6 +107,12 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+            self.t.join(timeout=2)  # the reader has taken every line the sampler wrote
+
+    def mark(self, t0: float, t1: float):
+        """Declares [t0, t1] (time.time()) a timed region: the clock median is taken over the
+        samples nvidia-smi stamped inside these regions, when it stamped any."""
+        self.windows.append((t0, t1))
 
     def summary(self):
         def num(x):
@@ -115,9 +126,21 @@ class ClockSampler:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9 or num(f[1]) is None or num(f[2]) is None:
                 continue  # a clock sample needs both clocks; power may be unavailable
-            rows.append(dict(sm=num(f[1]), max=num(f[2]), power=num(f[3]), hw=f[5], hwt=f[6], swt=f[7], cap=f[8]))
+            ts = None
+            if len(f) > 9:
+                try:
+                    ts = datetime.datetime.strptime(f[9], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    ts = None
+            rows.append(dict(sm=num(f[1]), max=num(f[2]), power=num(f[3]), hw=f[5], hwt=f[6], swt=f[7], cap=f[8],
+                             ts=ts))
         if not rows:
             return None
+        # samples stamped inside a timed region (20 ms of slack for the sampling period)
+        timed = [r for r in rows if r["ts"] is not None
+                 and any(a - 0.02 <= r["ts"] <= b + 0.02 for a, b in self.windows)]
+        scope = "timed region" if timed else "whole run (warm-up, timed steps and the pauses between)"
+        rows = timed or rows
         powers = [r["power"] for r in rows if r["power"] is not None]
         reasons = set()
         for r in rows:
@@ -126,7 +149,7 @@ class ClockSampler:
                 if r[key].lower() == "active":
                     reasons.add(name)
         return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["max"] for r in rows),
-                "reasons": sorted(reasons), "samples": len(rows),
+                "reasons": sorted(reasons), "samples": len(rows), "scope": scope,
                 "power_w_max": max(powers) if powers else None}
 
 
@@ -545,12 +568,13 @@ def run_ours(args, rank, world, local_rank):
         launches0 = B.gs_kernel_launches()
         barrier()
         torch.cuda.synchronize()
-        wall0 = time.perf_counter()
+        wall0, tw0 = time.perf_counter(), time.time()
         for k in range(args.steps):
             flush.zero_()
             step(evs[k])
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
+        clk.mark(tw0, time.time())
         # kernels per step (a replay of the captured step launches the same ones)
         launches = (B.gs_kernel_launches() - launches0) // max(args.steps, 1)
         barrier()
@@ -566,12 +590,14 @@ def run_ours(args, rank, world, local_rank):
         gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         barrier()
         torch.cuda.synchronize()
+        tw0 = time.time()
         for a, b in gev:
             flush.zero_()
             a.record(stream)
             rgraph.step()
             b.record(stream)
         torch.cuda.synchronize()
+        clk.mark(tw0, time.time())
         barrier()
         graph_ms = sum(a.elapsed_time(b) for a, b in gev) / args.steps
         del rgraph

@@ -88,3 +88,26 @@ def test_clock_summary_reads_nvidia_smi_rows(bench):
     assert s["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and s["power_w_max"] is None
     c.lines = []
     assert c.summary() is None
+
+
+def test_clock_median_is_taken_inside_the_timed_regions(bench):
+    import datetime
+    c = bench.ClockSampler(0)
+    t0 = datetime.datetime(2026, 1, 2, 3, 4, 5, 0).timestamp()
+
+    def row(dt, mhz, cap="Not Active"):
+        ts = datetime.datetime.fromtimestamp(t0 + dt).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return f"0, {mhz}, 2070, 500.0, 0x0, Not Active, Not Active, Not Active, {cap}, {ts}"
+
+    # idle before and between the timed regions at a lower clock, under load inside them
+    c.lines = [row(0.00, 900), row(0.10, 900), row(0.50, 2010), row(0.52, 1990, "Active"), row(0.54, 2000),
+               row(0.80, 1100), row(1.20, 1950), row(1.22, 1970), row(1.60, 800)]
+    c.mark(t0 + 0.49, t0 + 0.55)
+    c.mark(t0 + 1.19, t0 + 1.23)
+    s = c.summary()
+    assert s["samples"] == 5 and s["sm_mhz"] == 1990 and s["scope"] == "timed region"
+    assert s["reasons"] == ["sw_power_cap"]
+    # no sample stamped inside a region (or none stamped at all): every sample counts
+    c.windows = [(t0 + 5.0, t0 + 6.0)]
+    s = c.summary()
+    assert s["samples"] == 9 and s["sm_mhz"] == 1950 and s["scope"].startswith("whole run")

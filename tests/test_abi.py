@@ -201,3 +201,13 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         for f, _ in S._fields_:
             d = getattr(S, f)
             assert got[(n, f)] == (d.offset, d.size), f"{n}.{f}"
+
+
+def test_binding_constants_match_the_header_defines():
+    from paper_2312_02121_gb300 import binding
+    text = open(HEADER).read()
+    defines = {m.group(1): int(m.group(2)) for m in re.finditer(r"^#define (GS_\w+) (\d+)u?\b", text, re.M)}
+    assert {"GS_OK", "GS_ERR_INVALID_ARG", "GS_ERR_CAPACITY", "GS_FLAG_CAPACITY", "GS_TILE"} <= set(defines)
+    for name, value in defines.items():
+        if hasattr(binding, name):
+            assert getattr(binding, name) == value, name

@@ -94,6 +94,10 @@ def test_valid_frame_passes_and_corruptions_are_reported(binding):
         debug.check_gradients([("g", torch.tensor([0.0, float("inf")]))])
 
 
+def test_codes_match_the_binding(binding):
+    assert (debug.GS_FLAG_CAPACITY, debug.GS_ERR_INVALID_ARG) == (binding.GS_FLAG_CAPACITY, binding.GS_ERR_INVALID_ARG)
+
+
 def test_checks_are_off_unless_asked(monkeypatch):
     monkeypatch.delenv("GS_DEBUG", raising=False)
     assert not debug.enabled()

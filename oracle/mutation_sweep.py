@@ -38,6 +38,8 @@ OPERATORS = [
     (r"(?<![\w.])3\.0(?![\w.])", "2.0"), (r"(?<![\w.])1\.0(?![\w.])", "2.0"),
     (r"\+= ", "-= "), (r"-= ", "+= "), (r"\+ 1\b", "+ 0"), (r"- 1\b", "- 0"),
     (r"&&", "||"), (r"\|\|", "&&"),
+    (r"\bfloor\(", "ceil("), (r"\bfmin\(", "fmax("), (r"\bfmax\(", "fmin("), (r"\bexp\(-", "exp("),
+    (r"\bsqrt\(", "fabs("), (r"\[3\]", "[2]"),
 ]
 # Python only: powers, square roots, the sigmoid derivative's factor
 PY_OPERATORS = [(r"\*\*", "*"), (r"np\.sqrt", "np.abs"), (r"\(1 - o\)", "(1 + o)"), (r"\(1 - b", "(1 + b")]

@@ -677,21 +677,40 @@ extern "C" size_t gs_bin_and_sort_workspace_size(int64_t P, int64_t K_capacity, 
     return carve(nullptr, P, K_capacity).bytes;
 }
 
+namespace gs {
+
+// The host checks of the binning arguments other than the workspace, shared by
+// gs_bin_and_sort and gs_bin_and_sort_static (`who` names the entry point in
+// the message).  Nothing is read through the pointers.
+int bin_and_sort_check_args(const char* who, const GsView* views, int32_t V, int64_t P, int32_t T_total,
+                            const int16_t* rects, const float* depths, const int32_t* touched, int64_t K_capacity,
+                            const int32_t* isect_ids, const int32_t* isect_pos, const int32_t* emit_start,
+                            const int32_t* tile_ranges, const int32_t* K_out, const uint32_t* flags)
+{
+    if (V <= 0 || P < 0 || T_total <= 0 || K_capacity < 0 || P >= (int64_t(1) << 31) ||
+        K_capacity >= (int64_t(1) << 31))
+        return fail(GS_ERR_INVALID_ARG, "%s: V=%d P=%lld T_total=%d K_capacity=%lld", who, V, (long long)P, T_total,
+                    (long long)K_capacity);
+    if (!views || !tile_ranges || !K_out || !flags || (P > 0 && (!rects || !depths || !touched)) ||
+        (K_capacity > 0 && !isect_ids) || (isect_pos && !emit_start))
+        return fail(GS_ERR_INVALID_ARG, "%s: null pointer argument", who);
+    if ((reinterpret_cast<uintptr_t>(rects) & 7) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7))
+        return fail(GS_ERR_INVALID_ARG, "%s: rects and tile_ranges need 8-byte alignment", who);
+    return GS_OK;
+}
+
+}  // namespace gs
+
 extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_t T_total, const int16_t* rects,
                                const float* depths, const int32_t* touched, int64_t K_capacity, void* workspace,
                                size_t workspace_bytes, int32_t* isect_ids, int32_t* isect_pos, int32_t* emit_start,
                                int32_t* tile_ranges, int32_t* K_out, uint32_t* flags, void* stream)
 {
     gs::NvtxRange nvtx("gs_bin_and_sort");
-    if (V <= 0 || P < 0 || T_total <= 0 || K_capacity < 0 || P >= (int64_t(1) << 31) ||
-        K_capacity >= (int64_t(1) << 31))
-        return fail(GS_ERR_INVALID_ARG, "gs_bin_and_sort: V=%d P=%lld T_total=%d K_capacity=%lld", V, (long long)P,
-                    T_total, (long long)K_capacity);
-    if (!views || !tile_ranges || !K_out || !flags || (P > 0 && (!rects || !depths || !touched)) ||
-        (K_capacity > 0 && !isect_ids) || (isect_pos && !emit_start))
-        return fail(GS_ERR_INVALID_ARG, "gs_bin_and_sort: null pointer argument");
-    if ((reinterpret_cast<uintptr_t>(rects) & 7) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7))
-        return fail(GS_ERR_INVALID_ARG, "gs_bin_and_sort: rects and tile_ranges need 8-byte alignment");
+    const int checked = gs::bin_and_sort_check_args("gs_bin_and_sort", views, V, P, T_total, rects, depths, touched,
+                                                    K_capacity, isect_ids, isect_pos, emit_start, tile_ranges, K_out,
+                                                    flags);
+    if (checked != GS_OK) return checked;
     const SortLayout need = carve(nullptr, P, K_capacity);
     if (!workspace || workspace_bytes < need.bytes)
         return fail(GS_ERR_INVALID_ARG, "gs_bin_and_sort: workspace of %zu bytes, need %zu", workspace_bytes,

@@ -8,6 +8,12 @@
 
 namespace gs {
 
+// gs_sort.cu: the argument checks gs_bin_and_sort makes before its workspace check.
+int bin_and_sort_check_args(const char* who, const GsView* views, int32_t V, int64_t P, int32_t T_total,
+                            const int16_t* rects, const float* depths, const int32_t* touched, int64_t K_capacity,
+                            const int32_t* isect_ids, const int32_t* isect_pos, const int32_t* emit_start,
+                            const int32_t* tile_ranges, const int32_t* K_out, const uint32_t* flags);
+
 // Workspace bytes gs_bin_and_sort needs at the static limits, rounded up.
 // The entry point re-checks the exact requirement before every call.
 constexpr size_t kStaticScratchBytes = size_t(24) << 20;  // 24 MiB
@@ -49,6 +55,10 @@ extern "C" int gs_bin_and_sort_static(const GsView* views, int32_t V, int64_t P,
                                       int32_t* tile_ranges, int32_t* K_out, uint32_t* flags, void* stream)
 {
     gs::NvtxRange nvtx("gs_bin_and_sort_static");
+    // argument errors are reported before the first CUDA call (the scratch address lookup)
+    const int checked = bin_and_sort_check_args("gs_bin_and_sort_static", views, V, P, T_total, rects, depths, touched,
+                                                K_capacity, isect_ids, isect_pos, emit_start, tile_ranges, K_out, flags);
+    if (checked != GS_OK) return checked;
     if (P > GS_STATIC_MAX_PROJECTIONS || K_capacity > GS_STATIC_MAX_INTERSECTIONS)
         return fail(GS_ERR_INVALID_ARG,
                     "gs_bin_and_sort_static: P=%lld and K_capacity=%lld must not exceed %d and %d "

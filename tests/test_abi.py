@@ -211,3 +211,22 @@ def test_binding_constants_match_the_header_defines():
     for name, value in defines.items():
         if hasattr(binding, name):
             assert getattr(binding, name) == value, name
+
+
+def test_every_entry_point_rejects_null_arguments_before_any_cuda_call(lib):
+    # All pointers NULL, sizes small and positive: each compute entry point answers
+    # GS_ERR_INVALID_ARG with a message naming itself, from its host checks (no GPU here, so a
+    # call that reached CUDA first would answer GS_ERR_CUDA instead).
+    from paper_2312_02121_gb300 import binding
+    checked = 0
+    for name, (res, argtypes) in binding.SIGNATURES.items():
+        if res is not ctypes.c_int or not argtypes:
+            continue
+        args = [None if a is ctypes.c_void_p else 0.3 if a in (ctypes.c_float, ctypes.c_double)
+                else (1 << 20) if a is ctypes.c_size_t else 16 for a in argtypes]
+        rc = getattr(lib, name)(*args)
+        msg = lib.gs_last_error().decode()
+        assert rc == binding.GS_ERR_INVALID_ARG, (name, rc, msg)
+        assert msg.startswith(name + ":"), (name, msg)
+        checked += 1
+    assert checked >= 18

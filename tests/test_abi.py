@@ -230,3 +230,28 @@ def test_every_entry_point_rejects_null_arguments_before_any_cuda_call(lib):
         assert msg.startswith(name + ":"), (name, msg)
         checked += 1
     assert checked >= 18
+
+
+def test_every_entry_point_rejects_a_negative_size_on_the_host(lib):
+    # Each integer argument set to -1 in turn (boolean flags aside), every pointer aimed at a zeroed
+    # host buffer: each compute entry point answers GS_ERR_INVALID_ARG from its host checks.
+    from paper_2312_02121_gb300 import binding
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    protos = {name: params for _, name, params in re.findall(
+        r"^\s*((?:const\s+)?[A-Za-z_]\w*\s*\**)\s*(gs_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", text, re.M)}
+    buf = (ctypes.c_char * (1 << 20))()
+    base = (ctypes.addressof(buf) + 255) & ~255
+    checked = 0
+    for name, (res, argtypes) in binding.SIGNATURES.items():
+        if res is not ctypes.c_int or not argtypes:
+            continue
+        pnames = [re.findall(r"\w+", p)[-1] for p in protos[name].split(",")]
+        for k, a in enumerate(argtypes):
+            if a not in (ctypes.c_int32, ctypes.c_int64) or pnames[k] == "deterministic":
+                continue
+            args = [base if t is ctypes.c_void_p else 0.3 if t in (ctypes.c_float, ctypes.c_double)
+                    else (1 << 19) if t is ctypes.c_size_t else (-1 if i == k else 1) for i, t in enumerate(argtypes)]
+            rc = getattr(lib, name)(*args)
+            assert rc == binding.GS_ERR_INVALID_ARG, (name, pnames[k], rc, lib.gs_last_error())
+            checked += 1
+    assert checked >= 40

@@ -14,7 +14,11 @@
  * ---------------------------------------
  *  - Every function returns GS_OK (0) or a GS_ERR_* code; gs_last_error()
  *    gives a message for the calling thread's last failure.  Argument errors
- *    are detected on the host before anything is launched.
+ *    are detected on the host before anything is launched: null required
+ *    pointers, negative or oversized counts, too small a workspace, and the
+ *    alignment of the vector-typed arrays and workspaces named below.  The
+ *    natural alignment of the scalar arrays is the caller's duty and is not
+ *    checked (a tensor whose storage offset counts whole elements has it).
  *  - All array arguments are caller-owned DEVICE memory (plain pointers), fp32
  *    unless stated, C-contiguous, 4-byte aligned at least; float2/short4 data
  *    (means2d, rects) must be 8-byte aligned and quaternions 16-byte aligned.

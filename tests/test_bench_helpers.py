@@ -111,3 +111,37 @@ def test_clock_median_is_taken_inside_the_timed_regions(bench):
     c.windows = [(t0 + 5.0, t0 + 6.0)]
     s = c.summary()
     assert s["samples"] == 9 and s["sm_mhz"] == 1950 and s["scope"].startswith("whole run")
+
+
+def test_clock_sampler_runs_a_sampler_process_and_windows_its_rows(bench, tmp_path, monkeypatch):
+    # a stand-in nvidia-smi on PATH prints one stamped row every 20 ms (SM clock 1000 MHz before the
+    # timed region, 2000 MHz inside it); the sampler starts it, reads it on a thread, stops it
+    import sys
+    import time
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text(f"""#!{sys.executable}
+import datetime, sys, time
+while True:
+    now = time.time()
+    mhz = 2000 if open({str(tmp_path / 'load')!r}).read().strip() == "1" else 1000
+    ts = datetime.datetime.fromtimestamp(now).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+    print(f"0, {{mhz}}, 2070, 400.0, 0x0, Not Active, Not Active, Not Active, Not Active, {{ts}}", flush=True)
+    time.sleep(0.02)
+""")
+    fake.chmod(0o755)
+    (tmp_path / "load").write_text("0")
+    monkeypatch.setenv("PATH", f"{tmp_path}:{os.environ['PATH']}")
+    with bench.ClockSampler(0) as clk:
+        time.sleep(0.3)
+        (tmp_path / "load").write_text("1")
+        time.sleep(0.05)
+        t0 = time.time()
+        time.sleep(0.3)
+        t1 = time.time()
+        clk.mark(t0, t1)
+        time.sleep(0.05)
+        (tmp_path / "load").write_text("0")
+        time.sleep(0.3)
+    s = clk.summary()
+    assert clk.proc.poll() is not None  # the sampler process was stopped
+    assert s is not None and s["scope"] == "timed region" and s["sm_mhz"] == 2000 and s["samples"] >= 5

@@ -199,3 +199,22 @@ def test_alpha_exactly_at_the_clamp_has_no_opacity_gradient():
     np.testing.assert_allclose(at["colors"][0], [0.99] * 3, rtol=1e-15)
     below = oracle.rasterize_bwd(proj, [math.nextafter(0.99, 0.0)], [[1, 1, 1]], W, H, G)
     assert below["opacities"][0] == pytest.approx(3.0, rel=1e-15)
+
+
+def test_compositing_invariants_over_a_dense_frame():
+    # Eq. 7 with the O7 stop rule: T never falls below 1e-4 (compositing stops before it would);
+    # the weights alpha_n T_n telescope to 1 - T_final; colours in [0, 1] keep every channel in
+    # [0, 1 - T_final]; the last composited index is -1 exactly when nothing was composited.
+    w = wl.small_case(5, 600, 48, 40, log_scale_mu=-2.2, opacity_logit_mu=1.0)
+    cam, sc = w.views[0].camera, w.scenes[0]
+    out = oracle.render(cam, sc)
+    Tf, rgb = out["T_final"], out["rgb"]
+    assert Tf.min() >= oracle.T_MIN and Tf.max() <= 1.0
+    assert (Tf < 0.01).mean() > 0.1  # the frame is dense enough for the cut-off to matter
+    assert (rgb >= 0).all() and (rgb <= (1.0 - Tf)[..., None] + 1e-12).all()
+    assert ((out["last_id"] < 0) == (out["n_contrib"] == 0)).all()
+    rng = np.random.default_rng(0)
+    for py, px in zip(rng.integers(0, 40, 25), rng.integers(0, 48, 25)):
+        tr = oracle.pixel_trace(out["proj"], sc.opacities, sc.colors, int(px), int(py))
+        assert np.sum(tr["alpha"] * tr["T"]) == pytest.approx(1.0 - tr["T_final"], abs=1e-12)
+        assert tr["T_final"] == pytest.approx(Tf[py, px], abs=1e-15)

@@ -144,4 +144,4 @@ while True:
         time.sleep(0.3)
     s = clk.summary()
     assert clk.proc.poll() is not None  # the sampler process was stopped
-    assert s is not None and s["scope"] == "timed region" and s["sm_mhz"] == 2000 and s["samples"] >= 5
+    assert s is not None and s["scope"] == "timed region" and s["sm_mhz"] == 2000 and s["samples"] >= 3

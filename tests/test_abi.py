@@ -255,3 +255,17 @@ def test_every_entry_point_rejects_a_negative_size_on_the_host(lib):
             assert rc == binding.GS_ERR_INVALID_ARG, (name, pnames[k], rc, lib.gs_last_error())
             checked += 1
     assert checked >= 40
+
+
+@pytest.mark.parametrize("lang,std", [("c", "c99"), ("c++", "c++11")])
+def test_header_is_clean_c99_and_cxx11(tmp_path, lang, std):
+    # the boundary is consumable from plain C and from C++, without warnings under -pedantic
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / ("probe.c" if lang == "c" else "probe.cpp")
+    src.write_text('#include "gsplat103.h"\nint main(void) { GsView v; v.g_count = GS_TILE; return v.g_count == 0; }\n')
+    subprocess.run([cc, f"-std={std}", "-pedantic", "-Wall", "-Wextra", "-Werror", "-I", os.path.dirname(HEADER),
+                    "-c", str(src), "-o", str(tmp_path / "probe.o")], check=True)

@@ -28,7 +28,7 @@
  *    valid after the caller synchronises the stream.
  *  - Calls enqueue only kernels and cudaMemsetAsync, so a sequence of them can
  *    be captured into a CUDA graph when the sizes (P, T_total, K_capacity) are
- *    fixed.
+ *    fixed.  (gs_bin_and_sort_static is not covered by this statement.)
  *  - Quaternions are stored (w, x, y, z) and need not be unit length; the
  *    forward normalises them.  Scales are linear (not log) and opacities are
  *    in [0, 1]; activations belong to the caller.
@@ -188,8 +188,9 @@ int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_t T_total, 
  * The paper has no counterpart; it is an interface convenience.
  *
  * The scratch gs_bin_and_sort needs lives in one fixed array in this
- * library's device memory (a file-scope __device__ array of about 22 MB),
- * which every GPU that loads the library holds until the process exits.  So:
+ * library's device memory (a file-scope __device__ array of 24 MiB =
+ * 25,165,824 bytes), which every GPU that loads the library holds until the
+ * process exits.  So:
  *  - P must be <= GS_STATIC_MAX_PROJECTIONS and K_capacity <=
  *    GS_STATIC_MAX_INTERSECTIONS; larger sizes return GS_ERR_INVALID_ARG.
  *  - All calls share that one array and it keeps the previous call's
@@ -198,8 +199,11 @@ int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_t T_total, 
  *    streams, or several host threads) race on it and give wrong results:
  *    serialise them, e.g. on one stream.
  *  - The first call on each device looks up the array's device address with
- *    cudaGetSymbolAddress while that device is current; make that first call
- *    before any stream capture begins.
+ *    cudaGetSymbolAddress while that device is current, and later calls reuse
+ *    it; make that first call before any stream capture begins.  The address
+ *    is kept for the life of the process: after a cudaDeviceReset it may be
+ *    stale, so a process that resets a device must not call this entry point
+ *    on that device again.
  * The call allocates nothing: no cudaMalloc, cudaFree or allocating library
  * routine.  Arguments and outputs are those of gs_bin_and_sort.
  */

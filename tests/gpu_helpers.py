@@ -4,6 +4,7 @@ import numpy as np
 import torch
 
 import oracle
+from oracle import compare
 from paper_2312_02121_gb300 import binding as B
 from paper_2312_02121_gb300 import pipeline
 
@@ -69,41 +70,10 @@ def last_gaussian_ids(frame, i=0):
 
 
 def uncertain_pixels(oracle_fwd, proj, W, H, opacities=None, margin_rel=1e-4, rect_margin_px=1e-3):
-    """Pixels whose result may legitimately differ between fp32 and fp64: a
-    threshold test within ``margin_rel`` (relative), or -- for a Gaussian whose
-    3-sigma box edge lies within ``rect_margin_px`` of a tile line, so that the
-    tile beyond that line may or may not list it -- the pixels of that tile
-    where the Gaussian's alpha reaches 1/255 (elsewhere the flip is inert)."""
-    bad = oracle_fwd["margin"] < margin_rel
-    if "cov2d" not in proj:
-        return bad
-    TX, TY = oracle.tiles(W, H)
-    m2, cov, con = proj["means2d"], proj["cov2d"], proj["conics"]
-    op = np.ones(len(m2)) if opacities is None else np.asarray(opacities, np.float64)
-    ys, xs = np.mgrid[0:H, 0:W]
-    for n in np.nonzero((proj["rect_margin"] < rect_margin_px) & (proj["valid"] > 0))[0]:
-        x0, y0, x1, y1 = proj["rects"][n]
-        rx, ry = 3 * np.sqrt(cov[n, 0]), 3 * np.sqrt(cov[n, 2])
-        for axis, side, edge in ((0, 0, m2[n, 0] - rx), (0, 1, m2[n, 0] + rx), (1, 0, m2[n, 1] - ry),
-                                 (1, 1, m2[n, 1] + ry)):
-            k = int(np.floor(edge / 16 + 0.5))
-            if abs(edge - 16 * k) >= rect_margin_px:
-                continue
-            t = k - 1 if side == 0 else k  # the tile that may flip
-            if axis == 0:
-                if not 0 <= t < TX:
-                    continue
-                sel = (xs // 16 == t) & (ys // 16 >= max(y0 - 1, 0)) & (ys // 16 < y1 + 1)
-            else:
-                if not 0 <= t < TY:
-                    continue
-                sel = (ys // 16 == t) & (xs // 16 >= max(x0 - 1, 0)) & (xs // 16 < x1 + 1)
-            dx, dy = m2[n, 0] - (xs + 0.5), m2[n, 1] - (ys + 0.5)
-            sigma = 0.5 * (con[n, 0] * dx * dx + 2 * con[n, 1] * dx * dy + con[n, 2] * dy * dy)
-            bad |= sel & (op[n] * np.exp(-sigma) >= (1 / 255) * (1 - 1e-3))
-    return bad
+    """Pixels whose result may legitimately differ between fp32 and fp64 (see
+    ``oracle.compare.uncertain_pixels``), from an oracle forward of the whole
+    image."""
+    return compare.uncertain_pixels(oracle_fwd["margin"], proj, W, H, opacities, None, margin_rel, rect_margin_px)
 
 
-def rel_l2(a, b):
-    a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+rel_l2 = compare.rel_l2

@@ -124,15 +124,25 @@ int gs_views_layout(GsView* views, int32_t V, int64_t* P_total, int32_t* T_total
  * every view: t = T_cw [mu; 1]; mu' = (fx t_x/t_z + cx, fy t_y/t_z + cy);
  * J of Eq. 3; R(q/|q|) of Eq. 5 (with R_11 = 1 - 2(x^2 + z^2), the orthonormal
  * form); Sigma = R S S^T R^T; Sigma' = J R_cw Sigma R_cw^T J^T + eps2d I;
- * conic Y = Sigma'^-1 packed (a, b, c) for [[a, b], [b, c]]; the tight box
- * r = 3 (sqrt(Sigma'_00), sqrt(Sigma'_11)) and its tile rectangle
- * [floor((mu' - r)/16), floor((mu' + r)/16) + 1) clamped to the tile grid.
+ * the conic Y = Sigma'^-1; the tight box r = 3 (sqrt(Sigma'_00),
+ * sqrt(Sigma'_11)) and its tile rectangle [floor((mu' - r)/16),
+ * floor((mu' + r)/16) + 1) clamped to the tile grid.
  * A projection is culled (touched = 0, zero rect) when t_z <= near,
  * t_z >= far, det Sigma' <= 0, the rectangle is empty, or a value is not
  * finite.
+ *
+ * The conic is stored FACTORED, as (a, k, d) with
+ *     sigma = 1/2 Delta^T Y Delta = 1/2 (a (Delta_x + k Delta_y)^2 + d Delta_y^2),
+ * i.e. Y = [[a, a k], [a k, a k^2 + d]] (the LDL^T factors of Y):
+ * a = Sigma'_11 / det Sigma', k = -Sigma'_01 / Sigma'_11, d = 1 / Sigma'_11.
+ * The packed entries (Y_00, Y_01, Y_11) of a thin Gaussian lose the long
+ * axis in fp32 (d = Y_11 - Y_01^2 / Y_00 cancels); the factors keep both axes
+ * to full precision.  Sigma' is formed as A A^T + eps2d I from the images
+ * A = J R_cw R S of the scaled axes, and det Sigma' by Cauchy-Binet (a sum of
+ * non-negative terms), so no step cancels.
  *   in : views[V] (device), means[N,3], quats[N,4], scales[N,3]
- *   out: means2d[P,2], conics[P,3], depths[P] (t_z), rects[P,4] int16
- *        (x0, y0, x1, y1 tile indices, half-open), touched[P] int32
+ *   out: means2d[P,2], conics[P,3] = (a, k, d), depths[P] (t_z), rects[P,4]
+ *        int16 (x0, y0, x1, y1 tile indices, half-open), touched[P] int32
  *        (tiles in the rectangle), K_total (device int64, nullable): set to
  *        the sum of touched (the intersection count).
  */
@@ -212,8 +222,11 @@ int gs_bin_and_sort_static(const GsView* views, int32_t V, int64_t P, int32_t T_
                            int32_t* isect_pos, int32_t* emit_start, int32_t* tile_ranges, int32_t* K_out,
                            uint32_t* flags, void* stream);
 
-/* How the two compositing kernels walk the tiles (NULL = defaults: one CTA
- * per tile, in tile id order).  None of these choices changes any result. */
+/* How the two compositing kernels walk the tiles and the shape of the
+ * backward's work (NULL or zeroed fields = defaults: one CTA per tile, in
+ * tile id order, the default batch shape).  None of these choices changes
+ * any result beyond the fp32 summation order of the fast backward's atomics;
+ * in the deterministic mode the results are identical. */
 typedef struct GsRasterConfig {
     int32_t persistent;         /* 1: a persistent grid pops tiles from a global queue */
     int32_t ctas_per_sm;        /* persistent grid = ctas_per_sm x SMs (<= 0: as many as fit) */
@@ -230,7 +243,19 @@ typedef struct GsRasterConfig {
                                    repeating the same test.  Give the backward the buffer the
                                    forward of the same frame filled; words the forward had no
                                    use for are left as they were. */
+    int32_t bwd_pixels;         /* pixels per thread of gs_rasterize_bwd (fp32, up to 3 channels):
+                                   0 = the default (GS_BWD_PIXELS_DEFAULT), 1 = one (8 warps per
+                                   tile, each on an 8x4 box), 2 = two (4 warps, each on an 8x8 box:
+                                   a Gaussian that reaches both 8x4 halves is reduced over the warp
+                                   once for 64 pixels) */
+    int32_t bwd_batch;          /* Gaussians per staged batch of gs_rasterize_bwd: 0 = the default
+                                   for the pixel count; otherwise one of the compiled shapes -- 64 or
+                                   96 with one pixel per thread, 64 or 128 with two.  The fp64 entry
+                                   points ignore both fields (one pixel, batches of 32). */
 } GsRasterConfig;
+
+/* The backward's default pixels per thread. */
+#define GS_BWD_PIXELS_DEFAULT 1
 
 /* Bytes of scratch gs_tile_order needs for T_total tiles. */
 size_t gs_tile_order_workspace_size(int32_t T_total);
@@ -276,8 +301,9 @@ size_t gs_rasterize_bwd_workspace_size(int64_t K_capacity, int32_t deterministic
  *   dC/dc_n = alpha_n T_n,
  *   dC/dalpha_n = c_n T_n - S_n/(1 - alpha_n) - background T_final/(1 - alpha_n),
  *   dalpha/do = exp(-sigma), dalpha/dsigma = -o exp(-sigma) (both 0 where the
- *   0.99 clamp was active), dsigma/dmu' = Y Delta, dsigma/d(a,b,c) =
- *   (Delta_x^2/2, Delta_x Delta_y, Delta_y^2/2).
+ *   0.99 clamp was active), dsigma/dmu' = Y Delta, and for the factored conic
+ *   (a, k, d) of gs_project, with u = Delta_x + k Delta_y,
+ *   dsigma/d(a, k, d) = (u^2/2, a u Delta_y, Delta_y^2/2).
  * Per-pixel terms are first summed per (tile, Gaussian) inside each tile (warp
  * reduce-scatter, then a fixed-order sum over the tile's warps).  The tile sums
  * then reach the per-projection outputs in one of two ways:
@@ -292,7 +318,7 @@ size_t gs_rasterize_bwd_workspace_size(int64_t K_capacity, int32_t deterministic
  *        (these four are read only when deterministic; may be NULL otherwise),
  *        workspace (>= gs_rasterize_bwd_workspace_size bytes)
  *   out (ACCUMULATED: += into caller-initialised buffers):
- *        dL_dmeans2d[P,2], dL_dconics[P,3] (per projection),
+ *        dL_dmeans2d[P,2], dL_dconics[P,3] = dL/d(a, k, d) (per projection),
  *        dL_dopacities[N], dL_dcolors[N,3] (per Gaussian, summed over views).
  */
 int gs_rasterize_bwd(const GsView* views, int32_t V, int64_t P, int32_t T_total, const float* means2d,
@@ -306,14 +332,17 @@ int gs_rasterize_bwd(const GsView* views, int32_t V, int64_t P, int32_t T_total,
 
 /*
  * Sec. 3.2 (Eq. 16-20) and 3.2.1: for every projection with touched > 0,
- * recomputes the forward and maps dL/dmu' and dL/dconic to
- *   dL/dSigma' = -Y G Y (G = dL/dY, the packed b gradient split evenly),
+ * recomputes the forward and maps dL/dmu' and dL/dconic (w.r.t. the factored
+ * conic (a, k, d) of gs_project) to
+ *   dL/dSigma' (-Y G Y of Sec. 3.2 with G = dL/dY, written in the factors),
  *   dL/dSigma = T^T dL/dSigma' T with T = J R_cw, dL/dT, dL/dJ = dL/dT R_cw^T,
  *   dL/dt = J^T dL/dmu' + <dL/dJ, dJ/dt>, dL/dmu = R_cw^T dL/dt,
  *   dL/dM = 2 dL/dSigma M, dL/dR = dL/dM S, dL/ds = diag(R^T dL/dM),
- *   dL/dq_hat from the four dR/dq matrices, then through q_hat = q/|q|.
+ *   dL/dq from dL/dR through R(q/|q|) (Sec. 3.2.1; the kernel takes the
+ *   equivalent route through the rotation about the Gaussian's own axes,
+ *   which keeps fp32 precision for thin Gaussians).
  *   in : views, P, means, quats, scales, eps2d, touched, dL_dmeans2d,
- *        dL_dconics
+ *        dL_dconics (dL/d(a, k, d))
  *   out (ACCUMULATED, summed over views): dL_dmeans[N,3], dL_dquats[N,4]
  *        (w.r.t. the raw quaternion), dL_dscales[N,3].
  *   out (optional, may be NULL; ACCUMULATED): dL_dviewmats[V,4,4], dL/dT_cw of

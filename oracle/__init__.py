@@ -85,7 +85,7 @@ def _load():
                 "or_world_to_pixel": (None, [_P, _P, _P, _P]),
                 "or_project": (None, [_P, _I64, _P, _P, _P, _D, _I32] + [_P] * 7),
                 "or_rasterize": (None, [_I64, _P, _P, _P, _P, _I32, _P, _P, _P, _I32, _I32, _I32, _P,
-                                        _I64, _P, _P, _P, _P, _P, _P]),
+                                        _I64, _P, _P, _P, _P, _P, _P, _P]),
                 "or_rasterize_bwd": (None, [_I64, _P, _P, _P, _P, _I32, _P, _P, _P, _I32, _I32, _I32, _P,
                                             _I64, _P, _P, _P, _P, _P, _P]),
                 "or_project_bwd": (None, [_P, _I64, _P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
@@ -229,7 +229,9 @@ def rasterize(proj: dict, opacities, colors, width: int, height: int, background
     given flat); ``background`` has C values.  ``pixels``: optional int64
     array of linear pixel ids (y*W + x); outputs then follow that order.
     Returns rgb [.., C], T_final, last_id, n_contrib, margin (smallest
-    relative margin of any alpha / T threshold test)."""
+    relative margin of any alpha / T threshold test) and depth_gap (smallest
+    relative depth difference between consecutive Gaussians that pass the
+    alpha test, up to the one that stops the pixel; inf if fewer than two)."""
     m2, con, dep, rects, valid = _proj_arrays(proj)
     n = m2.shape[0]
     op, col = _d(opacities, (n,)), _colors(colors, n)
@@ -238,14 +240,14 @@ def rasterize(proj: dict, opacities, colors, width: int, height: int, background
     pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int64)
     npix = width * height if pix is None else pix.shape[0]
     out = dict(rgb=np.zeros((npix, nc)), T_final=np.zeros(npix), last_id=np.zeros(npix, np.int64),
-               n_contrib=np.zeros(npix, np.int64), margin=np.zeros(npix))
+               n_contrib=np.zeros(npix, np.int64), margin=np.zeros(npix), depth_gap=np.zeros(npix))
     _load().or_rasterize(n, _ptr(m2), _ptr(con), _ptr(op), _ptr(col), nc, _ptr(dep), _ptr(rects), _ptr(valid),
                          width, height, tile, _ptr(bg), npix, _ptr(pix),
                          _ptr(out["rgb"]), _ptr(out["T_final"]), _ptr(out["last_id"]), _ptr(out["n_contrib"]),
-                         _ptr(out["margin"]))
+                         _ptr(out["margin"]), _ptr(out["depth_gap"]))
     if pix is None:
         out["rgb"] = out["rgb"].reshape(height, width, nc)
-        for k in ("T_final", "last_id", "n_contrib", "margin"):
+        for k in ("T_final", "last_id", "n_contrib", "margin", "depth_gap"):
             out[k] = out[k].reshape(height, width)
     return out
 

@@ -341,15 +341,20 @@ typedef struct {
 } contrib;
 
 /* Composites pixel (px, py) over the Gaussians of list[0..m) in order.
- * Fills out[] with the composited Gaussians (may be NULL), returns their count. */
+ * Fills out[] with the composited Gaussians (may be NULL), returns their count.
+ * With depth_gap (and depths) it also reports the smallest relative depth
+ * difference between consecutive Gaussians that pass the alpha test, up to
+ * the one that stops the pixel: where it is tiny, a lower-precision depth key
+ * may order them the other way (Readings O10, O12). */
 static int64_t composite_pixel(int px, int py, const int64_t* list, int64_t m,
                                const double* means2d, const double* conics, const double* opac,
                                const double* colors, int nc, const double* bg,
                                double* rgb, double* T_final, int64_t* last_id, double* margin,
-                               contrib* out)
+                               const double* depths, double* depth_gap, contrib* out)
 {
     const double x = px + 0.5, y = py + 0.5; /* Reading O2: pixel centres */
-    double T = 1.0, mg = INFINITY;
+    double T = 1.0, mg = INFINITY, gap = INFINITY, prev_depth = 0.0;
+    int have_prev = 0;
     if (rgb)
         for (int k = 0; k < nc; ++k) rgb[k] = 0.0;
     int64_t last = -1, cnt = 0;
@@ -364,6 +369,12 @@ static int64_t composite_pixel(int px, int py, const int64_t* list, int64_t m,
         mg = fmin(mg, fabs(raw - OR_ALPHA_MIN) / OR_ALPHA_MIN);
         mg = fmin(mg, fabs(raw - OR_ALPHA_MAX) / OR_ALPHA_MAX);
         if (!(raw >= OR_ALPHA_MIN)) continue; /* O7: also skips a non-finite o e^-sigma */
+        if (depth_gap) {
+            const double d = depths[n];
+            if (have_prev) gap = fmin(gap, fabs(d - prev_depth) / fmax(fabs(prev_depth), 1e-300));
+            prev_depth = d;
+            have_prev = 1;
+        }
         const double Tn = T * (1.0 - alpha);
         mg = fmin(mg, fabs(Tn - OR_T_MIN) / OR_T_MIN);
         if (Tn < OR_T_MIN) break;
@@ -387,6 +398,7 @@ static int64_t composite_pixel(int px, int py, const int64_t* list, int64_t m,
     if (T_final) *T_final = T;
     if (last_id) *last_id = last;
     if (margin) *margin = mg;
+    if (depth_gap) *depth_gap = gap;
     return cnt;
 }
 
@@ -446,7 +458,7 @@ int64_t or_pixel_trace(int64_t N, const double* means2d, const double* conics, c
     const int64_t m = depth_order(N, depths, valid, order);
     const int64_t k = tile_list(order, m, rects, px / tile, py / tile, list);
     const int64_t c = composite_pixel(px, py, list, k, means2d, conics, opac, colors, nc, NULL,
-                                      NULL, T_final, NULL, NULL, cs);
+                                      NULL, T_final, NULL, NULL, NULL, NULL, cs);
     for (int64_t j = 0; j < c; ++j) { ids[j] = cs[j].id; alpha[j] = cs[j].alpha; T[j] = cs[j].T; }
     free(order); free(list); free(cs);
     return c;
@@ -459,13 +471,17 @@ int64_t or_pixel_trace(int64_t N, const double* means2d, const double* conics, c
  * W*H pixels in order.  Outputs are indexed by position in that list:
  * rgb[npix,nc], T_final[npix], last_id[npix] (index of the last composited
  * Gaussian or -1), n_contrib[npix], margin[npix] (smallest relative margin
- * of any alpha/T threshold test met; +inf if none).  bg (nc values) may be NULL.
+ * of any alpha/T threshold test met; +inf if none), depth_gap[npix] (may be
+ * NULL: smallest relative depth difference between consecutive Gaussians that
+ * pass the alpha test, up to the one that stops the pixel; +inf if fewer than
+ * two).  bg (nc values) may be NULL.
  */
 void or_rasterize(int64_t N, const double* means2d, const double* conics, const double* opac,
                   const double* colors, int32_t nc, const double* depths, const int32_t* rects,
                   const int32_t* valid, int32_t W, int32_t H, int32_t tile, const double* bg,
                   int64_t npix, const int64_t* pix,
-                  double* rgb, double* T_final, int64_t* last_id, int64_t* n_contrib, double* margin)
+                  double* rgb, double* T_final, int64_t* last_id, int64_t* n_contrib, double* margin,
+                  double* depth_gap)
 {
     const int TX = tiles_across(W, tile);
     int64_t* all = NULL;
@@ -492,7 +508,8 @@ void or_rasterize(int64_t N, const double* means2d, const double* conics, const 
                 const int64_t p = groups[i].pix, o = groups[i].pos;
                 const int64_t c = composite_pixel((int)(p % W), (int)(p / W), list, k, means2d, conics, opac, colors, nc,
                                                   bg, rgb ? rgb + (int64_t)nc * o : NULL, T_final ? T_final + o : NULL,
-                                                  last_id ? last_id + o : NULL, margin ? margin + o : NULL, NULL);
+                                                  last_id ? last_id + o : NULL, margin ? margin + o : NULL, depths,
+                                                  depth_gap ? depth_gap + o : NULL, NULL);
                 if (n_contrib) n_contrib[o] = c;
             }
         }
@@ -559,7 +576,7 @@ void or_rasterize_bwd(int64_t N, const double* means2d, const double* conics, co
                 const int px = (int)(p % W), py = (int)(p / W);
                 double Tf;
                 const int64_t c = composite_pixel(px, py, list, k, means2d, conics, opac, colors, nc, bg,
-                                                  NULL, &Tf, NULL, NULL, cs);
+                                                  NULL, &Tf, NULL, NULL, NULL, NULL, cs);
                 const double* G = dL_drgb + (int64_t)nc * i;
                 /* S_n as explicit suffix sums */
                 for (int q = 0; q < nc; ++q) S[(int64_t)nc * c + q] = 0.0;

@@ -53,7 +53,8 @@ class GsView(ctypes.Structure):
 
 class GsRasterConfig(ctypes.Structure):
     _fields_ = [("persistent", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("tile_order", ctypes.c_void_p), ("queue", ctypes.c_void_p), ("warp_hits", ctypes.c_void_p)]
+                ("tile_order", ctypes.c_void_p), ("queue", ctypes.c_void_p), ("warp_hits", ctypes.c_void_p),
+                ("bwd_pixels", ctypes.c_int32), ("bwd_batch", ctypes.c_int32)]
 
 
 class GsAdamConfig(ctypes.Structure):
@@ -61,7 +62,7 @@ class GsAdamConfig(ctypes.Structure):
                 ("eps", ctypes.c_float)]
 
 
-assert ctypes.sizeof(GsCamera) == 80 and ctypes.sizeof(GsView) == 120 and ctypes.sizeof(GsRasterConfig) == 32
+assert ctypes.sizeof(GsCamera) == 80 and ctypes.sizeof(GsView) == 120 and ctypes.sizeof(GsRasterConfig) == 40
 assert ctypes.sizeof(GsAdamConfig) == 32
 
 _P = ctypes.c_void_p
@@ -257,10 +258,11 @@ class RasterConfig:
     are kept alive by this object."""
 
     def __init__(self, persistent: bool = False, ctas_per_sm: int = 0, tile_order=None, device="cuda",
-                 warp_hits=None):
+                 warp_hits=None, bwd_pixels: int = 0, bwd_batch: int = 0):
         """``warp_hits``: optional device int32 [K_capacity] buffer through which the forward hands
         its per-pair warp-box cull (one 32-bit ballot per warp box and chunk of 32 pairs) to the
-        backward of the same frame."""
+        backward of the same frame.  ``bwd_pixels`` / ``bwd_batch``: the backward's pixels per
+        thread and staged batch (0 = defaults; see GsRasterConfig in gsplat103.h)."""
         if warp_hits is not None and (warp_hits.dtype != torch.int32 or warp_hits.device.type != "cuda"):
             raise TypeError("warp_hits must be a device int32 tensor of K_capacity words")
         self.persistent = bool(persistent)
@@ -268,10 +270,12 @@ class RasterConfig:
         self.tile_order = tile_order
         self.warp_hits = warp_hits
         self.queue = torch.zeros(1, dtype=torch.int32, device=device) if persistent else None
+        self.bwd_pixels, self.bwd_batch = int(bwd_pixels), int(bwd_batch)
         self.c = GsRasterConfig(int(self.persistent), self.ctas_per_sm,
                                 None if tile_order is None else tile_order.data_ptr(),
                                 None if self.queue is None else self.queue.data_ptr(),
-                                None if warp_hits is None else warp_hits.data_ptr())
+                                None if warp_hits is None else warp_hits.data_ptr(),
+                                self.bwd_pixels, self.bwd_batch)
 
     def ref(self):
         return ctypes.byref(self.c)
@@ -279,7 +283,8 @@ class RasterConfig:
     def describe(self) -> dict:
         return {"persistent": self.persistent, "ctas_per_sm": self.ctas_per_sm,
                 "tile_order": "longest-first" if self.tile_order is not None else "tile id",
-                "warp_hits": self.warp_hits is not None}
+                "warp_hits": self.warp_hits is not None, "bwd_pixels": self.bwd_pixels,
+                "bwd_batch": self.bwd_batch}
 
 
 def _cfg(config: Optional[RasterConfig]):

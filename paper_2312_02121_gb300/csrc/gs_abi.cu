@@ -30,7 +30,7 @@ int launch_status(const char* what)
 
 }  // namespace gs
 
-extern "C" int gs_version(void) { return 104; }
+extern "C" int gs_version(void) { return 200; }
 
 extern "C" const char* gs_last_error(void) { return gs::g_last_error; }
 

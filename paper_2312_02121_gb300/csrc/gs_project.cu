@@ -26,6 +26,16 @@ __device__ __forceinline__ void quat_to_rot(S w, S x, S y, S z, S R[9])
 }
 
 // Forward quantities shared by both kernels.
+//
+// Sigma' is formed from the images of the Gaussian's scaled axes, A = T R S
+// (T = J R_cw, 2x3), as Sigma' = A A^T + eps2d I -- the same matrix as
+// T Sigma T^T of Eq. 4 with Sigma = R S S^T R^T of Eq. 6, but without
+// forming Sigma: the product M M^T buries the variance of a thin Gaussian's
+// short axes under the long one (fp32 keeps about 7 digits of the largest
+// entry), A A^T keeps every axis to full relative precision.  Its
+// determinant comes from Cauchy-Binet, det(A A^T) = sum_{i<j} (a_i ^ a_j)^2
+// over the columns a_i of A, plus eps2d (|row 0|^2 + |row 1|^2) + eps2d^2: a
+// sum of non-negative terms, where a c - b^2 cancels for a thin Gaussian.
 template <typename S>
 struct Proj {
     S t[3];       // camera-space mean
@@ -34,10 +44,11 @@ struct Proj {
     S q[4];       // unit quaternion
     S qinv;       // 1 / |q|
     S R[9];       // rotation of the Gaussian
-    S M[9];       // R S
-    S Sig[6];     // Sigma: 00 01 02 11 12 22
+    S s[3];       // scales
     S T[6];       // J R_cw (2x3)
-    S a, b, c;    // Sigma' + eps2d I
+    S Bx[3], By[3];  // T R: the image of each unit axis (column j: (Bx[j], By[j])); A = B S
+    S a, b, c;    // Sigma' + eps2d I = [[a, b], [b, c]]
+    S det;        // det of that
 };
 
 template <typename S>
@@ -62,52 +73,48 @@ __device__ __forceinline__ void project_one(const GsCamera& cam, const S* __rest
     o.J11 = fy * o.rz;
     o.J02 = -fx * o.t[0] * o.rz * o.rz;
     o.J12 = -fy * o.t[1] * o.rz * o.rz;
-    // Eq. 5-6: Sigma = R S S^T R^T with q normalised
+    // Eq. 5: R of the normalised quaternion
     const V4<S> q = quats[g];
     o.qinv = S(1) / sqrt(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
     o.q[0] = q.x * o.qinv; o.q[1] = q.y * o.qinv; o.q[2] = q.z * o.qinv; o.q[3] = q.w * o.qinv;
     quat_to_rot(o.q[0], o.q[1], o.q[2], o.q[3], o.R);
-    const S s0 = scales[3 * g + 0], s1 = scales[3 * g + 1], s2 = scales[3 * g + 2];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        o.M[3 * i + 0] = o.R[3 * i + 0] * s0;
-        o.M[3 * i + 1] = o.R[3 * i + 1] * s1;
-        o.M[3 * i + 2] = o.R[3 * i + 2] * s2;
-    }
-    const S* M = o.M;
-    o.Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
-    o.Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
-    o.Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
-    o.Sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
-    o.Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
-    o.Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
-    // Eq. 4: Sigma' = T Sigma T^T with T = J R_cw
+    o.s[0] = scales[3 * g + 0];
+    o.s[1] = scales[3 * g + 1];
+    o.s[2] = scales[3 * g + 2];
+    // Eq. 4 and 6: T = J R_cw, A = T R S, Sigma' = A A^T + eps2d I
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         o.T[j] = o.J00 * W[j] + o.J02 * W[6 + j];
         o.T[3 + j] = o.J11 * W[3 + j] + o.J12 * W[6 + j];
     }
-    const S* Sg = o.Sig;
-    S U[6];  // T Sigma
+    S Ax[3], Ay[3];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const S* Tr = o.T + 3 * r;
-        U[3 * r + 0] = Tr[0] * Sg[0] + Tr[1] * Sg[1] + Tr[2] * Sg[2];
-        U[3 * r + 1] = Tr[0] * Sg[1] + Tr[1] * Sg[3] + Tr[2] * Sg[4];
-        U[3 * r + 2] = Tr[0] * Sg[2] + Tr[1] * Sg[4] + Tr[2] * Sg[5];
+    for (int j = 0; j < 3; ++j) {
+        o.Bx[j] = o.T[0] * o.R[j] + o.T[1] * o.R[3 + j] + o.T[2] * o.R[6 + j];
+        o.By[j] = o.T[3] * o.R[j] + o.T[4] * o.R[3 + j] + o.T[5] * o.R[6 + j];
+        Ax[j] = o.Bx[j] * o.s[j];
+        Ay[j] = o.By[j] * o.s[j];
     }
-    o.a = U[0] * o.T[0] + U[1] * o.T[1] + U[2] * o.T[2] + eps2d;
-    o.b = U[0] * o.T[3] + U[1] * o.T[4] + U[2] * o.T[5];
-    o.c = U[3] * o.T[3] + U[4] * o.T[4] + U[5] * o.T[5] + eps2d;
+    const S rx2 = Ax[0] * Ax[0] + Ax[1] * Ax[1] + Ax[2] * Ax[2];
+    const S ry2 = Ay[0] * Ay[0] + Ay[1] * Ay[1] + Ay[2] * Ay[2];
+    o.a = rx2 + eps2d;
+    o.c = ry2 + eps2d;
+    o.b = Ax[0] * Ay[0] + Ax[1] * Ay[1] + Ax[2] * Ay[2];
+    const S w01 = Ax[0] * Ay[1] - Ay[0] * Ax[1], w02 = Ax[0] * Ay[2] - Ay[0] * Ax[2], w12 = Ax[1] * Ay[2] - Ay[1] * Ax[2];
+    o.det = w01 * w01 + w02 * w02 + w12 * w12 + eps2d * (rx2 + ry2) + eps2d * eps2d;
 }
 
-// a c - b^2 with the rounding error of b^2 compensated (Kahan's 2x2 determinant).
+// The conic Y = Sigma'^-1 in the factored form (ya, yk, yd) of the ABI:
+// sigma = (ya (dx + yk dy)^2 + yd dy^2) / 2, i.e. Y = [[ya, ya yk], [ya yk, ya yk^2 + yd]] -- the LDL^T
+// factors of Y.  ya = c / det, yk = -b / c, yd = 1 / c: quotients only, no cancellation, so both axes of a
+// thin Gaussian keep their digits (the packed entries of Y lose the long axis: yd = Y_11 - Y_01^2 / Y_00
+// cancels).
 template <typename S>
-__device__ __forceinline__ S det2(S a, S b, S c)
+__device__ __forceinline__ void conic_factors(const Proj<S>& o, S& ya, S& yk, S& yd)
 {
-    const S bb = b * b;
-    const S e = fma(b, b, -bb);
-    return fma(a, c, -bb) - e;
+    ya = o.c / o.det;
+    yk = -o.b / o.c;
+    yd = S(1) / o.c;
 }
 
 template <typename S>
@@ -128,16 +135,12 @@ k_project_fwd(const GsView* __restrict__ views, int V, int64_t P, const S* __res
         Proj<S> o;
         S u, v;
         project_one(cam, means, quats, scales, g, eps2d, o, u, v);
-        const S det = det2(o.a, o.b, o.c);
-        bool ok = o.t[2] > S(cam.near_plane) && o.t[2] < S(cam.far_plane) && det > S(0) && isfinite(u) &&
-                  isfinite(v) && isfinite(o.a) && isfinite(o.c) && isfinite(det);
+        bool ok = o.t[2] > S(cam.near_plane) && o.t[2] < S(cam.far_plane) && o.det > S(0) && o.c > S(0) &&
+                  isfinite(u) && isfinite(v) && isfinite(o.a) && isfinite(o.c) && isfinite(o.det);
         S ca = 0, cb = 0, cc = 0;
         short4 r = make_short4(0, 0, 0, 0);
         if (ok) {
-            const S inv = S(1) / det;
-            ca = o.c * inv;
-            cb = -o.b * inv;
-            cc = o.a * inv;
+            conic_factors(o, ca, cb, cc);
             // Sec. 2.2: tight 3-sigma box and the tiles it touches (1/16 is exact)
             const S rx = S(3) * sqrt(o.a), ry = S(3) * sqrt(o.c);
             const S TX = (S)view.tiles_x, TY = (S)view.tiles_y;
@@ -180,6 +183,35 @@ k_project_fwd(const GsView* __restrict__ views, int V, int64_t P, const S* __res
 
 // The backward of one projection p of view `view`.  With kView it also returns
 // this projection's share of dL/dT_cw (rows 0-2 of the 4x4, row-major) in vg.
+//
+// Sec. 3.2 (Eq. 16-20) and 3.2.1, arranged so that fp32 keeps its digits for a
+// thin Gaussian.  The conic gradient arrives as dL/d(ya, yk, yd), the factored
+// conic of the forward.  Through ya = c / det, yk = -b / c, yd = 1 / c it gives
+// dL/dSigma' (the -Y G Y of Sec. 3.2, written in the factors):
+//   dL/dSigma' = al [[1, yk], [yk, yk^2]] + be [[0, 1], [1, 2 yk]] + ga [[0, 0], [0, 1]],
+//   al = -ya^2 dL/dya,  be = -yd dL/dyk / 2,  ga = -yd^2 dL/dyd.
+// Each unit axis image b_j = (Bx_j, By_j) (column j of T R) is written in the
+// conic's coordinates u_j = Bx_j + yk By_j, y_j = By_j; the bilinear form of
+// dL/dSigma' is then Q_ij = b_i^T dL/dSigma' b_j = u_i p_j + y_i r_j with
+// p_j = al u_j + be y_j and r_j = be u_j + ga y_j.  With A = B S and
+// Sigma' = A A^T + eps2d I:
+//   dL/dA_j = 2 dL/dSigma' a_j = 2 s_j (p_j, yk p_j + r_j)
+//   dL/dT   = dL/dA (R S)^T          (-> dL/dJ = dL/dT R_cw^T, dL/dt, dL/dmu)
+//   dL/ds_j = (R^T dL/dM)_jj = 2 s_j Q_jj
+//   R^T dL/dR = E S with E = R^T dL/dM, E_ij = 2 s_j Q_ij, whose antisymmetric
+//   part is the gradient of a rotation of the Gaussian about its own axes:
+//   dL/domega = 2 (Q_12 (s_1^2 - s_2^2), Q_20 (s_2^2 - s_0^2), Q_01 (s_0^2 - s_1^2)).
+// Since R(q (x) r) = R(q) R(r), such a rotation moves the unit quaternion by
+// q_hat (x) (0, omega) / 2, so dL/dq = 2 q_hat (x) (0, dL/domega) / |q|: the
+// gradient the printed dR/dq matrices of Sec. 3.2.1 give, projected on the
+// sphere (dL/dq = (I - q_hat q_hat^T) dL/dq_hat / |q|), but without the large
+// component along q_hat that the projection would cancel.
+//
+// u_j of the longest axis image cancels when that axis lies along the
+// conic's direction (1, -1 / yk); it is then taken from the identity
+// sum_j s_j^2 u_j y_j = -eps2d yk (the off-diagonal of P Sigma' P^T, which is
+// diagonal for the factor P = [[1, yk], [0, 1]] of Y = P^T diag(ya, yd) P),
+// whose other terms are small and exact.
 template <typename S, bool kView>
 __device__ __forceinline__ void project_bwd_one(const GsView& view, int64_t p, const S* __restrict__ means,
                                                 const V4<S>* __restrict__ quats, const S* __restrict__ scales,
@@ -190,42 +222,62 @@ __device__ __forceinline__ void project_bwd_one(const GsView& view, int64_t p, c
     const GsCamera& cam = view.cam;
     const int64_t g = view.g_begin + (p - view.proj_offset);
     Proj<S> o;
-    S u, v;
-    project_one(cam, means, quats, scales, g, eps2d, o, u, v);
-    const S inv = S(1) / det2(o.a, o.b, o.c);
-    const S Y0 = o.c * inv, Y1 = -o.b * inv, Y2 = o.a * inv;  // Y = [[Y0, Y1], [Y1, Y2]]
+    S u2, v2;
+    project_one(cam, means, quats, scales, g, eps2d, o, u2, v2);
+    S ya, yk, yd;
+    conic_factors(o, ya, yk, yd);
+    const S al = -ya * ya * dL_dconics[3 * p + 0];
+    const S be = S(-0.5) * yd * dL_dconics[3 * p + 1];
+    const S ga = -yd * yd * dL_dconics[3 * p + 2];
 
-    // Sec. 3.1: G = dL/dY from the packed conic gradient (the b gradient covers both off-diagonals)
-    const S ga = dL_dconics[3 * p + 0], gb = S(0.5) * dL_dconics[3 * p + 1], gc = dL_dconics[3 * p + 2];
-    // dL/dSigma' = -Y G Y
-    const S YG00 = Y0 * ga + Y1 * gb, YG01 = Y0 * gb + Y1 * gc;
-    const S YG10 = Y1 * ga + Y2 * gb, YG11 = Y1 * gb + Y2 * gc;
-    const S D00 = -(YG00 * Y0 + YG01 * Y1);
-    const S D01 = -(YG00 * Y1 + YG01 * Y2);
-    const S D10 = -(YG10 * Y0 + YG11 * Y1);
-    const S D11 = -(YG10 * Y1 + YG11 * Y2);
-    const S Ds = S(0.5) * (D01 + D10);  // symmetric part
-
-    // Sec. 3.2: dL/dSigma = T^T D T ; dL/dT = D T Sigma^T + D^T T Sigma = 2 D T Sigma
-    S Vm[6];  // D T (2x3)
+    const S* s = o.s;
+    S ut[3], yt[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        Vm[j] = D00 * o.T[j] + Ds * o.T[3 + j];
-        Vm[3 + j] = Ds * o.T[j] + D11 * o.T[3 + j];
+        ut[j] = fma(yk, o.By[j], o.Bx[j]);
+        yt[j] = o.By[j];
     }
-    S dSig[9];
+    {  // the longest axis image, from the identity when its u cancels
+        S mag[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) mag[j] = s[j] * (fabs(o.Bx[j]) + fabs(o.By[j]));
+        const int L = mag[0] >= mag[1] ? (mag[0] >= mag[2] ? 0 : 2) : (mag[1] >= mag[2] ? 1 : 2);
+        S uL = ut[0], yL = yt[0], bxL = o.Bx[0], sL = s[0];
+        if (L == 1) { uL = ut[1]; yL = yt[1]; bxL = o.Bx[1]; sL = s[1]; }
+        if (L == 2) { uL = ut[2]; yL = yt[2]; bxL = o.Bx[2]; sL = s[2]; }
+        if (fabs(uL) < S(0.25) * (fabs(bxL) + fabs(yk * yL)) && yL != S(0) && sL != S(0)) {
+            S num = eps2d * yk;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) dSig[3 * i + j] = o.T[i] * Vm[j] + o.T[3 + i] * Vm[3 + j];
-    const S* Sg = o.Sig;
-    const S Sf[9] = {Sg[0], Sg[1], Sg[2], Sg[1], Sg[3], Sg[4], Sg[2], Sg[4], Sg[5]};
-    S dT[6];
+            for (int j = 0; j < 3; ++j)
+                if (j != L) num = fma(s[j] * s[j] * ut[j], yt[j], num);
+            const S uf = -num / (sL * sL * yL);
+            if (isfinite(uf)) {
+                if (L == 0) ut[0] = uf;
+                if (L == 1) ut[1] = uf;
+                if (L == 2) ut[2] = uf;
+            }
+        }
+    }
+    S pt[3], rt[3];
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
+    for (int j = 0; j < 3; ++j) {
+        pt[j] = fma(al, ut[j], be * yt[j]);
+        rt[j] = fma(be, ut[j], ga * yt[j]);
+    }
+    auto Q = [&](int i, int j) { return fma(ut[i], pt[j], yt[i] * rt[j]); };
+
+    // dL/dT = dL/dA (R S)^T
+    S dT[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
-            dT[3 * r + j] = S(2) * (Vm[3 * r + 0] * Sf[j] + Vm[3 * r + 1] * Sf[3 + j] + Vm[3 * r + 2] * Sf[6 + j]);
+    for (int j = 0; j < 3; ++j) {
+        const S w0 = S(2) * s[j] * s[j] * pt[j];
+        const S w1 = S(2) * s[j] * s[j] * fma(yk, pt[j], rt[j]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            dT[i] = fma(w0, o.R[3 * i + j], dT[i]);
+            dT[3 + i] = fma(w1, o.R[3 * i + j], dT[3 + i]);
+        }
+    }
     // dL/dJ = dL/dT R_cw^T (only the four non-constant entries of J matter)
     S W[9];
 #pragma unroll
@@ -261,36 +313,17 @@ __device__ __forceinline__ void project_bwd_one(const GsView& view, int64_t p, c
         vg[11] = dtz;
     }
 
-    // Sec. 3.2.1: dL/dM = (G + G^T) M = 2 dSigma M (dSigma is symmetric)
-    S dM[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            dM[3 * i + j] = S(2) * (dSig[3 * i + 0] * o.M[j] + dSig[3 * i + 1] * o.M[3 + j] + dSig[3 * i + 2] * o.M[6 + j]);
-    const S s[3] = {scales[3 * g + 0], scales[3 * g + 1], scales[3 * g + 2]};
-    S dR[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) dR[3 * i + j] = dM[3 * i + j] * s[j];
-    S ds3[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) ds3[j] = o.R[j] * dM[j] + o.R[3 + j] * dM[3 + j] + o.R[6 + j] * dM[6 + j];
-    atomic_add3(dL_dscales + 3 * g, ds3[0], ds3[1], ds3[2]);
-    // <dL/dR, dR/dq> with the four Jacobians of Sec. 3.2.1 at the unit quaternion
+    // Sec. 3.2.1: the scales and the rotation
+    atomic_add3(dL_dscales + 3 * g, S(2) * s[0] * Q(0, 0), S(2) * s[1] * Q(1, 1), S(2) * s[2] * Q(2, 2));
+    const S s00 = s[0] * s[0], s11 = s[1] * s[1], s22 = s[2] * s[2];
+    const S om0 = S(2) * Q(1, 2) * (s11 - s22);
+    const S om1 = S(2) * Q(2, 0) * (s22 - s00);
+    const S om2 = S(2) * Q(0, 1) * (s00 - s11);
+    // 2 q_hat (x) (0, omega) / |q|
     const S w = o.q[0], x = o.q[1], y = o.q[2], z = o.q[3];
-    const S gw = S(2) * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
-    const S gx = S(2) * (y * dR[1] + z * dR[2] + y * dR[3] - S(2) * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] -
-                         S(2) * x * dR[8]);
-    const S gy = S(2) * (-S(2) * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] -
-                         S(2) * y * dR[8]);
-    const S gz = S(2) * (-S(2) * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - S(2) * z * dR[4] + y * dR[5] +
-                         x * dR[6] + y * dR[7]);
-    // through q_hat = q / |q|: dq = (I - q_hat q_hat^T) dq_hat / |q|
-    const S dot = gw * w + gx * x + gy * y + gz * z;
-    atomic_add4(dL_dquats + 4 * g, (gw - w * dot) * o.qinv, (gx - x * dot) * o.qinv, (gy - y * dot) * o.qinv,
-                (gz - z * dot) * o.qinv);
+    const S k2 = S(2) * o.qinv;
+    atomic_add4(dL_dquats + 4 * g, -k2 * (x * om0 + y * om1 + z * om2), k2 * (w * om0 + y * om2 - z * om1),
+                k2 * (w * om1 + z * om0 - x * om2), k2 * (w * om2 + x * om1 - y * om0));
 }
 
 template <typename S>

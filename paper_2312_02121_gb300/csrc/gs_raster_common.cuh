@@ -45,9 +45,11 @@ template <> struct RT<double> {
     __device__ static int unstash(double v) { return (int)v; }
 };
 
-// One staged Gaussian (4 x V4 = 64 bytes in fp32):
+// One staged Gaussian (4 x V4 = 64 bytes in fp32).  The conic arrives in the
+// factored form of the ABI, (a, k, D) with sigma = (a (dx + k dy)^2 + D dy^2) / 2
+// (Y = [[a, b], [b, c]] with b = a k, c = a k^2 + D):
 //   xy  : mu'.x, mu'.y, opacity, a
-//   q   : -log2e/2 * a, k = b/a, -log2e/2 * D, b     (D = det/a = c - b^2/a)
+//   q   : -log2e/2 * a, k, -log2e/2 * D, b
 //   col : r, g, b, D
 //   cull: sigma threshold (<0: never reaches 1/255; +inf: never culled),
 //         -b/c, c, (backward: the projection index)
@@ -67,21 +69,18 @@ __device__ __forceinline__ S neg_sigma_log2(const V4<S>& q, S dx, S dy, S& u)
 
 template <typename S>
 __device__ __forceinline__ void stage_gaussian(V4<S>* sh_xy, V4<S>* sh_q, V4<S>* sh_col, V4<S>* sh_cull, int j,
-                                               V2<S> m, S a, S b, S c, S o, S r, S g, S bl, bool need_cull = true)
+                                               V2<S> m, S a, S k, S D, S o, S r, S g, S bl, bool need_cull = true)
 {
-    // det with the rounding error of b^2 compensated (Kahan's 2x2 determinant)
-    const S bb = b * b;
-    const S det = fma(a, c, -bb) - fma(b, b, -bb);
-    const S k = b / a;
-    const S D = det / a;
+    const S b = a * k;
     sh_xy[j] = mk4<S>(m.x, m.y, o, a);
     sh_q[j] = mk4<S>(S(-0.5) * RT<S>::kLog2e * a, k, S(-0.5) * RT<S>::kLog2e * D, b);
     sh_col[j] = mk4<S>(r, g, bl, D);
     if (!need_cull) return;  // a walk that takes its cull from elsewhere
+    const S c = fma(b, k, D);
     S thr;
     if (!(o >= RT<S>::alpha_min())) {
         thr = S(-1);  // o e^-sigma < 1/255 everywhere
-    } else if (!(a > S(0) && det > S(0)) || S(4) * a * c > S(1e7) * det) {
+    } else if (!(a > S(0) && D > S(0)) || S(4) * c > S(1e7) * D) {
         thr = S(INFINITY);  // degenerate or extremely elongated conic: never culled
     } else {
         thr = S(1.05) * log(S(255) * o) + S(1e-3);
@@ -189,9 +188,9 @@ inline bool cull_enabled()
     return !(e && e[0] == '1');
 }
 
-// Grid for a launch of `kernel`: one CTA per tile, or a persistent grid.
+// Grid for a launch of `kernel` with `threads` per CTA: one CTA per tile, or a persistent grid.
 template <typename K>
-inline int raster_grid(K kernel, const GsRasterConfig* cfg, int32_t T_total, unsigned* grid)
+inline int raster_grid(K kernel, const GsRasterConfig* cfg, int32_t T_total, unsigned* grid, int threads = 256)
 {
     if (!cfg || !cfg->persistent) {
         *grid = (unsigned)T_total;
@@ -199,7 +198,7 @@ inline int raster_grid(K kernel, const GsRasterConfig* cfg, int32_t T_total, uns
     }
     int dev = 0, sms = 0, fit = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
-        cudaSuccess || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kernel, 256, 0) != cudaSuccess)
+        cudaSuccess || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kernel, threads, 0) != cudaSuccess)
         return launch_status("raster grid");
     int per = cfg->ctas_per_sm > 0 ? std::min(cfg->ctas_per_sm, fit) : fit;
     per = std::max(per, 1);

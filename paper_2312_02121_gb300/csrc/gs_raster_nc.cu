@@ -283,14 +283,13 @@ k_raster_bwd_nc(const GsView* __restrict__ views, int V, int T_total, const int3
                         SdL = fmaf(wgt, cdot, SdL);
                         T = contrib ? Tn : T;
                         const float ds = -xy.z * gd;
-                        const float dsdx = ds * dx;
-                        // sums the flush turns into dL/dmu' = (a S_u, b S_u + D S_dy) and the packed
-                        // dL/dconic = (S_dx2 / 2, S_dxdy, S_dy2 / 2)
+                        // sums the flush turns into dL/dmu' = (a S_u, b S_u + D S_dy) and the factored
+                        // conic's dL/d(a, k, D) = (S_u2 / 2, a S_udy, S_dy2 / 2)
                         float r[kR];
                         r[0] = ds * u;
                         r[1] = ds * dy;
-                        r[2] = dsdx * dx;
-                        r[3] = dsdx * dy;
+                        r[2] = r[0] * u;
+                        r[3] = r[0] * dy;
                         r[4] = r[1] * dy;
                         r[5] = gd;
 #pragma unroll
@@ -319,7 +318,7 @@ k_raster_bwd_nc(const GsView* __restrict__ views, int V, int T_total, const int3
                     const float ca = sh_xy[j].w, cb = sh_q[j].w, D = sh_col[j].w;
                     atomicAdd(dL_dmeans2d + p, make_float2(ca * a[0], fmaf(cb, a[0], D * a[1])));
                     atomicAdd(dL_dconics + 3 * p + 0, 0.5f * a[2]);
-                    atomicAdd(dL_dconics + 3 * p + 1, a[3]);
+                    atomicAdd(dL_dconics + 3 * p + 1, ca * a[3]);
                     atomicAdd(dL_dconics + 3 * p + 2, 0.5f * a[4]);
                     atomicAdd(dL_dopacities + gg, a[5]);
                     float* dc = dL_dcolors + (int64_t)C * gg + c0;

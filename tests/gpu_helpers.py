@@ -36,12 +36,15 @@ def np_(t):
 
 
 def gpu_projection(frame, i=0):
-    """The CUDA projection of view i as an oracle ``proj`` dict (fp32 values upcast)."""
+    """The CUDA projection of view i as an oracle ``proj`` dict (fp32 values upcast; the conic packed
+    from the library's factors, which ``conic_factors`` keeps)."""
     v = frame.views.host[i]
     s, e = v.proj_offset, v.proj_offset + v.g_count
-    return dict(means2d=np_(frame.means2d[s:e]).astype(np.float64), conics=np_(frame.conics[s:e]).astype(np.float64),
-                depths=np_(frame.depths[s:e]).astype(np.float64), rects=np_(frame.rects[s:e]).astype(np.int32),
-                valid=(np_(frame.touched[s:e]) > 0).astype(np.int32), depths32=np_(frame.depths[s:e]))
+    factors = np_(frame.conics[s:e]).astype(np.float64)
+    return dict(means2d=np_(frame.means2d[s:e]).astype(np.float64), conics=compare.conic_from_factors(factors),
+                conic_factors=factors, depths=np_(frame.depths[s:e]).astype(np.float64),
+                rects=np_(frame.rects[s:e]).astype(np.int32), valid=(np_(frame.touched[s:e]) > 0).astype(np.int32),
+                depths32=np_(frame.depths[s:e]))
 
 
 def view_image(frame, i=0):

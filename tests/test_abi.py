@@ -43,7 +43,7 @@ def test_binding_covers_every_declared_symbol():
 
 def test_version_and_struct_sizes(lib):
     from paper_2312_02121_gb300 import binding
-    assert binding.gs_version() == 104
+    assert binding.gs_version() == 200
     assert ctypes.sizeof(binding.GsView) == 120
 
 

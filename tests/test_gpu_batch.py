@@ -8,6 +8,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import oracle
+from oracle import compare
 from paper_2312_02121_gb300 import batch as GB
 from paper_2312_02121_gb300 import binding as B
 from paper_2312_02121_gb300 import pipeline
@@ -112,7 +113,8 @@ def _sampled_view_parity(w, view_ids, n_pix=400, seed=0):
         cam, sc = v.camera, w.scenes[v.scene]
         hv = views.host[vi]
         s, e = hv.proj_offset, hv.proj_offset + hv.g_count
-        gp = dict(means2d=np_(r.means2d[s:e]).astype(float), conics=np_(r.conics[s:e]).astype(float),
+        gp = dict(means2d=np_(r.means2d[s:e]).astype(float),
+                  conics=compare.conic_from_factors(np_(r.conics[s:e])),
                   depths=np_(r.depths[s:e]).astype(float), rects=np_(r.rects[s:e]).astype(np.int32),
                   valid=(np_(r.touched[s:e]) > 0).astype(np.int32))
         pix = np.sort(rng.choice(cam.pixels, n_pix, replace=False))
@@ -129,7 +131,8 @@ def _sampled_view_parity(w, view_ids, n_pix=400, seed=0):
         r.dL.copy_(G)
         r.backward()
         torch.cuda.synchronize()
-        ob = oracle.rasterize_bwd(gp, sc.opacities, sc.colors, cam.width, cam.height, Gs, pixels=pix)
+        ob = compare.with_factored_conic_grad(
+            oracle.rasterize_bwd(gp, sc.opacities, sc.colors, cam.width, cam.height, Gs, pixels=pix), gp["conics"])
         g0 = ranges[vi][0]
         for k, gk in (("opacities", r.g_op), ("colors", r.g_col)):
             got = np_(gk[g0:g0 + sc.n])

@@ -13,6 +13,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import oracle
+from oracle import compare
 from paper_2312_02121_gb300 import binding as B
 from paper_2312_02121_gb300 import pipeline
 from paper_2312_02121_gb300 import workloads as wl
@@ -57,6 +58,7 @@ def test_multichannel_parity_with_oracle(C):
     G[bad] = 0
     g = pipeline.backward(f, p, torch.tensor(G.reshape(-1, C), device="cuda"))
     ob = oracle.backward(cam, s, G, w.eps2d, background=bg)
+    ob = compare.with_factored_conic_grad(ob, ob["proj"]["conics"])
     for k in ("means2d", "conics", "means", "quats", "scales", "opacities", "colors"):
         assert rel_l2(np_(g[k]), ob[k]) <= GRAD_TOL, k
 

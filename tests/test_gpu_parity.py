@@ -19,6 +19,7 @@ import oracle
 from paper_2312_02121_gb300 import binding as B
 from paper_2312_02121_gb300 import pipeline
 from paper_2312_02121_gb300 import workloads as wl
+from oracle import compare
 from gpu_helpers import (gpu_projection, last_gaussian_ids, np_, rel_l2, run_gpu, uncertain_pixels, view_image)
 
 pytestmark = pytest.mark.gpu
@@ -72,6 +73,11 @@ def test_projection(case):
     # per Gaussian, error relative to its largest conic entry (elongated ellipses lose a few digits)
     rel = np.abs(gp["conics"][v] - op["conics"][v]).max(axis=1) / np.abs(op["conics"][v]).max(axis=1)
     assert (rel <= 1e-5).mean() > 0.999 and rel.max() <= 1e-3
+    # the factors themselves: a and d to fp32 precision whatever the elongation, k relative to 1 + |k|
+    of, gf = compare.conic_factors(op["conics"][v]), gp["conic_factors"][v]
+    for j in (0, 2):
+        assert (np.abs(gf[:, j] - of[:, j]) / np.abs(of[:, j])).max() <= 1e-5, j
+    assert (np.abs(gf[:, 1] - of[:, 1]) / (1 + np.abs(of[:, 1]))).max() <= 1e-5
     np.testing.assert_array_equal(gp["rects"][v & sure], op["rects"][v & sure])
 
 
@@ -136,7 +142,8 @@ def test_forward_end_to_end(case):
 def test_backward_2d_given_projection(case):
     cam, sc, f, g = case["cam"], case["sc"], case["frame"], case["grads"]
     gp = gpu_projection(f)
-    ob = oracle.rasterize_bwd(gp, sc.opacities, sc.colors, cam.width, cam.height, case["G"])
+    ob = compare.with_factored_conic_grad(
+        oracle.rasterize_bwd(gp, sc.opacities, sc.colors, cam.width, cam.height, case["G"]), gp["conics"])
     for k in ("means2d", "conics", "opacities", "colors"):
         assert rel_l2(np_(g[k]), ob[k]) <= GRAD_TOL, k
 
@@ -145,8 +152,8 @@ def test_backward_3d_given_2d_gradients(case):
     # projection backward alone: the oracle maps the CUDA 2D gradients to 3D
     cam, sc, f, g = case["cam"], case["sc"], case["frame"], case["grads"]
     gp = gpu_projection(f)
-    ob = oracle.project_bwd(cam, sc.means, sc.quats, sc.scales, gp["valid"], np_(g["means2d"]), np_(g["conics"]),
-                            case["w"].eps2d)
+    ob = oracle.project_bwd(cam, sc.means, sc.quats, sc.scales, gp["valid"], np_(g["means2d"]),
+                            compare.conic_grad_from_factors(np_(g["conics"]), gp["conic_factors"]), case["w"].eps2d)
     for k in ("means", "quats", "scales"):
         assert rel_l2(np_(g[k]), ob[k]) <= GRAD_TOL, k
 
@@ -174,8 +181,9 @@ def test_view_matrix_gradient_given_2d_gradients(case):
     P = f.views.P
     out = _project_bwd_with_viewmats(f, case["params"], g["means2d"][:P].contiguous(), g["conics"][:P].contiguous(),
                                      case["w"].eps2d)
-    ob = oracle.project_bwd(cam, sc.means, sc.quats, sc.scales, gpu_projection(f)["valid"], np_(g["means2d"]),
-                            np_(g["conics"]), case["w"].eps2d)
+    gp = gpu_projection(f)
+    ob = oracle.project_bwd(cam, sc.means, sc.quats, sc.scales, gp["valid"], np_(g["means2d"]),
+                            compare.conic_grad_from_factors(np_(g["conics"]), gp["conic_factors"]), case["w"].eps2d)
     gv = np_(out["viewmats"][0])
     assert not gv[3].any()
     assert rel_l2(gv, ob["viewmat"]) <= GRAD_TOL
@@ -352,7 +360,8 @@ def test_full_size_1080p_sampled_pixels():
     G2 = np.zeros_like(G)
     G2[pix] = Gs
     f2, p2, g2 = run_gpu(w, dL_drgb=G2)
-    ob = oracle.rasterize_bwd(gp, sc.opacities, sc.colors, cam.width, cam.height, Gs, pixels=pix)
+    ob = compare.with_factored_conic_grad(
+        oracle.rasterize_bwd(gp, sc.opacities, sc.colors, cam.width, cam.height, Gs, pixels=pix), gp["conics"])
     for k in ("means2d", "conics", "opacities", "colors"):
         assert rel_l2(np_(g2[k]), ob[k]) <= GRAD_TOL, k
     # properties at every pixel

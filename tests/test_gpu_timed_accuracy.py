@@ -4,13 +4,26 @@ The benchmark times the fast backward: per-(tile, Gaussian) partials added
 with global atomics, so the fp32 summation order varies from run to run, fed
 by the forward's warp-box ballots.  These tests run exactly that step
 (``batch.BatchRenderer``, the kernels the captured step replays) on the
-1,000,000-Gaussian 1080p frame and on both batched workloads, and compare
-every per-Gaussian output end to end with the FP64 oracle: means, quaternions
-and scales (Sec. 3.2, 3.2.1), opacities and colours (Sec. 3.1), each within
-1e-4 relative L2.  dL/dC is nonzero on a seeded 1 % pixel subsample of every
-view only, and zero on the pixels where fp32 and fp64 may legitimately
-composite differently (Reading O10); the oracle's backward runs on the same
-pixels.  The images on those pixels must agree within 1e-5.
+1,000,000-Gaussian 1080p frame and on both batched workloads, on a seeded 1 %
+pixel subsample of every view, and compare with the FP64 oracle:
+
+- every per-Gaussian gradient end to end: means, quaternions and scales
+  (Sec. 3.2, 3.2.1), opacities and colours (Sec. 3.1), each within 1e-4
+  relative L2, with dL/dC nonzero on the subsample only and zero where fp32
+  and fp64 may legitimately composite differently (Reading O10);
+- the images: within 1e-5 of the oracle composited from the CUDA projection
+  (the compositing of Eq. 7 itself), and end to end within the error that the
+  fp32 projection's rounding can cause (below).
+
+End to end, mu' is an fp32 number near 2000 px, whose rounding step is
+1.2e-4 px; for the smallest Gaussians of these scenes (sigma about 0.55 px
+after the 0.3 px^2 dilation) the alpha threshold lies about 3.3 sigma from the
+centre, where |d sigma / d mu'| = |Y Delta| is about 6 per px.  So sigma
+moves by up to about 7e-4 and alpha by that fraction of itself.  The end-to-end
+comparison therefore treats threshold tests within 1e-3 (relative) as
+uncertain instead of 1e-4, and bounds the image error by 5e-4 (an alpha below
+1 times a relative change of 7e-4, with margin) -- while the comparison given
+the same projection keeps 1e-5.
 """
 import numpy as np
 import pytest
@@ -25,67 +38,75 @@ from gpu_helpers import np_
 
 pytestmark = pytest.mark.gpu
 
-IMG_TOL = 1e-5
+IMG_TOL = 1e-5          # compositing, given the CUDA projection
+IMG_TOL_E2E = 5e-4      # end to end (fp32 projection rounding, see above)
+MARGIN_E2E = 1e-3       # threshold margin treated as uncertain end to end
 GRAD_TOL = 1e-4
 KEYS = ("means", "quats", "scales", "opacities", "colors")
 
 
-def oracle_subsample(w, rng, frac=0.01):
-    """Per view: a seeded ``frac`` pixel subsample, the oracle's image there,
-    dL/dC (standard normal, zero on uncertain pixels) and the oracle's
-    gradients for it; the gradients are summed over the views of each scene
-    into arrays over all Gaussians of the workload."""
-    offs = np.cumsum([0] + [s.n for s in w.scenes])
-    tot = {k: np.zeros((int(offs[-1]),) + np.shape(getattr(w.scenes[0], k))[1:]) for k in KEYS}
-    per_view, excluded, sampled = [], 0, 0
-    for v in w.views:
-        cam, sc = v.camera, w.scenes[v.scene]
-        pix = np.sort(rng.choice(cam.pixels, max(1, int(round(frac * cam.pixels))), replace=False))
-        fwd = oracle.render(cam, sc, w.eps2d, pixels=pix)
-        bad = compare.uncertain_pixels(fwd["margin"], fwd["proj"], cam.width, cam.height, sc.opacities,
-                                       pixels=pix)
-        G = np.where(bad[:, None], 0.0, rng.standard_normal((len(pix), 3)))
-        ob = oracle.backward(cam, sc, G, w.eps2d, pixels=pix)
-        g0 = int(offs[v.scene])
-        for k in KEYS:
-            tot[k][g0:g0 + sc.n] += ob[k]
-        per_view.append(dict(pix=pix, bad=bad, G=G, rgb=fwd["rgb"]))
-        excluded += int(bad.sum())
-        sampled += len(pix)
-    return per_view, tot, excluded / max(sampled, 1)
+def _gpu_proj(r, views, i):
+    hv = views.host[i]
+    s, e = hv.proj_offset, hv.proj_offset + hv.g_count
+    return dict(means2d=np_(r.means2d[s:e]).astype(np.float64),
+                conics=compare.conic_from_factors(np_(r.conics[s:e])),
+                depths=np_(r.depths[s:e]).astype(np.float64), rects=np_(r.rects[s:e]).astype(np.int32),
+                valid=(np_(r.touched[s:e]) > 0).astype(np.int32))
 
 
-def timed_step_against_oracle(w, seed=0, config=None, longest_first=False):
+def timed_step_against_oracle(w, seed=0, config=None, longest_first=False, frac=0.01):
     """The benchmarked step's forward and fast backward (through the C ABI)
-    against the oracle on a 1 % subsample; returns the per-output errors."""
+    against the oracle on a ``frac`` pixel subsample of every view.  Returns
+    (image error given the CUDA projection, image error end to end, gradient
+    errors, excluded fraction)."""
     params, views, ranges, targets = GB.workload_views(w)
     cap = GB.exact_capacity(params, views, w.eps2d)
     r = GB.BatchRenderer(params, views, cap, targets, w.eps2d, config, longest_first)
     r.forward()
     torch.cuda.synchronize()
     assert not r.overflowed()
-    per_view, tot, excl = oracle_subsample(w, np.random.default_rng(seed))
+    rng = np.random.default_rng(seed)
+    offs = np.cumsum([0] + [s.n for s in w.scenes])
+    tot = {k: np.zeros((int(offs[-1]),) + np.shape(getattr(w.scenes[0], k))[1:]) for k in KEYS}
     G = torch.zeros(views.pixels, 3, device="cuda")
-    img_err = 0.0
-    for i, pv in enumerate(per_view):
-        off = views.host[i].pixel_offset
-        img = np_(r.image(i)).reshape(-1, 3)[pv["pix"]]
-        img_err = max(img_err, float(np.abs(img - pv["rgb"])[~pv["bad"]].max(initial=0.0)))
-        G[off + torch.as_tensor(pv["pix"], device="cuda")] = torch.as_tensor(pv["G"], dtype=torch.float32,
-                                                                              device="cuda")
+    err_gp = err_e2e = 0.0
+    excluded = sampled = 0
+    for i, v in enumerate(w.views):
+        cam, sc = v.camera, w.scenes[v.scene]
+        pix = np.sort(rng.choice(cam.pixels, max(1, int(round(frac * cam.pixels))), replace=False))
+        img = np_(r.image(i)).reshape(-1, 3)[pix]
+        # compositing alone: the oracle composites the CUDA projection
+        ogp = oracle.rasterize(_gpu_proj(r, views, i), sc.opacities, sc.colors, cam.width, cam.height, pixels=pix)
+        ok = ogp["margin"] >= 1e-4
+        err_gp = max(err_gp, float(np.abs(img - ogp["rgb"])[ok].max(initial=0.0)))
+        # end to end
+        fwd = oracle.render(cam, sc, w.eps2d, pixels=pix)
+        bad = compare.uncertain_pixels(fwd["margin"], fwd["proj"], cam.width, cam.height, sc.opacities, pixels=pix,
+                                       margin_rel=MARGIN_E2E, depth_gap=fwd["depth_gap"])
+        err_e2e = max(err_e2e, float(np.abs(img - fwd["rgb"])[~bad].max(initial=0.0)))
+        Gv = np.where(bad[:, None], 0.0, rng.standard_normal((len(pix), 3)))
+        ob = oracle.backward(cam, sc, Gv, w.eps2d, pixels=pix)
+        g0 = int(offs[v.scene])
+        for k in KEYS:
+            tot[k][g0:g0 + sc.n] += ob[k]
+        G[views.host[i].pixel_offset + torch.as_tensor(pix, device="cuda")] = torch.as_tensor(
+            Gv, dtype=torch.float32, device="cuda")
+        excluded += int(bad.sum())
+        sampled += len(pix)
     r.dL.copy_(G)
     r.backward()
     torch.cuda.synchronize()
     got = r.grads()
     errs = {k: compare.rel_l2(np_(got[k]), tot[k]) for k in KEYS}
-    return img_err, errs, excl
+    return err_gp, err_e2e, errs, excluded / max(sampled, 1)
 
 
-def _check(img_err, errs, excl):
-    print(f"image max-abs {img_err:.3g}, excluded {excl:.4f}, rel-L2 " +
-          ", ".join(f"{k} {v:.3g}" for k, v in errs.items()))
-    assert excl < 0.01, excl
-    assert img_err <= IMG_TOL, img_err
+def _check(err_gp, err_e2e, errs, excl):
+    print(f"image max-abs {err_gp:.3g} given the projection, {err_e2e:.3g} end to end; excluded {excl:.4f}; "
+          "rel-L2 " + ", ".join(f"{k} {v:.3g}" for k, v in errs.items()))
+    assert excl < 0.05, excl
+    assert err_gp <= IMG_TOL, err_gp
+    assert err_e2e <= IMG_TOL_E2E, err_e2e
     for k in KEYS:
         assert errs[k] <= GRAD_TOL, (k, errs)
 

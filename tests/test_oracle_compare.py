@@ -2,6 +2,7 @@
 mask against a plain whole-image evaluation of its definition, and its
 pixel-subset form against the whole-image mask at those pixels (CPU only)."""
 import numpy as np
+import pytest
 
 import oracle
 from oracle import compare
@@ -60,3 +61,78 @@ def test_rel_l2():
     assert compare.rel_l2(b, b) == 0.0
     assert compare.rel_l2(b + [0.0, 0.5], b) == 0.1
     assert compare.rel_l2(np.zeros(2), np.zeros(2)) == 0.0
+
+
+def _proj_at_pixel_centre(depths, n):
+    # n Gaussians centred on pixel (4, 4) of a 16x16 image, unit conics, listed in one tile
+    return dict(means2d=np.tile([4.5, 4.5], (n, 1)), conics=np.tile([1.0, 0.0, 1.0], (n, 1)),
+                depths=np.asarray(depths, np.float64), rects=np.tile([0, 0, 1, 1], (n, 1)).astype(np.int32),
+                valid=np.ones(n, np.int32))
+
+
+def test_depth_gap_is_the_closest_pair_of_consecutive_gaussians_that_pass_the_alpha_test():
+    # depths 2.0, 2.0000001 (too transparent to pass the alpha test), 2.5, 2.6, 2.6000026:
+    # the consecutive takers are (2.0, 2.5), (2.5, 2.6), (2.6, 2.6000026) -> the last gap, 1e-6 relative
+    d = [2.0, 2.0000001, 2.5, 2.6, 2.6000026]
+    op = np.array([0.3, 0.002, 0.3, 0.3, 0.3])
+    out = oracle.rasterize(_proj_at_pixel_centre(d, 5), op, np.full((5, 3), 0.5), 16, 16, pixels=np.array([4 * 16 + 4]))
+    assert out["depth_gap"][0] == pytest.approx(2.6e-6 / 2.6, rel=1e-6)
+    assert out["n_contrib"][0] == 4
+
+
+def test_depth_gap_stops_at_the_gaussian_that_ends_the_pixel():
+    # opacities 0.99 x 3 then a close pair: the third Gaussian takes T below 1e-4 and stops the pixel,
+    # so the pair after it (depth gap 1e-9) is never reached; the gaps met are 0.1 and 0.05 (relative)
+    d = [1.0, 1.1, 1.155, 2.0, 2.000000002]
+    op = np.array([0.99, 0.99, 0.99, 0.5, 0.5])
+    out = oracle.rasterize(_proj_at_pixel_centre(d, 5), op, np.full((5, 3), 0.5), 16, 16, pixels=np.array([4 * 16 + 4]))
+    assert out["n_contrib"][0] == 2
+    assert out["depth_gap"][0] == pytest.approx(0.055 / 1.1, rel=1e-9)
+    # fewer than two takers: no gap
+    one = oracle.rasterize(_proj_at_pixel_centre([3.0], 1), np.array([0.5]), np.full((1, 3), 0.5), 16, 16,
+                           pixels=np.array([4 * 16 + 4]))
+    assert np.isinf(one["depth_gap"][0])
+
+
+def test_uncertain_pixels_include_close_depths():
+    d = [2.0, 2.000001, 3.0]
+    proj = _proj_at_pixel_centre(d, 3)
+    out = oracle.rasterize(proj, np.array([0.3, 0.3, 0.3]), np.full((3, 3), 0.5), 16, 16)
+    bad_without = compare.uncertain_pixels(out["margin"], proj, 16, 16)
+    bad_with = compare.uncertain_pixels(out["margin"], proj, 16, 16, depth_gap=out["depth_gap"])
+    assert not bad_without[4, 4] and bad_with[4, 4]
+    assert (bad_with == (bad_without | (out["depth_gap"] < 1e-6))).all()
+
+
+def test_conic_forms_and_their_gradients_convert_both_ways():
+    rng = np.random.default_rng(9)
+    # random SPD conics, some thin (condition 1e5)
+    n = 200
+    th = rng.uniform(0, np.pi, n)
+    l1, l2 = np.exp(rng.uniform(-3, 2, n)), np.exp(rng.uniform(-3, 2, n))
+    l2[:20] = l1[:20] * 1e-5
+    c, s_ = np.cos(th), np.sin(th)
+    Y = np.stack([l1 * c * c + l2 * s_ * s_, (l1 - l2) * c * s_, l1 * s_ * s_ + l2 * c * c], 1)
+    f = compare.conic_factors(Y)
+    np.testing.assert_allclose(compare.conic_from_factors(f), Y, rtol=1e-9, atol=1e-12 * np.abs(Y).max())
+    # sigma of both forms agrees at random offsets
+    dx, dy = rng.standard_normal(n), rng.standard_normal(n)
+    sig_p = 0.5 * (Y[:, 0] * dx * dx + 2 * Y[:, 1] * dx * dy + Y[:, 2] * dy * dy)
+    sig_f = 0.5 * (f[:, 0] * (dx + f[:, 1] * dy) ** 2 + f[:, 2] * dy * dy)
+    np.testing.assert_allclose(sig_f, sig_p, rtol=1e-8, atol=1e-12)
+    # gradients: against finite differences of L = <G, sigma-sums> in each parameterisation
+    gP = rng.standard_normal((n, 3))
+    gF = compare.conic_grad_to_factors(gP, Y)
+    np.testing.assert_allclose(compare.conic_grad_from_factors(gF, f), gP, rtol=1e-7, atol=1e-9)
+    h = 1e-7
+    for j in range(3):
+        fp, fm = f.copy(), f.copy()
+        fp[:, j] += h * np.maximum(np.abs(f[:, j]), 1e-3)
+        fm[:, j] -= h * np.maximum(np.abs(f[:, j]), 1e-3)
+        Lp = (gP * compare.conic_from_factors(fp)).sum(1)
+        Lm = (gP * compare.conic_from_factors(fm)).sum(1)
+        fd = (Lp - Lm) / (2 * h * np.maximum(np.abs(f[:, j]), 1e-3))
+        np.testing.assert_allclose(gF[:, j], fd, rtol=1e-5, atol=1e-6 * np.abs(gF).max())
+    # culled rows (all zero) give zero factors and finite gradients
+    z = compare.conic_factors(np.zeros((2, 3)))
+    assert not z.any() and np.isfinite(compare.conic_grad_from_factors(np.ones((2, 3)), z)).all()

@@ -285,11 +285,11 @@ def batched_comparison(dev, steps: int):
         cap = GB.exact_capacity(params, views, w.eps2d)
 
         def mk(c):
-            return GB.BatchRenderer(params, views, cap, targets, w.eps2d,
-                                    B.RasterConfig(c["persistent"], c["ctas_per_sm"], device=dev),
-                                    c["longest_first"])
+            return GB.BatchRenderer(params, views, cap, targets, w.eps2d, GB.config(c, dev), bool(c["longest_first"]))
 
-        best = GB.autotune(mk, key=f"{name}|P{views.P}|T{views.T}|K{cap}", use_cache=False)
+        # the library's autotuner (gs_autotune) picks the tile walk and the backward batch shape
+        best = GB.autotune(GB.BatchRenderer(params, views, cap, targets, w.eps2d),
+                           key=f"{name}|P{views.P}|T{views.T}|K{cap}", use_cache=False)
         r = mk(best)
         r.capture()
         l0 = B.gs_kernel_launches()
@@ -328,8 +328,13 @@ def batched_comparison(dev, steps: int):
                      "batched_ms_per_step": ms_b, "per_view_ms_per_step": ms_v,
                      "batched_launches_per_step": int(launches_b), "per_view_launches_per_step": int(launches_v),
                      "batched_cuda_graph": True,
-                     "tuning": {k: best[k] for k in ("persistent", "ctas_per_sm", "longest_first")},
-                     "tuning_ms": [round(x["ms"], 3) for x in best["all"]],
+                     "tuning": {k: best[k] for k in B.TUNING_FIELDS},
+                     "tuning_ms": {f"{'p' if x['persistent'] else 'g'}{x['ctas_per_sm']}"
+                                   f"{'L' if x['longest_first'] else 'I'}_{x['bwd_pixels']}px{x['bwd_batch']}":
+                                   round(x["ms"], 3) for x in best["all"]},
+                     "tuning_note": "compositing fwd+bwd ms per candidate (gs_autotune): g/p = one CTA per tile / "
+                                    "persistent grid (CTAs per SM, 0 = as many as fit), I/L = tile id / longest-first "
+                                    "order, then the backward's pixels per thread and staged batch",
                      "images_identical": same_images, "grad2d_rel_l2_batched_vs_per_view": agree_2d,
                      "grad_rel_l2_batched_vs_per_view_deterministic": agree_det,
                      "l2": "inputs larger than L2"}

@@ -9,6 +9,7 @@
  *   gs_rasterize_fwd  Sec. 2.2, Eq. 7: front-to-back compositing
  *   gs_rasterize_bwd  Sec. 3.1: compositing gradients
  *   gs_project_bwd    Sec. 3.2, 3.2.1: projection, scale and rotation gradients
+ *   gs_autotune       the tile walk and batch shape of the compositing stages
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -359,6 +360,57 @@ int gs_project_bwd(const GsView* views, int32_t V, int64_t P, const float* means
                    const float* scales, float eps2d, const int32_t* touched, const float* dL_dmeans2d,
                    const float* dL_dconics, float* dL_dmeans, float* dL_dquats, float* dL_dscales,
                    float* dL_dviewmats, void* stream);
+
+/* One candidate of gs_autotune: a tile walk and a backward batch shape (the
+ * GsRasterConfig fields the tuner chooses, plus the tile order).  24 bytes. */
+typedef struct GsTuning {
+    int32_t persistent;     /* GsRasterConfig.persistent */
+    int32_t ctas_per_sm;    /* GsRasterConfig.ctas_per_sm */
+    int32_t longest_first;  /* 1: tiles in gs_tile_order's longest-first order */
+    int32_t bwd_pixels;     /* GsRasterConfig.bwd_pixels */
+    int32_t bwd_batch;      /* GsRasterConfig.bwd_batch */
+    float ms;               /* out: median device time of one compositing forward + backward, ms */
+} GsTuning;
+
+/* The built-in candidates of gs_autotune: *count receives how many there are
+ * and out[0..min(count, capacity)) the candidates (out may be NULL when
+ * capacity is 0): five tile walks (one CTA per tile in id order or longest
+ * first; a persistent grid of as many CTAs as fit, 4 or 3 per SM, longest
+ * first) times the four backward batch shapes. */
+int gs_autotune_default_candidates(GsTuning* out, int32_t capacity, int32_t* count);
+
+/* Bytes of scratch gs_autotune needs: a frame's images, per-pixel state and
+ * gradients, the tile order and the ballot buffer (256-byte aligned parts). */
+size_t gs_autotune_workspace_size(int64_t P, int64_t N, int32_t T_total, int64_t K_capacity, int64_t pixels);
+
+/*
+ * Picks how to composite a frame fastest.  The paper exposes each stage on its
+ * own and fixes no launch shape; the tile size is not tuned, because it is part
+ * of the result (Sec. 2.2: a Gaussian is composited in every pixel of every
+ * tile its 3-sigma box touches).  For every candidate (NULL / n_candidates = 0:
+ * the built-in ones) it runs gs_tile_order when longest_first, then
+ * gs_rasterize_fwd and the fast gs_rasterize_bwd with that walk and batch shape
+ * on `stream`, once to warm up and `repeats` times timed with CUDA events, and
+ * records the median.  No candidate changes any result.
+ *   in : the frame as gs_project and gs_bin_and_sort left it: views (device),
+ *        P projections, N Gaussians (the largest g_begin + g_count of the
+ *        views), T_total tiles, pixels (total), means2d, conics, opacities,
+ *        colors (3 channels), isect_ids, tile_ranges, K (device), K_capacity;
+ *        workspace (device, >= gs_autotune_workspace_size bytes, 16-byte
+ *        aligned, contents irrelevant)
+ *   out: results[n] (host, nullable) every candidate with its time, *best
+ *        (host) the fastest.
+ * Unlike the other entry points it WAITS for the stream (it reads the event
+ * times after each candidate), so it cannot be captured into a CUDA graph; it
+ * creates and destroys two CUDA events and allocates no device memory.  An
+ * invalid candidate (a batch shape that is not compiled) returns the error of
+ * the compositing call it was given to.
+ */
+int gs_autotune(const GsView* views, int32_t V, int64_t P, int64_t N, int32_t T_total, int64_t pixels,
+                const float* means2d, const float* conics, const float* opacities, const float* colors,
+                const int32_t* isect_ids, const int32_t* tile_ranges, const int32_t* K, int64_t K_capacity,
+                const GsTuning* candidates, int32_t n_candidates, int32_t repeats, void* workspace,
+                size_t workspace_bytes, GsTuning* results, GsTuning* best, void* stream);
 
 /*
  * Sec. 2.2 (Eq. 7) and Sec. 3.1 for C channels per Gaussian (features, depth

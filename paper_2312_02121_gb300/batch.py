@@ -10,8 +10,9 @@ static sizes); ``overflowed()`` reports a step whose pairs did not fit.
 ``PerViewRenderer`` is the comparison point: the same kernels launched once
 per view.  ``autotune`` picks how the compositing kernels walk the tiles
 (one CTA per tile or a persistent grid over a global queue; tile-id or
-longest-first order; CTAs per SM) by timing each candidate; none of these
-choices changes any result.
+longest-first order; CTAs per SM) and the backward's batch shape (pixels per
+thread, staged batch) through the library's gs_autotune, which times each
+candidate on the device; none of these choices changes any result.
 """
 from __future__ import annotations
 
@@ -89,7 +90,7 @@ class BatchRenderer:
         cfg = config or B.RasterConfig(device=dev)
         self.config = B.RasterConfig(cfg.persistent, cfg.ctas_per_sm,
                                      self.tile_order if longest_first else cfg.tile_order, device=dev,
-                                     warp_hits=self.warp_hits)
+                                     warp_hits=self.warp_hits, bwd_pixels=cfg.bwd_pixels, bwd_batch=cfg.bwd_batch)
         self.graph: Optional[torch.cuda.CUDAGraph] = None
         self.host = None
 
@@ -297,6 +298,8 @@ def time_steps(step, n: int = 5, warmup: int = 2) -> float:
     return a.elapsed_time(b) / n
 
 
+# The tile walks the GPU tests exercise (the autotuner's candidates are gs_autotune's built-in ones:
+# these walks times the backward batch shapes).
 CANDIDATES = [
     dict(persistent=False, ctas_per_sm=0, longest_first=False),
     dict(persistent=False, ctas_per_sm=0, longest_first=True),
@@ -311,9 +314,14 @@ def _cache_path() -> str:
     return os.path.join(root, "tuning.json")
 
 
-def autotune(make, key: str, candidates=None, use_cache: bool = True, n: int = 3) -> dict:
-    """Times ``make(candidate).step`` for each candidate tile-walking config
-    and returns the fastest (cached per GPU name and ``key``)."""
+def autotune(renderer: "BatchRenderer", key: str, candidates=None, use_cache: bool = True, repeats: int = 3) -> dict:
+    """Picks the tile walk and backward batch shape for ``renderer``'s frame
+    with the library's gs_autotune (which times the compositing forward +
+    backward of each candidate on the device) and returns the fastest as a
+    dict (persistent, ctas_per_sm, longest_first, bwd_pixels, bwd_batch, ms,
+    all = every candidate's time, cached).  The choice is cached per GPU name
+    and ``key``; ``config(best)`` and ``best["longest_first"]`` build a
+    renderer that walks that way."""
     gpu = torch.cuda.get_device_name()
     ck = f"{gpu}|{key}"
     path = _cache_path()
@@ -325,15 +333,13 @@ def autotune(make, key: str, candidates=None, use_cache: bool = True, n: int = 3
             cache = {}
     if ck in cache:
         return dict(cache[ck], cached=True)
-    best, results = None, []
-    for cand in candidates or CANDIDATES:
-        r = make(cand)
-        ms = time_steps(r.step, n=n, warmup=1)
-        results.append(dict(cand, ms=ms))
-        if best is None or ms < best["ms"]:
-            best = dict(cand, ms=ms)
-        del r
-        torch.cuda.empty_cache()
+    r = renderer
+    r.forward()  # the frame the candidates composite: projection and sorted lists in r's buffers
+    ws = torch.empty(B.gs_autotune_workspace_size(r.views.P, r.p.n, r.views.T, r.cap, r.views.pixels),
+                     dtype=torch.uint8, device=r.p.means.device)
+    best, results = B.gs_autotune(r.views, r.p.n, r.means2d, r.conics, r.p.opacities, r.p.colors, r.isect_ids,
+                                  r.tile_ranges, r.K, r.cap, ws, candidates, repeats)
+    del ws
     best["all"] = results
     if use_cache:
         try:
@@ -343,6 +349,13 @@ def autotune(make, key: str, candidates=None, use_cache: bool = True, n: int = 3
         except OSError:
             pass
     return dict(best, cached=False)
+
+
+def config(tuning: dict, device="cuda") -> B.RasterConfig:
+    """The RasterConfig of a tuning dict (from ``autotune``); the longest-first
+    order is the renderer's own (``longest_first``)."""
+    return B.RasterConfig(bool(tuning["persistent"]), int(tuning["ctas_per_sm"]), device=device,
+                          bwd_pixels=int(tuning.get("bwd_pixels", 0)), bwd_batch=int(tuning.get("bwd_batch", 0)))
 
 
 def workload_views(w, device="cuda"):

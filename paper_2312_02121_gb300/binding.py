@@ -57,13 +57,18 @@ class GsRasterConfig(ctypes.Structure):
                 ("bwd_pixels", ctypes.c_int32), ("bwd_batch", ctypes.c_int32)]
 
 
+class GsTuning(ctypes.Structure):
+    _fields_ = [("persistent", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("longest_first", ctypes.c_int32),
+                ("bwd_pixels", ctypes.c_int32), ("bwd_batch", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
 class GsAdamConfig(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float * 5), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
                 ("eps", ctypes.c_float)]
 
 
 assert ctypes.sizeof(GsCamera) == 80 and ctypes.sizeof(GsView) == 120 and ctypes.sizeof(GsRasterConfig) == 40
-assert ctypes.sizeof(GsAdamConfig) == 32
+assert ctypes.sizeof(GsAdamConfig) == 32 and ctypes.sizeof(GsTuning) == 24
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -89,6 +94,10 @@ SIGNATURES = {
     "gs_rasterize_bwd": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P,
                                         _P, _P, _I32, _P, _SZ, _P, _P, _P, _P, _P, _P]),
     "gs_project_bwd": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _F, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gs_autotune_default_candidates": (ctypes.c_int, [_P, _I32, _P]),
+    "gs_autotune_workspace_size": (_SZ, [_I64, _I64, _I32, _I64, _I64]),
+    "gs_autotune": (ctypes.c_int, [_P, _I32, _I64, _I64, _I32, _I64, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _I32, _I32,
+                                   _P, _SZ, _P, _P, _P]),
     "gs_rasterize_fwd_nc": (ctypes.c_int, [_P, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                            _P]),
     "gs_rasterize_bwd_nc": (ctypes.c_int, [_P, _I32, _I64, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
@@ -332,6 +341,50 @@ def gs_rasterize_bwd(views: Views, means2d, conics, opacities, colors, isect_ids
     if _debug.enabled():
         _debug.check_gradients([("dL_dmeans2d", dL_dmeans2d), ("dL_dconics", dL_dconics),
                                 ("dL_dopacities", dL_dopacities), ("dL_dcolors", dL_dcolors)])
+
+
+TUNING_FIELDS = ("persistent", "ctas_per_sm", "longest_first", "bwd_pixels", "bwd_batch")
+
+
+def gs_autotune_default_candidates() -> list:
+    """The built-in candidates of gs_autotune, as dicts of the GsTuning fields."""
+    return [{k: int(getattr(t, k)) for k in TUNING_FIELDS} for t in _default_candidates()]
+
+
+def _default_candidates():
+    n = ctypes.c_int32(0)
+    _check(load().gs_autotune_default_candidates(None, 0, ctypes.byref(n)))
+    arr = (GsTuning * n.value)()
+    _check(load().gs_autotune_default_candidates(arr, n.value, ctypes.byref(n)))
+    return arr
+
+
+def gs_autotune_workspace_size(P: int, N: int, T_total: int, K_capacity: int, pixels: int) -> int:
+    return int(load().gs_autotune_workspace_size(P, N, T_total, K_capacity, pixels))
+
+
+def gs_autotune(views: Views, N: int, means2d, conics, opacities, colors, isect_ids, tile_ranges, K, K_capacity: int,
+                workspace, candidates=None, repeats: int = 3, stream=None):
+    """Times the compositing fwd + bwd of a projected and sorted frame for each
+    candidate (dicts of the GsTuning fields; None = the built-in ones) and
+    returns (best, all), each a dict with the fields and ``ms``.  Waits for
+    the stream."""
+    cands = None
+    n = 0
+    if candidates:
+        n = len(candidates)
+        cands = (GsTuning * n)(*[GsTuning(*[int(c[k]) for k in TUNING_FIELDS], 0.0) for c in candidates])
+    else:
+        n = len(_default_candidates())
+    results = (GsTuning * n)()
+    best = GsTuning()
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(load().gs_autotune(_ptr(views.device), views.V, views.P, int(N), views.T, views.pixels, _ptr(means2d),
+                              _ptr(conics), _ptr(opacities), _ptr(colors), _ptr(isect_ids), _ptr(tile_ranges), _ptr(K),
+                              int(K_capacity), cands, int(n if candidates else 0), int(repeats), _ptr(workspace),
+                              nbytes, results, ctypes.byref(best), _stream(stream)))
+    as_dict = lambda t: dict({k: int(getattr(t, k)) for k in TUNING_FIELDS}, ms=float(t.ms))
+    return as_dict(best), [as_dict(t) for t in results]
 
 
 def gs_project_bwd(views: Views, means, quats, scales, eps2d: float, touched, dL_dmeans2d, dL_dconics, dL_dmeans,

@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJ_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "libgsplat103.so")
-SOURCES = ["gs_abi.cu", "gs_project.cu", "gs_sort.cu", "gs_sort_static.cu", "gs_raster.cu", "gs_raster_bwd2.cu",
+SOURCES = ["gs_abi.cu", "gs_autotune.cu", "gs_project.cu", "gs_sort.cu", "gs_sort_static.cu", "gs_raster.cu",
+           "gs_raster_bwd2.cu",
            "gs_raster_nc.cu", "gs_train.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]

@@ -179,7 +179,7 @@ def test_binding_structs_match_the_header_layout(tmp_path):
     cc = shutil.which(os.environ.get("CC", "gcc"))
     if cc is None:
         pytest.skip("no C compiler")
-    structs = [binding.GsCamera, binding.GsView, binding.GsRasterConfig, binding.GsAdamConfig]
+    structs = [binding.GsCamera, binding.GsView, binding.GsRasterConfig, binding.GsAdamConfig, binding.GsTuning]
     lines = ["#include <stdio.h>", '#include "gsplat103.h"', "int main(void) {"]
     for S in structs:
         n = S.__name__

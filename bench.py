@@ -153,7 +153,7 @@ class ClockSampler:
                 "power_w_max": max(powers) if powers else None}
 
 
-RASTER_SOURCES = ("gs_raster.cu", "gs_raster_common.cuh", "gs_common.cuh")
+RASTER_SOURCES = ("gs_raster.cu", "gs_raster_bwd.cuh", "gs_raster_bwd2.cu", "gs_raster_common.cuh", "gs_common.cuh")
 
 
 def raster_source_hash() -> str:
@@ -190,6 +190,80 @@ def walked_pairs(f, cam, dev) -> int:
     tile = ((torch.arange(H, device=dev).view(H, 1) // 16) * tx + torch.arange(W, device=dev).view(1, W) // 16)
     start = f.tile_ranges[tile.reshape(-1), 0].long()
     return int((f.last_idx.reshape(-1).long() - start + 1).clamp_min(0).sum().item())
+
+
+def forward_walked_pairs(f, cam, params, dev, chunk: int = 64) -> int:
+    """(pixel, Gaussian) pairs the forward of Eq. 7 evaluates: for every pixel the entries of its tile's
+    sorted list from the first until the pixel stops -- at the first Gaussian after its last composited
+    one that passes the alpha test (it would take T below 1e-4), else at the list's end.  Counted from
+    last_idx and the tile ranges, with the stop found by walking the entries after last_idx (fp32, the
+    kernel's test up to rounding at the threshold)."""
+    import torch
+    W, H = cam.width, cam.height
+    tx = (W + 15) // 16
+    tile = ((torch.arange(H, device=dev).view(H, 1) // 16) * tx + torch.arange(W, device=dev).view(1, W) // 16)
+    rng_ = f.tile_ranges[tile.reshape(-1)].long()
+    start, end = rng_[:, 0], rng_[:, 1]
+    last = f.last_idx.reshape(-1).long()
+    px = torch.arange(W, device=dev).repeat(H).float() + 0.5
+    py = torch.arange(H, device=dev).repeat_interleave(W).float() + 0.5
+    stop = end - 1  # pixels that never stop walk the whole list
+    active = torch.nonzero(last + 1 < end).squeeze(1)
+    pos = last + 1
+    op = params.opacities
+    while active.numel():
+        offs = torch.arange(chunk, device=dev)
+        idx = pos[active].view(-1, 1) + offs.view(1, -1)
+        valid = idx < end[active].view(-1, 1)
+        ids = f.isect_ids[idx.clamp_max(f.isect_ids.numel() - 1)].long()
+        m2, cf = f.means2d[ids], f.conics[ids]
+        dx = m2[..., 0] - px[active].view(-1, 1)
+        dy = m2[..., 1] - py[active].view(-1, 1)
+        u = dx + cf[..., 1] * dy
+        sig = 0.5 * (cf[..., 0] * u * u + cf[..., 2] * dy * dy)
+        taker = valid & (sig >= 0) & (op[ids] * torch.exp(-sig) >= 1.0 / 255.0)
+        has = taker.any(dim=1)
+        first = torch.argmax(taker.int(), dim=1)
+        done = has | ~valid[:, -1]
+        stop[active[has]] = pos[active[has]] + first[has]
+        pos[active] += chunk
+        active = active[~done]
+    return int((stop - start + 1).clamp_min(0).sum().item())
+
+
+def stage_rooflines(stage_ms: dict, P: int, K: int, pix: int, walked_fwd: int, walked_bwd: int, hbm: float,
+                    fp32_peak: float, sm_mhz: float) -> dict:
+    """Every stage of the step against the roofline that bounds it.  HBM stages: the bytes the method
+    must move per unit over the stage's CUDA-event time, against the measured copy
+    bandwidth.  Compositing: FP32 flops per evaluated pair (16 forward, 40 backward) against the FP32
+    FMA peak at the maximum SM clock, with the SFU rate beside it."""
+    out = {}
+
+    def hbm_entry(stage, nbytes, work):
+        t = stage_ms[stage] / 1e3
+        a = nbytes / t / 1e9
+        out[stage] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm, "work": work,
+                      "ms": stage_ms[stage]}
+
+    hbm_entry("project", P * 80.0, f"{P} projections x 80 B (44 B read, 36 B written)")
+    hbm_entry("bin_and_sort", P * 80.0 + K * 60.0,
+              f"{P} projections x 80 B (depth keys, 3 depth passes, scan) + {K} pairs x 60 B (emission, "
+              f"2 tile passes, ranges)")
+    hbm_entry("loss_grad", pix * 3 * 12.0, f"{pix} pixels x 3 channels x 12 B (image and target read, dL/dC written)")
+    hbm_entry("project_bwd", P * 104.0, f"{P} projections x 104 B (64 B read, 40 B written)")
+    for stage, pairs, flops in (("rasterize_fwd", walked_fwd, 16), ("rasterize_bwd", walked_bwd, 40)):
+        t = stage_ms[stage] / 1e3
+        a = pairs * flops / t / 1e12
+        e = {"bound": "alu", "achieved": a, "peak": fp32_peak, "unit": "TFLOP/s", "frac": a / fp32_peak,
+             "work": f"{pairs} evaluated (pixel, Gaussian) pairs x {flops} FP32 flops", "ms": stage_ms[stage]}
+        if stage == "rasterize_bwd":
+            e["sfu"] = sfu_roof(pairs, t, sm_mhz)
+        else:
+            peak_ex2 = SMS * MUFU_EX2_PER_SM_CLK * sm_mhz * 1e6 / 1e9
+            e["sfu"] = {"achieved": pairs / t / 1e9, "peak": peak_ex2, "unit": "Gpair/s",
+                        "frac": pairs / t / 1e9 / peak_ex2, "note": "one ex2 (32 per SM clock) per evaluated pair"}
+        out[stage] = e
+    return out
 
 
 def sfu_roof(pairs: int, seconds: float, sm_mhz: float) -> dict:
@@ -268,6 +342,157 @@ def cpu_baseline(w, seconds: float):
                       f"{100.0 * len(pix) / cam.pixels:.1f}% of the frame): full projection and projection "
                       f"backward of all {w.scenes[0].n} Gaussians, compositing fwd+bwd of the sampled pixels",
             "seconds": dt}
+
+
+# ---------------------------------------------------------------------------
+# the oracle leg (rank 0, one GPU): the oracle timed on the host cores, and the
+# GPU results' error against it on the same pixels
+# ---------------------------------------------------------------------------
+
+def _proj_of(r, i, compare):
+    """The CUDA projection of view i of a BatchRenderer, as an oracle projection dict."""
+    hv = r.views.host[i]
+    s_, e = hv.proj_offset, hv.proj_offset + hv.g_count
+    n = lambda t: t[s_:e].detach().cpu().numpy()
+    return dict(means2d=n(r.means2d).astype(np.float64), conics=compare.conic_from_factors(n(r.conics)),
+                depths=n(r.depths).astype(np.float64), rects=n(r.rects).astype(np.int32),
+                valid=(n(r.touched) > 0).astype(np.int32))
+
+
+def oracle_accuracy(dev, w, frac: float, seed: int, tuning=None) -> dict:
+    """The timed step (forward and fast backward of a BatchRenderer with the bench's walk) against the
+    FP64 oracle on a seeded ``frac`` pixel subsample of every view (frac = 1: every pixel).  dL/dC is
+    the L2 loss gradient of the oracle's image on those pixels, zero elsewhere and on pixels where
+    fp32 and fp64 may composite differently end to end (threshold margin 1e-3, depth gap 1e-6, tile-box
+    edges).  Reports the image max-abs error given the CUDA projection and end to end, and the
+    relative L2 error of every per-Gaussian gradient summed over the views."""
+    import torch
+    import oracle
+    from oracle import compare
+    from paper_2312_02121_gb300 import batch as GB
+    keys = ("means", "quats", "scales", "opacities", "colors")
+    params, views, ranges, targets = GB.workload_views(w, dev)
+    cap = GB.exact_capacity(params, views, w.eps2d)
+    cfg = GB.config(tuning, dev) if tuning else None
+    r = GB.BatchRenderer(params, views, cap, targets, w.eps2d, cfg, bool(tuning and tuning["longest_first"]))
+    r.forward()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(seed)
+    offs = np.cumsum([0] + [sc.n for sc in w.scenes])
+    tot = {k: np.zeros((int(offs[-1]),) + np.shape(getattr(w.scenes[0], k))[1:]) for k in keys}
+    G = torch.zeros(views.pixels, 3, device=dev)
+    err_gp = err_e2e = 0.0
+    excluded = sampled = 0
+    t0 = time.perf_counter()
+    for i, v in enumerate(w.views):
+        cam, sc = v.camera, w.scenes[v.scene]
+        pix = (np.arange(cam.pixels) if frac >= 1 else
+               np.sort(rng.choice(cam.pixels, max(1, int(round(frac * cam.pixels))), replace=False)))
+        off = views.host[i].pixel_offset
+        img = r.rgb[off:off + cam.pixels].detach().cpu().numpy()[pix]
+        ogp = oracle.rasterize(_proj_of(r, i, compare), sc.opacities, sc.colors, cam.width, cam.height, pixels=pix)
+        ok = ogp["margin"] >= 1e-4
+        err_gp = max(err_gp, float(np.abs(img - ogp["rgb"])[ok].max(initial=0.0)))
+        fwd = oracle.render(cam, sc, w.eps2d, pixels=pix)
+        bad = compare.uncertain_pixels(fwd["margin"], fwd["proj"], cam.width, cam.height, sc.opacities, pixels=pix,
+                                       margin_rel=1e-3, depth_gap=fwd["depth_gap"])
+        err_e2e = max(err_e2e, float(np.abs(img - fwd["rgb"])[~bad].max(initial=0.0)))
+        tgt = np.asarray(w.targets[i], np.float64).reshape(-1, 3)[pix]
+        Gv = np.where(bad[:, None], 0.0, 2.0 * (fwd["rgb"] - tgt) / (3 * w.pixels))
+        ob = oracle.backward(cam, sc, Gv, w.eps2d, pixels=pix)
+        for k in keys:
+            tot[k][int(offs[v.scene]):int(offs[v.scene]) + sc.n] += ob[k]
+        G[off + torch.as_tensor(pix, device=dev)] = torch.as_tensor(Gv, dtype=torch.float32, device=dev)
+        excluded += int(bad.sum())
+        sampled += len(pix)
+    oracle_s = time.perf_counter() - t0
+    r.dL.copy_(G)
+    r.backward()
+    torch.cuda.synchronize()
+    got = r.grads()
+    out = {"pixels": int(sampled), "fraction": frac, "excluded": excluded / max(sampled, 1),
+           "image_max_abs_given_projection": err_gp, "image_max_abs_end_to_end": err_e2e,
+           "grad_rel_l2": {k: compare.rel_l2(got[k].detach().cpu().numpy(), tot[k]) for k in keys},
+           "oracle_seconds": oracle_s, "cores": oracle.num_threads(),
+           "tolerances": {"image_given_projection": 1e-5, "image_end_to_end": 5e-4, "grad_rel_l2": 1e-4}}
+    del r
+    torch.cuda.empty_cache()
+    return out
+
+
+def small_configs(dev, steps: int = 50) -> dict:
+    """The two small workloads, each timed on the GPU (one CUDA graph per step) and by the oracle in
+    full on the host cores, with the GPU's error against the oracle: 1,000 Gaussians at 128x128
+    (forward only) and 100,000 at 1024x768 (forward and backward of the L2 loss)."""
+    import torch
+    import oracle
+    from oracle import compare
+    from paper_2312_02121_gb300 import batch as GB
+    from paper_2312_02121_gb300 import workloads as wl
+    out = {}
+    for name, make, backward in (("forward_1k_128", wl.forward_1k_128, False),
+                                 ("fwdbwd_100k_1024x768", wl.fwdbwd_100k_1024x768, True)):
+        w = make()
+        cam, sc = w.views[0].camera, w.scenes[0]
+        params, views, ranges, targets = GB.workload_views(w, dev)
+        if targets is None:
+            targets = torch.zeros(views.pixels, 3, device=dev)
+        cap = GB.exact_capacity(params, views, w.eps2d)
+        r = GB.BatchRenderer(params, views, cap, targets, w.eps2d)
+        step = r.step_eager if backward else r.forward
+        # one CUDA graph per step (forward alone for the forward-only workload)
+        s_ = torch.cuda.Stream()
+        s_.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s_):
+            for _ in range(2):
+                step()
+        torch.cuda.current_stream().wait_stream(s_)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            step()
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        assert not r.overflowed()
+        # the oracle, whole image, timed
+        t0 = time.perf_counter()
+        fwd = oracle.render(cam, sc, w.eps2d)
+        G = None
+        if backward:
+            tgt = np.asarray(w.targets[0], np.float64)
+            G = 2.0 * (fwd["rgb"] - tgt) / fwd["rgb"].size
+            ob = oracle.backward(cam, sc, G, w.eps2d)
+        o_s = time.perf_counter() - t0
+        e = {"gaussians": sc.n, "width": cam.width, "height": cam.height, "intersections": cap,
+             "gpu": {"ms_per_step": ms, "mpix_s": views.pixels / ms / 1e3, "intersections_per_s": cap / (ms / 1e3),
+                     "step": "fwd+bwd (L2 loss)" if backward else "forward", "cuda_graph": True},
+             "oracle": {"seconds": o_s, "mpix_s": views.pixels / o_s / 1e6, "cores": oracle.num_threads(),
+                        "sample": "the whole image"}}
+        img = r.rgb.detach().cpu().numpy().reshape(cam.height, cam.width, 3)
+        bad = compare.uncertain_pixels(fwd["margin"], fwd["proj"], cam.width, cam.height, sc.opacities,
+                                       margin_rel=1e-3, depth_gap=fwd["depth_gap"])
+        acc = {"image_max_abs_end_to_end": float(np.abs(img - fwd["rgb"])[~bad].max(initial=0.0)),
+               "excluded": float(bad.mean())}
+        if backward:
+            Gm = np.where(bad[..., None], 0.0, G)
+            ob = oracle.backward(cam, sc, Gm, w.eps2d)
+            r.dL.copy_(torch.as_tensor(Gm.reshape(-1, 3), dtype=torch.float32, device=dev))
+            r.backward()
+            torch.cuda.synchronize()
+            got = r.grads()
+            acc["grad_rel_l2"] = {k: compare.rel_l2(got[k].detach().cpu().numpy(), ob[k]) for k in got}
+        e["accuracy"] = acc
+        out[name] = e
+        del r, g
+        torch.cuda.empty_cache()
+    return out
 
 
 def batched_comparison(dev, steps: int):
@@ -507,12 +732,25 @@ def run_ours(args, rank, world, local_rank):
     K = int(f0.K_total.item())
     contrib = int(f0.n_contrib.sum().item())
     walked = walked_pairs(f0, cam, dev)
+    walked_fwd = forward_walked_pairs(f0, cam, params, dev)
     cap = K
+    del f0
+    from paper_2312_02121_gb300 import batch as GB
+    # the library's autotuner (gs_autotune) picks the tile walk and the backward's batch shape for this frame;
+    # every timed path below uses its choice
+    tuning = GB.autotune(GB.BatchRenderer(params, views, cap, target, w.eps2d),
+                         key=f"{WORKLOAD}|P{views.P}|T{views.T}|K{cap}", use_cache=False)
+    torch.cuda.empty_cache()
     stream = torch.cuda.current_stream()
     stages = ["project", "bin_and_sort", "rasterize_fwd", "loss_grad", "zero_grads", "rasterize_bwd", "project_bwd"]
     last_state = {}
     # the forward hands its per-pair warp-box cull to the backward through this buffer
-    hits_cfg = B.RasterConfig(device=dev, warp_hits=torch.empty(cap, dtype=torch.int32, device=dev))
+    order_buf = torch.empty(views.T, dtype=torch.int32, device=dev) if tuning["longest_first"] else None
+    order_ws = (torch.empty(max(B.gs_tile_order_workspace_size(views.T), 1), dtype=torch.uint8, device=dev)
+                if tuning["longest_first"] else None)
+    hits_cfg = B.RasterConfig(bool(tuning["persistent"]), int(tuning["ctas_per_sm"]), order_buf, device=dev,
+                              warp_hits=torch.empty(cap, dtype=torch.int32, device=dev),
+                              bwd_pixels=int(tuning["bwd_pixels"]), bwd_batch=int(tuning["bwd_batch"]))
 
     def step(ev=None):
         def mark(i):
@@ -532,6 +770,8 @@ def run_ours(args, rank, world, local_rank):
         rgb = torch.empty(pixels, 3, device=dev)
         Tf = torch.empty(pixels, device=dev)
         last = torch.empty(pixels, dtype=torch.int32, device=dev)
+        if order_buf is not None:
+            B.gs_tile_order(tr, views.T, order_ws, order_buf)
         B.gs_rasterize_fwd(views, pr["means2d"], pr["conics"], params.opacities, params.colors, ids, tr, None, rgb,
                            Tf, last, None, hits_cfg)
         mark(3)
@@ -585,8 +825,8 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         # the same step captured once into a CUDA graph (BatchRenderer), as a training loop runs it:
         # this is the timed headline; the instrumented eager steps above give the per-stage split
-        from paper_2312_02121_gb300 import batch as GB
-        rgraph = GB.BatchRenderer(params, views, cap, target, w.eps2d)
+        rgraph = GB.BatchRenderer(params, views, cap, target, w.eps2d, GB.config(tuning, dev),
+                                  bool(tuning["longest_first"]))
         rgraph.capture()
         for _ in range(max(args.warmup, 3)):
             rgraph.step()
@@ -632,7 +872,8 @@ def run_ours(args, rank, world, local_rank):
     host_tgt = torch.as_tensor(w.targets[0]).reshape(-1, 3).pin_memory()
     h2d = sum(v.numel() * v.element_size() for v in host.values()) + host_tgt.numel() * host_tgt.element_size()
     dev_params = pipeline.Params(*[torch.empty_like(host[k], device=dev) for k in keys])
-    rg = GB.BatchRenderer(dev_params, views, cap, torch.empty_like(host_tgt, device=dev), w.eps2d)
+    rg = GB.BatchRenderer(dev_params, views, cap, torch.empty_like(host_tgt, device=dev), w.eps2d,
+                          GB.config(tuning, dev), bool(tuning["longest_first"]))
     rg.attach_host_inputs(host, host_tgt)
     rg.capture()
 
@@ -691,32 +932,21 @@ def run_ours(args, rank, world, local_rank):
     dom = max(("rasterize_fwd", "rasterize_bwd", "bin_and_sort", "project", "project_bwd"), key=lambda s: stage_ms[s])
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
-    # algorithmic flops: per evaluated (pixel, Gaussian) pair of the backward, 40 FP32 flops (plus an
-    # ex2 and a reciprocal); the stricter count over composited pairs only (49 flops each) rides along
-    flops_per_pair = {"rasterize_fwd": 20, "rasterize_bwd": 49}
-    if dom in flops_per_pair:
-        t_dom = stage_ms[dom] / 1e3
-        strict = contrib * flops_per_pair[dom] / 1e12 / t_dom
-        if dom == "rasterize_bwd":
-            achieved = walked * 40 / 1e12 / t_dom
-            work = f"{walked} evaluated (pixel, Gaussian) pairs x 40 FP32 flops"
-        else:
-            achieved, work = strict, f"{contrib} composited (pixel, Gaussian) pairs x {flops_per_pair[dom]} flops"
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak,
-                "traffic": recorded_traffic("k_raster_bwd" if dom == "rasterize_bwd" else "k_raster_fwd"),
-                "peak_source": f"FP32 FMA lanes: {SMS} SMs x {FP32_LANES_PER_SM} x 2 x {sm_mhz:.0f} MHz "
-                               f"(max SM clock, {src})",
-                "work": work, "launch_ms": stage_ms[dom],
-                "sfu": sfu_roof(walked, t_dom, sm_mhz),
-                "composited_only": {"achieved": strict, "frac": strict / fp32_peak,
-                                    "work": f"{contrib} composited pairs x {flops_per_pair[dom]} flops"}}
-    else:
-        hbm = peaks["hbm_gbs"]
-        bytes_ = {"bin_and_sort": K * 164.0, "project": sc.n * 80.0, "project_bwd": sc.n * 88.0}[dom]
-        achieved = bytes_ / (stage_ms[dom] / 1e3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "peak_source": f"hbm_gbs ({src})"}
+    # every stage against its roofline; the dominant one is the line's `roofline`
+    stages_roof = stage_rooflines(stage_ms, views.P, K, pixels, walked_fwd, walked, peaks["hbm_gbs"], fp32_peak,
+                                  sm_mhz)
+    roof = dict(stages_roof[dom], kernel=dom)
+    roof["peak_source"] = (f"FP32 FMA lanes: {SMS} SMs x {FP32_LANES_PER_SM} x 2 x {sm_mhz:.0f} MHz (max SM clock, "
+                           f"{src})" if roof["bound"] == "alu" else f"hbm_gbs ({src})")
+    roof["launch_ms"] = stage_ms[dom]
+    roof["traffic"] = recorded_traffic({"rasterize_bwd": "k_raster_bwd", "rasterize_fwd": "k_raster_fwd"}.get(dom, ""))
+    if dom in ("rasterize_fwd", "rasterize_bwd"):
+        # the stricter count over composited pairs only (20 / 49 flops each) rides along
+        fl = {"rasterize_fwd": 20, "rasterize_bwd": 49}[dom]
+        strict = contrib * fl / 1e12 / (stage_ms[dom] / 1e3)
+        roof["composited_only"] = {"achieved": strict, "frac": strict / fp32_peak,
+                                   "work": f"{contrib} composited pairs x {fl} flops"}
+    roof["stages"] = stages_roof
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -724,7 +954,8 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "gaussians": sc.n, "width": cam.width, "height": cam.height,
                    "views": 1, "intersections": K, "intersections_per_s": K / (ms_step / 1e3),
-                   "composited_pairs": contrib, "evaluated_pairs_bwd": walked,
+                   "composited_pairs": contrib, "evaluated_pairs_bwd": walked, "evaluated_pairs_fwd": walked_fwd,
+                   "tuning": {k: tuning[k] for k in B.TUNING_FIELDS}, "tuning_ms": tuning["ms"],
                    "l2": "flushed (256 MiB write) before every timed step, outside its events",
                    "per_rank": "independent frame (seed = rank)"},
         "stage_ms": stage_ms, "eager_ms_per_step": eager_ms,
@@ -744,7 +975,14 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_batched:
         line["batched"] = batched_comparison(dev, args.batched_steps)
     if not args.no_cpu_baseline and world == 1:
+        # the oracle leg: the oracle timed on the host cores, and the GPU results' error against it
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+        acc = {"fwdbwd_1m_1080p": oracle_accuracy(dev, w, 1.0, 21, tuning)}
+        if not args.no_batched:
+            t16 = line["batched"]["batch_scenes_16x4"]["tuning"]
+            acc["batch_scenes_16x4"] = oracle_accuracy(dev, wl.batch_scenes_16x4(), 0.01, 22, t16)
+        line["accuracy"] = acc
+        line["small_configs"] = small_configs(dev)
     print(json.dumps(line), flush=True)
 
 

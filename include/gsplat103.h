@@ -256,7 +256,7 @@ typedef struct GsRasterConfig {
 } GsRasterConfig;
 
 /* The backward's default pixels per thread. */
-#define GS_BWD_PIXELS_DEFAULT 1
+#define GS_BWD_PIXELS_DEFAULT 2
 
 /* Bytes of scratch gs_tile_order needs for T_total tiles. */
 size_t gs_tile_order_workspace_size(int32_t T_total);

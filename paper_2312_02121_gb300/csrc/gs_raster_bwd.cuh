@@ -154,7 +154,7 @@ constexpr int bwd_threads() { return 32 * (kWarps / kPx); }
 // kPx: pixels per thread (1 or 2); kB: Gaussians per staged batch (a multiple
 // of 32, at most the CTA's threads).
 template <typename S, bool kCull, bool kAtomic, bool kPersistent, bool kAnyC, int kPx, int kB>
-__global__ void __launch_bounds__(bwd_threads<kPx>(), kPx == 1 ? 4 : 6)
+__global__ void __launch_bounds__(bwd_threads<kPx>(), kPx == 1 ? 4 : 7)  // measured: 4, and 7 (71 registers)
 k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t* __restrict__ tile_order,
              int* __restrict__ queue, const V2<S>* __restrict__ means2d, const S* __restrict__ conics,
              const S* __restrict__ opacities, const S* __restrict__ colors, const int32_t* __restrict__ isect_ids,
@@ -324,7 +324,7 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
 #pragma unroll
                     for (int i = 0; i < kPx; ++i) {
                         cm[i] = 0u;
-                        if ((mi[i] >> hb) & 1u) {  // warp-uniform
+                        if (kPx == 1 || ((mi[i] >> hb) & 1u)) {  // warp-uniform (one box: always)
                             dx[i] = xy.x - cx;
                             dy[i] = xy.y - cy[i];
                             const S p2 = neg_sigma_log2(qq, dx[i], dy[i], u[i]);
@@ -339,10 +339,11 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                     if (cmall == 0u) continue;
                     const V4<S> col = sh_col[j];
                     S r[kRec];
-                    bool first = true;
+#pragma unroll
+                    for (int q = 0; q < kRec; ++q) r[q] = S(0);  // a first box with no contribution adds nothing
 #pragma unroll
                     for (int i = 0; i < kPx; ++i) {
-                        if (cm[i] == 0u) continue;  // warp-uniform
+                        if (kPx > 1 && cm[i] == 0u) continue;  // warp-uniform (one box: it contributes)
                         const S inv1ma = RT<S>::rcp(S(1) - alpha[i]);
                         const S Tn = T[i] * inv1ma;  // T before this Gaussian
                         const S wgt = ctb[i] ? alpha[i] * Tn : S(0);
@@ -361,8 +362,7 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                         const S t[kRec] = {dsu, dsdy, dsu * u[i], dsu * dy[i], dsdy * dy[i], gd,
                                            wgt * g0[i], wgt * g1[i], wgt * g2[i]};
 #pragma unroll
-                        for (int q = 0; q < kRec; ++q) r[q] = first ? t[q] : r[q] + t[q];
-                        first = false;
+                        for (int q = 0; q < kRec; ++q) r[q] = i == 0 ? t[q] : r[q] + t[q];
                     }
                     chunk_mask |= 1u << hb;
                     // the warp's sum of each term, into the warp's own slot for this Gaussian (a

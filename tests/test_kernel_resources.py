@@ -1,7 +1,7 @@
 """ptxas resources of the kernels a fwd+bwd step times (compiled here, no GPU):
 the compositing kernels stay within the register budget their launch bounds
 give (6 CTAs of 256 threads per SM for the forward, 4 of 256 for the
-one-pixel backward, 6 of 128 for the two-pixel one), the backward does not
+one-pixel backward, 7 of 128 for the two-pixel one), the backward does not
 spill, and no timed kernel spills more than it does today.
 A kernel edit that breaks one of these changes its speed before its results."""
 import pytest
@@ -36,7 +36,7 @@ def test_timed_kernels_keep_their_register_budget_and_spills(rows):
     timed = [
         ("gs::k_raster_fwd<float, true, false, false, false>", 65536 // (256 * 6), 8),
         ("gs::k_raster_bwd<float, true, true, false, false, 1, 96>", 65536 // (256 * 4), 0),
-        ("gs::k_raster_bwd<float, true, true, false, false, 2, 64>", 65536 // (128 * 6), 0),
+        ("gs::k_raster_bwd<float, true, true, false, false, 2, 64>", 65536 // (128 * 7), 0),
         ("gs::k_project_fwd<float>", 255, 0),
         ("gs::k_project_bwd<float>", 65536 // (256 * 4), 16),
         ("gs::k_emit", 255, 0),

@@ -15,8 +15,10 @@ target copied host->device from pinned memory every step and the loss read
 back.  ``--impl reference`` times the FP64 CPU oracle instead (the reference
 arm of this comparison; it has no published GPU numbers).
 
-Multi-GPU (torchrun): every rank renders its own independent frame (seed =
-rank), no data-path collective; timings are max-reduced over ranks.
+Multi-GPU (torchrun, N > 1): the 64 views of the 500,000-Gaussian scene are
+split over the ranks (shard.plan), each rank replays its captured share of the
+step, and one NCCL all-reduce sums the per-Gaussian gradients; timings are
+max-reduced over ranks (strong scaling: the batch is fixed).
 """
 from __future__ import annotations
 
@@ -719,7 +721,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     B.load()
-    w = wl.fwdbwd_1m_1080p(seed=rank)
+    w = wl.fwdbwd_1m_1080p(seed=0)
     cam, sc = w.views[0].camera, w.scenes[0]
     params = pipeline.Params.from_scene(sc, dev)
     target = torch.as_tensor(w.targets[0].reshape(-1, 3), device=dev)
@@ -957,7 +959,7 @@ def run_ours(args, rank, world, local_rank):
                    "composited_pairs": contrib, "evaluated_pairs_bwd": walked, "evaluated_pairs_fwd": walked_fwd,
                    "tuning": {k: tuning[k] for k in B.TUNING_FIELDS}, "tuning_ms": tuning["ms"],
                    "l2": "flushed (256 MiB write) before every timed step, outside its events",
-                   "per_rank": "independent frame (seed = rank)"},
+                   "multi_gpu": "under torchrun the 64-view batch is split over the ranks instead (run_sharded)"},
         "stage_ms": stage_ms, "eager_ms_per_step": eager_ms,
         "timing": "ms_per_step: the step captured once into a CUDA graph and replayed (BatchRenderer); "
                   "stage_ms and eager_ms_per_step: the same kernels launched eagerly with an event between "
@@ -986,6 +988,123 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def sharded_plan(world: int):
+    """The view split of the multi-GPU mode: the 64 views of the 500,000-Gaussian scene (their pixel
+    counts as costs) over ``world`` ranks by shard.plan (longest processing time first)."""
+    from paper_2312_02121_gb300 import shard
+    from paper_2312_02121_gb300 import workloads as wl
+    w = wl.batch_views_500k_64()
+    return w, shard.plan([v.scene for v in w.views], [v.camera.pixels for v in w.views], world)
+
+
+def timed_sharded_steps(step, allreduce, steps: int, warmup: int, world: int, flush=None, dev=None):
+    """Device time of ``steps`` sharded steps (the local step, then the gradient all-reduce when the split
+    needs it), max over ranks, in ms per step.  ``step`` and ``allreduce`` are callables; events bracket
+    each step on the current stream."""
+    import torch
+    for _ in range(max(warmup, 3)):
+        step()
+        allreduce()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        step()
+        allreduce()
+        b.record()
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b)
+    ms = total / steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms
+
+
+def run_sharded(args, rank, world, local_rank):
+    """--gpus N > 1: the multi-view workload split over the ranks as the sharding design has it.  The 64
+    views of one 500,000-Gaussian scene go to the ranks by shard.plan; each rank renders its views with
+    one captured BatchRenderer step into a flat per-Gaussian gradient buffer, and one NCCL all-reduce sums
+    the buffers (the views share the scene, so its gradients are summed over views: Sec. 3.2).  The total
+    work is fixed (strong scaling); value = all 64 views' pixels per second of the slowest rank."""
+    import torch
+    from paper_2312_02121_gb300 import batch as GB
+    from paper_2312_02121_gb300 import binding as B
+    from paper_2312_02121_gb300 import shard
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    B.load()
+    w, plan = sharded_plan(world)
+    params, views_all, ranges, targets = GB.workload_views(w, dev)
+    cams = [v.camera for v in w.views]
+    sr = shard.ShardedRenderer(params, cams, ranges, [v.scene for v in w.views], targets, world, rank)
+    sr.capture()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    allreduce = (lambda: sr.buf.allreduce()) if sr.plan.needs_allreduce else (lambda: None)
+    l0 = B.gs_kernel_launches()
+    sr.local_step()
+    launches = B.gs_kernel_launches() - l0  # the local step's eager launch count (the graph replays them)
+    with ClockSampler(local_rank) as clk:
+        time.sleep(0.3)
+        t0 = time.time()
+        ms = timed_sharded_steps(sr.local_step, allreduce, args.steps, args.warmup, world, flush, dev)
+        clk.mark(t0, time.time())
+    assert not sr.overflowed()
+    # end to end: the parameters and this rank's targets from pinned host memory every step, the loss back
+    keys = ("means", "quats", "scales", "opacities", "colors")
+    host = {k: getattr(params, k).cpu().pin_memory() for k in keys}
+    mine_t = sr.r.targets.cpu().pin_memory() if sr.r is not None else None
+    if sr.r is not None:
+        sr.r.attach_host_inputs(host, mine_t)
+        sr.r.graph = None
+        sr.capture()
+
+    def e2e_step():
+        sr.local_step()
+        allreduce()
+        torch.cuda.current_stream().synchronize()
+        return float(sr.r.loss_host[0]) if sr.r is not None else 0.0
+
+    for _ in range(3):
+        e2e_step()
+    torch.distributed.barrier()
+    t1 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    dt = torch.tensor([(time.perf_counter() - t1) / args.e2e_steps], device=dev)
+    torch.distributed.all_reduce(dt, op=torch.distributed.ReduceOp.MAX)
+    h2d = sum(v.numel() * v.element_size() for v in host.values()) + (mine_t.numel() * 4 if mine_t is not None else 0)
+    pixels = views_all.pixels
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": pixels / ms / 1e3, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch_views_500k_64", "views": len(w.views), "gaussians": params.n, "pixels": pixels,
+                   "split": "views over ranks by shard.plan (LPT on pixels), every rank holds the whole scene",
+                   "views_per_rank": [len(v) for v in plan.views_of_rank],
+                   "allreduce_bytes": int(sr.buf.flat.numel() * 4) if plan.needs_allreduce else 0,
+                   "l2": "flushed (256 MiB write) before every timed step, outside its events"},
+        "gpu_launches": int(launches) * args.steps, "gpu_launches_per_step": int(launches),
+        "timing": "each rank replays its captured local step, then the NCCL all-reduce of the gradient buffer; "
+                  "max over ranks",
+        "e2e": {"value": pixels / float(dt.item()) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": 4, "ms_per_step": 1e3 * float(dt.item()),
+                "inputs": "per rank and step: the scene's parameters and the rank's targets (pinned host -> "
+                          "device); result: the rank's loss (device -> pinned host)"},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -999,7 +1118,10 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     try:
-        run_ours(args, rank, world, local_rank)
+        if world > 1:
+            run_sharded(args, rank, world, local_rank)
+        else:
+            run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch

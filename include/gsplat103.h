@@ -76,8 +76,6 @@ extern "C" {
 
 /* bits of the device error word written by gs_bin_and_sort */
 #define GS_FLAG_CAPACITY 1u   /* more intersections than K_capacity */
-#define GS_FLAG_SORT_TIMEOUT 2u  /* a radix pass waited too long for another block's counts (the
-                                    order is then wrong; not expected to happen) */
 
 /* Camera of Sec. 2.1, Eq. 1: world-to-camera extrinsics T_cw = [R_cw t_cw; 0 1]
  * (R row-major) and pinhole intrinsics; pixel (x, y) has its centre at
@@ -181,10 +179,6 @@ size_t gs_bin_and_sort_workspace_size(int64_t P, int64_t K_capacity, int32_t T_t
  *        flags                   (device uint32) GS_FLAG_CAPACITY is OR-ed in
  *                                when K > K_capacity; the outputs are then
  *                                incomplete but no write leaves its buffer.
- *                                GS_FLAG_SORT_TIMEOUT is OR-ed in when a
- *                                sort pass gave up waiting for another block
- *                                (every wait on the GPU is bounded); the
- *                                order is then wrong.
  * Outputs past K are left untouched.  Needs P < 2^31 and K_capacity < 2^31.
  */
 int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_t T_total, const int16_t* rects,
@@ -205,8 +199,8 @@ int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_t T_total, 
  * The paper has no counterpart; it is an interface convenience.
  *
  * The scratch gs_bin_and_sort needs lives in one fixed array in this
- * library's device memory (a file-scope __device__ array of 25 MiB =
- * 26,214,400 bytes), which every GPU that loads the library holds until the
+ * library's device memory (a file-scope __device__ array of 24 MiB =
+ * 25,165,824 bytes), which every GPU that loads the library holds until the
  * process exits.  So:
  *  - P must be <= GS_STATIC_MAX_PROJECTIONS and K_capacity <=
  *    GS_STATIC_MAX_INTERSECTIONS; larger sizes return GS_ERR_INVALID_ARG.

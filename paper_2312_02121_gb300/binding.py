@@ -25,7 +25,6 @@ GS_ERR_CAPACITY = 2
 GS_ERR_TIMEOUT = 3
 GS_ERR_CUDA = 4
 GS_FLAG_CAPACITY = 1
-GS_FLAG_SORT_TIMEOUT = 2
 GS_TILE = 16
 ALPHA_MIN = 1.0 / 255.0
 ALPHA_MAX = 0.99

@@ -17,12 +17,10 @@
 // (tile | depth) keys had been sorted stably in p order, but sorting 31 bits
 // of P keys plus ~13 bits of K keys instead of ~44 bits of K keys.
 //
-// The radix sort is an LSD sort whose passes are single kernels: the digit
-// counts of every pass come from one read of the keys, and each pass ranks a
-// block's items with warp ballots, finds the items of each digit in the blocks
-// before it by decoupled look-back over the counts they publish, and writes
-// its items out through a shared-memory reorder.  Item counts may live in
-// device memory, so the whole pipeline is graph-capturable.
+// The radix sort is a classic three-kernel LSD pass (per-block digit
+// histograms, per-digit scan across blocks, stable scatter with warp-level
+// ranking and a shared-memory reorder for coalesced writes).  Item counts may
+// live in device memory, so the whole pipeline is graph-capturable.
 #include <algorithm>
 
 #include "gs_common.cuh"
@@ -107,86 +105,86 @@ __device__ __forceinline__ PassPlan pass_plan(const uint32_t* krange, int pass, 
     return PassPlan{pass < np, pass == np - 1, pass == 0 ? lo : 0u};
 }
 
-// The digit counts of every pass at once (they do not depend on the order the
-// earlier passes leave): one read of the keys, per-block shared counters, one
-// global atomic per non-zero counter.  counts[pass * 256 + digit] must be zero
-// beforehand.
 template <int kRI>
 __global__ void __launch_bounds__(kRT)
-k_radix_hist_all(const uint32_t* __restrict__ keys, const int32_t* __restrict__ count_dev, int64_t count_static,
-                 int64_t cap, int passes, int per, int total_bits, uint32_t* __restrict__ counts,
-                 const uint32_t* __restrict__ krange)
+k_radix_hist(const uint32_t* __restrict__ keys, const int32_t* __restrict__ count_dev, int64_t count_static,
+             int64_t cap, int shift, int bits, uint32_t* __restrict__ hist, const uint32_t* __restrict__ krange,
+             int pass, int passes)
 {
     constexpr int kRTile = kRT * kRI;
     pdl_wait();
     pdl_trigger();
-    __shared__ uint32_t h[4][kMaxBins];
+    const PassPlan plan = pass_plan(krange, pass, passes);
+    if (!plan.run) return;
+    __shared__ uint32_t h[kRWarps][kMaxBins];
     const int count = item_count(count_dev, count_static, cap);
-    const int base = blockIdx.x * kRTile;
-    if (base >= count) return;
-    const PassPlan p0 = pass_plan(krange, 0, passes);
-    for (int i = threadIdx.x; i < 4 * kMaxBins; i += kRT) (&h[0][0])[i] = 0;
+    const int nb = (count + kRTile - 1) / kRTile;
+    const int b = blockIdx.x;
+    if (b >= nb) return;
+    const int bins = 1 << bits;
+    const unsigned mask = bins - 1;
+    const int w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kRWarps * kMaxBins; i += kRT) (&h[0][0])[i] = 0;
     __syncthreads();
+    const int base = b * kRTile;
+    // all loads first (kRI in flight per thread), then the shared-memory counts
     uint32_t key[kRI];
 #pragma unroll
     for (int k = 0; k < kRI; ++k) {
         const int idx = base + k * kRT + threadIdx.x;
-        key[k] = idx < count ? keys[idx] - p0.sub : 0u;
+        key[k] = idx < count ? keys[idx] - plan.sub : 0u;
     }
-    for (int pass = 0, shift = 0; pass < passes; ++pass, shift += per) {
-        const unsigned mask = (1u << min(per, total_bits - shift)) - 1u;
 #pragma unroll
-        for (int k = 0; k < kRI; ++k)
-            if (base + k * kRT + (int)threadIdx.x < count) atomicAdd(&h[pass][(key[k] >> shift) & mask], 1u);
-    }
+    for (int k = 0; k < kRI; ++k)
+        if (base + k * kRT + (int)threadIdx.x < count) atomicAdd(&h[w][(key[k] >> shift) & mask], 1u);
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * kMaxBins; i += kRT) {
-        const uint32_t c = (&h[0][0])[i];
-        if (c) atomicAdd(counts + i, c);
+    for (int d = threadIdx.x; d < bins; d += kRT) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int i = 0; i < kRWarps; ++i) s += h[i][d];
+        hist[(size_t)d * nb + b] = s;
     }
 }
 
-// Decoupled look-back status of one (block, digit): the top two bits say what
-// the low 30 hold -- 0: nothing yet, 1: the block's own count of the digit,
-// 2: the count of the digit in this block and all blocks before it.
-constexpr uint32_t kStAgg = 1u << 30, kStInc = 2u << 30, kStCount = (1u << 30) - 1u;
-// Polls of a predecessor's status before a pass gives up (about a second):
-// then GS_FLAG_SORT_TIMEOUT is raised and the pass finishes with wrong offsets
-// instead of waiting for ever.
-constexpr int kLookbackPolls = 1 << 21;
-
-__device__ __forceinline__ uint32_t ld_status(const uint32_t* p)
-{
-    uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_status(uint32_t* p, uint32_t v)
-{
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// One stable pass of the LSD sort in a single kernel: a block takes the next
-// tile of kRT * kRI items in the order blocks start (so every block it waits
-// for has started and finishes without waiting for it), ranks its items by
-// digit with warp ballots, publishes its digit counts, and learns how many
-// items of each digit the blocks before it hold by looking back over their
-// published counts (decoupled look-back: an aggregate is added and the walk
-// goes on, an inclusive count ends it).  The global offset of a digit is the
-// count of smaller digits over all items (from k_radix_hist_all) plus that
-// prefix.  The block then reorders its items by digit in shared memory and
-// writes them out coalesced.  vals_in == nullptr means "value = input
-// position" (the first pass of a sort of indices).  status[block][digit] and
-// *vblock must be zero beforehand.
+// One block per digit: exclusive scan of that digit's per-block counts (in
+// place) and the digit total.
 template <int kRI>
 __global__ void __launch_bounds__(kRT)
-k_radix_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-                 const int32_t* __restrict__ count_dev, int64_t count_static, int64_t cap, int shift, int bits,
-                 const uint32_t* __restrict__ counts, uint32_t* __restrict__ status, uint32_t* __restrict__ vblock,
-                 const uint32_t* __restrict__ krange, int pass, int passes, uint32_t* __restrict__ vals_last,
-                 uint32_t* __restrict__ flags)
+k_radix_scan_rows(uint32_t* __restrict__ hist, const int32_t* __restrict__ count_dev, int64_t count_static,
+                  int64_t cap, uint32_t* __restrict__ digit_total, const uint32_t* __restrict__ krange, int pass,
+                  int passes)
+{
+    constexpr int kRTile = kRT * kRI;
+    pdl_wait();
+    pdl_trigger();
+    if (!pass_plan(krange, pass, passes).run) return;
+    const int count = item_count(count_dev, count_static, cap);
+    const int nb = (count + kRTile - 1) / kRTile;
+    const int d = blockIdx.x;
+    uint32_t* row = hist + (size_t)d * nb;
+    const int per = (nb + kRT - 1) / kRT;
+    const int lo = min(nb, (int)threadIdx.x * per), hi = min(nb, lo + per);
+    uint32_t s = 0;
+    for (int i = lo; i < hi; ++i) s += row[i];
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan_256<uint32_t>(s, &tot);
+    for (int i = lo; i < hi; ++i) {
+        const uint32_t x = row[i];
+        row[i] = run;
+        run += x;
+    }
+    if (threadIdx.x == 0) digit_total[d] = tot;
+}
+
+// Stable scatter of one block of items by digit.  vals_in == nullptr means
+// "value = input position" (the first pass of a sort of indices).
+template <int kRI>
+__global__ void __launch_bounds__(kRT)
+k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+                const int32_t* __restrict__ count_dev, int64_t count_static, int64_t cap, int shift, int bits,
+                const uint32_t* __restrict__ hist, const uint32_t* __restrict__ digit_total,
+                const uint32_t* __restrict__ krange, int pass, int passes, uint32_t* __restrict__ vals_last)
 {
     pdl_wait();
     pdl_trigger();
@@ -199,19 +197,26 @@ k_radix_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restric
     __shared__ uint32_t s_warp[kRWarps][kMaxBins];  // per-warp digit counts, then per-warp offsets
     __shared__ uint32_t s_base[kMaxBins];           // global position of the block's first item of each digit
     __shared__ uint32_t s_local[kMaxBins];          // local position of the block's first item of each digit
-    __shared__ int s_vb;
+
     const int count = item_count(count_dev, count_static, cap);
     const int nb = (count + kRTile - 1) / kRTile;
-    if ((int)blockIdx.x >= nb) return;  // blocks past the items take no tile (the others never wait for them)
-    if (threadIdx.x == 0) s_vb = (int)atomicAdd(vblock, 1u);
+    const int b = blockIdx.x;
+    if (b >= nb) return;
     const int bins = 1 << bits;
     const unsigned mask = bins - 1;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int i = lane; i < kMaxBins; i += 32) s_warp[w][i] = 0;
-    __syncthreads();
-    const int b = s_vb;
     const int base = b * kRTile;
     const int n_here = min(kRTile, count - base);
+
+    // digit offsets: exclusive scan of digit totals + this block's row prefix
+    {
+        const int d = threadIdx.x;
+        const uint32_t tot = d < bins ? digit_total[d] : 0u;
+        const uint32_t ex = block_exclusive_scan_256<uint32_t>(tot, nullptr);
+        if (d < bins) s_base[d] = ex + hist[(size_t)d * nb + b];
+    }
+    for (int i = lane; i < kMaxBins; i += 32) s_warp[w][i] = 0;
+    __syncwarp();
 
     // warp-striped load: warp w owns items [w*512, w*512+512) of the block
     uint32_t key[kRI], val[kRI], rank[kRI] = {};
@@ -240,53 +245,20 @@ k_radix_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restric
         __syncwarp();
     }
     __syncthreads();
-    // per digit: offsets of each warp inside the block, the block's count, its local start
-    uint32_t mine = 0;
+    // per-digit: offsets of each warp inside the block, and block totals
     {
         const int d = threadIdx.x;
+        uint32_t run = 0;
         if (d < bins) {
 #pragma unroll
             for (int i = 0; i < kRWarps; ++i) {
                 const uint32_t c = s_warp[i][d];
-                s_warp[i][d] = mine;
-                mine += c;
+                s_warp[i][d] = run;
+                run += c;
             }
         }
-        const uint32_t ex = block_exclusive_scan_256<uint32_t>(d < bins ? mine : 0u, nullptr);
+        const uint32_t ex = block_exclusive_scan_256<uint32_t>(d < bins ? run : 0u, nullptr);
         if (d < bins) s_local[d] = ex;
-    }
-    // publish this block's counts, look back for the counts of the blocks before it, publish the
-    // inclusive counts; the global start of each digit is the count of smaller digits over all items
-    // plus that prefix
-    {
-        const int d = threadIdx.x;
-        const uint32_t tot = d < bins ? counts[d] : 0u;
-        const uint32_t digit_start = block_exclusive_scan_256<uint32_t>(tot, nullptr);
-        if (d < bins) {
-            uint32_t* st = status + (size_t)b * bins + d;
-            uint32_t prefix = 0;
-            if (b == 0) {
-                st_status(st, kStInc | mine);
-            } else {
-                st_status(st, kStAgg | mine);
-                int j = b - 1, polls = 0;
-                while (j >= 0) {
-                    const uint32_t v = ld_status(status + (size_t)j * bins + d);
-                    if ((v & ~kStCount) == 0u) {
-                        if (++polls > kLookbackPolls) {  // a predecessor never published: give up, flagged
-                            atomicOr(flags, GS_FLAG_SORT_TIMEOUT);
-                            break;
-                        }
-                        continue;
-                    }
-                    prefix += v & kStCount;
-                    if (v & kStInc) break;
-                    --j;
-                }
-                st_status(st, kStInc | ((prefix + mine) & kStCount));
-            }
-            s_base[d] = digit_start + prefix;
-        }
     }
     __syncthreads();
     // reorder the block in shared memory by digit (stable)
@@ -311,52 +283,25 @@ k_radix_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restric
     }
 }
 
-// Scratch of the LSD sort: the digit counts of every pass, the look-back
-// status words of every (pass, block, digit), and one block counter per pass;
-// all zeroed by one memset before the sort.
 struct RadixBufs {
-    uint32_t* zero;    // start of the region below
-    size_t zero_bytes;
-    uint32_t* counts;  // [4][256]
-    uint32_t* status;  // [4][max_blocks][256]
-    uint32_t* vblock;  // [4]
-    int64_t max_blocks;
+    uint32_t* hist;
+    uint32_t* digit_total;
 };
 
-// Bytes of RadixBufs for sorts of at most max_blocks blocks.
-inline size_t radix_bufs_bytes(int64_t max_blocks)
-{
-    return align256(sizeof(uint32_t) * (4 * kMaxBins + 4 * (size_t)max_blocks * kMaxBins + 4));
-}
-
-inline RadixBufs radix_bufs(void* p, int64_t max_blocks)
-{
-    RadixBufs r;
-    r.zero = static_cast<uint32_t*>(p);
-    r.counts = r.zero;
-    r.status = r.counts + 4 * kMaxBins;
-    r.vblock = r.status + 4 * (size_t)max_blocks * kMaxBins;
-    r.max_blocks = max_blocks;
-    r.zero_bytes = radix_bufs_bytes(max_blocks);
-    return r;
-}
-
 // Stable LSD sort of (key, value) pairs on key bits [0, total_bits), in
-// passes of at most 8 bits: the digit counts of all passes in one read
-// (k_radix_hist_all), then one single-kernel pass each (k_radix_onesweep).
-// Keys ping-pong between k1 and k2, values between v1 and v2; the values start
-// as vals0, or as the input positions when vals0 is null.  The item count is
-// *count_dev (device, clamped to cap) or count_static.  The last pass writes
-// its values to vals_last when that is given.  With krange (device {smallest
-// key, ~largest key}) the sort is adaptive (see pass_plan): it needs
-// vals_last, which then always receives the values.  Returns the buffers
-// holding the result (for an adaptive sort only the values: the keys are left
-// relative and in either buffer).  Returns a CUDA error code (cudaSuccess).
+// passes of at most 8 bits.  Keys ping-pong between k1 and k2, values between
+// v1 and v2; the values start as vals0, or as the input positions when vals0
+// is null.  The item count is *count_dev (device, clamped to cap) or
+// count_static.  The last pass writes its values to vals_last when that is
+// given.  With krange (device {smallest key, ~largest key}) the sort is
+// adaptive (see pass_plan): it needs vals_last, which then always receives
+// the values.  Returns the buffers holding the result (for an adaptive sort
+// only the values: the keys are left relative and in either buffer).
 template <int kRI>
-static cudaError_t lsd_sort(uint32_t* k1, uint32_t* k2, uint32_t* v1, uint32_t* v2, const uint32_t* vals0,
-                            const int32_t* count_dev, int64_t count_static, int64_t cap, int total_bits,
-                            const RadixBufs& rb, uint32_t* flags, cudaStream_t s, uint32_t** keys_out,
-                            uint32_t** vals_out, uint32_t* vals_last = nullptr, const uint32_t* krange = nullptr)
+static void lsd_sort(uint32_t* k1, uint32_t* k2, uint32_t* v1, uint32_t* v2, const uint32_t* vals0,
+                     const int32_t* count_dev, int64_t count_static, int64_t cap, int total_bits,
+                     const RadixBufs& rb, cudaStream_t s, uint32_t** keys_out, uint32_t** vals_out,
+                     uint32_t* vals_last = nullptr, const uint32_t* krange = nullptr)
 {
     constexpr int kRTile = kRT * kRI;
     uint32_t *kin = k1, *kout = k2, *vout = v1;
@@ -365,18 +310,16 @@ static cudaError_t lsd_sort(uint32_t* k1, uint32_t* k2, uint32_t* v1, uint32_t* 
         const int passes = (total_bits + 7) / 8;
         const int per = (total_bits + passes - 1) / passes;
         const unsigned grid = (unsigned)((cap + kRTile - 1) / kRTile);
-        cudaError_t e = cudaMemsetAsync(rb.zero, 0, rb.zero_bytes, s);
-        if (e != cudaSuccess) return e;
-        launch_pdl(k_radix_hist_all<kRI>, grid, kRT, s, kin, count_dev, count_static, cap, passes, per, total_bits,
-                   rb.counts, krange);
-        count_launches(1);
         for (int pass = 0, shift = 0; pass < passes; ++pass, shift += per) {
             const int bits = std::min(per, total_bits - shift);
             // the device picks vals_last for the last pass that runs (the host's last one when not adaptive)
-            launch_pdl(k_radix_onesweep<kRI>, grid, kRT, s, kin, vin, kout, vout, count_dev, count_static, cap, shift,
-                       bits, rb.counts + pass * kMaxBins, rb.status + (size_t)pass * rb.max_blocks * kMaxBins,
-                       rb.vblock + pass, krange, pass, passes, vals_last, flags);
-            count_launches(1);
+            launch_pdl(k_radix_hist<kRI>, grid, kRT, s, kin, count_dev, count_static, cap, shift, bits, rb.hist, krange,
+                       pass, passes);
+            launch_pdl(k_radix_scan_rows<kRI>, 1u << bits, kRT, s, rb.hist, count_dev, count_static, cap,
+                       rb.digit_total, krange, pass, passes);
+            launch_pdl(k_radix_scatter<kRI>, grid, kRT, s, kin, vin, kout, vout, count_dev, count_static, cap, shift,
+                       bits, rb.hist, rb.digit_total, krange, pass, passes, vals_last);
+            count_launches(3);
             std::swap(kin, kout);
             vin = (vals_last && pass == passes - 1) ? vals_last : vout;
             vout = (vout == v1) ? v2 : v1;
@@ -384,7 +327,6 @@ static cudaError_t lsd_sort(uint32_t* k1, uint32_t* k2, uint32_t* v1, uint32_t* 
     }
     *keys_out = kin;
     *vals_out = const_cast<uint32_t*>(krange ? vals_last : vin);  // vals0 itself when no pass ran
-    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------
@@ -665,8 +607,7 @@ __global__ void k_copy_u32(int32_t n, const uint32_t* __restrict__ src, int32_t*
 }
 
 struct OrderLayout {
-    uint32_t *ka, *kb, *va, *vb, *flags;
-    RadixBufs rb;
+    uint32_t *ka, *kb, *va, *vb, *hist, *digit_total;
     size_t bytes;
 };
 
@@ -678,9 +619,8 @@ static OrderLayout carve_order(void* ws, int64_t T)
     L.kb = c.take<uint32_t>(T);
     L.va = c.take<uint32_t>(T);
     L.vb = c.take<uint32_t>(T);
-    L.flags = c.take<uint32_t>(1);
-    const int64_t nb = (T + kRTileMin - 1) / kRTileMin;
-    L.rb = radix_bufs(c.take<unsigned char>(radix_bufs_bytes(nb)), nb);
+    L.hist = c.take<uint32_t>((size_t)((T + kRTileMin - 1) / kRTileMin) * kMaxBins + 1);
+    L.digit_total = c.take<uint32_t>(kMaxBins);
     L.bytes = c.used;
     return L;
 }
@@ -690,7 +630,7 @@ struct SortLayout {
     int32_t* cnt_sorted;
     int64_t* block_sums;
     uint32_t *tkey_a, *tkey_b, *tval_a, *tval_b, *owner;
-    RadixBufs rb;
+    uint32_t *hist, *digit_total;
     size_t bytes;
 };
 
@@ -713,7 +653,8 @@ static SortLayout carve(void* ws, int64_t P, int64_t cap)
     L.owner = c.take<uint32_t>(cap);
     // radix blocks of the depth sort (short blocks) and of the tile sort (long blocks)
     const int64_t nb = std::max((P + kRTileMin - 1) / kRTileMin, (cap + kRT * kRILong - 1) / (kRT * kRILong));
-    L.rb = radix_bufs(c.take<unsigned char>(radix_bufs_bytes(nb)), nb);
+    L.hist = c.take<uint32_t>((size_t)nb * kMaxBins + 1);
+    L.digit_total = c.take<uint32_t>(kMaxBins);
     L.bytes = c.used;
     return L;
 }
@@ -782,6 +723,7 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
         cudaMemsetAsync(K_out, 0, sizeof(int32_t), s) != cudaSuccess)
         return launch_status("gs_bin_and_sort memset");
     if (P == 0) return launch_status("gs_bin_and_sort");
+    const RadixBufs rb{L.hist, L.digit_total};
 
     // 1. projections in (depth, p) order: an adaptive sort on the spread of the visible depth keys
     if (cudaMemsetAsync(L.krange, 0xff, 2 * sizeof(uint32_t), s) != cudaSuccess)
@@ -790,9 +732,8 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
                L.dkey_a, L.krange);
     count_launches(1);
     uint32_t *dk, *order;
-    if (lsd_sort<kRIShort>(L.dkey_a, L.dkey_b, L.dval_a, L.dval_b, nullptr, nullptr, P, P, 31, L.rb, flags, s, &dk,
-                           &order, L.order, L.krange) != cudaSuccess)
-        return launch_status("gs_bin_and_sort depth sort");
+    lsd_sort<kRIShort>(L.dkey_a, L.dkey_b, L.dval_a, L.dval_b, nullptr, nullptr, P, P, 31, rb, s, &dk, &order, L.order,
+                       L.krange);
 
     // 2. scan of touched in depth order, K, emission
     const int64_t nblk = (P + kEmitTile - 1) / kEmitTile;
@@ -807,10 +748,9 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
     //    inverse positions are wanted, else directly the owning projections
     //    (in the latter case the last pass writes them straight into isect_ids)
     uint32_t *tk, *tv;
-    if (lsd_sort<kRILong>(L.tkey_a, L.tkey_b, L.tval_a, L.tval_b, isect_pos ? nullptr : L.owner, K_out, 0,
-                          K_capacity, bit_length((int64_t)T_total - 1), L.rb, flags, s, &tk, &tv,
-                          isect_pos ? nullptr : reinterpret_cast<uint32_t*>(isect_ids)) != cudaSuccess)
-        return launch_status("gs_bin_and_sort tile sort");
+    lsd_sort<kRILong>(L.tkey_a, L.tkey_b, L.tval_a, L.tval_b, isect_pos ? nullptr : L.owner, K_out, 0, K_capacity,
+                      bit_length((int64_t)T_total - 1), rb, s, &tk, &tv,
+                      isect_pos ? nullptr : reinterpret_cast<uint32_t*>(isect_ids));
     // 4. projection ids, inverse positions, tile ranges
     launch_pdl(k_finalize, (unsigned)((K_capacity + 256 * kFinItems - 1) / (256 * kFinItems)), 256, s, K_out, K_capacity, tk, tv, L.owner,
                isect_ids, isect_pos, reinterpret_cast<int2*>(tile_ranges));
@@ -840,10 +780,8 @@ extern "C" int gs_tile_order(const int32_t* tile_ranges, int32_t T_total, void* 
     const unsigned g = (unsigned)((T_total + 255) / 256);
     launch_pdl(k_tile_len_keys, g, 256, s, T_total, reinterpret_cast<const int2*>(tile_ranges), L.ka);
     uint32_t *k, *v;
-    if (cudaMemsetAsync(L.flags, 0, sizeof(uint32_t), s) != cudaSuccess ||
-        lsd_sort<kRIShort>(L.ka, L.kb, L.va, L.vb, nullptr, nullptr, T_total, T_total, 16, L.rb, L.flags, s, &k, &v) !=
-            cudaSuccess)
-        return launch_status("gs_tile_order");
+    lsd_sort<kRIShort>(L.ka, L.kb, L.va, L.vb, nullptr, nullptr, T_total, T_total, 16, RadixBufs{L.hist, L.digit_total}, s, &k,
+             &v);
     launch_pdl(k_copy_u32, g, 256, s, T_total, v, order);
     count_launches(2);
     return launch_status("gs_tile_order");

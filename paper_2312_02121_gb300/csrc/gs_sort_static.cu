@@ -16,7 +16,7 @@ int bin_and_sort_check_args(const char* who, const GsView* views, int32_t V, int
 
 // Workspace bytes gs_bin_and_sort needs at the static limits, rounded up.
 // The entry point re-checks the exact requirement before every call.
-constexpr size_t kStaticScratchBytes = size_t(25) << 20;  // 25 MiB
+constexpr size_t kStaticScratchBytes = size_t(24) << 20;  // 24 MiB
 
 static __device__ __align__(256) unsigned char g_sort_scratch[kStaticScratchBytes];
 

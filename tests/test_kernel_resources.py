@@ -42,9 +42,9 @@ def test_timed_kernels_keep_their_register_budget_and_spills(rows):
         ("gs::k_emit", 255, 0),
         ("gs::k_finalize", 255, 0),
         ("gs::k_depth_keys", 255, 0),
-        ("gs::k_radix_onesweep<16>", 255, 0),
-        ("gs::k_radix_onesweep<8>", 255, 0),
-        ("gs::k_radix_hist_all<16>", 255, 0),
+        ("gs::k_radix_scatter<16>", 255, 0),
+        ("gs::k_radix_scatter<8>", 255, 0),
+        ("gs::k_radix_hist<16>", 255, 0),
         ("gs::k_l2_loss<float>", 255, 0),
     ]
     for name, cap, spill in timed:

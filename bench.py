@@ -65,6 +65,9 @@ def parse_args():
     ap.add_argument("--optim-steps", type=int, default=20)
     ap.add_argument("--profile", action="store_true",
                     help="run warmup + steps untimed and exit (a fixed command line for ncu)")
+    ap.add_argument("--tuning", default=None,
+                    help="persistent,ctas_per_sm,longest_first,bwd_pixels,bwd_batch instead of gs_autotune's "
+                         "choice (e.g. for an ncu launch list without the tuner's launches)")
     return ap.parse_args()
 
 
@@ -740,8 +743,11 @@ def run_ours(args, rank, world, local_rank):
     from paper_2312_02121_gb300 import batch as GB
     # the library's autotuner (gs_autotune) picks the tile walk and the backward's batch shape for this frame;
     # every timed path below uses its choice
-    tuning = GB.autotune(GB.BatchRenderer(params, views, cap, target, w.eps2d),
-                         key=f"{WORKLOAD}|P{views.P}|T{views.T}|K{cap}", use_cache=False)
+    if args.tuning:
+        tuning = dict(zip(B.TUNING_FIELDS, (int(x) for x in args.tuning.split(","))), ms=float("nan"))
+    else:
+        tuning = GB.autotune(GB.BatchRenderer(params, views, cap, target, w.eps2d),
+                             key=f"{WORKLOAD}|P{views.P}|T{views.T}|K{cap}", use_cache=False)
     torch.cuda.empty_cache()
     stream = torch.cuda.current_stream()
     stages = ["project", "bin_and_sort", "rasterize_fwd", "loss_grad", "zero_grads", "rasterize_bwd", "project_bwd"]
@@ -914,17 +920,49 @@ def run_ours(args, rank, world, local_rank):
             dt = float(t.item())
         return dt
 
-    e2e_s = timed(e2e_graph_step)
+    e2e_serial_s = timed(e2e_graph_step)
     e2e_ag_s = timed(e2e_autograd_step)
     assert not rg.overflowed()
+    del rg
+    torch.cuda.empty_cache()
+
+    # the headline end-to-end path: the same captured step, two deep (batch.HostPipeline): step k's copies
+    # and compute overlap step k-1's on a second stream; every step copies its own inputs and reads back
+    # its own loss
+    def make_host_renderer():
+        dp = pipeline.Params(*[torch.empty_like(host[k], device=dev) for k in keys])
+        r = GB.BatchRenderer(dp, views, cap, torch.empty_like(host_tgt, device=dev), w.eps2d, GB.config(tuning, dev),
+                             bool(tuning["longest_first"]))
+        r.attach_host_inputs(host, host_tgt)
+        return r
+
+    pipe = GB.HostPipeline(make_host_renderer)
+    for _ in range(3):
+        pipe.step()
+    pipe.finish()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        pipe.step()
+    pipe.finish()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    assert not pipe.overflowed()
+    del pipe
+    torch.cuda.empty_cache()
     e2e = {"value": world * pixels / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": 4, "ms_per_step": 1e3 * e2e_s,
            "inputs": "per step: Gaussian parameters and target image (pinned host -> device); result: the loss "
                      "(device -> pinned host)",
-           "api": "BatchRenderer.attach_host_inputs + capture (one CUDA graph per step, copies overlapped)",
+           "api": "batch.HostPipeline: BatchRenderer.attach_host_inputs + capture, two steps in flight on two "
+                  "streams (each step's copies and compute overlap the previous step's)",
+           "serial": {"value": world * pixels / e2e_serial_s / 1e6, "ms_per_step": 1e3 * e2e_serial_s,
+                      "api": "one captured step at a time: copies, step, loss read back, then the next"},
            "autograd_api": {"value": world * pixels / e2e_ag_s / 1e6, "ms_per_step": 1e3 * e2e_ag_s,
                             "api": "autograd.render + autograd.l2_loss + backward, views laid out per step"}}
-    del rg
 
     if rank != 0:
         return

@@ -226,6 +226,52 @@ class BatchRenderer:
         return self.rgb[off:off + w * h].view(h, w, -1)
 
 
+class HostPipeline:
+    """Steps fed from pinned host memory, two deep: two renderers (each with
+    its own device buffers and host inputs attached, see
+    ``BatchRenderer.attach_host_inputs``) replay their captured steps on two
+    streams in turn, so that one step's host->device copies and compute
+    overlap the previous step's.  Every step still copies its own inputs from
+    the host and reads its own loss back; ``step`` returns the loss of the
+    step before it (None for the first), ``finish`` the last one's."""
+
+    def __init__(self, make):
+        """``make()`` returns a BatchRenderer whose host inputs are attached."""
+        self.r = [make(), make()]
+        self.s = [torch.cuda.Stream(), torch.cuda.Stream()]
+        self.done = [torch.cuda.Event(), torch.cuda.Event()]
+        for r, st in zip(self.r, self.s):
+            if r.host is None:
+                raise ValueError("HostPipeline needs renderers with host inputs attached")
+            st.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(st):
+                r.capture()
+        self.k = 0
+
+    def step(self) -> Optional[float]:
+        i = self.k % 2
+        with torch.cuda.stream(self.s[i]):
+            self.r[i].step()
+            self.done[i].record()
+        prev = None
+        if self.k > 0:
+            j = 1 - i
+            self.done[j].synchronize()
+            prev = float(self.r[j].loss_host[0])
+        self.k += 1
+        return prev
+
+    def finish(self) -> Optional[float]:
+        if self.k == 0:
+            return None
+        j = (self.k - 1) % 2
+        self.done[j].synchronize()
+        return float(self.r[j].loss_host[0])
+
+    def overflowed(self) -> bool:
+        return any(r.overflowed() for r in self.r)
+
+
 class PerViewRenderer:
     """The same step with one set of launches per view (the per-view path the
     batched launch is measured against).  All views accumulate into one

@@ -179,3 +179,35 @@ def test_host_inputs_are_uploaded_by_every_replay():
         assert float(r.loss_host[0]) == pytest.approx(float(ref.loss.item()), rel=1e-6)
         for k, g in ref.grads().items():
             assert rel_l2(np_(r.grads()[k]), np_(g)) <= 1e-6, k
+
+
+def test_host_pipeline_two_deep_gives_each_step_its_own_inputs_and_loss():
+    # batch.HostPipeline keeps two captured steps in flight on two streams; each step copies the host
+    # inputs and reads back its own loss, which must equal the loss of a plain step on the same inputs.
+    # Host inputs may change only while no step is in flight (after finish), as for any async copy.
+    w = _mixed_workload()
+    params, views, ranges, targets = GB.workload_views(w)
+    cap = GB.exact_capacity(params, views, w.eps2d) + 1000
+    keys = ("means", "quats", "scales", "opacities", "colors")
+    host = {k: getattr(params, k).cpu().pin_memory() for k in keys}
+    host_t = targets.cpu().pin_memory()
+
+    def make():
+        dev_p = pipeline.Params(*[torch.empty_like(getattr(params, k)) for k in keys])
+        r = GB.BatchRenderer(dev_p, views, cap, torch.empty_like(targets), w.eps2d)
+        r.attach_host_inputs(host, host_t)
+        return r
+
+    pipe = GB.HostPipeline(make)
+    ref = GB.BatchRenderer(params, views, cap, targets, w.eps2d)
+    for trial in range(2):
+        if trial == 1:  # nothing in flight: change the inputs on the host and in the reference
+            host["colors"].mul_(0.5)
+            params.colors.mul_(0.5)
+        ref.step_eager()
+        want = float(ref.loss.item())
+        first = pipe.step()
+        assert (first is None) == (trial == 0)
+        got = [pipe.step() for _ in range(3)] + [pipe.finish()]
+        assert got == pytest.approx([want] * 4, rel=1e-6), trial
+    assert not pipe.overflowed()

@@ -161,6 +161,14 @@ class ClockSampler:
 RASTER_SOURCES = ("gs_raster.cu", "gs_raster_bwd.cuh", "gs_raster_bwd2.cu", "gs_raster_common.cuh", "gs_common.cuh")
 
 
+def tuning_table(best: dict) -> dict:
+    """gs_autotune's time of every candidate, keyed g/p (one CTA per tile / persistent grid) + CTAs per
+    SM + I/L (tile id / longest-first order) + the backward's pixels per thread and batch."""
+    return {f"{'p' if x['persistent'] else 'g'}{x['ctas_per_sm']}"
+            f"{'L' if x['longest_first'] else 'I'}_{x['bwd_pixels']}px{x['bwd_batch']}": round(x["ms"], 3)
+            for x in best["all"]}
+
+
 def raster_source_hash() -> str:
     """sha256 over the sources the 3-channel raster kernels are compiled from."""
     import hashlib
@@ -559,9 +567,7 @@ def batched_comparison(dev, steps: int):
                      "batched_launches_per_step": int(launches_b), "per_view_launches_per_step": int(launches_v),
                      "batched_cuda_graph": True,
                      "tuning": {k: best[k] for k in B.TUNING_FIELDS},
-                     "tuning_ms": {f"{'p' if x['persistent'] else 'g'}{x['ctas_per_sm']}"
-                                   f"{'L' if x['longest_first'] else 'I'}_{x['bwd_pixels']}px{x['bwd_batch']}":
-                                   round(x["ms"], 3) for x in best["all"]},
+                     "tuning_ms": tuning_table(best),
                      "tuning_note": "compositing fwd+bwd ms per candidate (gs_autotune): g/p = one CTA per tile / "
                                     "persistent grid (CTAs per SM, 0 = as many as fit), I/L = tile id / longest-first "
                                     "order, then the backward's pixels per thread and staged batch",
@@ -996,6 +1002,7 @@ def run_ours(args, rank, world, local_rank):
                    "views": 1, "intersections": K, "intersections_per_s": K / (ms_step / 1e3),
                    "composited_pairs": contrib, "evaluated_pairs_bwd": walked, "evaluated_pairs_fwd": walked_fwd,
                    "tuning": {k: tuning[k] for k in B.TUNING_FIELDS}, "tuning_ms": tuning["ms"],
+                   "tuning_candidates_ms": tuning_table(tuning) if "all" in tuning else None,
                    "l2": "flushed (256 MiB write) before every timed step, outside its events",
                    "multi_gpu": "under torchrun the 64-view batch is split over the ranks instead (run_sharded)"},
         "stage_ms": stage_ms, "eager_ms_per_step": eager_ms,

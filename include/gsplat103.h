@@ -390,8 +390,10 @@ size_t gs_autotune_workspace_size(int64_t P, int64_t N, int32_t T_total, int64_t
  * tile its 3-sigma box touches).  For every candidate (NULL / n_candidates = 0:
  * the built-in ones) it runs gs_tile_order when longest_first, then
  * gs_rasterize_fwd and the fast gs_rasterize_bwd with that walk and batch shape
- * on `stream`, once to warm up and `repeats` times timed with CUDA events, and
- * records the median.  No candidate changes any result.
+ * on `stream`: every candidate once to warm up, then `repeats` rounds that
+ * time every candidate in turn with CUDA events (so a drift of the clocks
+ * weighs on all of them alike), and records each one's median.  No candidate
+ * changes any result.
  *   in : the frame as gs_project and gs_bin_and_sort left it: views (device),
  *        P projections, N Gaussians (the largest g_begin + g_count of the
  *        views), T_total tiles, pixels (total), means2d, conics, opacities,

@@ -360,7 +360,7 @@ def _cache_path() -> str:
     return os.path.join(root, "tuning.json")
 
 
-def autotune(renderer: "BatchRenderer", key: str, candidates=None, use_cache: bool = True, repeats: int = 3) -> dict:
+def autotune(renderer: "BatchRenderer", key: str, candidates=None, use_cache: bool = True, repeats: int = 5) -> dict:
     """Picks the tile walk and backward batch shape for ``renderer``'s frame
     with the library's gs_autotune (which times the compositing forward +
     backward of each candidate on the device) and returns the fastest as a

@@ -135,10 +135,8 @@ extern "C" int gs_autotune(const GsView* views, int32_t V, int64_t P, int64_t N,
     EventPair ev;
     if (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess) return launch_status(who);
 
-    int best_i = -1;
-    std::vector<float> times;
-    for (size_t ci = 0; ci < cands.size(); ++ci) {
-        GsTuning& c = cands[ci];
+    // one run of candidate c: its tile order (when longest first), the forward and the backward
+    auto once = [&](const GsTuning& c) -> int {
         GsRasterConfig cfg{};
         cfg.persistent = c.persistent;
         cfg.ctas_per_sm = c.ctas_per_sm;
@@ -147,30 +145,35 @@ extern "C" int gs_autotune(const GsView* views, int32_t V, int64_t P, int64_t N,
         cfg.warp_hits = L.hits;
         cfg.bwd_pixels = c.bwd_pixels;
         cfg.bwd_batch = c.bwd_batch;
-        auto once = [&]() -> int {
-            if (c.longest_first)
-                if (int rc = gs_tile_order(tile_ranges, T_total, L.order_ws, L.order_ws_bytes, L.order, stream))
-                    return rc;
-            if (int rc = gs_rasterize_fwd(views, V, T_total, means2d, conics, opacities, colors, isect_ids,
-                                          tile_ranges, nullptr, L.rgb, L.T_final, L.last, nullptr, &cfg, stream))
-                return rc;
-            return gs_rasterize_bwd(views, V, P, T_total, means2d, conics, opacities, colors, isect_ids, nullptr,
-                                    nullptr, nullptr, tile_ranges, K, K_capacity, nullptr, L.T_final, L.last, L.dL,
-                                    0, nullptr, 0, L.g2, L.gc, L.go, L.gcol, &cfg, stream);
-        };
-        if (int rc = once()) return rc;  // warm-up (and the argument checks of the candidate)
-        times.clear();
-        for (int r = 0; r < repeats; ++r) {
+        if (c.longest_first)
+            if (int rc = gs_tile_order(tile_ranges, T_total, L.order_ws, L.order_ws_bytes, L.order, stream)) return rc;
+        if (int rc = gs_rasterize_fwd(views, V, T_total, means2d, conics, opacities, colors, isect_ids, tile_ranges,
+                                      nullptr, L.rgb, L.T_final, L.last, nullptr, &cfg, stream))
+            return rc;
+        return gs_rasterize_bwd(views, V, P, T_total, means2d, conics, opacities, colors, isect_ids, nullptr, nullptr,
+                                nullptr, tile_ranges, K, K_capacity, nullptr, L.T_final, L.last, L.dL, 0, nullptr, 0,
+                                L.g2, L.gc, L.go, L.gcol, &cfg, stream);
+    };
+    // a warm-up of every candidate (and its argument checks), then the repeats round-robin over the
+    // candidates, so that a drift of the clocks during the tuning weighs on all of them alike
+    for (const GsTuning& c : cands)
+        if (int rc = once(c)) return rc;
+    std::vector<std::vector<float>> times(cands.size());
+    for (int r = 0; r < repeats; ++r)
+        for (size_t ci = 0; ci < cands.size(); ++ci) {
             if (cudaEventRecord(ev.a, s) != cudaSuccess) return launch_status(who);
-            if (int rc = once()) return rc;
+            if (int rc = once(cands[ci])) return rc;
             if (cudaEventRecord(ev.b, s) != cudaSuccess || cudaEventSynchronize(ev.b) != cudaSuccess)
                 return launch_status(who);
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, ev.a, ev.b) != cudaSuccess) return launch_status(who);
-            times.push_back(ms);
+            times[ci].push_back(ms);
         }
-        std::sort(times.begin(), times.end());
-        c.ms = times[times.size() / 2];
+    int best_i = -1;
+    for (size_t ci = 0; ci < cands.size(); ++ci) {
+        GsTuning& c = cands[ci];
+        std::sort(times[ci].begin(), times[ci].end());
+        c.ms = times[ci][times[ci].size() / 2];
         if (results) results[ci] = c;
         if (best_i < 0 || c.ms < cands[best_i].ms) best_i = (int)ci;
     }

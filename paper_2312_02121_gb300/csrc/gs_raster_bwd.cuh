@@ -154,7 +154,7 @@ constexpr int bwd_threads() { return 32 * (kWarps / kPx); }
 // kPx: pixels per thread (1 or 2); kB: Gaussians per staged batch (a multiple
 // of 32, at most the CTA's threads).
 template <typename S, bool kCull, bool kAtomic, bool kPersistent, bool kAnyC, int kPx, int kB>
-__global__ void __launch_bounds__(bwd_threads<kPx>(), kPx == 1 ? 4 : 7)  // measured: 4, and 7 (71 registers)
+__global__ void __launch_bounds__(bwd_threads<kPx>(), kPx == 1 ? 4 : 7)  // measured: 4, and 7 (72 registers; 8 CTAs at 63 was 5 % slower)
 k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t* __restrict__ tile_order,
              int* __restrict__ queue, const V2<S>* __restrict__ means2d, const S* __restrict__ conics,
              const S* __restrict__ opacities, const S* __restrict__ colors, const int32_t* __restrict__ isect_ids,
@@ -182,7 +182,7 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
     __shared__ S s_grad[kNW][kB][kRec];
     __shared__ unsigned s_mask[kNW][(kB + 31) / 32];
     __shared__ V4<S> s_fl[2][kB];  // (a, b, D, projection) of the last two staged batches, for the flush
-    __shared__ uint32_t s_hitw[(kB + 31) / 32][kWarps];  // the forward's cull ballots of the staged chunks
+    __shared__ uint32_t s_hitw[(kB + 31) / 32][kWarps];  // box ballots of the staged chunks (word b: box b)
     __shared__ __align__(16) S s_red[kNW][32 * kRedStride];
     __shared__ int s_maxlast[kNW];
     __shared__ int s_next;
@@ -202,8 +202,9 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
         const int local = tile - view->tile_offset;
         const int Wd = view->cam.width, Hd = view->cam.height;
         // this warp's box: 8 pixels wide, 4 kPx high; pixel i of the lane sits 4 i rows below the first
-        const int bx = (local % view->tiles_x) * kTile + (w & 1) * 8;
-        const int by = (local / view->tiles_x) * kTile + (w >> 1) * 4 * kPx;
+        const int tx0 = (local % view->tiles_x) * kTile, ty0 = (local / view->tiles_x) * kTile;
+        const int bx = tx0 + (w & 1) * 8;
+        const int by = ty0 + (w >> 1) * 4 * kPx;
         const int px = bx + (lane & 7);
         const S cx = S(px) + S(0.5);
         S T[kPx], g0[kPx], g1[kPx], g2[kPx], cy[kPx], SdL[kPx];
@@ -276,6 +277,25 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                 s_fl[k & 1][threadIdx.x] = mk4<S>(sh_xy[threadIdx.x].w, sh_q[threadIdx.x].w, sh_col[threadIdx.x].w,
                                                   RT<S>::stash(p));
             }
+            if (kCull && !warp_hits && threadIdx.x < kB) {
+                // without the forward's ballots: the same box test for each staged Gaussian against the
+                // tile's 8 boxes, turned into the forward's word layout by one ballot per box over each
+                // staging warp (whole warps: kB is a multiple of 32)
+                unsigned reach = 0u;
+                if (threadIdx.x < n) {
+                    const Staged<S> st = load_staged<S>(sh_xy, sh_q, sh_col, sh_cull, threadIdx.x);
+#pragma unroll
+                    for (int b = 0; b < kWarps; ++b) {
+                        const S x0 = S(tx0 + (b & 1) * 8) + S(0.5), y0 = S(ty0 + (b >> 1) * 4) + S(0.5);
+                        reach |= (unsigned)reaches_box(st, x0, x0 + S(7), y0, y0 + S(3)) << b;
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < kWarps; ++b) {
+                    const unsigned word = __ballot_sync(kFull, (reach >> b) & 1u);
+                    if (lane == b) s_hitw[threadIdx.x >> 5][b] = word;
+                }
+            }
             if (kFlushOff == 0 || threadIdx.x >= kFlushOff) {
                 const int j = threadIdx.x - kFlushOff;
                 if (j < prev_n)
@@ -296,74 +316,59 @@ k_raster_bwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                 for (int i = 0; i < kPx; ++i) {
                     const int lim = min(n, wl[i] - b0 + 1) - s;
                     const unsigned valid = lim <= 0 ? 0u : lim >= 32 ? kFull : (1u << lim) - 1u;
-                    if (warp_hits) {  // the forward's cull of the same entry against the same box
-                        mi[i] = s_hitw[s >> 5][(w & 1) + 2 * (kPx * (w >> 1) + i)] & valid;
-                    } else if (kCull) {
-                        const bool mine = (valid >> lane) & 1u;
-                        const S y0 = S(by + 4 * i) + S(0.5);
-                        mi[i] = __ballot_sync(kFull, mine && reaches_box(load_staged<S>(sh_xy, sh_q, sh_col, sh_cull,
-                                                                                        s + lane),
-                                                                            S(bx) + S(0.5), S(bx) + S(7.5), y0,
-                                                                            y0 + S(3)));
-                    } else {
-                        mi[i] = valid;
-                    }
+                    // the box's ballot of this chunk (the forward's, or the staging's box test)
+                    mi[i] = (kCull || warp_hits) ? s_hitw[s >> 5][(w & 1) + 2 * (kPx * (w >> 1) + i)] & valid
+                                                 : valid;
                     m |= mi[i];
                 }
                 while (m) {
                     const int hb = 31 - __clz(m);
                     m ^= 1u << hb;
                     const int j = s + hb;  // back to front
-                    // every lane evaluates the pixels of the half-boxes the Gaussian can reach; lanes
-                    // whose pixel does not composite it carry zero terms (selects, no branches)
+                    // each box the Gaussian can reach is evaluated and, when one of its pixels composites
+                    // it, turned into gradient terms at once (lanes whose pixel does not composite it carry
+                    // zero terms: selects, no branches); the warp then reduces once for all its pixels
                     const V4<S> xy = sh_xy[j];
                     const V4<S> qq = sh_q[j];
-                    S dx[kPx], dy[kPx], u[kPx], ge[kPx], raw[kPx], alpha[kPx];
-                    bool ctb[kPx];
-                    unsigned cm[kPx], cmall = 0u;
-#pragma unroll
-                    for (int i = 0; i < kPx; ++i) {
-                        cm[i] = 0u;
-                        if (kPx == 1 || ((mi[i] >> hb) & 1u)) {  // warp-uniform (one box: always)
-                            dx[i] = xy.x - cx;
-                            dy[i] = xy.y - cy[i];
-                            const S p2 = neg_sigma_log2(qq, dx[i], dy[i], u[i]);
-                            ge[i] = RT<S>::ex2(p2);  // exp(-sigma)
-                            raw[i] = mul_rn(xy.z, ge[i]);
-                            alpha[i] = fmin(RT<S>::alpha_max(), raw[i]);
-                            ctb[i] = (j <= lastj[i]) && (p2 <= S(0)) && (raw[i] >= RT<S>::alpha_min());
-                            cm[i] = __ballot_sync(kFull, ctb[i]);
-                            cmall |= cm[i];
-                        }
-                    }
-                    if (cmall == 0u) continue;
                     const V4<S> col = sh_col[j];
+                    const S dx = xy.x - cx;
                     S r[kRec];
 #pragma unroll
-                    for (int q = 0; q < kRec; ++q) r[q] = S(0);  // a first box with no contribution adds nothing
+                    for (int q = 0; q < kRec; ++q) r[q] = S(0);
+                    bool any = false;
 #pragma unroll
                     for (int i = 0; i < kPx; ++i) {
-                        if (kPx > 1 && cm[i] == 0u) continue;  // warp-uniform (one box: it contributes)
-                        const S inv1ma = RT<S>::rcp(S(1) - alpha[i]);
+                        if (kPx > 1 && !((mi[i] >> hb) & 1u)) continue;  // warp-uniform
+                        const S dy = xy.y - cy[i];
+                        S u;
+                        const S p2 = neg_sigma_log2(qq, dx, dy, u);
+                        const S ge = RT<S>::ex2(p2);  // exp(-sigma)
+                        const S raw = mul_rn(xy.z, ge);
+                        const S alpha = fmin(RT<S>::alpha_max(), raw);
+                        const bool ctb = (j <= lastj[i]) && (p2 <= S(0)) && (raw >= RT<S>::alpha_min());
+                        if (__ballot_sync(kFull, ctb) == 0u) continue;  // warp-uniform
+                        const S inv1ma = RT<S>::rcp(S(1) - alpha);
                         const S Tn = T[i] * inv1ma;  // T before this Gaussian
-                        const S wgt = ctb[i] ? alpha[i] * Tn : S(0);
+                        const S wgt = ctb ? alpha * Tn : S(0);
                         const S cdot = fma(col.x, g0[i], fma(col.y, g1[i], col.z * g2[i]));
                         const S dL_dalpha = fma(Tn, cdot, -SdL[i] * inv1ma);
-                        const S gd = (ctb[i] && raw[i] < RT<S>::alpha_max()) ? ge[i] * dL_dalpha : S(0);  // dL/do
+                        const S gd = (ctb && raw < RT<S>::alpha_max()) ? ge * dL_dalpha : S(0);  // dL/do
                         SdL[i] = fma(wgt, cdot, SdL[i]);
-                        T[i] = ctb[i] ? Tn : T[i];
+                        T[i] = ctb ? Tn : T[i];
                         const S ds = -xy.z * gd;  // dL/dsigma
                         // the sums the warp reduces; the flush turns them into the gradients: with
                         // sigma = (a u^2 + D dy^2) / 2, u = dx + k dy,
                         // dL/dmu' = (a sum ds u, b sum ds u + D sum ds dy) and
                         // dL/d(a, k, D) = (sum ds u^2 / 2, a sum ds u dy, sum ds dy^2 / 2)
-                        const S dsu = ds * u[i];
-                        const S dsdy = ds * dy[i];
-                        const S t[kRec] = {dsu, dsdy, dsu * u[i], dsu * dy[i], dsdy * dy[i], gd,
+                        const S dsu = ds * u;
+                        const S dsdy = ds * dy;
+                        const S t[kRec] = {dsu, dsdy, dsu * u, dsu * dy, dsdy * dy, gd,
                                            wgt * g0[i], wgt * g1[i], wgt * g2[i]};
 #pragma unroll
                         for (int q = 0; q < kRec; ++q) r[q] = i == 0 ? t[q] : r[q] + t[q];
+                        any = true;
                     }
+                    if (!any) continue;
                     chunk_mask |= 1u << hb;
                     // the warp's sum of each term, into the warp's own slot for this Gaussian (a
                     // lone contributing lane is not special-cased: the transpose is cheaper than its

@@ -598,6 +598,52 @@ __global__ void k_tile_len_keys(int32_t T, const int2* __restrict__ tile_ranges,
     }
 }
 
+// The same order for up to kOrderRankMax tiles in one launch, by counting: a
+// tile's key packs its length key above its id (unique keys, so the order is
+// the rank of each key among all of them, ties by id included), and each group
+// of kOrderSplit threads counts the keys below its tile's over interleaved
+// quads of the whole key array, staged in shared memory by every CTA.  O(T^2)
+// compares, spread over ceil(T / 64) CTAs of 1024 threads; larger batches take
+// the radix sort.
+constexpr int kOrderRankMax = 12288;
+constexpr int kOrderSplit = 16;
+constexpr int kOrderThreads = 1024;
+
+__device__ __forceinline__ uint32_t order_key(int2 r, int t)
+{
+    return ((65535u - (uint32_t)min(max(r.y - r.x, 0), 65535)) << 16) | (uint32_t)t;
+}
+
+__global__ void __launch_bounds__(kOrderThreads)
+k_tile_order_rank(int32_t T, const int2* __restrict__ tile_ranges, int32_t* __restrict__ order)
+{
+    extern __shared__ uint4 s_keys4[];
+    uint32_t* s_key = reinterpret_cast<uint32_t*>(s_keys4);
+    pdl_wait();
+    pdl_trigger();
+    const int n4 = (T + 3) & ~3;  // padded with keys above every real one (ids < 2^14)
+#pragma unroll 4
+    for (int i = threadIdx.x; i < n4; i += kOrderThreads) s_key[i] = i < T ? order_key(tile_ranges[i], i) : ~0u;
+    __syncthreads();
+    const int sub = threadIdx.x % kOrderSplit;
+    const int t = blockIdx.x * (kOrderThreads / kOrderSplit) + threadIdx.x / kOrderSplit;
+    const uint32_t mine = t < T ? s_key[t] : 0u;
+    // the 16 threads of a group read 16 consecutive quads; the warp's two groups the same ones
+    int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+#pragma unroll 4
+    for (int i = sub; i < n4 / 4; i += kOrderSplit) {
+        const uint4 k = s_keys4[i];
+        c0 += k.x < mine;
+        c1 += k.y < mine;
+        c2 += k.z < mine;
+        c3 += k.w < mine;
+    }
+    int c = (c0 + c1) + (c2 + c3);
+#pragma unroll
+    for (int d = 1; d < kOrderSplit; d <<= 1) c += __shfl_xor_sync(kFull, c, d);
+    if (sub == 0 && t < T) order[c] = t;
+}
+
 __global__ void k_copy_u32(int32_t n, const uint32_t* __restrict__ src, int32_t* __restrict__ dst)
 {
     pdl_wait();
@@ -776,6 +822,14 @@ extern "C" int gs_tile_order(const int32_t* tile_ranges, int32_t T_total, void* 
         return fail(GS_ERR_INVALID_ARG, "gs_tile_order: workspace of %zu bytes, need %zu", workspace_bytes,
                     need.bytes);
     cudaStream_t s = as_stream(stream);
+    if (T_total <= kOrderRankMax) {
+        const size_t smem = sizeof(uint32_t) * (size_t)((T_total + 3) & ~3);  // at most 48 KB: no opt-in
+        launch_pdl_smem(k_tile_order_rank, (unsigned)((T_total + kOrderThreads / kOrderSplit - 1) /
+                                                      (kOrderThreads / kOrderSplit)),
+                        kOrderThreads, smem, s, T_total, reinterpret_cast<const int2*>(tile_ranges), order);
+        count_launches(1);
+        return launch_status("gs_tile_order");
+    }
     const OrderLayout L = carve_order(workspace, T_total);
     const unsigned g = (unsigned)((T_total + 255) / 256);
     launch_pdl(k_tile_len_keys, g, 256, s, T_total, reinterpret_cast<const int2*>(tile_ranges), L.ka);

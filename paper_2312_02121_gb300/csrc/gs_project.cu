@@ -217,7 +217,8 @@ __device__ __forceinline__ void project_bwd_one(const GsView& view, int64_t p, c
                                                 const V4<S>* __restrict__ quats, const S* __restrict__ scales,
                                                 S eps2d, const V2<S>* __restrict__ dL_dmeans2d,
                                                 const S* __restrict__ dL_dconics, S* __restrict__ dL_dmeans,
-                                                S* __restrict__ dL_dquats, S* __restrict__ dL_dscales, S vg[12])
+                                                S* __restrict__ dL_dquats, S* __restrict__ dL_dscales, S vg[12],
+                                                bool live = true)
 {
     const GsCamera& cam = view.cam;
     const int64_t g = view.g_begin + (p - view.proj_offset);
@@ -295,7 +296,8 @@ __device__ __forceinline__ void project_bwd_one(const GsView& view, int64_t p, c
     const S dtz = -fx * rz2 * dJ00 + S(2) * fx * o.t[0] * rz3 * dJ02 - fy * rz2 * dJ11 +
                   S(2) * fy * o.t[1] * rz3 * dJ12 + o.J02 * gm.x + o.J12 * gm.y;
     // Eq. 20: dL/dmu = R_cw^T dL/dt
-    atomic_add3(dL_dmeans + 3 * g, W[0] * dtx + W[3] * dty + W[6] * dtz, W[1] * dtx + W[4] * dty + W[7] * dtz,
+    if (live)
+        atomic_add3(dL_dmeans + 3 * g, W[0] * dtx + W[3] * dty + W[6] * dtz, W[1] * dtx + W[4] * dty + W[7] * dtz,
                 W[2] * dtx + W[5] * dty + W[8] * dtz);
     if constexpr (kView) {
         // Eq. 20: dL/dT_cw = dL/dt [mu; 1]^T; the R_cw block also gains J^T dL/dT, the covariance route
@@ -314,7 +316,7 @@ __device__ __forceinline__ void project_bwd_one(const GsView& view, int64_t p, c
     }
 
     // Sec. 3.2.1: the scales and the rotation
-    atomic_add3(dL_dscales + 3 * g, S(2) * s[0] * Q(0, 0), S(2) * s[1] * Q(1, 1), S(2) * s[2] * Q(2, 2));
+    if (live) atomic_add3(dL_dscales + 3 * g, S(2) * s[0] * Q(0, 0), S(2) * s[1] * Q(1, 1), S(2) * s[2] * Q(2, 2));
     const S s00 = s[0] * s[0], s11 = s[1] * s[1], s22 = s[2] * s[2];
     const S om0 = S(2) * Q(1, 2) * (s11 - s22);
     const S om1 = S(2) * Q(2, 0) * (s22 - s00);
@@ -322,8 +324,9 @@ __device__ __forceinline__ void project_bwd_one(const GsView& view, int64_t p, c
     // 2 q_hat (x) (0, omega) / |q|
     const S w = o.q[0], x = o.q[1], y = o.q[2], z = o.q[3];
     const S k2 = S(2) * o.qinv;
-    atomic_add4(dL_dquats + 4 * g, -k2 * (x * om0 + y * om1 + z * om2), k2 * (w * om0 + y * om2 - z * om1),
-                k2 * (w * om1 + z * om0 - x * om2), k2 * (w * om2 + x * om1 - y * om0));
+    if (live)
+        atomic_add4(dL_dquats + 4 * g, -k2 * (x * om0 + y * om1 + z * om2), k2 * (w * om0 + y * om2 - z * om1),
+                    k2 * (w * om1 + z * om0 - x * om2), k2 * (w * om2 + x * om1 - y * om0));
 }
 
 template <typename S>
@@ -337,9 +340,12 @@ k_project_bwd(const GsView* __restrict__ views, int V, int64_t P, const S* __res
     pdl_wait();
     pdl_trigger();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P || touched[p] == 0) return;
+    if (p >= P) return;
+    // a culled projection runs the same arithmetic and stores nothing: its inputs are then loaded
+    // together with `touched` instead of after it
+    const bool live = touched[p] != 0;
     project_bwd_one<S, false>(views[view_of_projection(views, V, p)], p, means, quats, scales, eps2d, dL_dmeans2d,
-                              dL_dconics, dL_dmeans, dL_dquats, dL_dscales, nullptr);
+                              dL_dconics, dL_dmeans, dL_dquats, dL_dscales, nullptr, live);
 }
 
 // The same, plus dL/dT_cw per view.  A view's projections are contiguous, so a

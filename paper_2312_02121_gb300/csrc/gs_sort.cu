@@ -208,19 +208,10 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     const int base = b * kRTile;
     const int n_here = min(kRTile, count - base);
 
-    // digit offsets: exclusive scan of digit totals + this block's row prefix
-    {
-        const int d = threadIdx.x;
-        const uint32_t tot = d < bins ? digit_total[d] : 0u;
-        const uint32_t ex = block_exclusive_scan_256<uint32_t>(tot, nullptr);
-        if (d < bins) s_base[d] = ex + hist[(size_t)d * nb + b];
-    }
-    for (int i = lane; i < kMaxBins; i += 32) s_warp[w][i] = 0;
-    __syncwarp();
-
-    // warp-striped load: warp w owns items [w*512, w*512+512) of the block
+    // every global load first, so that their latencies overlap: the block's items (warp-striped: warp w
+    // owns items [w * 32 kRI, (w + 1) * 32 kRI) of the block), the digit totals and this block's count
+    // of each digit
     uint32_t key[kRI], val[kRI], rank[kRI] = {};
-    const unsigned lt = lanemask_lt();
 #pragma unroll
     for (int k = 0; k < kRI; ++k) {
         const int li = w * (kRI * 32) + k * 32 + lane;
@@ -228,6 +219,23 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
         const bool valid = li < n_here;
         key[k] = valid ? keys_in[idx] - plan.sub : 0u;
         val[k] = valid ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
+    }
+    // digit offsets: exclusive scan of digit totals + this block's row prefix
+    {
+        const int d = threadIdx.x;
+        const uint32_t tot = d < bins ? digit_total[d] : 0u;
+        const uint32_t mine = d < bins ? hist[(size_t)d * nb + b] : 0u;
+        const uint32_t ex = block_exclusive_scan_256<uint32_t>(tot, nullptr);
+        if (d < bins) s_base[d] = ex + mine;
+    }
+    for (int i = lane; i < kMaxBins; i += 32) s_warp[w][i] = 0;
+    __syncwarp();
+
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int k = 0; k < kRI; ++k) {
+        const int li = w * (kRI * 32) + k * 32 + lane;
+        const bool valid = li < n_here;
         const uint32_t d = (key[k] >> shift) & mask;
         // lanes holding the same digit, via one ballot per digit bit (__match_any_sync was measured slower)
         unsigned peers = __ballot_sync(kFull, valid);
@@ -350,12 +358,21 @@ k_depth_keys(int64_t P, const float* __restrict__ depths, const int32_t* __restr
     __shared__ uint32_t s_lo[8], s_hi[8];
     uint32_t lo = 0xffffffffu, hi_c = 0xffffffffu;
     const int64_t base = (int64_t)blockIdx.x * (256 * kKeyItems) + threadIdx.x;
+    // both loads of every item first (the depth unconditionally), so that no load waits for another
+    int32_t tc[kKeyItems];
+    float dz[kKeyItems];
+#pragma unroll
+    for (int k = 0; k < kKeyItems; ++k) {
+        const int64_t p = base + k * 256;
+        tc[k] = p < P ? touched[p] : 0;
+        dz[k] = p < P ? depths[p] : 0.f;
+    }
 #pragma unroll
     for (int k = 0; k < kKeyItems; ++k) {
         const int64_t p = base + k * 256;
         if (p < P) {
-            const bool vis = touched[p] > 0;
-            const uint32_t key = vis ? __float_as_uint(depths[p]) : 0x7fffffffu;
+            const bool vis = tc[k] > 0;
+            const uint32_t key = vis ? __float_as_uint(dz[k]) : 0x7fffffffu;
             keys[p] = key;
             if (vis) {
                 lo = min(lo, key);

@@ -164,14 +164,32 @@ k_radix_scan_rows(uint32_t* __restrict__ hist, const int32_t* __restrict__ count
     uint32_t* row = hist + (size_t)d * nb;
     const int per = (nb + kRT - 1) / kRT;
     const int lo = min(nb, (int)threadIdx.x * per), hi = min(nb, lo + per);
+    constexpr int kHeld = 8;  // a thread's slice is held in registers when it has at most this many counts
+    uint32_t held[kHeld];
     uint32_t s = 0;
-    for (int i = lo; i < hi; ++i) s += row[i];
+    if (per <= kHeld) {
+#pragma unroll
+        for (int i = 0; i < kHeld; ++i) held[i] = lo + i < hi ? row[lo + i] : 0u;
+#pragma unroll
+        for (int i = 0; i < kHeld; ++i) s += held[i];
+    } else {
+        for (int i = lo; i < hi; ++i) s += row[i];
+    }
     uint32_t tot;
     uint32_t run = block_exclusive_scan_256<uint32_t>(s, &tot);
-    for (int i = lo; i < hi; ++i) {
-        const uint32_t x = row[i];
-        row[i] = run;
-        run += x;
+    if (per <= kHeld) {
+#pragma unroll
+        for (int i = 0; i < kHeld; ++i)
+            if (lo + i < hi) {
+                row[lo + i] = run;
+                run += held[i];
+            }
+    } else {
+        for (int i = lo; i < hi; ++i) {
+            const uint32_t x = row[i];
+            row[i] = run;
+            run += x;
+        }
     }
     if (threadIdx.x == 0) digit_total[d] = tot;
 }

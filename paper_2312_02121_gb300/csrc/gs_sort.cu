@@ -490,10 +490,18 @@ k_scan_block_sums(int64_t nblk, int64_t* __restrict__ block_sums, int64_t cap, i
 // finding the slot's owner by a ten-step binary search over the block's first
 // slots -- so the stores are contiguous and the work is spread over the block
 // whatever the rectangle sizes.
+//
+// kOwnPrefix: block_prefix holds each block's total (not yet scanned), and
+// every block sums its predecessors' itself (at most kEmitOwnPrefixMax blocks,
+// so at most that many loads per block); the last block writes K and the
+// capacity flag.  This saves the single-block scan launch.
+constexpr int64_t kEmitOwnPrefixMax = 4096;
+template <bool kOwnPrefix>
 __global__ void __launch_bounds__(256)
 k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __restrict__ order,
        const int32_t* __restrict__ cnt_sorted, const short4* __restrict__ rects, const int64_t* __restrict__ block_prefix,
-       int64_t cap, uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ owner, int32_t* __restrict__ emit_start)
+       int64_t cap, uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ owner, int32_t* __restrict__ emit_start,
+       int32_t* __restrict__ K_out, uint32_t* __restrict__ flags)
 {
     pdl_wait();
     pdl_trigger();
@@ -504,7 +512,14 @@ k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __res
     __shared__ int s_tx[kEmitTile];        // tiles_x of the projection's view
     __shared__ float s_iw[kEmitTile];      // 1 / rectangle width
     const int64_t base = (int64_t)blockIdx.x * kEmitTile;
-    const int64_t gbase = block_prefix[blockIdx.x];
+    int64_t gbase;
+    if (kOwnPrefix) {
+        int64_t part = 0;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += 256) part += block_prefix[b];
+        block_exclusive_scan_256<int64_t>(part, &gbase);
+    } else {
+        gbase = block_prefix[blockIdx.x];
+    }
     int cnt[kEmitItems];
     int s = 0;
 #pragma unroll
@@ -539,6 +554,11 @@ k_emit(const GsView* __restrict__ views, int V, int64_t P, const uint32_t* __res
         off += cnt[k];
     }
     if (threadIdx.x == 0) s_off[kEmitTile] = total;
+    if (kOwnPrefix && threadIdx.x == 0 && blockIdx.x == gridDim.x - 1) {
+        const int64_t all = gbase + total;
+        *K_out = (int32_t)min(all, (int64_t)INT32_MAX);
+        if (all > cap) atomicOr(flags, GS_FLAG_CAPACITY);
+    }
     __syncthreads();
     // the block's slots go round-robin over all its threads (consecutive threads, consecutive slots),
     // so that a projection with thousands of tiles is shared by the block instead of one warp
@@ -819,10 +839,18 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
     // 2. scan of touched in depth order, K, emission
     const int64_t nblk = (P + kEmitTile - 1) / kEmitTile;
     launch_pdl(k_touched_block_sums, (unsigned)nblk, 256, s, P, order, touched, L.block_sums, L.cnt_sorted);
-    launch_pdl(k_scan_block_sums, 1, kScanThreads, s, nblk, L.block_sums, K_capacity, K_out, flags);
-    launch_pdl(k_emit, (unsigned)nblk, 256, s, views, V, P, order, L.cnt_sorted, reinterpret_cast<const short4*>(rects),
-                                          L.block_sums, K_capacity, L.tkey_a, L.owner, emit_start);
-    count_launches(3);
+    if (nblk <= kEmitOwnPrefixMax) {
+        launch_pdl(k_emit<true>, (unsigned)nblk, 256, s, views, V, P, order, L.cnt_sorted,
+                   reinterpret_cast<const short4*>(rects), L.block_sums, K_capacity, L.tkey_a, L.owner, emit_start,
+                   K_out, flags);
+        count_launches(2);
+    } else {
+        launch_pdl(k_scan_block_sums, 1, kScanThreads, s, nblk, L.block_sums, K_capacity, K_out, flags);
+        launch_pdl(k_emit<false>, (unsigned)nblk, 256, s, views, V, P, order, L.cnt_sorted,
+                   reinterpret_cast<const short4*>(rects), L.block_sums, K_capacity, L.tkey_a, L.owner, emit_start,
+                   K_out, flags);
+        count_launches(3);
+    }
     if (K_capacity == 0) return launch_status("gs_bin_and_sort");
 
     // 3. stable sort of the pairs by global tile id; the values are the emission indices when the

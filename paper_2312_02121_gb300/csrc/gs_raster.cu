@@ -102,6 +102,9 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
             const int n = min(kB, range.y - b0);
             int lastj = -1;  // this batch's last composited entry (the batch offset is added once, below)
             for (int s = 0; s < n; s += 32) {
+                // a warp whose pixels are all finished walks no further chunk (nor culls it: the backward
+                // reads no ballot past a warp's last composited entry)
+                if (__all_sync(kFull, done)) break;
                 bool hit = s + lane < n;
                 if (kCull && hit)
                     hit = reaches_box(load_staged<S>(sh_xy, sh_q, sh_col, sh_cull, s + lane), t.wx0, t.wx1, t.wy0,
@@ -135,7 +138,6 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
                     lastj = comp ? j : lastj;
                     if (kCount) count += comp;
                 }
-                if (__all_sync(kFull, done)) break;
             }
             if (lastj >= 0) last = b0 + lastj;
         }

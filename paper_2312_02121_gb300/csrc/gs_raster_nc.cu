@@ -125,6 +125,7 @@ k_raster_fwd_nc(const GsView* __restrict__ views, int V, int T_total, const int3
             stage_colors<NC>(sh_c, sh_g, n, colors, C, c0, nc);
             __syncthreads();
             for (int s = 0; s < n; s += 32) {
+                if (__all_sync(kFull, done)) break;  // a finished warp walks no further chunk
                 bool hit = s + lane < n;
                 if (kCull && hit)
                     hit = reaches_box(load_staged<float>(sh_xy, sh_q, sh_col, sh_cull, s + lane), t.wx0, t.wx1,
@@ -150,7 +151,6 @@ k_raster_fwd_nc(const GsView* __restrict__ views, int V, int T_total, const int3
                     last = comp ? b0 + j : last;
                     count += comp;
                 }
-                if (__all_sync(kFull, done)) break;
             }
         }
         if (t.inside) {

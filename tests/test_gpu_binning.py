@@ -71,3 +71,45 @@ def test_depth_sort_passes_follow_the_key_spread(spread):
         nonempty = ranges_o[:, 1] > ranges_o[:, 0]
         np.testing.assert_array_equal(rng_gpu[nonempty], ranges_o[nonempty])
         assert (rng_gpu[~nonempty, 1] - rng_gpu[~nonempty, 0] <= 0).all()
+
+
+def _bin(views, rects, depths, touched, cap):
+    dev = "cuda"
+    P, T = views.P, views.T
+    ws = torch.empty(B.gs_bin_and_sort_workspace_size(P, cap, T), dtype=torch.uint8, device=dev)
+    ids = torch.full((cap,), -7, dtype=torch.int32, device=dev)
+    tr = torch.full((T, 2), -7, dtype=torch.int32, device=dev)
+    K = torch.empty(1, dtype=torch.int32, device=dev)
+    fl = torch.zeros(1, dtype=torch.int32, device=dev)
+    B.gs_bin_and_sort(views, rects, depths, touched, cap, ws, ids, None, None, tr, K, fl)
+    torch.cuda.synchronize()
+    return ids.cpu().numpy(), tr.cpu().numpy(), int(K.item()), int(fl.item())
+
+
+@pytest.mark.gpu
+def test_binning_over_several_views_matches_the_oracle():
+    # two 16x8-tile views (256 tiles in all), uneven projection counts, rectangles up to 4x3 tiles: global
+    # tile ids follow each view's tile offset, and the depth sort runs over both views at once
+    parts = [synthetic("wide", P=5000, seed=5), synthetic("narrow", P=3500, seed=6)]
+    rects = np.concatenate([p[0] for p in parts])
+    depths = np.concatenate([p[1] for p in parts])
+    touched = np.concatenate([p[2] for p in parts])
+    TX, TY = parts[0][3], parts[0][4]
+    cams = [wl.camera_at_distance(3.0, W, H, 100.0)] * 2
+    views = B.Views(cams, [(0, 5000), (0, 3500)], device="cuda")
+    t = lambda a: torch.as_tensor(a, device="cuda")
+    cap = int(touched.sum())
+    got = _bin(views, t(rects), t(depths), t(touched), cap)
+    # the oracle bins each view on its own; global tile ids follow the views' tile offsets, and the
+    # pairs of view 1 follow those of view 0
+    ids0, rng0 = oracle.bin_tiles(rects[:5000], depths[:5000], (touched[:5000] > 0).astype(np.int32), TX, TY)
+    ids1, rng1 = oracle.bin_tiles(rects[5000:], depths[5000:], (touched[5000:] > 0).astype(np.int32), TX, TY)
+    ids_o = np.concatenate([ids0, ids1 + 5000])
+    rng_o = np.concatenate([rng0, rng1 + len(ids0)])
+    ids, tr, k, fl = got
+    assert k == len(ids_o) == cap and fl == 0
+    np.testing.assert_array_equal(ids[:k], ids_o)
+    ne = rng_o[:, 1] > rng_o[:, 0]
+    np.testing.assert_array_equal(tr[ne], rng_o[ne])
+    assert (tr[~ne, 1] - tr[~ne, 0] <= 0).all()
+

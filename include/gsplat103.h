@@ -291,6 +291,26 @@ int gs_rasterize_fwd(const GsView* views, int32_t V, int32_t T_total, const floa
                      float* out_rgb, float* T_final, int32_t* last_idx, int32_t* n_contrib,
                      const GsRasterConfig* config, void* stream);
 
+/*
+ * gs_rasterize_fwd with the L2 loss of gs_l2_loss folded in (the paper has no
+ * loss; this is the training step's common case).  Each pixel's colour C is
+ * composited exactly as gs_rasterize_fwd does it and written to out_rgb; the
+ * same kernel then reads target and writes dL_drgb = 2 inv_norm (C - target),
+ * bit-identical to gs_l2_loss on the stored image, and adds inv_norm (C -
+ * target)^2 to *loss (one atomic per CTA, so fp32 sums vary in the last bits
+ * run to run).  Three channels, no contributor count.
+ *   in : as gs_rasterize_fwd, plus target[pix,3] (device), inv_norm
+ *   out: as gs_rasterize_fwd (n_contrib omitted), plus dL_drgb[pix,3] (device,
+ *        nullable) and loss (device scalar, nullable, ACCUMULATED: the caller
+ *        zeroes it); at least one of the two.
+ */
+int gs_rasterize_fwd_l2(const GsView* views, int32_t V, int32_t T_total, const float* means2d,
+                        const float* conics, const float* opacities, const float* colors,
+                        const int32_t* isect_ids, const int32_t* tile_ranges, const float* background,
+                        float* out_rgb, float* T_final, int32_t* last_idx, const float* target,
+                        float inv_norm, float* dL_drgb, float* loss, const GsRasterConfig* config,
+                        void* stream);
+
 /* Bytes of scratch gs_rasterize_bwd needs for K_capacity intersections:
  * 0 unless deterministic. */
 size_t gs_rasterize_bwd_workspace_size(int64_t K_capacity, int32_t deterministic);

@@ -63,6 +63,9 @@ class BatchRenderer:
         self.rgb, self.T_final = e(pix, C), e(pix)
         self.last_idx = e(pix, dtype=torch.int32)
         self.targets = targets
+        # three channels with a target: the forward kernel takes the L2 loss and dL/dC itself
+        # (gs_rasterize_fwd_l2), so no second kernel reads the image back
+        self.fuse_loss = targets is not None and C == 3
         self.inv_norm = 1.0 / (C * (loss_pixels if loss_pixels is not None else max(pix, 1)))
         self.dL = e(pix, C)
         self.loss = e(1)
@@ -153,8 +156,13 @@ class BatchRenderer:
         if self.longest_first:
             B.gs_tile_order(self.tile_ranges, v.T, self.order_ws, self.tile_order)
         if self.host is not None:
-            torch.cuda.current_stream().wait_event(self.host["late"])
-        if self.C == 3:
+            torch.cuda.current_stream().wait_event(self.host["tgt" if self.fuse_loss else "late"])
+        if self.fuse_loss:
+            self.loss.zero_()
+            B.gs_rasterize_fwd_l2(v, self.means2d, self.conics, p.opacities, p.colors, self.isect_ids,
+                                  self.tile_ranges, self.background, self.rgb, self.T_final, self.last_idx,
+                                  self.targets, self.inv_norm, self.dL, self.loss, self.config)
+        elif self.C == 3:
             B.gs_rasterize_fwd(v, self.means2d, self.conics, p.opacities, p.colors, self.isect_ids, self.tile_ranges,
                                self.background, self.rgb, self.T_final, self.last_idx, None, self.config)
         else:
@@ -164,7 +172,10 @@ class BatchRenderer:
 
     def loss_grad(self):
         """L = mean((C - target)^2) over every pixel of every view (into
-        ``self.loss``, on the device) and dL/dC, in one kernel."""
+        ``self.loss``, on the device) and dL/dC, in one kernel; with three
+        channels the forward has already done both."""
+        if self.fuse_loss:
+            return
         if self.host is not None:
             torch.cuda.current_stream().wait_event(self.host["tgt"])
         self.loss.zero_()
@@ -289,22 +300,22 @@ class PerViewRenderer:
         self.n = params.n
         self.r: List[BatchRenderer] = []
         off = 0
+        # the same loss as the batch: a mean over every pixel of every view
+        self.n_pix = sum(cam.width * cam.height for cam in cameras)
         for cam, gr, cap in zip(cameras, g_ranges, K_caps):
             pix = cam.width * cam.height
             tgt = targets[off:off + pix]
             off += pix
             v = B.Views([cam], [gr], device=dev)
             self.r.append(BatchRenderer(params, v, cap, tgt, eps2d, deterministic=deterministic,
-                                        shared_grads=self.shared))
-        self.n_pix = sum(r.views.pixels for r in self.r)
+                                        shared_grads=self.shared, loss_pixels=self.n_pix))
 
     def step(self):
         for t in self.shared.values():
             t.zero_()
         for r in self.r:
             r.forward()
-            # same loss as the batch: mean over every pixel of every view
-            B.gs_l2_loss(r.rgb, r.targets, 1.0 / (self.C * self.n_pix), r.dL, None)
+            r.loss_grad()
             r.backward()
 
     def overflowed(self) -> bool:

@@ -90,6 +90,8 @@ SIGNATURES = {
     "gs_tile_order_workspace_size": (_SZ, [_I32]),
     "gs_tile_order": (ctypes.c_int, [_P, _I32, _P, _SZ, _P, _P]),
     "gs_rasterize_fwd": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gs_rasterize_fwd_l2": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _F, _P, _P, _P,
+                                           _P]),
     "gs_rasterize_bwd_workspace_size": (_SZ, [_I64, _I32]),
     "gs_rasterize_bwd": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P,
                                         _P, _P, _I32, _P, _SZ, _P, _P, _P, _P, _P, _P]),
@@ -398,6 +400,18 @@ def gs_project_bwd(views: Views, means, quats, scales, eps2d: float, touched, dL
 
 
 EXPORTED: List[str] = list(SIGNATURES)
+
+
+def gs_rasterize_fwd_l2(views: Views, means2d, conics, opacities, colors, isect_ids, tile_ranges, background,
+                        out_rgb, T_final, last_idx, target, inv_norm: float, dL_drgb=None, loss=None,
+                        config: Optional[RasterConfig] = None, stream=None):
+    """gs_rasterize_fwd with gs_l2_loss folded in (fp32, 3 channels); ``loss`` is accumulated."""
+    _check(load().gs_rasterize_fwd_l2(_ptr(views.device), views.V, views.T, _ptr(means2d), _ptr(conics),
+                                      _ptr(opacities), _ptr(colors), _ptr(isect_ids), _ptr(tile_ranges),
+                                      _ptr(background), _ptr(out_rgb), _ptr(T_final), _ptr(last_idx), _ptr(target),
+                                      float(inv_norm), _ptr(dL_drgb), _ptr(loss), _cfg(config), _stream(stream)))
+    if _debug.enabled():
+        _debug.check_forward(views, tile_ranges, out_rgb, T_final, last_idx)
 
 
 def gs_l2_loss(rgb, target, inv_norm: float, dL_drgb=None, loss=None, stream=None):

@@ -52,22 +52,35 @@ namespace gs {
 // composited Gaussians into n_contrib (a separate instantiation, so that the
 // usual walk carries no counter).  kAnyC: W_arg channels of colours C_arg
 // apart; otherwise 3 channels 3 apart (a separate instantiation: the runtime
-// stride cost the 3-channel walk 2 %).
-template <typename S, bool kCull, bool kPersistent, bool kCount, bool kAnyC>
+// stride cost the 3-channel walk 2 %).  kLoss (3 channels): each pixel's L2
+// loss against lo.target is taken as soon as its colour is known -- dL/dC =
+// 2 inv_norm (C - target) into lo.dL and inv_norm (C - target)^2 summed into
+// lo.loss -- so that no second kernel reads the image back.
+template <typename S>
+struct FwdLoss {
+    const S* target;
+    S* dL;    // nullable
+    S* loss;  // nullable (accumulated: one atomic per CTA)
+    S inv_norm;
+};
+
+template <typename S, bool kCull, bool kPersistent, bool kCount, bool kAnyC, bool kLoss = false>
 __global__ void __launch_bounds__(256, 6)  // 6 CTAs per SM (40 registers) measured fastest
 k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t* __restrict__ tile_order,
              int* __restrict__ queue, const V2<S>* __restrict__ means2d, const S* __restrict__ conics,
              const S* __restrict__ opacities, const S* __restrict__ colors, const int32_t* __restrict__ isect_ids,
              const int2* __restrict__ tile_ranges, const S* __restrict__ background, S* __restrict__ out_rgb,
              S* __restrict__ T_final, int32_t* __restrict__ last_idx, int32_t* __restrict__ n_contrib,
-             uint32_t* __restrict__ warp_hits, int C_arg, int W_arg)
+             uint32_t* __restrict__ warp_hits, int C_arg, int W_arg, FwdLoss<S> lo)
 {
+    static_assert(!kLoss || !kAnyC, "the folded loss takes 3 channels 3 apart");
     pdl_wait();
     pdl_trigger();
     const int C = kAnyC ? C_arg : 3, CW = kAnyC ? W_arg : 3;
     constexpr int kB = RT<S>::kFwdBatch;
     __shared__ V4<S> sh_xy[kB], sh_q[kB], sh_col[kB], sh_cull[kB];
     __shared__ int s_next;
+    S lsum = 0;  // this thread's share of the loss (kLoss)
     for (int qi = blockIdx.x;;) {
         if (kPersistent) {
             __syncthreads();  // the previous tile is done with shared memory
@@ -145,14 +158,40 @@ k_raster_fwd(const GsView* __restrict__ views, int V, int T_total, const int32_t
             S bg0 = 0, bg1 = 0, bg2 = 0;
             if (background) load_c3(background, 0, C, CW, bg0, bg1, bg2);
             S* o = out_rgb + (int64_t)C * t.pix;
-            o[0] = fma(T, bg0, C0);
-            if (CW > 1) o[1] = fma(T, bg1, C1);
-            if (CW > 2) o[2] = fma(T, bg2, C2);
+            const S r0 = fma(T, bg0, C0), r1 = fma(T, bg1, C1), r2 = fma(T, bg2, C2);
+            o[0] = r0;
+            if (CW > 1) o[1] = r1;
+            if (CW > 2) o[2] = r2;
             T_final[t.pix] = T;
             last_idx[t.pix] = last;
             if (kCount) n_contrib[t.pix] = count;
+            if (kLoss) {  // as gs_l2_loss computes it from the stored image
+                const S* tg = lo.target + 3 * t.pix;
+                const S d0 = r0 - tg[0], d1 = r1 - tg[1], d2 = r2 - tg[2];
+                if (lo.dL) {
+                    const S two = S(2) * lo.inv_norm;
+                    S* g = lo.dL + 3 * t.pix;
+                    g[0] = two * d0;
+                    g[1] = two * d1;
+                    g[2] = two * d2;
+                }
+                lsum += (d0 * d0 + d1 * d1) + d2 * d2;
+            }
         }
         if (!kPersistent) break;
+    }
+    if (kLoss && lo.loss) {  // one atomic per CTA
+        __shared__ S s_loss[kWarps];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) lsum += __shfl_xor_sync(kFull, lsum, d);
+        if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = lsum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            S tot = 0;
+#pragma unroll
+            for (int i = 0; i < kWarps; ++i) tot += s_loss[i];
+            atomicAdd(lo.loss, tot * lo.inv_norm);
+        }
     }
 }
 
@@ -206,7 +245,7 @@ static int rasterize_fwd_impl(const char* who, int C, int CW, const GsView* view
                               const S* conics, const S* opacities, const S* colors, const int32_t* isect_ids,
                               const int32_t* tile_ranges, const S* background, S* out_rgb, S* T_final,
                               int32_t* last_idx, int32_t* n_contrib, uint32_t* warp_hits,
-                              const GsRasterConfig* config, void* stream)
+                              const GsRasterConfig* config, void* stream, const FwdLoss<S>* loss = nullptr)
 {
     if (V <= 0 || T_total < 0 || CW < 1 || CW > 3 || C < CW)
         return fail(GS_ERR_INVALID_ARG, "%s: V=%d T_total=%d C=%d", who, V, T_total, C);
@@ -231,7 +270,19 @@ static int rasterize_fwd_impl(const char* who, int C, int CW, const GsView* view
           {k_raster_fwd<S, true, false, true, false>, k_raster_fwd<S, true, false, true, kA>}},
          {{k_raster_fwd<S, true, true, false, false>, k_raster_fwd<S, true, true, false, kA>},
           {k_raster_fwd<S, true, true, true, false>, k_raster_fwd<S, true, true, true, kA>}}}};
-    const KF kern = table[cull][pers][n_contrib != nullptr][C != 3 || CW != 3];
+    KF kern = table[cull][pers][n_contrib != nullptr][C != 3 || CW != 3];
+    if (loss) {
+        if constexpr (kA) {
+            static const KF with_loss[2][2] = {
+                {k_raster_fwd<S, false, false, false, false, true>, k_raster_fwd<S, false, true, false, false, true>},
+                {k_raster_fwd<S, true, false, false, false, true>, k_raster_fwd<S, true, true, false, false, true>}};
+            if (n_contrib || C != 3 || CW != 3) return fail(GS_ERR_INVALID_ARG, "%s: the folded loss takes 3 channels "
+                                                            "and no contributor count", who);
+            kern = with_loss[cull][pers];
+        } else {
+            return fail(GS_ERR_INVALID_ARG, "%s: no folded loss in this precision", who);
+        }
+    }
     unsigned grid;
     if (int rc = raster_grid(kern, config, T_total, &grid)) return rc;
     int* queue = pers ? config->queue : nullptr;
@@ -239,7 +290,7 @@ static int rasterize_fwd_impl(const char* who, int C, int CW, const GsView* view
     launch_pdl(kern, grid, 256, s, views, V, T_total, config ? config->tile_order : nullptr, queue,
                               reinterpret_cast<const V2<S>*>(means2d), conics, opacities, colors, isect_ids,
                               reinterpret_cast<const int2*>(tile_ranges), background, out_rgb, T_final, last_idx,
-                              n_contrib, warp_hits, C, CW);
+                              n_contrib, warp_hits, C, CW, loss ? *loss : FwdLoss<S>{nullptr, nullptr, nullptr, S(0)});
     count_launches(1);
     return launch_status(who);
 }
@@ -421,6 +472,22 @@ extern "C" int gs_rasterize_fwd(const GsView* views, int32_t V, int32_t T_total,
     return rasterize_fwd_impl<float>("gs_rasterize_fwd", 3, 3, views, V, T_total, means2d, conics, opacities, colors,
                                      isect_ids, tile_ranges, background, out_rgb, T_final, last_idx, n_contrib,
                                      config ? config->warp_hits : nullptr, config, stream);
+}
+
+extern "C" int gs_rasterize_fwd_l2(const GsView* views, int32_t V, int32_t T_total, const float* means2d,
+                                   const float* conics, const float* opacities, const float* colors,
+                                   const int32_t* isect_ids, const int32_t* tile_ranges, const float* background,
+                                   float* out_rgb, float* T_final, int32_t* last_idx, const float* target,
+                                   float inv_norm, float* dL_drgb, float* loss, const GsRasterConfig* config,
+                                   void* stream)
+{
+    gs::NvtxRange nvtx("gs_rasterize_fwd_l2");
+    if (!target || (!dL_drgb && !loss))
+        return fail(GS_ERR_INVALID_ARG, "gs_rasterize_fwd_l2: null target, or neither dL_drgb nor loss");
+    const FwdLoss<float> lo{target, dL_drgb, loss, inv_norm};
+    return rasterize_fwd_impl<float>("gs_rasterize_fwd_l2", 3, 3, views, V, T_total, means2d, conics, opacities,
+                                     colors, isect_ids, tile_ranges, background, out_rgb, T_final, last_idx, nullptr,
+                                     config ? config->warp_hits : nullptr, config, stream, &lo);
 }
 
 extern "C" int gs_rasterize_fwd_f64(const GsView* views, int32_t V, int32_t T_total, const double* means2d,

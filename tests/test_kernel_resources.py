@@ -34,7 +34,8 @@ def _one(rows, prefix):
 def test_timed_kernels_keep_their_register_budget_and_spills(rows):
     # (kernel with template arguments, register cap from its launch bounds, spill bytes allowed)
     timed = [
-        ("gs::k_raster_fwd<float, true, false, false, false>", 65536 // (256 * 6), 0),
+        ("gs::k_raster_fwd<float, true, false, false, false, false>", 65536 // (256 * 6), 0),
+        ("gs::k_raster_fwd<float, true, false, false, false, true>", 65536 // (256 * 6), 0),
         ("gs::k_raster_bwd<float, true, true, false, false, 1, 96>", 65536 // (256 * 4), 0),
         ("gs::k_raster_bwd<float, true, true, false, false, 2, 64>", 65536 // (128 * 7), 0),
         ("gs::k_project_fwd<float>", 255, 0),

@@ -146,6 +146,27 @@ k_radix_hist(const uint32_t* __restrict__ keys, const int32_t* __restrict__ coun
     }
 }
 
+// Exclusive scan of a row of counts by the 256 threads of a block, thread t
+// taking the slice [lo, hi) of at most H counts, held in registers between the
+// sum and the write-back; the row's total into *tot.
+template <int H>
+__device__ __forceinline__ void scan_row_held(uint32_t* __restrict__ row, int lo, int hi, uint32_t* tot)
+{
+    uint32_t held[H];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < H; ++i) held[i] = lo + i < hi ? row[lo + i] : 0u;
+#pragma unroll
+    for (int i = 0; i < H; ++i) s += held[i];
+    uint32_t run = block_exclusive_scan_256<uint32_t>(s, tot);
+#pragma unroll
+    for (int i = 0; i < H; ++i)
+        if (lo + i < hi) {
+            row[lo + i] = run;
+            run += held[i];
+        }
+}
+
 // One block per digit: exclusive scan of that digit's per-block counts (in
 // place) and the digit total.
 template <int kRI>
@@ -164,27 +185,19 @@ k_radix_scan_rows(uint32_t* __restrict__ hist, const int32_t* __restrict__ count
     uint32_t* row = hist + (size_t)d * nb;
     const int per = (nb + kRT - 1) / kRT;
     const int lo = min(nb, (int)threadIdx.x * per), hi = min(nb, lo + per);
-    constexpr int kHeld = 8;  // a thread's slice is held in registers when it has at most this many counts
-    uint32_t held[kHeld];
-    uint32_t s = 0;
-    if (per <= kHeld) {
-#pragma unroll
-        for (int i = 0; i < kHeld; ++i) held[i] = lo + i < hi ? row[lo + i] : 0u;
-#pragma unroll
-        for (int i = 0; i < kHeld; ++i) s += held[i];
-    } else {
-        for (int i = lo; i < hi; ++i) s += row[i];
-    }
     uint32_t tot;
-    uint32_t run = block_exclusive_scan_256<uint32_t>(s, &tot);
-    if (per <= kHeld) {
-#pragma unroll
-        for (int i = 0; i < kHeld; ++i)
-            if (lo + i < hi) {
-                row[lo + i] = run;
-                run += held[i];
-            }
+    // a thread's slice is held in registers between the sum and the write-back (all its loads in flight
+    // at once) when it has at most 64 counts, i.e. up to 16384 radix blocks
+    if (per <= 8) {
+        scan_row_held<8>(row, lo, hi, &tot);
+    } else if (per <= 64) {
+        scan_row_held<64>(row, lo, hi, &tot);
     } else {
+        uint32_t s = 0;
+#pragma unroll 8
+        for (int i = lo; i < hi; ++i) s += row[i];
+        uint32_t run = block_exclusive_scan_256<uint32_t>(s, &tot);
+#pragma unroll 8
         for (int i = lo; i < hi; ++i) {
             const uint32_t x = row[i];
             row[i] = run;
@@ -455,6 +468,7 @@ k_scan_block_sums(int64_t nblk, int64_t* __restrict__ block_sums, int64_t cap, i
     const int64_t per = (nblk + kScanThreads - 1) / kScanThreads;
     const int64_t lo = min(nblk, (int64_t)threadIdx.x * per), hi = min(nblk, lo + per);
     int64_t s = 0;
+#pragma unroll 8
     for (int64_t i = lo; i < hi; ++i) s += block_sums[i];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int64_t incl = s;
@@ -471,6 +485,7 @@ k_scan_block_sums(int64_t nblk, int64_t* __restrict__ block_sums, int64_t cap, i
         all += warp_tot[i];
     }
     int64_t run = before + incl - s;
+#pragma unroll 8
     for (int64_t i = lo; i < hi; ++i) {
         const int64_t x = block_sums[i];
         block_sums[i] = run;

@@ -32,6 +32,7 @@ constexpr int kRT = 256;              // threads per radix block
 // sorts, 8 for short ones, whose blocks are then small enough to fill the GPU.
 constexpr int kRIShort = 8, kRILong = 16;
 constexpr int kRTileMin = kRT * kRIShort;  // the smallest radix block (sizes the histogram)
+constexpr int64_t kDepthLongFrom = (int64_t(1) << 22);  // projections from which the depth sort takes long blocks
 constexpr int kRWarps = kRT / 32;
 constexpr int kMaxBins = 256;         // digits of at most 8 bits
 constexpr int kScanThreads = 1024;
@@ -848,8 +849,14 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
                L.dkey_a, L.krange);
     count_launches(1);
     uint32_t *dk, *order;
-    lsd_sort<kRIShort>(L.dkey_a, L.dkey_b, L.dval_a, L.dval_b, nullptr, nullptr, P, P, 31, rb, s, &dk, &order, L.order,
-                       L.krange);
+    // short radix blocks fill the GPU for a frame's million projections; long ones write longer runs of
+    // each digit (and scan fewer blocks) once there are millions of blocks' worth
+    if (P >= kDepthLongFrom)
+        lsd_sort<kRILong>(L.dkey_a, L.dkey_b, L.dval_a, L.dval_b, nullptr, nullptr, P, P, 31, rb, s, &dk, &order,
+                          L.order, L.krange);
+    else
+        lsd_sort<kRIShort>(L.dkey_a, L.dkey_b, L.dval_a, L.dval_b, nullptr, nullptr, P, P, 31, rb, s, &dk, &order,
+                           L.order, L.krange);
 
     // 2. scan of touched in depth order, K, emission
     const int64_t nblk = (P + kEmitTile - 1) / kEmitTile;

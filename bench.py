@@ -65,6 +65,8 @@ def parse_args():
     ap.add_argument("--optim-steps", type=int, default=20)
     ap.add_argument("--profile", action="store_true",
                     help="run warmup + steps untimed and exit (a fixed command line for ncu)")
+    ap.add_argument("--profile-batch", choices=["batch_views_500k_64", "batch_scenes_16x4"], default=None,
+                    help="with --profile: run that batched workload's step (BatchRenderer, eager) instead")
     ap.add_argument("--tuning", default=None,
                     help="persistent,ctas_per_sm,longest_first,bwd_pixels,bwd_batch instead of gs_autotune's "
                          "choice (e.g. for an ncu launch list without the tuner's launches)")
@@ -720,6 +722,26 @@ def run_reference(args, rank, world):
 # our arm
 # ---------------------------------------------------------------------------
 
+def run_profile_batch(args):
+    """--profile --profile-batch W: warm-up + steps of the batched workload W's step (the batch renderer,
+    eagerly, every stage in its own launches), untimed: a fixed command line for ncu."""
+    import torch
+    from paper_2312_02121_gb300 import batch as GB
+    from paper_2312_02121_gb300 import binding as B
+    from paper_2312_02121_gb300 import workloads as wl
+    B.load()
+    w = getattr(wl, args.profile_batch)()
+    params, views, ranges, targets = GB.workload_views(w, "cuda")
+    cap = GB.exact_capacity(params, views, w.eps2d)
+    t = (dict(zip(B.TUNING_FIELDS, (int(x) for x in args.tuning.split(",")))) if args.tuning else
+         dict(persistent=0, ctas_per_sm=0, longest_first=0, bwd_pixels=2, bwd_batch=64))
+    r = GB.BatchRenderer(params, views, cap, targets, w.eps2d, GB.config(t, "cuda"), bool(t["longest_first"]))
+    for _ in range(args.warmup + args.steps):
+        r.step_eager()
+    torch.cuda.synchronize()
+    assert not r.overflowed()
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2312_02121_gb300 import autograd as ga
@@ -1168,7 +1190,9 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     try:
-        if world > 1:
+        if args.profile and args.profile_batch:
+            run_profile_batch(args)
+        elif world > 1:
             run_sharded(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)

@@ -814,18 +814,19 @@ def run_ours(args, rank, world, local_rank):
         dL = torch.empty(pixels, 3, device=dev)
         B.gs_l2_loss(rgb, target, 1.0 / rgb.numel(), dL, None)
         mark(4)
-        # every gradient buffer in one allocation, zeroed by one fill
+        # the accumulated gradients in one allocation, zeroed by one fill; one view, so the projection
+        # backward writes the 3D gradients (gs_project_bwd_exclusive) and they need no fill
         N = sc.n
-        gz = torch.zeros(5 * P + 14 * N, device=dev)
+        gz = torch.zeros(5 * P + 4 * N, device=dev)
         g2, gc = gz[:2 * P].view(P, 2), gz[2 * P:5 * P].view(P, 3)
         go, gcol = gz[5 * P:5 * P + N], gz[5 * P + N:5 * P + 4 * N].view(N, 3)
-        gm, gq = gz[5 * P + 4 * N:5 * P + 7 * N].view(N, 3), gz[5 * P + 7 * N:5 * P + 11 * N].view(N, 4)
-        gs = gz[5 * P + 11 * N:].view(N, 3)
+        gm, gq, gs = (torch.empty(N, k, device=dev) for k in (3, 4, 3))
         mark(5)
         B.gs_rasterize_bwd(views, pr["means2d"], pr["conics"], params.opacities, params.colors, ids, None, None,
                            pr["touched"], tr, Kd, cap, None, Tf, last, dL, False, None, g2, gc, go, gcol, hits_cfg)
         mark(6)
-        B.gs_project_bwd(views, params.means, params.quats, params.scales, w.eps2d, pr["touched"], g2, gc, gm, gq, gs)
+        B.gs_project_bwd_exclusive(views, params.means, params.quats, params.scales, w.eps2d, pr["touched"], g2, gc,
+                                   gm, gq, gs)
         mark(7)
         last_state.update(pr=pr, g2=g2, gc=gc, ids=ids, tr=tr, Kd=Kd)
         return fl

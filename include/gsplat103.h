@@ -381,6 +381,24 @@ int gs_project_bwd(const GsView* views, int32_t V, int64_t P, const float* means
                    const float* dL_dconics, float* dL_dmeans, float* dL_dquats, float* dL_dscales,
                    float* dL_dviewmats, void* stream);
 
+/*
+ * gs_project_bwd for batches in which every Gaussian has exactly one
+ * projection: the views' Gaussian ranges [g_begin, g_begin + g_count) do not
+ * overlap (one view, or views of distinct scenes).  The caller guarantees this
+ * (the views live in device memory and are not read on the host).  The paper
+ * has no counterpart; it saves the fill of the 3D gradients before the step.
+ *   in : as gs_project_bwd (no view-matrix gradient)
+ *   out (WRITTEN, not accumulated): dL_dmeans[N,3], dL_dquats[N,4] (16-byte
+ *        aligned), dL_dscales[N,3] of every Gaussian of the views -- zeros for
+ *        a culled projection (touched == 0).  Gaussians outside every view are
+ *        left untouched.  The values are those gs_project_bwd adds to zeroed
+ *        outputs, bit for bit.
+ */
+int gs_project_bwd_exclusive(const GsView* views, int32_t V, int64_t P, const float* means, const float* quats,
+                             const float* scales, float eps2d, const int32_t* touched, const float* dL_dmeans2d,
+                             const float* dL_dconics, float* dL_dmeans, float* dL_dquats, float* dL_dscales,
+                             void* stream);
+
 /* One candidate of gs_autotune: a tile walk and a backward batch shape (the
  * GsRasterConfig fields the tuner chooses, plus the tile order).  24 bytes. */
 typedef struct GsTuning {

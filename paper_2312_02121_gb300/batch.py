@@ -78,12 +78,23 @@ class BatchRenderer:
         if self.owns_grads:
             shapes += [("g_op", (Nm,)), ("g_col", (Nm, C)), ("g_means", (Nm, 3)), ("g_quats", (Nm, 4)),
                        ("g_scales", (Nm, 3))]
-        self.grad_flat = e(sum(int(np.prod(sh)) for _, sh in shapes))
-        off = 0
+        # each buffer starts on a 16-byte boundary (the quaternion gradients take 16-byte stores)
+        offs, off = {}, 0
+        for name, sh in shapes:
+            offs[name] = off
+            off += (int(np.prod(sh)) + 3) // 4 * 4
+        self.grad_flat = e(off)
         for name, sh in shapes:
             n = int(np.prod(sh))
-            setattr(self, name, self.grad_flat[off:off + n].view(*sh))
-            off += n
+            setattr(self, name, self.grad_flat[offs[name]:offs[name] + n].view(*sh))
+        # when every Gaussian belongs to exactly one view, the projection backward writes the 3D gradients
+        # instead of adding to them (gs_project_bwd_exclusive), and the fill stops before them
+        spans = sorted((views.host[i].g_begin, views.host[i].g_begin + views.host[i].g_count)
+                       for i in range(views.V) if views.host[i].g_count > 0)
+        covers_once = bool(spans) and spans[0][0] == 0 and spans[-1][1] == N and all(
+            b[0] == a[1] for a, b in zip(spans, spans[1:]))
+        self.exclusive = self.owns_grads and covers_once
+        self.grad_fill = self.grad_flat[:offs["g_means"]] if self.exclusive else self.grad_flat
         if not self.owns_grads:
             sg = shared_grads
             self.g_op, self.g_col = sg["opacities"], sg["colors"]
@@ -183,7 +194,7 @@ class BatchRenderer:
 
     def backward(self):
         v, p = self.views, self.p
-        self.grad_flat.zero_()
+        self.grad_fill.zero_()
         if self.C == 3:
             B.gs_rasterize_bwd(v, self.means2d, self.conics, p.opacities, p.colors, self.isect_ids, self.isect_pos,
                                self.emit_start, self.touched, self.tile_ranges, self.K, self.cap, self.background,
@@ -193,8 +204,9 @@ class BatchRenderer:
             B.gs_rasterize_bwd_nc(v, self.C, self.means2d, self.conics, p.opacities, p.colors, self.isect_ids,
                                   self.tile_ranges, self.background, self.T_final, self.last_idx, self.dL, self.g2,
                                   self.gc, self.g_op, self.g_col, self.config)
-        B.gs_project_bwd(v, p.means, p.quats, p.scales, self.eps2d, self.touched, self.g2, self.gc, self.g_means,
-                         self.g_quats, self.g_scales)
+        project_bwd = B.gs_project_bwd_exclusive if self.exclusive else B.gs_project_bwd
+        project_bwd(v, p.means, p.quats, p.scales, self.eps2d, self.touched, self.g2, self.gc, self.g_means,
+                    self.g_quats, self.g_scales)
         if self.host is not None:
             self.loss_host.copy_(self.loss, non_blocking=True)
 

@@ -96,6 +96,7 @@ SIGNATURES = {
     "gs_rasterize_bwd": (ctypes.c_int, [_P, _I32, _I64, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P,
                                         _P, _P, _I32, _P, _SZ, _P, _P, _P, _P, _P, _P]),
     "gs_project_bwd": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _F, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gs_project_bwd_exclusive": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _F, _P, _P, _P, _P, _P, _P, _P]),
     "gs_autotune_default_candidates": (ctypes.c_int, [_P, _I32, _P]),
     "gs_autotune_workspace_size": (_SZ, [_I64, _I64, _I32, _I64, _I64]),
     "gs_autotune": (ctypes.c_int, [_P, _I32, _I64, _I64, _I32, _I64, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _I32, _I32,
@@ -397,6 +398,26 @@ def gs_project_bwd(views: Views, means, quats, scales, eps2d: float, touched, dL
     _check(fn(_ptr(views.device), views.V, views.P, _ptr(means), _ptr(quats), _ptr(scales),
                                  float(eps2d), _ptr(touched), _ptr(dL_dmeans2d), _ptr(dL_dconics), _ptr(dL_dmeans),
                                  _ptr(dL_dquats), _ptr(dL_dscales), _ptr(dL_dviewmats), _stream(stream)))
+
+
+def views_exclusive(views: Views) -> bool:
+    """True when no Gaussian belongs to two views (gs_project_bwd_exclusive applies)."""
+    ranges = sorted((views.host[i].g_begin, views.host[i].g_begin + views.host[i].g_count) for i in range(views.V)
+                    if views.host[i].g_count > 0)
+    return all(b[0] >= a[1] for a, b in zip(ranges, ranges[1:]))
+
+
+def gs_project_bwd_exclusive(views: Views, means, quats, scales, eps2d: float, touched, dL_dmeans2d, dL_dconics,
+                             dL_dmeans, dL_dquats, dL_dscales, stream=None):
+    """gs_project_bwd when every Gaussian has exactly one projection (the views' Gaussian ranges do not
+    overlap, checked here on the host copy of the views): the 3D gradients are written, not
+    accumulated, so they need no zero fill.  fp32."""
+    if not views_exclusive(views):
+        raise GsError(GS_ERR_INVALID_ARG, "gs_project_bwd_exclusive: the views' Gaussian ranges overlap")
+    _check(load().gs_project_bwd_exclusive(_ptr(views.device), views.V, views.P, _ptr(means), _ptr(quats),
+                                           _ptr(scales), float(eps2d), _ptr(touched), _ptr(dL_dmeans2d),
+                                           _ptr(dL_dconics), _ptr(dL_dmeans), _ptr(dL_dquats), _ptr(dL_dscales),
+                                           _stream(stream)))
 
 
 EXPORTED: List[str] = list(SIGNATURES)

@@ -4,6 +4,8 @@
 // per projection forward).  Instantiated for fp32 (the fast path) and fp64
 // (the gs_*_f64 entry points, used to check the analytic backward against
 // finite differences).
+#include <type_traits>
+
 #include "gs_common.cuh"
 
 namespace gs {
@@ -212,7 +214,9 @@ k_project_fwd(const GsView* __restrict__ views, int V, int64_t P, const S* __res
 // sum_j s_j^2 u_j y_j = -eps2d yk (the off-diagonal of P Sigma' P^T, which is
 // diagonal for the factor P = [[1, yk], [0, 1]] of Y = P^T diag(ya, yd) P),
 // whose other terms are small and exact.
-template <typename S, bool kView>
+// kStore: every Gaussian has this one projection only, so its gradients are
+// written instead of accumulated (zeros for a culled projection).
+template <typename S, bool kView, bool kStore = false>
 __device__ __forceinline__ void project_bwd_one(const GsView& view, int64_t p, const S* __restrict__ means,
                                                 const V4<S>* __restrict__ quats, const S* __restrict__ scales,
                                                 S eps2d, const V2<S>* __restrict__ dL_dmeans2d,
@@ -296,9 +300,15 @@ __device__ __forceinline__ void project_bwd_one(const GsView& view, int64_t p, c
     const S dtz = -fx * rz2 * dJ00 + S(2) * fx * o.t[0] * rz3 * dJ02 - fy * rz2 * dJ11 +
                   S(2) * fy * o.t[1] * rz3 * dJ12 + o.J02 * gm.x + o.J12 * gm.y;
     // Eq. 20: dL/dmu = R_cw^T dL/dt
-    if (live)
+    if (kStore) {
+        const S z = S(0);
+        dL_dmeans[3 * g + 0] = live ? W[0] * dtx + W[3] * dty + W[6] * dtz : z;
+        dL_dmeans[3 * g + 1] = live ? W[1] * dtx + W[4] * dty + W[7] * dtz : z;
+        dL_dmeans[3 * g + 2] = live ? W[2] * dtx + W[5] * dty + W[8] * dtz : z;
+    } else if (live) {
         atomic_add3(dL_dmeans + 3 * g, W[0] * dtx + W[3] * dty + W[6] * dtz, W[1] * dtx + W[4] * dty + W[7] * dtz,
                 W[2] * dtx + W[5] * dty + W[8] * dtz);
+    }
     if constexpr (kView) {
         // Eq. 20: dL/dT_cw = dL/dt [mu; 1]^T; the R_cw block also gains J^T dL/dT, the covariance route
         // (Sigma' = T Sigma T^T with T = J R_cw), for which the rows of J are (J00, 0, J02), (0, J11, J12)
@@ -316,7 +326,13 @@ __device__ __forceinline__ void project_bwd_one(const GsView& view, int64_t p, c
     }
 
     // Sec. 3.2.1: the scales and the rotation
-    if (live) atomic_add3(dL_dscales + 3 * g, S(2) * s[0] * Q(0, 0), S(2) * s[1] * Q(1, 1), S(2) * s[2] * Q(2, 2));
+    if (kStore) {
+        dL_dscales[3 * g + 0] = live ? S(2) * s[0] * Q(0, 0) : S(0);
+        dL_dscales[3 * g + 1] = live ? S(2) * s[1] * Q(1, 1) : S(0);
+        dL_dscales[3 * g + 2] = live ? S(2) * s[2] * Q(2, 2) : S(0);
+    } else if (live) {
+        atomic_add3(dL_dscales + 3 * g, S(2) * s[0] * Q(0, 0), S(2) * s[1] * Q(1, 1), S(2) * s[2] * Q(2, 2));
+    }
     const S s00 = s[0] * s[0], s11 = s[1] * s[1], s22 = s[2] * s[2];
     const S om0 = S(2) * Q(1, 2) * (s11 - s22);
     const S om1 = S(2) * Q(2, 0) * (s22 - s00);
@@ -324,12 +340,20 @@ __device__ __forceinline__ void project_bwd_one(const GsView& view, int64_t p, c
     // 2 q_hat (x) (0, omega) / |q|
     const S w = o.q[0], x = o.q[1], y = o.q[2], z = o.q[3];
     const S k2 = S(2) * o.qinv;
-    if (live)
+    if (kStore) {
+        V4<S> dq;
+        dq.x = live ? -k2 * (x * om0 + y * om1 + z * om2) : S(0);
+        dq.y = live ? k2 * (w * om0 + y * om2 - z * om1) : S(0);
+        dq.z = live ? k2 * (w * om1 + z * om0 - x * om2) : S(0);
+        dq.w = live ? k2 * (w * om2 + x * om1 - y * om0) : S(0);
+        reinterpret_cast<V4<S>*>(dL_dquats)[g] = dq;
+    } else if (live) {
         atomic_add4(dL_dquats + 4 * g, -k2 * (x * om0 + y * om1 + z * om2), k2 * (w * om0 + y * om2 - z * om1),
                     k2 * (w * om1 + z * om0 - x * om2), k2 * (w * om2 + x * om1 - y * om0));
+    }
 }
 
-template <typename S>
+template <typename S, bool kStore>
 __global__ void __launch_bounds__(256, 4)  // 4 CTAs per SM (64 registers): 8 % faster than 3
 k_project_bwd(const GsView* __restrict__ views, int V, int64_t P, const S* __restrict__ means,
               const V4<S>* __restrict__ quats, const S* __restrict__ scales, S eps2d,
@@ -344,7 +368,7 @@ k_project_bwd(const GsView* __restrict__ views, int V, int64_t P, const S* __res
     // a culled projection runs the same arithmetic and stores nothing: its inputs are then loaded
     // together with `touched` instead of after it
     const bool live = touched[p] != 0;
-    project_bwd_one<S, false>(views[view_of_projection(views, V, p)], p, means, quats, scales, eps2d, dL_dmeans2d,
+    project_bwd_one<S, false, kStore>(views[view_of_projection(views, V, p)], p, means, quats, scales, eps2d, dL_dmeans2d,
                               dL_dconics, dL_dmeans, dL_dquats, dL_dscales, nullptr, live);
 }
 
@@ -448,15 +472,16 @@ template <typename S>
 static int project_bwd_impl(const char* who, const GsView* views, int32_t V, int64_t P, const S* means,
                             const S* quats, const S* scales, S eps2d, const int32_t* touched, const S* dL_dmeans2d,
                             const S* dL_dconics, S* dL_dmeans, S* dL_dquats, S* dL_dscales, S* dL_dviewmats,
-                            void* stream)
+                            void* stream, bool exclusive = false)
 {
     if (V < 0 || P < 0 || (P > 0 && V == 0)) return fail(GS_ERR_INVALID_ARG, "%s: V=%d P=%lld", who, V, (long long)P);
     if (P > 0 && (!views || !means || !quats || !scales || !touched || !dL_dmeans2d || !dL_dconics || !dL_dmeans ||
                   !dL_dquats || !dL_dscales))
         return fail(GS_ERR_INVALID_ARG, "%s: null pointer argument", who);
-    if (misaligned(quats, 4 * sizeof(S)) || misaligned(dL_dmeans2d, 2 * sizeof(S)))
-        return fail(GS_ERR_INVALID_ARG, "%s: quats need %zu-byte, dL_dmeans2d %zu-byte alignment", who,
-                    4 * sizeof(S), 2 * sizeof(S));
+    if (misaligned(quats, 4 * sizeof(S)) || misaligned(dL_dmeans2d, 2 * sizeof(S)) ||
+        (exclusive && misaligned(dL_dquats, 4 * sizeof(S))))
+        return fail(GS_ERR_INVALID_ARG, "%s: quats%s need %zu-byte, dL_dmeans2d %zu-byte alignment", who,
+                    exclusive ? " and dL_dquats" : "", 4 * sizeof(S), 2 * sizeof(S));
     if (P == 0) return GS_OK;
     const int threads = 256;
     const unsigned blocks = (unsigned)((P + threads - 1) / threads);
@@ -464,10 +489,14 @@ static int project_bwd_impl(const char* who, const GsView* views, int32_t V, int
         launch_pdl(k_project_bwd_view<S>, blocks, threads, as_stream(stream),
             views, V, P, means, reinterpret_cast<const V4<S>*>(quats), scales, eps2d, touched,
             reinterpret_cast<const V2<S>*>(dL_dmeans2d), dL_dconics, dL_dmeans, dL_dquats, dL_dscales, dL_dviewmats);
-    else
-        launch_pdl(k_project_bwd<S>, blocks, threads, as_stream(stream),
+    else {
+        auto kernel = k_project_bwd<S, false>;
+        if constexpr (std::is_same<S, float>::value)  // the exclusive entry point is fp32
+            if (exclusive) kernel = k_project_bwd<S, true>;
+        launch_pdl(kernel, blocks, threads, as_stream(stream),
             views, V, P, means, reinterpret_cast<const V4<S>*>(quats), scales, eps2d, touched,
             reinterpret_cast<const V2<S>*>(dL_dmeans2d), dL_dconics, dL_dmeans, dL_dquats, dL_dscales);
+    }
     count_launches(1);
     return launch_status(who);
 }
@@ -502,6 +531,16 @@ extern "C" int gs_project_bwd(const GsView* views, int32_t V, int64_t P, const f
     gs::NvtxRange nvtx("gs_project_bwd");
     return project_bwd_impl<float>("gs_project_bwd", views, V, P, means, quats, scales, eps2d, touched, dL_dmeans2d,
                                    dL_dconics, dL_dmeans, dL_dquats, dL_dscales, dL_dviewmats, stream);
+}
+
+extern "C" int gs_project_bwd_exclusive(const GsView* views, int32_t V, int64_t P, const float* means,
+                                        const float* quats, const float* scales, float eps2d, const int32_t* touched,
+                                        const float* dL_dmeans2d, const float* dL_dconics, float* dL_dmeans,
+                                        float* dL_dquats, float* dL_dscales, void* stream)
+{
+    gs::NvtxRange nvtx("gs_project_bwd_exclusive");
+    return project_bwd_impl<float>("gs_project_bwd_exclusive", views, V, P, means, quats, scales, eps2d, touched,
+                                   dL_dmeans2d, dL_dconics, dL_dmeans, dL_dquats, dL_dscales, nullptr, stream, true);
 }
 
 extern "C" int gs_project_bwd_f64(const GsView* views, int32_t V, int64_t P, const double* means,

@@ -39,7 +39,8 @@ def test_timed_kernels_keep_their_register_budget_and_spills(rows):
         ("gs::k_raster_bwd<float, true, true, false, false, 1, 96>", 65536 // (256 * 4), 0),
         ("gs::k_raster_bwd<float, true, true, false, false, 2, 64>", 65536 // (128 * 7), 0),
         ("gs::k_project_fwd<float>", 255, 0),
-        ("gs::k_project_bwd<float>", 65536 // (256 * 4), 0),
+        ("gs::k_project_bwd<float, false>", 65536 // (256 * 4), 0),
+        ("gs::k_project_bwd<float, true>", 65536 // (256 * 4), 0),
         ("gs::k_emit<true>", 255, 0),
         ("gs::k_tile_order_rank", 255, 0),
         ("gs::k_finalize", 255, 0),

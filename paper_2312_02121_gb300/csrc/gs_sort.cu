@@ -380,13 +380,18 @@ static void lsd_sort(uint32_t* k1, uint32_t* k2, uint32_t* v1, uint32_t* v2, con
 // sets both words to ~0 first): the depth sort then sorts only the bits their
 // spread needs.  A culled projection's key may fall outside that range; its
 // place in the order does not matter, as it has no pairs.
+//
+// The blocks also zero tile_ranges (T entries): the finalization writes only
+// the ranges of tiles that have pairs, and this is the call's first kernel.
 constexpr int kKeyItems = 8;
 __global__ void __launch_bounds__(256)
 k_depth_keys(int64_t P, const float* __restrict__ depths, const int32_t* __restrict__ touched,
-             uint32_t* __restrict__ keys, uint32_t* __restrict__ krange)
+             uint32_t* __restrict__ keys, uint32_t* __restrict__ krange, int2* __restrict__ tile_ranges, int32_t T)
 {
     pdl_wait();
     pdl_trigger();
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < T; i += (int64_t)gridDim.x * 256)
+        tile_ranges[i] = make_int2(0, 0);
     __shared__ uint32_t s_lo[8], s_hi[8];
     uint32_t lo = 0xffffffffu, hi_c = 0xffffffffu;
     const int64_t base = (int64_t)blockIdx.x * (256 * kKeyItems) + threadIdx.x;
@@ -836,17 +841,20 @@ extern "C" int gs_bin_and_sort(const GsView* views, int32_t V, int64_t P, int32_
         return fail(GS_ERR_INVALID_ARG, "gs_bin_and_sort: workspace needs 16-byte alignment");
     cudaStream_t s = as_stream(stream);
     const SortLayout L = carve(workspace, P, K_capacity);
-    if (cudaMemsetAsync(tile_ranges, 0, sizeof(int32_t) * 2 * (size_t)T_total, s) != cudaSuccess ||
-        cudaMemsetAsync(K_out, 0, sizeof(int32_t), s) != cudaSuccess)
-        return launch_status("gs_bin_and_sort memset");
-    if (P == 0) return launch_status("gs_bin_and_sort");
+    if (P == 0) {
+        if (cudaMemsetAsync(tile_ranges, 0, sizeof(int32_t) * 2 * (size_t)T_total, s) != cudaSuccess ||
+            cudaMemsetAsync(K_out, 0, sizeof(int32_t), s) != cudaSuccess)
+            return launch_status("gs_bin_and_sort memset");
+        return launch_status("gs_bin_and_sort");
+    }
+    // otherwise k_depth_keys zeroes tile_ranges, and the emission (or the block-sum scan) writes K_out
     const RadixBufs rb{L.hist, L.digit_total};
 
     // 1. projections in (depth, p) order: an adaptive sort on the spread of the visible depth keys
     if (cudaMemsetAsync(L.krange, 0xff, 2 * sizeof(uint32_t), s) != cudaSuccess)
         return launch_status("gs_bin_and_sort memset");
     launch_pdl(k_depth_keys, (unsigned)((P + 256 * kKeyItems - 1) / (256 * kKeyItems)), 256, s, P, depths, touched,
-               L.dkey_a, L.krange);
+               L.dkey_a, L.krange, reinterpret_cast<int2*>(tile_ranges), T_total);
     count_launches(1);
     uint32_t *dk, *order;
     // short radix blocks fill the GPU for a frame's million projections; long ones write longer runs of

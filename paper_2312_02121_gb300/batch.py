@@ -57,7 +57,6 @@ class BatchRenderer:
         self.emit_start = e(max(P, 1), dtype=torch.int32)
         self.tile_ranges = e(T, 2, dtype=torch.int32)
         self.K = e(1, dtype=torch.int32)
-        self.flags = torch.zeros(1, dtype=torch.int32, device=dev)
         self.order_ws = e(max(B.gs_tile_order_workspace_size(T), 1), dtype=torch.uint8)
         self.tile_order = e(T, dtype=torch.int32)
         self.rgb, self.T_final = e(pix, C), e(pix)
@@ -68,13 +67,13 @@ class BatchRenderer:
         self.fuse_loss = targets is not None and C == 3
         self.inv_norm = 1.0 / (C * (loss_pixels if loss_pixels is not None else max(pix, 1)))
         self.dL = e(pix, C)
-        self.loss = e(1)
         nbw = B.gs_rasterize_bwd_workspace_size(self.cap, deterministic)
         self.bwd_ws = e(nbw, dtype=torch.uint8) if nbw else None
-        # every gradient buffer the step zeroes lives in one allocation, cleared by one fill
+        # every buffer the step zeroes lives in one allocation, cleared by one fill at the start of the
+        # step: the sort's flag word and the loss (the "state" words), then the gradient accumulators
         self.owns_grads = shared_grads is None
         Pm, Nm = max(P, 1), max(N, 1)
-        shapes = [("g2", (Pm, 2)), ("gc", (Pm, 3))]
+        shapes = [("state", (4,)), ("g2", (Pm, 2)), ("gc", (Pm, 3))]
         if self.owns_grads:
             shapes += [("g_op", (Nm,)), ("g_col", (Nm, C)), ("g_means", (Nm, 3)), ("g_quats", (Nm, 4)),
                        ("g_scales", (Nm, 3))]
@@ -83,7 +82,7 @@ class BatchRenderer:
         for name, sh in shapes:
             offs[name] = off
             off += (int(np.prod(sh)) + 3) // 4 * 4
-        self.grad_flat = e(off)
+        self.grad_flat = torch.zeros(off, device=dev)  # the state words read zero before the first step
         for name, sh in shapes:
             n = int(np.prod(sh))
             setattr(self, name, self.grad_flat[offs[name]:offs[name] + n].view(*sh))
@@ -94,7 +93,12 @@ class BatchRenderer:
         covers_once = bool(spans) and spans[0][0] == 0 and spans[-1][1] == N and all(
             b[0] == a[1] for a, b in zip(spans, spans[1:]))
         self.exclusive = self.owns_grads and covers_once
-        self.grad_fill = self.grad_flat[:offs["g_means"]] if self.exclusive else self.grad_flat
+        fill_end = offs["g_means"] if self.exclusive else off
+        self.step_fill = self.grad_flat[:fill_end]  # zeroed by forward
+        self.grad_fill = self.grad_flat[offs["g2"]:fill_end]  # the gradients alone, for a repeated backward
+        self.flags = self.state[0:1].view(torch.int32)
+        self.loss = self.state[1:2]
+        self.grads_cleared = False  # set by forward's fill, used up by the next backward
         if not self.owns_grads:
             sg = shared_grads
             self.g_op, self.g_col = sg["opacities"], sg["colors"]
@@ -157,9 +161,10 @@ class BatchRenderer:
         v, p = self.views, self.p
         if self.host is not None:
             self._upload()
+        self.step_fill.zero_()  # the flag word, the loss and the gradient accumulators of this step
+        self.grads_cleared = True
         B.gs_project(v, p.means, p.quats, p.scales, self.eps2d, self.means2d, self.conics, self.depths, self.rects,
                      self.touched, None)  # the pair count comes from the sort (no per-block atomics here)
-        self.flags.zero_()
         B.gs_bin_and_sort(v, self.rects, self.depths, self.touched, self.cap, self.sort_ws, self.isect_ids,
                           self.isect_pos if self.deterministic else None,
                           self.emit_start if self.deterministic else None, self.tile_ranges, self.K,
@@ -169,7 +174,6 @@ class BatchRenderer:
         if self.host is not None:
             torch.cuda.current_stream().wait_event(self.host["tgt" if self.fuse_loss else "late"])
         if self.fuse_loss:
-            self.loss.zero_()
             B.gs_rasterize_fwd_l2(v, self.means2d, self.conics, p.opacities, p.colors, self.isect_ids,
                                   self.tile_ranges, self.background, self.rgb, self.T_final, self.last_idx,
                                   self.targets, self.inv_norm, self.dL, self.loss, self.config)
@@ -194,7 +198,9 @@ class BatchRenderer:
 
     def backward(self):
         v, p = self.views, self.p
-        self.grad_fill.zero_()
+        if not self.grads_cleared:  # a second backward after one forward starts from zero again
+            self.grad_fill.zero_()
+        self.grads_cleared = False
         if self.C == 3:
             B.gs_rasterize_bwd(v, self.means2d, self.conics, p.opacities, p.colors, self.isect_ids, self.isect_pos,
                                self.emit_start, self.touched, self.tile_ranges, self.K, self.cap, self.background,

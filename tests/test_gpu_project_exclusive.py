@@ -72,8 +72,8 @@ def test_batch_renderer_skips_the_fill_with_the_same_gradients():
     for exclusive in (True, False):
         r = GB.BatchRenderer(params, views, cap, targets, w.eps2d, deterministic=True)
         assert r.exclusive
-        if not exclusive:  # the accumulating path with the whole fill
-            r.exclusive, r.grad_fill = False, r.grad_flat
+        if not exclusive:  # the accumulating path, with the step's fill over the whole buffer
+            r.exclusive, r.step_fill = False, r.grad_flat
         for _ in range(2):  # the second step finds the first one's gradients in the buffers
             r.step_eager()
         torch.cuda.synchronize()

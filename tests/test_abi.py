@@ -269,3 +269,17 @@ def test_header_is_clean_c99_and_cxx11(tmp_path, lang, std):
     src.write_text('#include "gsplat103.h"\nint main(void) { GsView v; v.g_count = GS_TILE; return v.g_count == 0; }\n')
     subprocess.run([cc, f"-std={std}", "-pedantic", "-Wall", "-Wextra", "-Werror", "-I", os.path.dirname(HEADER),
                     "-c", str(src), "-o", str(tmp_path / "probe.o")], check=True)
+
+
+def test_views_exclusive_only_when_no_gaussian_is_shared():
+    # gs_project_bwd_exclusive applies when the views' Gaussian ranges do not overlap (empty views
+    # aside); the binding decides this on the host copy of the view table
+    from paper_2312_02121_gb300 import binding
+    from paper_2312_02121_gb300 import workloads as wl
+    cam = wl.camera_at_distance(3.0, 40, 20, 50.0)
+    mk = lambda ranges: binding.Views([cam] * len(ranges), ranges, device="cpu")
+    assert binding.views_exclusive(mk([(0, 10)]))
+    assert binding.views_exclusive(mk([(10, 5), (0, 10), (15, 0)]))
+    assert binding.views_exclusive(mk([(0, 10), (10, 0), (20, 3)]))
+    assert not binding.views_exclusive(mk([(0, 10), (9, 3)]))
+    assert not binding.views_exclusive(mk([(0, 10), (0, 10)]))
